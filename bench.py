@@ -1,0 +1,330 @@
+"""Benchmark: batched product-convolution apply on one GB300 per rank.
+
+Workload (the throughput figure's configuration): 512x512 box, regular 16x16
+sample grid (r = 256), rotated anisotropic Gaussian with smooth random
+sigma1, sigma2 in [2, 8] and angle in [0, pi), R = 24, 128^2 patch FFTs, 64
+right-hand sides of iid N(0,1) (synthetic, seeded).  One step = one
+pc_apply_batched of the 64 vectors: gather . w, FFTs, spectral products,
+inverse FFTs and the ordered overlap-add, all in libpc's kernels.
+
+Metric: right-hand sides per second (higher is better).  ``value`` times the
+step with x and y resident in HBM (L2 flushed between steps by writing a
+256 MB buffer outside the timed window); ``e2e`` times the same call with the
+inputs copied from pinned host memory and the result copied back inside the
+timed window.  ``plain_gpu`` is the plain per-vector path (gather, cuFFT,
+product, cuFFT, overlap-add) on the same operator.
+
+--impl reference times the FP64 CPU oracle on the host cores on the same
+workload (a bounded random sample of output pixels per step, scaled to
+right-hand sides per second).
+
+Multi-GPU: the operator and the batch are replicated (weak scaling, no
+collective on the data path); value = all ranks' right-hand sides / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "product-convolution RHS/s"
+WORKLOAD = "fp32_512"
+
+
+def algorithmic_work(shape, lo, hi, R, nrhs, spectra_bytes, elem=4):
+    """FLOPs and HBM bytes per apply of the workload, by the nominal formula
+    sum_k 5 L_k log2 L_k + 3 L_k with L_k = prod_a (n_a + 2R) (the exact
+    linear-convolution extent of patch k), and x + y + spectra bytes."""
+    flops = 0.0
+    for a, b in zip(lo, hi):
+        L = float(np.prod([(bb - aa + 1) + 2 * R for aa, bb in zip(a, b)]))
+        flops += 5.0 * L * math.log2(L) + 3.0 * L
+    N = int(np.prod(shape))
+    return flops * nrhs, 2.0 * N * elem * nrhs + spectra_bytes
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 4 + i and r[4 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_rate(wl, x, seconds, seed=0):
+    """Time the oracle on random output pixels until `seconds` have passed;
+    returns (RHS/s-equivalent, pixels, threads, elapsed)."""
+    from oracle import PCOracle
+    orc = PCOracle.from_workload(wl)
+    rng = np.random.default_rng(seed)
+    done = 0
+    t0 = time.perf_counter()
+    chunk = 512
+    while time.perf_counter() - t0 < seconds:
+        pts = rng.choice(wl.n, chunk, replace=False)
+        orc.apply(x, points=pts)
+        done += chunk
+        chunk = min(chunk * 2, 16384)
+    el = time.perf_counter() - t0
+    return wl.nrhs * (done / wl.n) / el, done, os.cpu_count(), el
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import workloads
+    from workloads import configs
+    from oracle import build as obuild
+    obuild.build()
+    wl = configs.get(WORKLOAD)
+    x = workloads.rhs(wl.rhs_seed, wl.nrhs, wl.shape)
+    from oracle import PCOracle
+    orc = PCOracle.from_workload(wl)
+    rng = np.random.default_rng(1)
+    per_step = 2048
+    times = []
+    for i in range(args.warmup + args.steps):
+        pts = rng.choice(wl.n, per_step, replace=False)
+        t0 = time.perf_counter()
+        orc.apply(x, points=pts)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = args.steps * wl.nrhs * (per_step / wl.n) / tot
+    sample = "%d random output pixels x %d RHS per step (of %d pixels)" % (per_step, wl.nrhs, wl.n)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "512x512 r=256 anisotropic Gaussian R=24, 64 RHS",
+                                            "global_batch": wl.nrhs, "parallelism": "cpu"},
+            "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    import workloads
+    from workloads import configs
+    import paper_1805_06018_gb300 as pcg
+    from paper_1805_06018_gb300 import build as libbuild
+
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(pcg.binding.LIB_PATH):
+        libbuild.build()
+    if world > 1:
+        dist.barrier()
+
+    wl = configs.get(WORKLOAD)
+    pts = pcg.pc_sample_points(wl.shape, wl.cells)
+    phi = workloads.impulse_windows(wl.shape, pts, wl.kernel)
+    ctx = pcg.Context(local)
+    op = pcg.Operator(ctx, wl.shape, wl.cells, wl.radius, phi, precision="fp32")
+    info = op.info()
+    x_host = workloads.rhs(wl.rhs_seed, wl.nrhs, wl.shape)
+    x = torch.from_numpy(x_host).cuda()
+    y = torch.empty_like(x)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    N = wl.n
+
+    def step():
+        op.pc_apply_batched(wl.nrhs, x.data_ptr(), N, y.data_ptr(), N, sp)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    op.check()
+
+    # ---- device-resident timing
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev0[i].record(stream)
+            step()
+            ev1[i].record(stream)
+            kms.append(op.kernel_ms())
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    op.check()
+    step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
+    tot_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * args.steps * wl.nrhs / (tot_ms / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    xh = torch.from_numpy(x_host).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    e2e_steps = max(3, min(args.steps, 50))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        x.copy_(xh, non_blocking=True)
+        step()
+        yh.copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * e2e_steps * wl.nrhs / e2e_s
+
+    # ---- plain per-vector path on the same operator
+    plain = None
+    if not args.no_plain:
+        yp = torch.empty_like(x)
+        op.pc_apply_plain(wl.nrhs, x.data_ptr(), N, yp.data_ptr(), N, sp)
+        torch.cuda.synchronize()
+        pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        psteps = max(3, min(args.steps // 10, 20))
+        pms = []
+        for _ in range(psteps):
+            flush.fill_(1.0)
+            pe0.record(stream)
+            op.pc_apply_plain(wl.nrhs, x.data_ptr(), N, yp.data_ptr(), N, sp)
+            pe1.record(stream)
+            torch.cuda.synchronize()
+            pms.append(pe0.elapsed_time(pe1))
+        rel = float(torch.max(torch.linalg.vector_norm((yp - y).reshape(wl.nrhs, -1), dim=1) /
+                              torch.linalg.vector_norm(y.reshape(wl.nrhs, -1), dim=1)).item())
+        plain = {"value": wl.nrhs / (np.mean(pms) / 1e3), "unit": "RHS/s", "p50_ms": float(np.median(pms)),
+                 "max_rel_l2_vs_fused": rel, "kernels_per_step": op.launches()}
+        step()  # leave the operator's last launch = the fused path
+
+    # ---- roofline of the fused kernel (FP32 ALU bound)
+    lo, hi = pcg.pc_neighbourhood_boxes(wl.shape, wl.cells)
+    flops, bytes_ = algorithmic_work(wl.shape, lo, hi, wl.radius, wl.nrhs, info["spectra_bytes"])
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+    kern_ms = float(np.mean(kms))
+    achieved = flops / (kern_ms / 1e3) / 1e12
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic_fft2d_fp32_512.json")
+    if os.path.exists(tr_path):
+        traffic = json.load(open(tr_path)).get("bytes_per_launch")
+
+    line = {"metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "512x512 regular 16x16 grid (r=256), anisotropic Gaussian R=24, "
+                                   "128^2 patch FFTs, 64 RHS", "global_batch": wl.nrhs * world,
+                       "per_gpu_batch": wl.nrhs, "grid": [512, 512], "radius": wl.radius, "fft": info["fft_size"],
+                       "parallelism": "replicas%d" % world, "l2": "flushed between steps (256 MB write)"},
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                           "per": "apply of 64 RHS"},
+            "plain_gpu": plain,
+            "e2e": {"value": e2e_value, "unit": "RHS/s", "h2d_bytes_per_step": int(x_host.nbytes),
+                    "d2h_bytes_per_step": int(x_host.nbytes)},
+            "gpu_launches": int(op.launches()) * args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak, "traffic": traffic,
+                         "kernel": "fft2d_kernel<float,128>", "kernel_ms": kern_ms,
+                         "algorithmic_flop_per_launch": flops, "algorithmic_bytes_per_launch": bytes_,
+                         "peak_basis": "FP32 FMA pipe: SMs x 128 lanes x 2 x %.0f MHz" % sm_max},
+            "clocks": clk.summary()}
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        rate, pix, cores, el = cpu_oracle_rate(wl, x_host, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "RHS/s", "cores": cores, "kind": "oracle",
+                                "sample": "%d random output pixels x 64 RHS in %.1f s" % (pix, el)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    op.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

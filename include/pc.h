@@ -1,0 +1,219 @@
+/*
+ * pc.h - C ABI of the GB300 product-convolution library (libpc.so).
+ *
+ * The library applies the adaptive product-convolution approximation of
+ * Alger, Rao, Myers, Bui-Thanh, Ghattas (arXiv 1805.06018):
+ *
+ *     y = A~ x = sum_{k=1}^{r} phi_k^E * (w_k . x)          (Section 2.1, Eq. conv_op_approx_main)
+ *
+ * on a box Omega = prod_i [0, shape_i - 1] in Z^d (d = 2 or 3), where
+ *   - the sample points p_k are the corners of the leaf cells of a given grid
+ *     (Section 2.2),
+ *   - w_k are the harmonic partition-of-unity weights on the blocky
+ *     neighbourhoods U_k (Section 2.4),
+ *   - phi_k^E are the caller's impulse responses phi_k[z] = (A delta_{p_k})[z + p_k]
+ *     (Eq. varphi_p_section2) extended with the neighbour average of Section 2.5
+ *     (Eqs. vj_def, def_varphiE),
+ *   - '*' is convolution with extension by zero (Eq. convolution_definition),
+ *     evaluated with FFTs after zero padding (Section 3.2), patch by patch
+ *     (the block translation of Section 3.3), output restricted to Omega.
+ *
+ * Conventions shared by every entry point:
+ *   - Errors are returned as pc_status, never thrown and never abort().  The
+ *     text of the last error of a context is available from pc_last_error().
+ *   - Arrays are C order (last axis fastest).  A batch of vectors is
+ *     [nrhs][n_1]...[n_d] with a stride (ld) between consecutive vectors.
+ *   - "device" pointers are CUDA device memory of the context's device (the
+ *     caller allocates them, e.g. with PyTorch); "host" pointers are ordinary
+ *     host memory.  The library never frees caller memory.
+ *   - Applies are asynchronous and stream ordered: they enqueue kernels on the
+ *     caller's stream and return.  y is overwritten, not accumulated.  x and y
+ *     must stay valid until the work on that stream has completed.  x and y
+ *     must not overlap.  Applies of one operator must not run concurrently
+ *     on the device (they share the operator's ordering flags); successive
+ *     applies on one stream are fine.
+ *   - pc_stream is a cudaStream_t passed as an opaque pointer (NULL = the
+ *     legacy default stream).
+ */
+#ifndef PC_H
+#define PC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PC_OK = 0,
+    PC_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, misaligned ld) */
+    PC_ERR_GRID = 2,         /* leaf cells do not tile the box */
+    PC_ERR_NOMEM = 3,        /* a host or device allocation failed */
+    PC_ERR_BUDGET = 4,       /* a request does not fit the configured memory budget */
+    PC_ERR_CUDA = 5,         /* a CUDA runtime call failed (message in pc_last_error) */
+    PC_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up */
+    PC_ERR_NOT_READY = 7,    /* an asynchronous request has not finished */
+    PC_ERR_UNSUPPORTED = 8   /* valid input outside what this build implements */
+} pc_status;
+
+typedef enum {
+    PC_FP64 = 0,             /* FP64 data, FP64 FFTs (correctness configuration) */
+    PC_FP32 = 1,             /* FP32 data, FP32 FFTs, spectra built in FP64 and rounded once */
+    PC_BF16X3 = 2,           /* reserved: tensor-core DFT with split BF16 operands */
+    PC_TF32X3 = 3            /* reserved: tensor-core DFT with split TF32 operands */
+} pc_precision;
+
+typedef void *pc_stream;     /* cudaStream_t */
+
+/* Omega = prod_{i<ndim} [0, shape[i]-1]; ndim is 2 or 3, shape[i] >= 2. */
+typedef struct {
+    int32_t ndim;
+    int64_t shape[3];
+} pc_box;
+
+/* Leaf cells of the binary tree of Section 2.2: num_cells closed integer
+ * boxes, cells[(c*2 + 0)*ndim + i] = min point, cells[(c*2 + 1)*ndim + i] =
+ * max point (host memory).  They must tile Omega, sharing facets: every
+ * point of Omega lies in some cell, interiors are disjoint, and every cell has
+ * max > min on each axis. */
+typedef struct {
+    int32_t num_cells;
+    const int32_t *cells;
+} pc_grid;
+
+/* Launch-shape knobs; a NULL pc_tuning, or a field of 0, means "choose". */
+typedef struct {
+    int32_t fft_size;        /* padded FFT extent P per axis: 64, 128 (2D) */
+    int32_t tile;            /* input tile extent T <= P - 2R (0: P - 2R) */
+    int32_t ctas_per_sm;     /* persistent CTAs per SM (0: occupancy limit) */
+    int32_t reserved[5];
+} pc_tuning;
+
+/* Read-only description of a built operator. */
+typedef struct {
+    int32_t ndim;
+    int64_t shape[3];
+    int32_t radius;          /* R: phi_k^E lives on [-R, R]^d */
+    int32_t r;               /* number of sample points = number of convolutions */
+    int32_t fft_size;        /* P */
+    int32_t tile;            /* T */
+    int32_t num_tiles;       /* work units per right-hand side pair */
+    int32_t num_colors;      /* overlap-add order classes */
+    int32_t precision;       /* pc_precision */
+    int64_t spectra_bytes;   /* device bytes of the stored spectra */
+    int64_t device_bytes;    /* all device bytes owned by the operator */
+    double build_seconds;
+} pc_operator_info;
+
+typedef struct pc_context pc_context;
+typedef struct pc_operator pc_operator;
+
+/* Create a library context bound to CUDA device `device`.  *ctx receives a
+ * handle that the caller releases with pc_context_destroy.  Fails with
+ * PC_ERR_CUDA if the device cannot be used and PC_ERR_UNSUPPORTED if it is
+ * not compute capability 10.3. */
+pc_status pc_context_create(int32_t device, pc_context **ctx);
+pc_status pc_context_destroy(pc_context *ctx);
+
+/* Text of the last error recorded in ctx (never NULL; "" when none).  With a
+ * NULL ctx it returns the last error of a failed pc_context_create or of a
+ * context-free call such as pc_sample_points.  Valid until the next call on
+ * the same context. */
+const char *pc_last_error(pc_context *ctx);
+
+/* Sample points {p_k} = union of the corners of the leaf cells (Section 2.2),
+ * in lexicographic order of their coordinates; that order defines k in every
+ * other call.  *r receives their number; if points is not NULL it must hold
+ * r*ndim int32 values (host) and receives them as [r][ndim].  Validates the
+ * grid (PC_ERR_GRID). */
+pc_status pc_sample_points(const pc_box *box, const pc_grid *grid, int32_t *r, int32_t *points);
+
+/* Bounding boxes of the blocky neighbourhoods U_k (Section 2.2): lo and hi
+ * receive [r][ndim] int32 (host); either may be NULL.  This is the layout of
+ * caller-supplied weights in pc_build_spectra. */
+pc_status pc_neighbourhood_boxes(const pc_box *box, const pc_grid *grid, int32_t *lo, int32_t *hi);
+
+/* The harmonic partition-of-unity weights of Section 2.4 as the library
+ * builds them (host computation, FP64, no GPU needed): on a leaf whose only
+ * sample points are its corners the recursive Laplace construction gives the
+ * multilinear hat; leaves with hanging nodes (2D) solve the discrete Laplace
+ * equation with piecewise-linear edge data.  *count receives the number of
+ * values (sum over k of |bbox(U_k)|); if weights is not NULL it must hold
+ * that many doubles and receives w_k on bbox(U_k), C order, k ascending
+ * (zero outside U_k). */
+pc_status pc_harmonic_weights(const pc_box *box, const pc_grid *grid, int64_t *count, double *weights);
+
+/* The extended impulse responses phi_k^E of Section 2.5 (Eqs. vj_def,
+ * def_varphiE) as the library builds them (host, FP64, no GPU needed):
+ * impulse and impulse_ext are [r][(2R+1)^ndim] (layout of pc_build_spectra's
+ * impulse argument).  Where p_k + z is outside Omega, phi_k^E[z] is the plain
+ * average of the neighbours phi_j[z] (j in nbrs(k)) whose domain Omega - p_j
+ * contains z, and 0 if there is none. */
+pc_status pc_extend_impulse(const pc_box *box, const pc_grid *grid, int32_t radius, const double *impulse,
+                            double *impulse_ext);
+
+/* Build an operator: weights, extended impulse responses and their padded
+ * spectra (a one-time construction; spectra are computed in FP64 on the
+ * device and stored in `prec`).
+ *   radius   R >= 1: the operator is truncated so that phi_k vanishes
+ *            outside [-R, R]^d (2R+1 <= fft_size - 1).
+ *   impulse  host FP64 [r][(2R+1)^ndim]: phi_k[z] at window index z + R (C
+ *            order over the window), k in sample-point order.  Values at
+ *            z with p_k + z outside Omega are ignored (phi_k is only defined
+ *            on Omega - p_k; Section 2.5 fills that region from neighbours).
+ *   weights  NULL: the library builds the harmonic weights of Section 2.4
+ *            (closed-form multilinear hats on cells without hanging nodes,
+ *            a discrete Laplace solve on 2D cells with hanging nodes).
+ *            Otherwise host FP64, w_k on bbox(U_k) (pc_neighbourhood_boxes),
+ *            C order, concatenated for k = 0..r-1; entries outside U_k must
+ *            be 0.
+ *   prec     PC_FP64 or PC_FP32.
+ *   tune     NULL or knobs (see pc_tuning).
+ * The operator owns its device memory until pc_operator_destroy.  The call
+ * synchronises the device. */
+pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *grid, int32_t radius,
+                           const double *impulse, const double *weights, pc_precision prec,
+                           const pc_tuning *tune, pc_operator **op);
+
+pc_status pc_operator_info_get(const pc_operator *op, pc_operator_info *info);
+
+/* y = A~ x for one vector: x and y are device arrays of N = prod(shape)
+ * elements of the operator's precision (float or double). */
+pc_status pc_apply(pc_operator *op, const void *x, void *y, pc_stream stream);
+
+/* Y[b] = A~ X[b] for b < nrhs: X[b] starts at x + b*ldx elements, Y[b] at
+ * y + b*ldy elements (device), ldx, ldy >= N.  nrhs = 0 is a no-op. */
+pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx,
+                           void *y, int64_t ldy, pc_stream stream);
+
+/* Plain path for comparison: the same operator applied one vector at a time
+ * through a gather kernel, a library FFT (cuFFT) of each padded patch, a
+ * spectral product kernel, an inverse library FFT and an output-stationary
+ * overlap-add kernel.  FP32 operators only.  Same arguments as
+ * pc_apply_batched; it allocates its scratch on first use. */
+pc_status pc_apply_plain(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx,
+                         void *y, int64_t ldy, pc_stream stream);
+
+/* Synchronise the operator's last stream and report device-side status:
+ * PC_ERR_TIMEOUT if a bounded wait inside a kernel gave up since the last
+ * call (the flag is then cleared), PC_ERR_CUDA on an asynchronous CUDA error. */
+pc_status pc_operator_check(pc_operator *op);
+
+/* Device time of the fused patch kernel of the operator's most recent
+ * pc_apply / pc_apply_batched, in milliseconds, from CUDA events the library
+ * records on the caller's stream just before and after that launch (the
+ * zero-fill of y is outside the pair).  Waits for the end event.
+ * PC_ERR_NOT_READY if no apply has been issued. */
+pc_status pc_operator_kernel_time(pc_operator *op, float *ms);
+
+/* Counters of the operator's most recent apply (host): kernels launched. */
+pc_status pc_operator_launches(const pc_operator *op, int64_t *kernels_last_apply);
+
+pc_status pc_operator_destroy(pc_operator *op);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PC_H */

@@ -1,0 +1,283 @@
+"""ctypes binding of libpc (include/pc.h): the same entry points, argument
+marshalling only.  Every step of an apply runs in the library's kernels.
+
+The library is loaded on first use; if it has not been built the call raises
+``LibraryMissing`` (there is no fallback path).  Device arrays are passed as
+raw pointers; :class:`Operator` adds the PyTorch conveniences (data_ptr(),
+current stream) on top.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libpc.so")
+
+PC_OK, PC_ERR_ARG, PC_ERR_GRID, PC_ERR_NOMEM, PC_ERR_BUDGET, PC_ERR_CUDA, PC_ERR_TIMEOUT, \
+    PC_ERR_NOT_READY, PC_ERR_UNSUPPORTED = range(9)
+STATUS_NAMES = ["PC_OK", "PC_ERR_ARG", "PC_ERR_GRID", "PC_ERR_NOMEM", "PC_ERR_BUDGET", "PC_ERR_CUDA",
+                "PC_ERR_TIMEOUT", "PC_ERR_NOT_READY", "PC_ERR_UNSUPPORTED"]
+PC_FP64, PC_FP32, PC_BF16X3, PC_TF32X3 = range(4)
+PRECISIONS = {"fp64": PC_FP64, "fp32": PC_FP32, "bf16x3": PC_BF16X3, "tf32x3": PC_TF32X3}
+
+
+class LibraryMissing(ImportError):
+    pass
+
+
+class PCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status, msg))
+
+
+class pc_box(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("shape", ctypes.c_int64 * 3)]
+
+
+class pc_grid(ctypes.Structure):
+    _fields_ = [("num_cells", ctypes.c_int32), ("cells", ctypes.POINTER(ctypes.c_int32))]
+
+
+class pc_tuning(ctypes.Structure):
+    _fields_ = [("fft_size", ctypes.c_int32), ("tile", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class pc_operator_info(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("shape", ctypes.c_int64 * 3), ("radius", ctypes.c_int32),
+                ("r", ctypes.c_int32), ("fft_size", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("num_tiles", ctypes.c_int32), ("num_colors", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("spectra_bytes", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("build_seconds", ctypes.c_double)]
+
+
+# every entry point of include/pc.h: name -> (restype, argtypes)
+_VP = ctypes.c_void_p
+_PROTOS = {
+    "pc_context_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(_VP)]),
+    "pc_context_destroy": (ctypes.c_int, [_VP]),
+    "pc_last_error": (ctypes.c_char_p, [_VP]),
+    "pc_sample_points": (ctypes.c_int, [ctypes.POINTER(pc_box), ctypes.POINTER(pc_grid),
+                                        ctypes.POINTER(ctypes.c_int32), _VP]),
+    "pc_neighbourhood_boxes": (ctypes.c_int, [ctypes.POINTER(pc_box), ctypes.POINTER(pc_grid), _VP, _VP]),
+    "pc_harmonic_weights": (ctypes.c_int, [ctypes.POINTER(pc_box), ctypes.POINTER(pc_grid),
+                                           ctypes.POINTER(ctypes.c_int64), _VP]),
+    "pc_extend_impulse": (ctypes.c_int, [ctypes.POINTER(pc_box), ctypes.POINTER(pc_grid), ctypes.c_int32,
+                                         _VP, _VP]),
+    "pc_build_spectra": (ctypes.c_int, [_VP, ctypes.POINTER(pc_box), ctypes.POINTER(pc_grid), ctypes.c_int32,
+                                        _VP, _VP, ctypes.c_int, ctypes.POINTER(pc_tuning), ctypes.POINTER(_VP)]),
+    "pc_operator_info_get": (ctypes.c_int, [_VP, ctypes.POINTER(pc_operator_info)]),
+    "pc_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "pc_apply_batched": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
+    "pc_apply_plain": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
+    "pc_operator_check": (ctypes.c_int, [_VP]),
+    "pc_operator_kernel_time": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "pc_operator_launches": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
+    "pc_operator_destroy": (ctypes.c_int, [_VP]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libpc (raises LibraryMissing when it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise LibraryMissing("libpc.so is not built (%s); run paper_1805_06018_gb300/build.py" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _PROTOS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, ctx=None):
+    if status != PC_OK:
+        msg = lib().pc_last_error(ctx)
+        raise PCError(status, msg.decode() if msg else "")
+
+
+def _box(shape: Sequence[int]) -> pc_box:
+    b = pc_box()
+    b.ndim = len(shape)
+    for i in range(3):
+        b.shape[i] = int(shape[i]) if i < len(shape) else 1
+    return b
+
+
+def _grid(cells: np.ndarray):
+    arr = np.ascontiguousarray(np.asarray(cells, dtype=np.int32))
+    g = pc_grid()
+    g.num_cells = arr.shape[0]
+    g.cells = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    return g, arr   # keep arr alive
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(_VP)
+
+
+def pc_sample_points(shape, cells) -> np.ndarray:
+    b = _box(shape)
+    g, keep = _grid(cells)
+    r = ctypes.c_int32()
+    _check(lib().pc_sample_points(ctypes.byref(b), ctypes.byref(g), ctypes.byref(r), None))
+    out = np.zeros((r.value, len(shape)), dtype=np.int32)
+    _check(lib().pc_sample_points(ctypes.byref(b), ctypes.byref(g), ctypes.byref(r), _ptr(out)))
+    del keep
+    return out
+
+
+def pc_neighbourhood_boxes(shape, cells):
+    r = len(pc_sample_points(shape, cells))
+    b = _box(shape)
+    g, keep = _grid(cells)
+    lo = np.zeros((r, len(shape)), dtype=np.int32)
+    hi = np.zeros((r, len(shape)), dtype=np.int32)
+    _check(lib().pc_neighbourhood_boxes(ctypes.byref(b), ctypes.byref(g), _ptr(lo), _ptr(hi)))
+    del keep
+    return lo, hi
+
+
+def pc_harmonic_weights(shape, cells) -> np.ndarray:
+    b = _box(shape)
+    g, keep = _grid(cells)
+    n = ctypes.c_int64()
+    _check(lib().pc_harmonic_weights(ctypes.byref(b), ctypes.byref(g), ctypes.byref(n), None))
+    out = np.zeros(n.value)
+    _check(lib().pc_harmonic_weights(ctypes.byref(b), ctypes.byref(g), ctypes.byref(n), _ptr(out)))
+    del keep
+    return out
+
+
+def pc_extend_impulse(shape, cells, radius: int, impulse: np.ndarray) -> np.ndarray:
+    b = _box(shape)
+    g, keep = _grid(cells)
+    imp = np.ascontiguousarray(impulse, dtype=np.float64)
+    out = np.zeros_like(imp)
+    _check(lib().pc_extend_impulse(ctypes.byref(b), ctypes.byref(g), ctypes.c_int32(radius), _ptr(imp), _ptr(out)))
+    del keep
+    return out
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        h = _VP()
+        _check(lib().pc_context_create(ctypes.c_int32(device), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            lib().pc_context_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class Operator:
+    """A built product-convolution operator (pc_build_spectra)."""
+
+    def __init__(self, ctx: Context, shape, cells, radius: int, impulse: np.ndarray, precision: str = "fp32",
+                 weights: Optional[np.ndarray] = None, fft_size: int = 0, tile: int = 0, ctas_per_sm: int = 0):
+        self.ctx = ctx
+        self.shape = tuple(int(s) for s in shape)
+        self.N = int(np.prod(self.shape))
+        self.precision = precision
+        b = _box(shape)
+        g, keep = _grid(cells)
+        imp = np.ascontiguousarray(impulse, dtype=np.float64)
+        wts = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+        tune = pc_tuning()
+        tune.fft_size, tune.tile, tune.ctas_per_sm = fft_size, tile, ctas_per_sm
+        h = _VP()
+        _check(lib().pc_build_spectra(ctx.handle, ctypes.byref(b), ctypes.byref(g), ctypes.c_int32(radius),
+                                      _ptr(imp), _ptr(wts), PRECISIONS[precision], ctypes.byref(tune),
+                                      ctypes.byref(h)), ctx.handle)
+        del keep
+        self.handle = h
+
+    def info(self) -> dict:
+        inf = pc_operator_info()
+        _check(lib().pc_operator_info_get(self.handle, ctypes.byref(inf)))
+        return {f: (list(getattr(inf, f)) if f == "shape" else getattr(inf, f)) for f, _ in inf._fields_}
+
+    # raw-pointer entry points -------------------------------------------------
+    def pc_apply(self, x_ptr: int, y_ptr: int, stream_ptr: int):
+        _check(lib().pc_apply(self.handle, _VP(x_ptr), _VP(y_ptr), _VP(stream_ptr)), self.ctx.handle)
+
+    def pc_apply_batched(self, nrhs: int, x_ptr: int, ldx: int, y_ptr: int, ldy: int, stream_ptr: int):
+        _check(lib().pc_apply_batched(self.handle, ctypes.c_int32(nrhs), _VP(x_ptr), ctypes.c_int64(ldx),
+                                      _VP(y_ptr), ctypes.c_int64(ldy), _VP(stream_ptr)), self.ctx.handle)
+
+    def pc_apply_plain(self, nrhs: int, x_ptr: int, ldx: int, y_ptr: int, ldy: int, stream_ptr: int):
+        _check(lib().pc_apply_plain(self.handle, ctypes.c_int32(nrhs), _VP(x_ptr), ctypes.c_int64(ldx),
+                                    _VP(y_ptr), ctypes.c_int64(ldy), _VP(stream_ptr)), self.ctx.handle)
+
+    def check(self):
+        _check(lib().pc_operator_check(self.handle), self.ctx.handle)
+
+    def kernel_ms(self) -> float:
+        """Device time of the fused kernel of the last apply (waits for it)."""
+        ms = ctypes.c_float()
+        _check(lib().pc_operator_kernel_time(self.handle, ctypes.byref(ms)), self.ctx.handle)
+        return ms.value
+
+    def launches(self) -> int:
+        n = ctypes.c_int64()
+        _check(lib().pc_operator_launches(self.handle, ctypes.byref(n)))
+        return n.value
+
+    # torch conveniences ----------------------------------------------------------
+    def _args(self, x, out):
+        import torch
+        if not (x.is_cuda and x.is_contiguous()):
+            raise ValueError("x must be a contiguous CUDA tensor")
+        want = torch.float64 if self.precision == "fp64" else torch.float32
+        if x.dtype != want:
+            raise ValueError("x must be %s" % want)
+        B = x.numel() // self.N
+        if x.numel() != B * self.N:
+            raise ValueError("x does not hold whole vectors of the operator's box")
+        y = torch.empty_like(x) if out is None else out
+        return B, y
+
+    def apply(self, x, out=None, stream=None):
+        """y = A~ x for x of shape [B, *box] (or [*box])."""
+        B, y = self._args(x, out)
+        self.pc_apply_batched(B, x.data_ptr(), self.N, y.data_ptr(), self.N, _stream_ptr(stream))
+        return y
+
+    def apply_plain(self, x, out=None, stream=None):
+        B, y = self._args(x, out)
+        self.pc_apply_plain(B, x.data_ptr(), self.N, y.data_ptr(), self.N, _stream_ptr(stream))
+        return y
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pc_operator_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,490 @@
+// C ABI of libpc: contexts, operator construction, applies, status.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "pc_internal.h"
+
+namespace {
+
+std::mutex g_err_mu;
+std::string g_err;  // last error of context-free calls
+
+pc_status fail(pc_context *ctx, pc_status st, const std::string &msg) {
+    if (ctx) {
+        ctx->last_error = msg;
+    } else {
+        std::lock_guard<std::mutex> lk(g_err_mu);
+        g_err = msg;
+    }
+    return st;
+}
+
+pc_status cuda_fail(pc_context *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? PC_ERR_NOMEM : PC_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Make ctx's device current for the duration of a call, then restore.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+cudaError_t upload(T **dst, const T *src, size_t n, size_t &acct) {
+    *dst = nullptr;
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), sizeof(T) * n);
+    if (e != cudaSuccess) return e;
+    acct += sizeof(T) * n;
+    return cudaMemcpy(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice);
+}
+
+// W_P^j = exp(-2 pi i j / P), j < P, from long-double cos/sin of the
+// first-octant-reduced angle.
+std::vector<double> twiddles64(int P) {
+    std::vector<double> tw(2 * size_t(P));
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int j = 0; j < P; ++j) {
+        const long double ang = 2.0L * pi * (long double)j / (long double)P;
+        tw[2 * j] = double(std::cos(ang));
+        tw[2 * j + 1] = double(-std::sin(ang));
+    }
+    // exact values on the axes
+    for (int j = 0; j < P; j += P / 4) {
+        const int q = j / (P / 4);
+        tw[2 * j] = q == 0 ? 1.0 : q == 2 ? -1.0 : 0.0;
+        tw[2 * j + 1] = q == 1 ? -1.0 : q == 3 ? 1.0 : 0.0;
+    }
+    return tw;
+}
+
+void free_operator(pc_operator *op) {
+    if (!op) return;
+    pc::plain_free(op);
+    cudaFree(op->d_spec);
+    cudaFree(op->d_w);
+    cudaFree(op->d_tiles);
+    cudaFree(op->d_color_start);
+    cudaFree(op->d_dep_start);
+    cudaFree(op->d_dep);
+    cudaFree(op->d_done);
+    cudaFree(op->d_ctrl);
+    cudaFree(op->d_tw);
+    if (op->ev_begin) cudaEventDestroy(op->ev_begin);
+    if (op->ev_end) cudaEventDestroy(op->ev_end);
+    delete op;
+}
+
+}  // namespace
+
+extern "C" {
+
+pc_status pc_context_create(int32_t device, pc_context **ctx) {
+    if (!ctx) return fail(nullptr, PC_ERR_ARG, "ctx is null");
+    *ctx = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(nullptr, PC_ERR_ARG, "no such CUDA device");
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDeviceProperties");
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(nullptr, PC_ERR_UNSUPPORTED,
+                    "libpc is built for sm_103a (GB300); device is sm_" + std::to_string(prop.major) +
+                        std::to_string(prop.minor));
+    auto *c = new (std::nothrow) pc_context;
+    if (!c) return fail(nullptr, PC_ERR_NOMEM, "out of host memory");
+    c->device = device;
+    c->num_sms = prop.multiProcessorCount;
+    c->cc_major = prop.major;
+    c->cc_minor = prop.minor;
+    c->smem_optin = prop.sharedMemPerBlockOptin;
+    *ctx = c;
+    return PC_OK;
+}
+
+pc_status pc_context_destroy(pc_context *ctx) {
+    delete ctx;
+    return PC_OK;
+}
+
+const char *pc_last_error(pc_context *ctx) {
+    if (ctx) return ctx->last_error.c_str();
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    static thread_local std::string copy;
+    copy = g_err;
+    return copy.c_str();
+}
+
+pc_status pc_sample_points(const pc_box *box, const pc_grid *grid, int32_t *r, int32_t *points) {
+    if (!r) return fail(nullptr, PC_ERR_ARG, "r is null");
+    pc::Geometry g;
+    std::string err;
+    pc_status st = pc::build_geometry(box, grid, g, err);
+    if (st != PC_OK) return fail(nullptr, st, err);
+    *r = int32_t(g.pts.size());
+    if (points)
+        for (size_t k = 0; k < g.pts.size(); ++k)
+            for (int a = 0; a < g.d; ++a) points[k * g.d + a] = int32_t(g.pts[k][a]);
+    return PC_OK;
+}
+
+pc_status pc_neighbourhood_boxes(const pc_box *box, const pc_grid *grid, int32_t *lo, int32_t *hi) {
+    pc::Geometry g;
+    std::string err;
+    pc_status st = pc::build_geometry(box, grid, g, err);
+    if (st != PC_OK) return fail(nullptr, st, err);
+    for (size_t k = 0; k < g.pts.size(); ++k)
+        for (int a = 0; a < g.d; ++a) {
+            if (lo) lo[k * g.d + a] = int32_t(g.bb_lo[k][a]);
+            if (hi) hi[k * g.d + a] = int32_t(g.bb_hi[k][a]);
+        }
+    return PC_OK;
+}
+
+pc_status pc_harmonic_weights(const pc_box *box, const pc_grid *grid, int64_t *count, double *weights) {
+    if (!count) return fail(nullptr, PC_ERR_ARG, "count is null");
+    pc::Geometry g;
+    std::string err;
+    pc_status st = pc::build_geometry(box, grid, g, err);
+    if (st != PC_OK) return fail(nullptr, st, err);
+    int64_t tot = 0;
+    for (size_t k = 0; k < g.pts.size(); ++k) tot += g.bbox_elems(int(k));
+    *count = tot;
+    if (!weights) return PC_OK;
+    std::vector<double> w;
+    std::vector<int64_t> off;
+    st = pc::build_weights(g, w, off, err);
+    if (st != PC_OK) return fail(nullptr, st, err);
+    std::memcpy(weights, w.data(), sizeof(double) * w.size());
+    return PC_OK;
+}
+
+pc_status pc_extend_impulse(const pc_box *box, const pc_grid *grid, int32_t radius, const double *impulse,
+                            double *impulse_ext) {
+    if (!impulse || !impulse_ext) return fail(nullptr, PC_ERR_ARG, "null impulse array");
+    if (radius < 1) return fail(nullptr, PC_ERR_ARG, "radius must be >= 1");
+    pc::Geometry g;
+    std::string err;
+    pc_status st = pc::build_geometry(box, grid, g, err);
+    if (st != PC_OK) return fail(nullptr, st, err);
+    std::vector<double> e;
+    pc::build_extension(g, radius, impulse, e);
+    std::memcpy(impulse_ext, e.data(), sizeof(double) * e.size());
+    return PC_OK;
+}
+
+pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *grid, int32_t radius,
+                           const double *impulse, const double *weights, pc_precision prec,
+                           const pc_tuning *tune, pc_operator **out) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!ctx) return fail(nullptr, PC_ERR_ARG, "ctx is null");
+    if (!out || !impulse) return fail(ctx, PC_ERR_ARG, "null impulse or output handle");
+    *out = nullptr;
+    if (prec != PC_FP32 && prec != PC_FP64)
+        return fail(ctx, PC_ERR_UNSUPPORTED, "precision not built: use PC_FP32 or PC_FP64");
+    pc::Geometry g;
+    std::string err;
+    pc_status st = pc::build_geometry(box, grid, g, err);
+    if (st != PC_OK) return fail(ctx, st, err);
+    if (g.d != 2) return fail(ctx, PC_ERR_UNSUPPORTED, "only 2D operators are built in this version");
+    if (radius < 1) return fail(ctx, PC_ERR_ARG, "radius must be >= 1");
+    int P = tune && tune->fft_size ? tune->fft_size : (prec == PC_FP64 ? 64 : 128);
+    if (prec == PC_FP64 && P != 64) return fail(ctx, PC_ERR_UNSUPPORTED, "FP64 operators use fft_size 64");
+    if (prec == PC_FP32 && P != 64 && P != 128) return fail(ctx, PC_ERR_UNSUPPORTED, "FP32 2D fft_size must be 64 or 128");
+    if (2 * radius + 1 > P - 1) return fail(ctx, PC_ERR_UNSUPPORTED, "radius too large for the FFT size");
+    int T = P - 2 * radius;
+    if (tune && tune->tile) {
+        if (tune->tile < 1 || tune->tile > T) return fail(ctx, PC_ERR_ARG, "tile must be in [1, fft_size - 2R]");
+        T = tune->tile;
+    }
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return fail(ctx, PC_ERR_CUDA, "cannot select the context's device");
+    int ctas_per_sm = 0;
+    size_t smem = 0;
+    cudaError_t e = pc::fft2d_configure(P, prec, &ctas_per_sm, &smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "configuring the patch kernel");
+    if (ctas_per_sm < 1) return fail(ctx, PC_ERR_UNSUPPORTED, "patch kernel does not fit on an SM");
+    if (tune && tune->ctas_per_sm > 0) ctas_per_sm = std::min(ctas_per_sm, int(tune->ctas_per_sm));
+
+    const int r = int(g.pts.size());
+    const int64_t W = 2 * radius + 1, wsz = W * W;
+    // weights
+    std::vector<double> w;
+    std::vector<int64_t> woff;
+    if (weights) {
+        int64_t tot = 0;
+        woff.resize(r);
+        for (int k = 0; k < r; ++k) {
+            woff[k] = tot;
+            tot += g.bbox_elems(k);
+        }
+        w.assign(weights, weights + tot);
+    } else {
+        st = pc::build_weights(g, w, woff, err);
+        if (st != PC_OK) return fail(ctx, st, err);
+    }
+    // extension (Section 2.5)
+    std::vector<double> phiE;
+    pc::build_extension(g, radius, impulse, phiE);
+    // schedule
+    pc::Schedule sch;
+    pc::build_schedule(g, radius, T, woff, sch);
+
+    auto *op = new (std::nothrow) pc_operator;
+    if (!op) return fail(ctx, PC_ERR_NOMEM, "out of host memory");
+    op->ctx = ctx;
+    op->d = g.d;
+    op->shape = g.shape;
+    op->N = g.shape[0] * g.shape[1] * g.shape[2];
+    op->R = radius;
+    op->P = P;
+    op->T = T;
+    op->r = r;
+    op->prec = prec;
+    op->elem = prec == PC_FP64 ? 8 : 4;
+    op->n_tiles = int(sch.tiles.size());
+    op->n_colors = int(sch.color_start.size()) - 1;
+    op->ctas = ctx->num_sms * ctas_per_sm;
+    op->color_start_h = sch.color_start;
+    op->tiles_h = sch.tiles;
+    size_t acct = 0;
+    auto bail = [&](cudaError_t ee, const char *what) {
+        pc_status s2 = cuda_fail(ctx, ee, what);
+        free_operator(op);
+        return s2;
+    };
+    // weights in compute precision
+    if (prec == PC_FP64) {
+        e = upload(reinterpret_cast<double **>(&op->d_w), w.data(), w.size(), acct);
+    } else {
+        std::vector<float> wf(w.begin(), w.end());
+        e = upload(reinterpret_cast<float **>(&op->d_w), wf.data(), wf.size(), acct);
+    }
+    if (e != cudaSuccess) return bail(e, "uploading weights");
+    op->w_bytes = w.size() * op->elem;
+    if ((e = upload(&op->d_tiles, sch.tiles.data(), sch.tiles.size(), acct)) != cudaSuccess) return bail(e, "tiles");
+    if ((e = upload(&op->d_color_start, sch.color_start.data(), sch.color_start.size(), acct)) != cudaSuccess)
+        return bail(e, "colours");
+    if ((e = upload(&op->d_dep_start, sch.dep_start.data(), sch.dep_start.size(), acct)) != cudaSuccess)
+        return bail(e, "dependencies");
+    std::vector<int32_t> depv = sch.dep;
+    if (depv.empty()) depv.push_back(0);
+    if ((e = upload(&op->d_dep, depv.data(), depv.size(), acct)) != cudaSuccess) return bail(e, "dependencies");
+    if ((e = cudaMalloc(&op->d_ctrl, 64)) != cudaSuccess) return bail(e, "control block");
+    acct += 64;
+    if ((e = cudaMemset(op->d_ctrl, 0, 64)) != cudaSuccess) return bail(e, "control block");
+    // twiddles
+    std::vector<double> tw = twiddles64(P);
+    double2 *d_tw64 = nullptr;
+    if ((e = upload(reinterpret_cast<double **>(&d_tw64), tw.data(), tw.size(), acct)) != cudaSuccess)
+        return bail(e, "twiddles");
+    acct -= tw.size() * sizeof(double);
+    if (prec == PC_FP64) {
+        e = upload(reinterpret_cast<double **>(&op->d_tw), tw.data(), tw.size(), acct);
+    } else {
+        std::vector<float> twf(tw.begin(), tw.end());
+        e = upload(reinterpret_cast<float **>(&op->d_tw), twf.data(), twf.size(), acct);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(d_tw64);
+        return bail(e, "twiddles");
+    }
+    // spectra (FP64 on the device, rounded once)
+    op->spec_stride = int64_t(P / 2 + 1) * P;
+    op->spec_bytes = size_t(r) * op->spec_stride * 2 * op->elem;
+    double *d_psi = nullptr;
+    e = cudaMalloc(&op->d_spec, op->spec_bytes);
+    if (e == cudaSuccess) {
+        acct += op->spec_bytes;
+        e = cudaMalloc(&d_psi, sizeof(double) * phiE.size());
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(d_psi, phiE.data(), sizeof(double) * phiE.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = pc::build_spectra_2d(d_psi, r, radius, P, prec, op->d_spec, d_tw64, nullptr);
+    cudaFree(d_psi);
+    cudaFree(d_tw64);
+    if (e != cudaSuccess) return bail(e, "building spectra");
+    (void)wsz;
+    op->device_bytes = acct;
+    op->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = op;
+    return PC_OK;
+}
+
+pc_status pc_operator_info_get(const pc_operator *op, pc_operator_info *info) {
+    if (!op || !info) return fail(nullptr, PC_ERR_ARG, "null operator or info");
+    std::memset(info, 0, sizeof(*info));
+    info->ndim = op->d;
+    for (int a = 0; a < 3; ++a) info->shape[a] = op->shape[a];
+    info->radius = op->R;
+    info->r = op->r;
+    info->fft_size = op->P;
+    info->tile = op->T;
+    info->num_tiles = op->n_tiles;
+    info->num_colors = op->n_colors;
+    info->precision = op->prec;
+    info->spectra_bytes = int64_t(op->spec_bytes);
+    info->device_bytes = int64_t(op->device_bytes);
+    info->build_seconds = op->build_seconds;
+    return PC_OK;
+}
+
+static pc_status ensure_done_capacity(pc_operator *op, int32_t npairs) {
+    if (npairs <= op->done_cap) return PC_OK;
+    cudaError_t e = cudaSuccess;
+    if (op->last_stream || op->d_done) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(op->ctx, e, "synchronising before growing flags");
+    cudaFree(op->d_done);
+    op->d_done = nullptr;
+    const int32_t cap = std::max<int32_t>(npairs, 32);
+    const size_t bytes = sizeof(uint32_t) * size_t(op->n_tiles) * cap;
+    e = cudaMalloc(&op->d_done, bytes);
+    if (e != cudaSuccess) {
+        op->done_cap = 0;
+        return cuda_fail(op->ctx, e, "allocating ordering flags");
+    }
+    e = cudaMemset(op->d_done, 0, bytes);
+    if (e != cudaSuccess) return cuda_fail(op->ctx, e, "clearing ordering flags");
+    op->done_cap = cap;
+    op->epoch = 0;
+    return PC_OK;
+}
+
+pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
+                           pc_stream stream) {
+    if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
+    pc_context *ctx = op->ctx;
+    if (nrhs < 0) return fail(ctx, PC_ERR_ARG, "nrhs < 0");
+    if (nrhs == 0) return PC_OK;
+    if (!x || !y) return fail(ctx, PC_ERR_ARG, "null x or y");
+    if (ldx < op->N || ldy < op->N) return fail(ctx, PC_ERR_ARG, "ldx and ldy must be >= N");
+    const uintptr_t xa = reinterpret_cast<uintptr_t>(x), ya = reinterpret_cast<uintptr_t>(y);
+    if (xa % op->elem || ya % op->elem) return fail(ctx, PC_ERR_ARG, "x and y must be aligned to the element size");
+    const uintptr_t xe = xa + uintptr_t((int64_t(nrhs - 1) * ldx + op->N) * op->elem);
+    const uintptr_t ye = ya + uintptr_t((int64_t(nrhs - 1) * ldy + op->N) * op->elem);
+    if (xa < ye && ya < xe) return fail(ctx, PC_ERR_ARG, "x and y overlap");
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return fail(ctx, PC_ERR_CUDA, "cannot select the context's device");
+    const int32_t npairs = (nrhs + 1) / 2;
+    pc_status st = ensure_done_capacity(op, npairs);
+    if (st != PC_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (++op->epoch == 0) op->epoch = 1;
+    pc::ApplyParams p{};
+    p.x = x;
+    p.y = y;
+    p.ldx = ldx;
+    p.ldy = ldy;
+    p.nrhs = nrhs;
+    p.npairs = npairs;
+    p.n[0] = int32_t(op->shape[0]);
+    p.n[1] = int32_t(op->shape[1]);
+    p.n[2] = int32_t(op->shape[2]);
+    p.R = op->R;
+    p.tiles = op->d_tiles;
+    p.color_start = op->d_color_start;
+    p.n_colors = op->n_colors;
+    p.dep_start = op->d_dep_start;
+    p.dep = op->d_dep;
+    p.done = op->d_done;
+    p.done_ld = op->done_cap;
+    p.epoch = op->epoch;
+    p.ctrl = op->d_ctrl;
+    p.spec = op->d_spec;
+    p.spec_stride = op->spec_stride;
+    p.w = op->d_w;
+    p.tw = op->d_tw;
+    p.total_items = int64_t(op->n_tiles) * npairs;
+    cudaError_t e = pc::launch_zero(p, op->N, op->prec, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the zero kernel");
+    const int ctas = int(std::min<int64_t>(op->ctas, p.total_items));
+    if (!op->ev_begin) {
+        if ((e = cudaEventCreate(&op->ev_begin)) != cudaSuccess) return cuda_fail(ctx, e, "creating events");
+        if ((e = cudaEventCreate(&op->ev_end)) != cudaSuccess) return cuda_fail(ctx, e, "creating events");
+    }
+    cudaEventRecord(op->ev_begin, s);
+    e = pc::launch_fft2d(p, op->P, op->prec, ctas, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the patch kernel");
+    cudaEventRecord(op->ev_end, s);
+    op->timed = true;
+    op->last_stream = s;
+    op->launches_last = 2;
+    return PC_OK;
+}
+
+pc_status pc_apply(pc_operator *op, const void *x, void *y, pc_stream stream) {
+    if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
+    return pc_apply_batched(op, 1, x, op->N, y, op->N, stream);
+}
+
+pc_status pc_apply_plain(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
+                         pc_stream stream) {
+    if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
+    pc_context *ctx = op->ctx;
+    if (op->prec != PC_FP32) return fail(ctx, PC_ERR_UNSUPPORTED, "the plain path is FP32 only");
+    if (nrhs < 0) return fail(ctx, PC_ERR_ARG, "nrhs < 0");
+    if (nrhs == 0) return PC_OK;
+    if (!x || !y) return fail(ctx, PC_ERR_ARG, "null x or y");
+    if (ldx < op->N || ldy < op->N) return fail(ctx, PC_ERR_ARG, "ldx and ldy must be >= N");
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return fail(ctx, PC_ERR_CUDA, "cannot select the context's device");
+    std::string err;
+    pc_status st = pc::plain_apply(op, nrhs, x, ldx, y, ldy, static_cast<cudaStream_t>(stream), err);
+    if (st != PC_OK) return fail(ctx, st, err);
+    op->last_stream = static_cast<cudaStream_t>(stream);
+    return PC_OK;
+}
+
+pc_status pc_operator_check(pc_operator *op) {
+    if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
+    DeviceGuard dg(op->ctx->device);
+    cudaError_t e = cudaStreamSynchronize(op->last_stream);
+    if (e != cudaSuccess) return cuda_fail(op->ctx, e, "asynchronous CUDA error");
+    int32_t ctrl[4] = {0, 0, 0, 0};
+    e = cudaMemcpy(ctrl, op->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(op->ctx, e, "reading the status word");
+    if (ctrl[2]) {
+        cudaMemset(op->d_ctrl + 2, 0, sizeof(int32_t));
+        return fail(op->ctx, PC_ERR_TIMEOUT, "a bounded wait in the patch kernel timed out");
+    }
+    return PC_OK;
+}
+
+pc_status pc_operator_kernel_time(pc_operator *op, float *ms) {
+    if (!op || !ms) return fail(nullptr, PC_ERR_ARG, "null argument");
+    if (!op->timed) return fail(op->ctx, PC_ERR_NOT_READY, "no apply has been issued");
+    DeviceGuard dg(op->ctx->device);
+    cudaError_t e = cudaEventSynchronize(op->ev_end);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, op->ev_begin, op->ev_end);
+    if (e != cudaSuccess) return cuda_fail(op->ctx, e, "reading kernel events");
+    return PC_OK;
+}
+
+pc_status pc_operator_launches(const pc_operator *op, int64_t *kernels_last_apply) {
+    if (!op || !kernels_last_apply) return fail(nullptr, PC_ERR_ARG, "null argument");
+    *kernels_last_apply = op->launches_last;
+    return PC_OK;
+}
+
+pc_status pc_operator_destroy(pc_operator *op) {
+    if (!op) return PC_OK;
+    DeviceGuard dg(op->ctx->device);
+    cudaDeviceSynchronize();
+    free_operator(op);
+    return PC_OK;
+}
+
+}  // extern "C"

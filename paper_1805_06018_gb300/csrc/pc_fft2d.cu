@@ -1,0 +1,265 @@
+// Fused 2D patch kernel for y = sum_k phi_k^E * (w_k . x)  (Eq. conv_op_approx_main).
+//
+// One work item = (input tile of bbox(U_k), pair of right-hand sides).  Two
+// real right-hand sides travel as the real and imaginary parts of one complex
+// field: since phi_k^E is real, IFFT(FFT(u0 + i u1) . phi^_k) = (phi*u0) +
+// i (phi*u1), so one complex P x P FFT serves two vectors with no unpacking.
+//
+//   phase A  gather w_k . x for the tile rows (coalesced global loads),
+//            row FFTs (length P, pruned to the tile's n1 non-zero rows)
+//   phase B  per column: FFT over the n1 non-zero rows, product with the
+//            stored spectrum phi^_k (Section 3.2: convolution theorem after
+//            zero padding to P >= n + 2R, so the circular product is the
+//            linear convolution), inverse FFT; all in registers, one shared
+//            memory round trip per column
+//   phase C  inverse row FFTs of the L1 = n1 + 2R needed rows, then the
+//            overlap-add of the L1 x L2 output box (clipped to Omega) into y
+//
+// Overlap-add order: tiles carry a colour such that tiles of one colour have
+// disjoint output boxes; before adding, a tile waits (bounded spin) until
+// every overlapping lower-colour tile of the same right-hand-side pair has
+// added.  Each output pixel therefore sums its contributions in colour order,
+// which makes y bitwise reproducible.  Items are taken from an atomic counter
+// in colour-major order, so a tile only ever waits on items that were taken
+// earlier by running CTAs: the wait always ends.
+#include "pc_fftcore.cuh"
+#include "pc_internal.h"
+
+namespace pc {
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+constexpr int kThreads2d = 512;
+constexpr long long kSpinLimit = 1ll << 24;   // x >= 64 ns per spin: about a second at least
+
+template <int P, typename C> struct RowScratch {
+    C *S;
+    int row;
+    __device__ __forceinline__ C ld(int s) const { return S[row * P + (s ^ swz(row))]; }
+    __device__ __forceinline__ void st(int s, C v) const { S[row * P + (s ^ swz(row))] = v; }
+};
+template <int P, typename C> struct ColScratch {
+    C *S;
+    int col;
+    __device__ __forceinline__ C ld(int s) const { return S[s * P + (col ^ swz(s))]; }
+    __device__ __forceinline__ void st(int s, C v) const { S[s * P + (col ^ swz(s))] = v; }
+};
+
+template <typename T, int P>
+__global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams p) {
+    using C = typename Cx<T>::type;
+    constexpr int R1 = FftShape<P>::R1, R2 = FftShape<P>::R2;
+    constexpr int LINES = kThreads2d / R2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *S = reinterpret_cast<C *>(smem_raw);
+    __shared__ int64_t s_item;
+
+    const int t = threadIdx.x % R2;
+    const int line = threadIdx.x / R2;
+    const unsigned lmask = FftShape<P>::line_mask();
+    const C *twg = static_cast<const C *>(p.tw);
+    C tw[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) tw[m] = twg[(t * m) & (P - 1)];
+
+    const T *x = static_cast<const T *>(p.x);
+    T *y = static_cast<T *>(p.y);
+    const T *w = static_cast<const T *>(p.w);
+    const C *spec = static_cast<const C *>(p.spec);
+    const int R = p.R;
+    const C zero{T(0), T(0)};
+
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(reinterpret_cast<unsigned long long *>(p.ctrl), 1ull);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= p.total_items) break;
+        // colour-major decode: item -> (colour, pair, tile)
+        int c = 0;
+        while (int64_t(p.color_start[c + 1]) * p.npairs <= item) ++c;
+        const int64_t base = int64_t(p.color_start[c]) * p.npairs;
+        const int ntc = p.color_start[c + 1] - p.color_start[c];
+        const int pair = int((item - base) / ntc);
+        const int ti = p.color_start[c] + int((item - base) % ntc);
+        const Tile tile = p.tiles[ti];
+        const int n1 = tile.in_ext[0], n2 = tile.in_ext[1];
+        const int i0 = tile.in_lo[0], j0 = tile.in_lo[1];
+        const int L1 = n1 + 2 * R, L2 = n2 + 2 * R;
+        const int b0 = 2 * pair;
+        const bool has1 = b0 + 1 < p.nrhs;
+        const T *x0 = x + int64_t(b0) * p.ldx;
+        const T *x1 = has1 ? x0 + p.ldx : x0;
+        const T *wt = w + tile.w_base;
+
+        // ---------------- phase A: gather w . x, row FFTs
+        for (int i = line; i < n1; i += LINES) {
+            C a[R1];
+            const int64_t xr = int64_t(i0 + i) * p.n[1] + j0;
+            const T *wr = wt + int64_t(i) * tile.w_ld[0];
+#pragma unroll
+            for (int j = 0; j < R1; ++j) {
+                const int col = t + R2 * j;
+                if (col < n2) {
+                    const T wv = wr[col];
+                    const T v0 = __ldg(x0 + xr + col);
+                    const T v1 = has1 ? __ldg(x1 + xr + col) : T(0);
+                    a[j] = C{wv * v0, wv * v1};
+                } else {
+                    a[j] = zero;
+                }
+            }
+            RowScratch<P, C> scr{S, i};
+            fft_line<P, false>(a, tw, t, scr, lmask);
+#pragma unroll
+            for (int j = 0; j < R1; ++j) S[i * P + ((t + R2 * j) ^ swz(i))] = a[j];
+        }
+        __syncthreads();
+
+        // ---------------- phase B: column FFT, spectral product, inverse column FFT
+        const C *sp = spec + int64_t(tile.patch) * p.spec_stride;
+        for (int col = line; col < P; col += LINES) {
+            C a[R1];
+#pragma unroll
+            for (int j = 0; j < R1; ++j) {
+                const int row = t + R2 * j;
+                a[j] = row < n1 ? S[row * P + (col ^ swz(row))] : zero;
+            }
+            ColScratch<P, C> scr{S, col};
+            fft_line<P, false>(a, tw, t, scr, lmask);
+            // Hermitian half spectrum stored as [k2 <= P/2][k1]
+            if (col <= P / 2) {
+                const C *sc = sp + int64_t(col) * P;
+#pragma unroll
+                for (int j = 0; j < R1; ++j) a[j] = cmul(a[j], sc[t + R2 * j]);
+            } else {
+                const C *sc = sp + int64_t(P - col) * P;
+#pragma unroll
+                for (int j = 0; j < R1; ++j) a[j] = cmulc(a[j], sc[(P - (t + R2 * j)) & (P - 1)]);
+            }
+            fft_line<P, true>(a, tw, t, scr, lmask);
+#pragma unroll
+            for (int j = 0; j < R1; ++j) {
+                const int row = t + R2 * j;
+                if (row < L1) S[row * P + (col ^ swz(row))] = a[j];
+            }
+        }
+        __syncthreads();
+
+        // ---------------- ordered overlap-add: wait for lower colours
+        if (threadIdx.x == 0) {
+            for (int d = p.dep_start[ti]; d < p.dep_start[ti + 1]; ++d) {
+                const uint32_t *f = p.done + int64_t(p.dep[d]) * p.done_ld + pair;
+                long long spins = 0;
+                while (ld_acquire_u32(f) != p.epoch) {
+                    if (++spins > kSpinLimit) {
+                        atomicExch(p.ctrl + 2, 1);   // timeout flag; result of this apply is invalid
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+        __syncthreads();
+
+        // ---------------- phase C: inverse row FFTs and overlap-add
+        T *y0 = y + int64_t(b0) * p.ldy;
+        T *y1 = has1 ? y0 + p.ldy : y0;
+        for (int n = line; n < L1; n += LINES) {
+            const int oy = i0 - R + n;
+            if (oy < 0 || oy >= p.n[0]) continue;
+            C a[R1];
+#pragma unroll
+            for (int j = 0; j < R1; ++j) a[j] = S[n * P + ((t + R2 * j) ^ swz(n))];
+            RowScratch<P, C> scr{S, n};
+            fft_line<P, true>(a, tw, t, scr, lmask);
+            const int64_t yr = int64_t(oy) * p.n[1];
+#pragma unroll
+            for (int j = 0; j < R1; ++j) {
+                const int m = t + R2 * j;
+                const int ox = j0 - R + m;
+                if (m < L2 && ox >= 0 && ox < p.n[1]) {
+                    T *q0 = y0 + yr + ox;
+                    __stcg(q0, __ldcg(q0) + a[j].x);
+                    if (has1) {
+                        T *q1 = y1 + yr + ox;
+                        __stcg(q1, __ldcg(q1) + a[j].y);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release_u32(p.done + int64_t(ti) * p.done_ld + pair, p.epoch);
+        }
+    }
+}
+
+template <typename T>
+__global__ void zero_kernel(T *y, int64_t ldy, int32_t nrhs, int64_t N, unsigned long long *counter) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0ull;
+    const int64_t total = int64_t(nrhs) * N;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t b = i / N, e = i - b * N;
+        y[b * ldy + e] = T(0);
+    }
+}
+
+cudaError_t launch_zero(const ApplyParams &p, int64_t N, pc_precision prec, cudaStream_t s) {
+    const int64_t total = int64_t(p.nrhs) * N;
+    int blocks = int(std::min<int64_t>((total + 255) / 256, 4096));
+    if (blocks < 1) blocks = 1;
+    auto *ctr = reinterpret_cast<unsigned long long *>(p.ctrl);
+    if (prec == PC_FP64)
+        zero_kernel<double><<<blocks, 256, 0, s>>>(static_cast<double *>(p.y), p.ldy, p.nrhs, N, ctr);
+    else
+        zero_kernel<float><<<blocks, 256, 0, s>>>(static_cast<float *>(p.y), p.ldy, p.nrhs, N, ctr);
+    return cudaGetLastError();
+}
+
+template <typename T, int P>
+static cudaError_t configure_one(int *ctas_per_sm, size_t *smem) {
+    using C = typename Cx<T>::type;
+    const size_t bytes = size_t(P) * P * sizeof(C);
+    cudaError_t e = cudaFuncSetAttribute(fft2d_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fft2d_kernel<T, P>, kThreads2d, bytes);
+    if (e != cudaSuccess) return e;
+    if (ctas_per_sm) *ctas_per_sm = n;
+    if (smem) *smem = bytes;
+    return cudaSuccess;
+}
+
+cudaError_t fft2d_configure(int P, pc_precision prec, int *ctas_per_sm, size_t *smem) {
+    if (prec == PC_FP64) {
+        if (P == 64) return configure_one<double, 64>(ctas_per_sm, smem);
+        return cudaErrorInvalidValue;
+    }
+    if (P == 64) return configure_one<float, 64>(ctas_per_sm, smem);
+    if (P == 128) return configure_one<float, 128>(ctas_per_sm, smem);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fft2d(const ApplyParams &p, int P, pc_precision prec, int ctas, cudaStream_t s) {
+    size_t smem = 0;
+    cudaError_t e = fft2d_configure(P, prec, nullptr, &smem);
+    if (e != cudaSuccess) return e;
+    if (prec == PC_FP64)
+        fft2d_kernel<double, 64><<<ctas, kThreads2d, smem, s>>>(p);
+    else if (P == 64)
+        fft2d_kernel<float, 64><<<ctas, kThreads2d, smem, s>>>(p);
+    else
+        fft2d_kernel<float, 128><<<ctas, kThreads2d, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace pc

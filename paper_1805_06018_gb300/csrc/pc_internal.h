@@ -1,0 +1,158 @@
+// Internal types of libpc: host-side geometry of the product-convolution
+// operator and the device-side descriptors its kernels consume.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <array>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "pc.h"
+
+namespace pc {
+
+// ---------------------------------------------------------------------------
+// Host geometry (Section 2.2 of the paper): box, leaves, sample points,
+// cells(p_k), nbrs(k), bbox(U_k).  Coordinates use 3 slots; for 2D operators
+// slot 2 is unused (extent 1, coordinate 0).
+// ---------------------------------------------------------------------------
+using I3 = std::array<int64_t, 3>;
+
+struct Geometry {
+    int d = 0;
+    I3 shape{1, 1, 1};
+    std::vector<I3> cell_lo, cell_hi;
+    std::vector<I3> pts;                       // sample points, lexicographic
+    std::vector<std::vector<int32_t>> points_of;  // per leaf: sample points in it (closed)
+    std::vector<std::vector<int32_t>> cells_of;   // per point: leaves containing it
+    std::vector<std::vector<int32_t>> nbrs;       // per point, ascending, includes itself
+    std::vector<I3> bb_lo, bb_hi;              // bbox(U_k)
+    int64_t bbox_elems(int k) const {
+        int64_t n = 1;
+        for (int a = 0; a < d; ++a) n *= bb_hi[k][a] - bb_lo[k][a] + 1;
+        return n;
+    }
+};
+
+// Validate the grid and build the geometry.  Returns PC_OK or PC_ERR_GRID /
+// PC_ERR_ARG with a message in err.
+pc_status build_geometry(const pc_box *box, const pc_grid *grid, Geometry &g, std::string &err);
+
+// Harmonic weights (Section 2.4) on bbox(U_k), FP64, concatenated for k =
+// 0..r-1; off[k] is the element offset of w_k.
+pc_status build_weights(const Geometry &g, std::vector<double> &w, std::vector<int64_t> &off,
+                        std::string &err);
+
+// Extended impulse responses (Section 2.5) on the window [-R, R]^d, FP64,
+// [r][(2R+1)^d].
+void build_extension(const Geometry &g, int R, const double *phi, std::vector<double> &phiE);
+
+// ---------------------------------------------------------------------------
+// Device descriptors
+// ---------------------------------------------------------------------------
+struct Tile {
+    int32_t patch;       // k
+    int32_t in_lo[3];    // input tile origin in Omega
+    int32_t in_ext[3];   // input tile extents (<= T)
+    int32_t w_ld[2];     // strides of the patch weight window: 2D {ext1, 1}; 3D {ext1*ext2, ext2}
+    int64_t w_base;      // element offset of the weight at in_lo
+};
+
+struct Schedule {
+    std::vector<Tile> tiles;                 // ordered by colour
+    std::vector<int32_t> color_start;        // [n_colors + 1] into tiles
+    std::vector<int32_t> dep_start;          // [n_tiles + 1]
+    std::vector<int32_t> dep;                // tiles (indices into `tiles`) that must add first
+};
+
+// Split each bbox(U_k) into input tiles of extent <= T, colour the tiles so
+// that tiles of one colour have disjoint output boxes (tile (+) [-R, R]^d,
+// clipped to Omega), and list for every tile the overlapping tiles of lower
+// colour.  Output pixels then receive their contributions in colour order.
+void build_schedule(const Geometry &g, int R, int T, const std::vector<int64_t> &w_off, Schedule &s);
+
+// Kernel parameter block shared by the 2D and 3D fused kernels.
+struct ApplyParams {
+    const void *x;
+    void *y;
+    int64_t ldx, ldy;
+    int32_t nrhs, npairs;
+    int32_t n[3];               // box extents (2D: n[2] = 1)
+    int32_t R;
+    const Tile *tiles;
+    const int32_t *color_start;
+    int32_t n_colors;
+    const int32_t *dep_start;
+    const int32_t *dep;
+    uint32_t *done;             // [n_tiles][done_ld]
+    int32_t done_ld;
+    uint32_t epoch;
+    int32_t *ctrl;              // [0..1] 64-bit work counter, [2] timeout flag
+    const void *spec;           // spectra, per patch spec_stride complex values
+    int64_t spec_stride;
+    const void *w;              // weights (compute precision)
+    const void *tw;             // W_P^k, k < P, compute precision complex
+    int64_t total_items;
+};
+
+}  // namespace pc
+
+struct pc_context {
+    int device = 0;
+    int num_sms = 0;
+    int cc_major = 0, cc_minor = 0;
+    size_t smem_optin = 0;
+    std::string last_error;
+};
+
+struct pc_operator {
+    pc_context *ctx = nullptr;
+    int d = 0;
+    pc::I3 shape{1, 1, 1};
+    int64_t N = 0;
+    int R = 0, P = 0, T = 0, r = 0;
+    pc_precision prec = PC_FP32;
+    int n_tiles = 0, n_colors = 0;
+    size_t elem = 4;             // bytes of one real value
+    // device memory
+    void *d_spec = nullptr;
+    size_t spec_bytes = 0;
+    int64_t spec_stride = 0;
+    void *d_w = nullptr;
+    size_t w_bytes = 0;
+    pc::Tile *d_tiles = nullptr;
+    int32_t *d_color_start = nullptr;
+    int32_t *d_dep_start = nullptr;
+    int32_t *d_dep = nullptr;
+    uint32_t *d_done = nullptr;
+    int32_t done_cap = 0;
+    int32_t *d_ctrl = nullptr;
+    void *d_tw = nullptr;
+    uint32_t epoch = 0;
+    cudaStream_t last_stream = nullptr;
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr;   // around the fused kernel of the last apply
+    bool timed = false;
+    int ctas = 0;
+    int64_t launches_last = 0;
+    size_t device_bytes = 0;
+    double build_seconds = 0;
+    // host copies used by the plain path
+    std::vector<int32_t> color_start_h;
+    std::vector<pc::Tile> tiles_h;
+    // plain-path scratch (lazily allocated)
+    void *plain = nullptr;
+};
+
+namespace pc {
+// kernels (pc_fft2d.cu, pc_spectra.cu, pc_plain.cu)
+cudaError_t launch_zero(const ApplyParams &p, int64_t N, pc_precision prec, cudaStream_t s);
+cudaError_t launch_fft2d(const ApplyParams &p, int P, pc_precision prec, int ctas, cudaStream_t s);
+cudaError_t fft2d_configure(int P, pc_precision prec, int *ctas_per_sm, size_t *smem);
+cudaError_t build_spectra_2d(const double *d_psi, int r, int R, int P, pc_precision prec, void *d_spec,
+                             const double2 *d_tw64, cudaStream_t s);
+pc_status plain_apply(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
+                      cudaStream_t s, std::string &err);
+void plain_free(pc_operator *op);
+}  // namespace pc

@@ -1,0 +1,179 @@
+// Plain single-vector path: the reference point the fused kernels are
+// measured against.  For each right-hand side separately:
+//   1. gather   u_t = w_k . x on every tile t, zero-padded to P x P (HBM buffer)
+//   2. cuFFT    batched R2C of all tiles
+//   3. product  U_t . phi^_k (half spectrum)
+//   4. cuFFT    batched C2R
+//   5. add      output-stationary overlap-add: every pixel sums the tiles that
+//               cover it in ascending tile order (deterministic, no atomics)
+// cuFFT is used here as a black-box library FFT.
+#include <cufft.h>
+
+#include "pc_internal.h"
+
+namespace pc {
+
+struct PlainState {
+    cufftHandle fwd = 0, inv = 0;
+    bool have_plans = false;
+    float *real = nullptr;       // [n_tiles][P][P]
+    float2 *freq = nullptr;      // [n_tiles][P][P/2+1]
+    int32_t *blk_start = nullptr;  // CSR over 32x32 output blocks
+    int32_t *blk_tiles = nullptr;
+    int nb0 = 0, nb1 = 0;
+};
+
+__global__ void plain_gather(const float *x, const Tile *tiles, const float *w, int n1box, int P, float *real) {
+    const Tile t = tiles[blockIdx.x];
+    float *u = real + int64_t(blockIdx.x) * P * P;
+    for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+        const int a = i / P, b = i % P;
+        float v = 0.0f;
+        if (a < t.in_ext[0] && b < t.in_ext[1])
+            v = w[t.w_base + int64_t(a) * t.w_ld[0] + b] * x[int64_t(t.in_lo[0] + a) * n1box + t.in_lo[1] + b];
+        u[i] = v;
+    }
+}
+
+__global__ void plain_product(float2 *freq, const Tile *tiles, const float2 *spec, int64_t spec_stride, int P) {
+    const int H = P / 2 + 1;
+    const Tile t = tiles[blockIdx.x];
+    float2 *f = freq + int64_t(blockIdx.x) * P * H;
+    const float2 *sp = spec + int64_t(t.patch) * spec_stride;
+    for (int i = threadIdx.x; i < P * H; i += blockDim.x) {
+        const int k1 = i / H, k2 = i % H;
+        const float2 a = f[i], s = sp[int64_t(k2) * P + k1];
+        f[i] = make_float2(a.x * s.x - a.y * s.y, a.x * s.y + a.y * s.x);
+    }
+}
+
+__global__ void plain_add(float *y, const float *real, const Tile *tiles, const int32_t *blk_start,
+                          const int32_t *blk_tiles, int nb1, int n0, int n1, int R, int P) {
+    const int i = blockIdx.y * 32 + threadIdx.y;
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    if (i >= n0 || j >= n1) return;
+    const int blk = blockIdx.y * nb1 + blockIdx.x;
+    float acc = 0.0f;
+    for (int q = blk_start[blk]; q < blk_start[blk + 1]; ++q) {
+        const int ti = blk_tiles[q];
+        const Tile t = tiles[ti];
+        const int o0 = i - (t.in_lo[0] - R), o1 = j - (t.in_lo[1] - R);
+        if (o0 >= 0 && o0 < t.in_ext[0] + 2 * R && o1 >= 0 && o1 < t.in_ext[1] + 2 * R)
+            acc += real[(int64_t(ti) * P + o0) * P + o1];
+    }
+    y[int64_t(i) * n1 + j] = acc;
+}
+
+static void destroy_state(PlainState *st) {
+    if (!st) return;
+    if (st->have_plans) {
+        cufftDestroy(st->fwd);
+        cufftDestroy(st->inv);
+    }
+    cudaFree(st->real);
+    cudaFree(st->freq);
+    cudaFree(st->blk_start);
+    cudaFree(st->blk_tiles);
+    delete st;
+}
+
+void plain_free(pc_operator *op) {
+    destroy_state(static_cast<PlainState *>(op->plain));
+    op->plain = nullptr;
+}
+
+static pc_status plain_init(pc_operator *op, std::string &err) {
+    auto *st = new PlainState;
+    const int P = op->P, H = P / 2 + 1, nt = op->n_tiles;
+    int dims[2] = {P, P};
+    cudaError_t e = cudaMalloc(&st->real, sizeof(float) * size_t(nt) * P * P);
+    if (e == cudaSuccess) e = cudaMalloc(&st->freq, sizeof(float2) * size_t(nt) * P * H);
+    if (e != cudaSuccess) {
+        destroy_state(st);
+        err = std::string("plain path scratch: ") + cudaGetErrorString(e);
+        return PC_ERR_NOMEM;
+    }
+    if (cufftPlanMany(&st->fwd, 2, dims, nullptr, 1, P * P, nullptr, 1, P * H, CUFFT_R2C, nt) != CUFFT_SUCCESS ||
+        cufftPlanMany(&st->inv, 2, dims, nullptr, 1, P * H, nullptr, 1, P * P, CUFFT_C2R, nt) != CUFFT_SUCCESS) {
+        destroy_state(st);
+        err = "cuFFT plan creation failed";
+        return PC_ERR_CUDA;
+    }
+    st->have_plans = true;
+    // tiles covering each 32x32 output block
+    const int n0 = int(op->shape[0]), n1 = int(op->shape[1]), R = op->R;
+    st->nb0 = (n0 + 31) / 32;
+    st->nb1 = (n1 + 31) / 32;
+    std::vector<std::vector<int32_t>> lists(size_t(st->nb0) * st->nb1);
+    for (int ti = 0; ti < nt; ++ti) {
+        const Tile &t = op->tiles_h[ti];
+        const int a0 = std::max(0, t.in_lo[0] - R), a1 = std::min(n0 - 1, t.in_lo[0] + t.in_ext[0] - 1 + R);
+        const int b0 = std::max(0, t.in_lo[1] - R), b1 = std::min(n1 - 1, t.in_lo[1] + t.in_ext[1] - 1 + R);
+        for (int bi = a0 / 32; bi <= a1 / 32; ++bi)
+            for (int bj = b0 / 32; bj <= b1 / 32; ++bj) lists[size_t(bi) * st->nb1 + bj].push_back(ti);
+    }
+    std::vector<int32_t> start(1, 0), flat;
+    for (auto &l : lists) {
+        flat.insert(flat.end(), l.begin(), l.end());
+        start.push_back(int32_t(flat.size()));
+    }
+    if (flat.empty()) flat.push_back(0);
+    e = cudaMalloc(&st->blk_start, sizeof(int32_t) * start.size());
+    if (e == cudaSuccess) e = cudaMalloc(&st->blk_tiles, sizeof(int32_t) * flat.size());
+    if (e == cudaSuccess) e = cudaMemcpy(st->blk_start, start.data(), sizeof(int32_t) * start.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(st->blk_tiles, flat.data(), sizeof(int32_t) * flat.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        destroy_state(st);
+        err = std::string("plain path tables: ") + cudaGetErrorString(e);
+        return PC_ERR_CUDA;
+    }
+    op->plain = st;
+    return PC_OK;
+}
+
+pc_status plain_apply(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
+                      cudaStream_t s, std::string &err) {
+    if (op->d != 2) {
+        err = "the plain path is 2D only";
+        return PC_ERR_UNSUPPORTED;
+    }
+    if (!op->plain) {
+        pc_status st = plain_init(op, err);
+        if (st != PC_OK) return st;
+    }
+    auto *st = static_cast<PlainState *>(op->plain);
+    if (cufftSetStream(st->fwd, s) != CUFFT_SUCCESS || cufftSetStream(st->inv, s) != CUFFT_SUCCESS) {
+        err = "cufftSetStream failed";
+        return PC_ERR_CUDA;
+    }
+    const int P = op->P, nt = op->n_tiles;
+    const int n0 = int(op->shape[0]), n1 = int(op->shape[1]);
+    int64_t launches = 0;
+    for (int b = 0; b < nrhs; ++b) {
+        const float *xb = static_cast<const float *>(x) + int64_t(b) * ldx;
+        float *yb = static_cast<float *>(y) + int64_t(b) * ldy;
+        plain_gather<<<nt, 256, 0, s>>>(xb, op->d_tiles, static_cast<const float *>(op->d_w), n1, P, st->real);
+        if (cufftExecR2C(st->fwd, st->real, reinterpret_cast<cufftComplex *>(st->freq)) != CUFFT_SUCCESS) {
+            err = "cufftExecR2C failed";
+            return PC_ERR_CUDA;
+        }
+        plain_product<<<nt, 256, 0, s>>>(st->freq, op->d_tiles, static_cast<const float2 *>(op->d_spec),
+                                         op->spec_stride, P);
+        if (cufftExecC2R(st->inv, reinterpret_cast<cufftComplex *>(st->freq), st->real) != CUFFT_SUCCESS) {
+            err = "cufftExecC2R failed";
+            return PC_ERR_CUDA;
+        }
+        plain_add<<<dim3(st->nb1, st->nb0), dim3(32, 32), 0, s>>>(yb, st->real, op->d_tiles, st->blk_start,
+                                                                st->blk_tiles, st->nb1, n0, n1, op->R, P);
+        launches += 3;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        err = std::string("plain path launch: ") + cudaGetErrorString(e);
+        return PC_ERR_CUDA;
+    }
+    op->launches_last = launches;
+    return PC_OK;
+}
+
+}  // namespace pc
