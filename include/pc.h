@@ -85,7 +85,7 @@ typedef struct {
 /* Launch-shape knobs; a NULL pc_tuning, or a field of 0, means "choose". */
 typedef struct {
     int32_t fft_size;        /* padded FFT extent P per axis: 64, 128 (2D) */
-    int32_t tile;            /* input tile extent T <= P - 2R (0: P - 2R) */
+    int32_t tile;            /* input tile extent T <= min(P - 2R, 2P/3) (0: that bound) */
     int32_t ctas_per_sm;     /* persistent CTAs per SM (0: occupancy limit) */
     int32_t reserved[5];
 } pc_tuning;

@@ -206,9 +206,13 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     if (prec == PC_FP64 && P != 64) return fail(ctx, PC_ERR_UNSUPPORTED, "FP64 operators use fft_size 64");
     if (prec == PC_FP32 && P != 64 && P != 128) return fail(ctx, PC_ERR_UNSUPPORTED, "FP32 2D fft_size must be 64 or 128");
     if (2 * radius + 1 > P - 1) return fail(ctx, PC_ERR_UNSUPPORTED, "radius too large for the FFT size");
-    int T = P - 2 * radius;
+    // input tiles: n + 2R <= P keeps the circular convolution linear; the kernel
+    // stages the weight and two right-hand-side rows of a tile in one workspace
+    // row of 2P reals, so also 3n <= 2P
+    int T = std::min(P - 2 * radius, (2 * P) / 3);
     if (tune && tune->tile) {
-        if (tune->tile < 1 || tune->tile > T) return fail(ctx, PC_ERR_ARG, "tile must be in [1, fft_size - 2R]");
+        if (tune->tile < 1 || tune->tile > T)
+            return fail(ctx, PC_ERR_ARG, "tile must be in [1, min(fft_size - 2R, 2 fft_size / 3)]");
         T = tune->tile;
     }
     DeviceGuard dg(ctx->device);

@@ -24,20 +24,13 @@
 // earlier by running CTAs: the wait always ends.
 #include "pc_fftcore.cuh"
 #include "pc_internal.h"
+#include "pc_ptx.cuh"
 
 namespace pc {
 
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 constexpr int kThreads2d = 512;
 constexpr long long kSpinLimit = 1ll << 24;   // x >= 64 ns per spin: about a second at least
+constexpr long long kMbarLimit = 1ll << 24;   // try_wait rounds for the spectrum copy
 
 template <int P, typename C> struct RowScratch {
     C *S;
@@ -52,13 +45,28 @@ template <int P, typename C> struct ColScratch {
     __device__ __forceinline__ void st(int s, C v) const { S[s * P + (col ^ swz(s))] = v; }
 };
 
+// Shared memory: the P x P complex workspace, then the patch's half spectrum
+// ([P/2+1] columns of P values, rows padded to P + 8 values), then an mbarrier.
+template <typename T, int P> struct Smem2d {
+    using C = typename Cx<T>::type;
+    static constexpr int SPLD = P + 8;
+    static constexpr size_t ws = size_t(P) * P * sizeof(C);
+    static constexpr size_t sp = size_t(P / 2 + 1) * SPLD * sizeof(C);
+    static constexpr size_t bytes = ws + sp + 16;
+};
+
 template <typename T, int P>
 __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams p) {
     using C = typename Cx<T>::type;
+    using L = Smem2d<T, P>;
     constexpr int R1 = FftShape<P>::R1, R2 = FftShape<P>::R2;
     constexpr int LINES = kThreads2d / R2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int H = P / 2 + 1;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     C *S = reinterpret_cast<C *>(smem_raw);
+    T *Sf = reinterpret_cast<T *>(smem_raw);
+    C *SP = reinterpret_cast<C *>(smem_raw + L::ws);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw + L::ws + L::sp);
     __shared__ int64_t s_item;
 
     const int t = threadIdx.x % R2;
@@ -75,6 +83,12 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
     const C *spec = static_cast<const C *>(p.spec);
     const int R = p.R;
     const C zero{T(0), T(0)};
+    uint32_t phase = 0;
+
+    if (threadIdx.x == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+    }
 
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(reinterpret_cast<unsigned long long *>(p.ctrl), 1ull);
@@ -98,19 +112,42 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
         const T *x1 = has1 ? x0 + p.ldx : x0;
         const T *wt = w + tile.w_base;
 
-        // ---------------- phase A: gather w . x, row FFTs
+        // ---------------- the patch spectrum streams into shared memory (TMA bulk
+        // copies, one per stored column) while phase A runs
+        if (threadIdx.x == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(mbar, uint32_t(H * P * sizeof(C)));
+            const C *sp = spec + int64_t(tile.patch) * p.spec_stride;
+            for (int col = 0; col < H; ++col)
+                bulk_g2s(SP + col * L::SPLD, sp + int64_t(col) * P, uint32_t(P * sizeof(C)), mbar);
+        }
+
+        // ---------------- phase A: stage w, x0, x1 rows (cp.async), weight, row FFTs
         for (int i = line; i < n1; i += LINES) {
-            C a[R1];
+            T *row = Sf + i * 2 * P;
             const int64_t xr = int64_t(i0 + i) * p.n[1] + j0;
             const T *wr = wt + int64_t(i) * tile.w_ld[0];
 #pragma unroll
             for (int j = 0; j < R1; ++j) {
                 const int col = t + R2 * j;
                 if (col < n2) {
-                    const T wv = wr[col];
-                    const T v0 = __ldg(x0 + xr + col);
-                    const T v1 = has1 ? __ldg(x1 + xr + col) : T(0);
-                    a[j] = C{wv * v0, wv * v1};
+                    cp_async<sizeof(T)>(row + col, wr + col);
+                    cp_async<sizeof(T)>(row + n2 + col, x0 + xr + col);
+                    if (has1) cp_async<sizeof(T)>(row + 2 * n2 + col, x1 + xr + col);
+                }
+            }
+        }
+        cp_async_wait_all();
+        __syncwarp(lmask);
+        for (int i = line; i < n1; i += LINES) {
+            const T *row = Sf + i * 2 * P;
+            C a[R1];
+#pragma unroll
+            for (int j = 0; j < R1; ++j) {
+                const int col = t + R2 * j;
+                if (col < n2) {
+                    const T wv = row[col];
+                    a[j] = C{wv * row[n2 + col], has1 ? wv * row[2 * n2 + col] : T(0)};
                 } else {
                     a[j] = zero;
                 }
@@ -123,7 +160,11 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
         __syncthreads();
 
         // ---------------- phase B: column FFT, spectral product, inverse column FFT
-        const C *sp = spec + int64_t(tile.patch) * p.spec_stride;
+        if (!mbar_wait_bounded(mbar, phase, kMbarLimit)) {
+            atomicExch(p.ctrl + 2, 2);   // copy did not land; wait once more, then carry on
+            mbar_wait_bounded(mbar, phase, kMbarLimit);
+        }
+        phase ^= 1u;
         for (int col = line; col < P; col += LINES) {
             C a[R1];
 #pragma unroll
@@ -135,11 +176,11 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
             fft_line<P, false>(a, tw, t, scr, lmask);
             // Hermitian half spectrum stored as [k2 <= P/2][k1]
             if (col <= P / 2) {
-                const C *sc = sp + int64_t(col) * P;
+                const C *sc = SP + col * L::SPLD;
 #pragma unroll
                 for (int j = 0; j < R1; ++j) a[j] = cmul(a[j], sc[t + R2 * j]);
             } else {
-                const C *sc = sp + int64_t(P - col) * P;
+                const C *sc = SP + (P - col) * L::SPLD;
 #pragma unroll
                 for (int j = 0; j < R1; ++j) a[j] = cmulc(a[j], sc[(P - (t + R2 * j)) & (P - 1)]);
             }
@@ -169,7 +210,9 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
         }
         __syncthreads();
 
-        // ---------------- phase C: inverse row FFTs and overlap-add
+        // ---------------- phase C: inverse row FFTs and overlap-add (fire-and-forget
+        // reductions: no two tiles that overlap add at the same time, so each pixel
+        // still sums in colour order)
         T *y0 = y + int64_t(b0) * p.ldy;
         T *y1 = has1 ? y0 + p.ldy : y0;
         for (int n = line; n < L1; n += LINES) {
@@ -186,12 +229,8 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
                 const int m = t + R2 * j;
                 const int ox = j0 - R + m;
                 if (m < L2 && ox >= 0 && ox < p.n[1]) {
-                    T *q0 = y0 + yr + ox;
-                    __stcg(q0, __ldcg(q0) + a[j].x);
-                    if (has1) {
-                        T *q1 = y1 + yr + ox;
-                        __stcg(q1, __ldcg(q1) + a[j].y);
-                    }
+                    atomicAdd(y0 + yr + ox, a[j].x);
+                    if (has1) atomicAdd(y1 + yr + ox, a[j].y);
                 }
             }
         }
@@ -227,8 +266,7 @@ cudaError_t launch_zero(const ApplyParams &p, int64_t N, pc_precision prec, cuda
 
 template <typename T, int P>
 static cudaError_t configure_one(int *ctas_per_sm, size_t *smem) {
-    using C = typename Cx<T>::type;
-    const size_t bytes = size_t(P) * P * sizeof(C);
+    const size_t bytes = Smem2d<T, P>::bytes;
     cudaError_t e = cudaFuncSetAttribute(fft2d_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
     if (e != cudaSuccess) return e;
     int n = 0;
