@@ -195,6 +195,37 @@ pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t
 pc_status pc_apply_plain(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx,
                          void *y, int64_t ldy, pc_stream stream);
 
+/* Allocation-free variant of pc_apply_batched.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * while they apply the operator - for example a service that reserves all
+ * of its GPU memory up front so that nothing on its request path can fail on
+ * an out-of-memory error or wait for the device-wide synchronisation that a
+ * cudaMalloc or cudaFree may imply, or code that runs where another allocator
+ * owns the free device memory.  pc_apply_batched may allocate (it grows the
+ * operator's ordering-flag buffer the first time a larger batch arrives);
+ * this variant never calls cudaMalloc, cudaFree or any other allocating
+ * routine.  Its scratch - one ordering flag per (tile, pair of right-hand
+ * sides) plus a 64-byte control block - lives in a statically sized device
+ * array of 1 MiB inside libpc that every GPU which loads the library holds
+ * until the process exits.
+ *   - Same arguments, layout and result as pc_apply_batched (y overwritten).
+ *     The operator (spectra, weights, tiles) was allocated by
+ *     pc_build_spectra; the caller owns x and y.
+ *   - Limit: num_tiles * ceil(nrhs/2) <= 262128 (pc_operator_info gives
+ *     num_tiles); larger batches fail with PC_ERR_ARG and a message, before
+ *     anything is launched.  Split such batches.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress with that device current) and caches it; make that
+ *     first call before any stream capture.
+ *   - Every call, on every operator, shares the one array; the call clears the
+ *     part it uses before its kernel reads it.  Calls whose work overlaps on
+ *     the GPU (different streams, or another thread) race on the array and
+ *     give wrong results: serialise them, e.g. on one stream.
+ *   - Device-side wait timeouts are not reported by this path (use
+ *     pc_apply_batched with pc_operator_check for that). */
+pc_status pc_apply_batched_noalloc(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx,
+                                   void *y, int64_t ldy, pc_stream stream);
+
 /* Synchronise the operator's last stream and report device-side status:
  * PC_ERR_TIMEOUT if a bounded wait inside a kernel gave up since the last
  * call (the flag is then cleared), PC_ERR_CUDA on an asynchronous CUDA error. */

@@ -74,6 +74,8 @@ _PROTOS = {
     "pc_operator_info_get": (ctypes.c_int, [_VP, ctypes.POINTER(pc_operator_info)]),
     "pc_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "pc_apply_batched": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
+    "pc_apply_batched_noalloc": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64,
+                                                 _VP]),
     "pc_apply_plain": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
     "pc_operator_check": (ctypes.c_int, [_VP]),
     "pc_operator_kernel_time": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
@@ -227,6 +229,10 @@ class Operator:
     def pc_apply_batched(self, nrhs: int, x_ptr: int, ldx: int, y_ptr: int, ldy: int, stream_ptr: int):
         _check(lib().pc_apply_batched(self.handle, ctypes.c_int32(nrhs), _VP(x_ptr), ctypes.c_int64(ldx),
                                       _VP(y_ptr), ctypes.c_int64(ldy), _VP(stream_ptr)), self.ctx.handle)
+
+    def pc_apply_batched_noalloc(self, nrhs: int, x_ptr: int, ldx: int, y_ptr: int, ldy: int, stream_ptr: int):
+        _check(lib().pc_apply_batched_noalloc(self.handle, ctypes.c_int32(nrhs), _VP(x_ptr), ctypes.c_int64(ldx),
+                                              _VP(y_ptr), ctypes.c_int64(ldy), _VP(stream_ptr)), self.ctx.handle)
 
     def pc_apply_plain(self, nrhs: int, x_ptr: int, ldx: int, y_ptr: int, ldy: int, stream_ptr: int):
         _check(lib().pc_apply_plain(self.handle, ctypes.c_int32(nrhs), _VP(x_ptr), ctypes.c_int64(ldx),
