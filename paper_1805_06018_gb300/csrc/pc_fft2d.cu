@@ -50,10 +50,140 @@ template <int P, typename C> struct ColScratch {
 template <typename T, int P> struct Smem2d {
     using C = typename Cx<T>::type;
     static constexpr int SPLD = P + 8;
+    // phase C reuses the spectrum region as one FP32 staging row per line:
+    // re part [0, P+4), im part [P+8, 2P+12) floats
+    static constexpr int STAGE = 2 * (P + 8);
     static constexpr size_t ws = size_t(P) * P * sizeof(C);
-    static constexpr size_t sp = size_t(P / 2 + 1) * SPLD * sizeof(C);
+    static constexpr size_t spec = size_t(P / 2 + 1) * SPLD * sizeof(C);
+    static constexpr size_t stage = size_t(kThreads2d / FftShape<P>::R2) * STAGE * sizeof(float);
+    static constexpr size_t sp = spec > stage ? spec : stage;
     static constexpr size_t bytes = ws + sp + 16;
 };
+
+constexpr int kMaxColorsCached = 63;
+
+// colour-major order: item -> (tile index, right-hand-side pair).  `cs` holds
+// the colour offsets (shared-memory copy when there are few colours).
+__device__ __forceinline__ void decode_item(const ApplyParams &p, const int *cs, int64_t item, int &ti, int &pair) {
+    int c = 0;
+    while (int64_t(cs[c + 1]) * p.npairs <= item) ++c;
+    const int64_t base = int64_t(cs[c]) * p.npairs;
+    const int ntc = cs[c + 1] - cs[c];
+    pair = int((item - base) / ntc);
+    ti = cs[c] + int((item - base) % ntc);
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *ptr) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+}
+
+// Pull the rows that `item` will gather (weights and both right-hand sides)
+// into L2, one 128-byte line per thread-iteration.
+template <typename T>
+__device__ __forceinline__ void prefetch_item(const ApplyParams &p, const int *cs, int64_t item) {
+    if (item >= p.total_items) return;
+    int ti, pair;
+    decode_item(p, cs, item, ti, pair);
+    const Tile tile = p.tiles[ti];
+    const int n1 = tile.in_ext[0], n2 = tile.in_ext[1];
+    constexpr int per_line = 128 / int(sizeof(T));
+    const int lines_per_row = (n2 + per_line - 1) / per_line + 1;   // +1: rows need not start on a line
+    const int b0 = 2 * pair;
+    const int narr = b0 + 1 < p.nrhs ? 3 : 2;
+    const int total = narr * n1 * lines_per_row;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        const int arr = q / (n1 * lines_per_row);
+        const int rem = q - arr * n1 * lines_per_row;
+        const int i = rem / lines_per_row, l = rem % lines_per_row;
+        const int col = min(l * per_line, n2 - 1);
+        const T *base;
+        if (arr == 0)
+            base = static_cast<const T *>(p.w) + tile.w_base + int64_t(i) * tile.w_ld[0];
+        else
+            base = static_cast<const T *>(p.x) + int64_t(b0 + arr - 1) * p.ldx +
+                   int64_t(tile.in_lo[0] + i) * p.n[1] + tile.in_lo[1];
+        prefetch_l2(base + col);
+    }
+}
+
+__device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float c, float d) {
+    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c),
+                 "f"(d)
+                 : "memory");
+}
+
+// Overlap-add of one output row of a line: value m (< L2) goes to y[g0 + m]
+// when 0 <= g0 + m < width.
+//
+// FP32: the values are laid out in the line's staging row `st` (re part, then
+// im part, each shifted so that a 16-byte aligned y address meets a 16-byte
+// aligned staging address), then lane 0 of the line hands the aligned
+// interior of each part to the TMA unit as one bulk add-reduction; the at most
+// three ragged values at either end are added by single atomics.  The
+// reductions stay asynchronous until the end of phase C.  FP64 adds element
+// by element.
+template <typename T, int P, typename C>
+__device__ __forceinline__ void add_row(const C *a, int t, unsigned lmask, float *st, T *y0, T *y1, bool has1, int g0,
+                                        int L2, int width) {
+    constexpr int R1 = FftShape<P>::R1, R2 = FftShape<P>::R2;
+    const int lo = max(g0, 0), hi = min(g0 + L2, width);   // [lo, hi) in y coordinates
+    if constexpr (sizeof(T) == 8) {
+        (void)st;
+        (void)lmask;
+        (void)lo;
+        (void)hi;
+#pragma unroll
+        for (int j = 0; j < R1; ++j) {
+            const int m = t + R2 * j;
+            const int ox = g0 + m;
+            if (m < L2 && ox >= 0 && ox < width) {
+                atomicAdd(y0 + ox, a[j].x);
+                if (has1) atomicAdd(y1 + ox, a[j].y);
+            }
+        }
+    } else {
+        constexpr int IMOFF = P + 8;
+        // y row alignment (in elements, mod 4) and the aligned origin q <= lo of each part
+        const int off0 = int((reinterpret_cast<uintptr_t>(y0) >> 2) & 3);
+        const int off1 = int((reinterpret_cast<uintptr_t>(y1) >> 2) & 3);
+        const int q0 = ((lo + off0) & ~3) - off0, q1 = ((lo + off1) & ~3) - off1;
+        // the previous row's bulk reductions have finished reading `st`
+        if (t == 0) bulk_wait_read();
+        __syncwarp(lmask);
+#pragma unroll
+        for (int j = 0; j < R1; ++j) {
+            const int gx = g0 + t + R2 * j;
+            if (gx >= lo && gx < hi) {
+                st[gx - q0] = a[j].x;
+                st[IMOFF + gx - q1] = a[j].y;
+            }
+        }
+        fence_proxy_async_smem();   // these generic writes are read by the bulk (async-proxy) reductions
+        __syncwarp(lmask);
+        // aligned interior [a, b) of each part; ragged ends by atomics
+        const int a0 = lo == q0 ? q0 : q0 + 4, b0 = q0 + ((hi - q0) & ~3);
+        const int a1 = lo == q1 ? q1 : q1 + 4, b1 = q1 + ((hi - q1) & ~3);
+        if (t == 0) {
+            if (b0 > a0) bulk_reduce_add_f32(y0 + a0, st + (a0 - q0), uint32_t(b0 - a0) * 4u);
+            if (has1 && b1 > a1) bulk_reduce_add_f32(y1 + a1, st + IMOFF + (a1 - q1), uint32_t(b1 - a1) * 4u);
+            bulk_commit();
+        }
+        if (b0 > a0) {
+            for (int gx = lo + t; gx < a0; gx += R2) atomicAdd(y0 + gx, st[gx - q0]);
+            for (int gx = b0 + t; gx < hi; gx += R2) atomicAdd(y0 + gx, st[gx - q0]);
+        } else {
+            for (int gx = lo + t; gx < hi; gx += R2) atomicAdd(y0 + gx, st[gx - q0]);
+        }
+        if (has1) {
+            if (b1 > a1) {
+                for (int gx = lo + t; gx < a1; gx += R2) atomicAdd(y1 + gx, st[IMOFF + gx - q1]);
+                for (int gx = b1 + t; gx < hi; gx += R2) atomicAdd(y1 + gx, st[IMOFF + gx - q1]);
+            } else {
+                for (int gx = lo + t; gx < hi; gx += R2) atomicAdd(y1 + gx, st[IMOFF + gx - q1]);
+            }
+        }
+    }
+}
 
 template <typename T, int P>
 __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams p) {
@@ -67,7 +197,10 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
     T *Sf = reinterpret_cast<T *>(smem_raw);
     C *SP = reinterpret_cast<C *>(smem_raw + L::ws);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw + L::ws + L::sp);
-    __shared__ int64_t s_item;
+    __shared__ int64_t s_next;
+    __shared__ int s_cstart_buf[kMaxColorsCached + 1];
+    const int *s_cstart = p.n_colors <= kMaxColorsCached ? s_cstart_buf : p.color_start;
+    for (int c = threadIdx.x; c <= p.n_colors && c <= kMaxColorsCached; c += blockDim.x) s_cstart_buf[c] = p.color_start[c];
 
     const int t = threadIdx.x % R2;
     const int line = threadIdx.x / R2;
@@ -90,19 +223,22 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
         fence_mbar_init();
     }
 
+    // Items are taken one ahead: while item i runs, item i+1 is already
+    // claimed so its input rows can be pulled into L2.  Claims still happen in
+    // increasing order, and the lowest unfinished item is always one that a
+    // CTA is working on, so every dependency wait ends.
+    unsigned long long *counter = reinterpret_cast<unsigned long long *>(p.ctrl);
+    if (threadIdx.x == 0) s_next = int64_t(atomicAdd(counter, 1ull));
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(reinterpret_cast<unsigned long long *>(p.ctrl), 1ull);
         __syncthreads();
-        const int64_t item = s_item;
+        const int64_t item = s_next;
         if (item >= p.total_items) break;
-        // colour-major decode: item -> (colour, pair, tile)
-        int c = 0;
-        while (int64_t(p.color_start[c + 1]) * p.npairs <= item) ++c;
-        const int64_t base = int64_t(p.color_start[c]) * p.npairs;
-        const int ntc = p.color_start[c + 1] - p.color_start[c];
-        const int pair = int((item - base) / ntc);
-        const int ti = p.color_start[c] + int((item - base) % ntc);
+        int ti, pair;
+        decode_item(p, s_cstart, item, ti, pair);
         const Tile tile = p.tiles[ti];
+        if (threadIdx.x == 0) mbar_arrive_expect_tx(mbar, uint32_t(H * P * sizeof(C)));
+        __syncthreads();   // everyone has read s_next; the spectrum copy is announced
+        if (threadIdx.x == kThreads2d - 1) s_next = int64_t(atomicAdd(counter, 1ull));
         const int n1 = tile.in_ext[0], n2 = tile.in_ext[1];
         const int i0 = tile.in_lo[0], j0 = tile.in_lo[1];
         const int L1 = n1 + 2 * R, L2 = n2 + 2 * R;
@@ -114,12 +250,11 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
 
         // ---------------- the patch spectrum streams into shared memory (TMA bulk
         // copies, one per stored column) while phase A runs
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < H) {
+            const int col = threadIdx.x;
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(mbar, uint32_t(H * P * sizeof(C)));
-            const C *sp = spec + int64_t(tile.patch) * p.spec_stride;
-            for (int col = 0; col < H; ++col)
-                bulk_g2s(SP + col * L::SPLD, sp + int64_t(col) * P, uint32_t(P * sizeof(C)), mbar);
+            bulk_g2s(SP + col * L::SPLD, spec + int64_t(tile.patch) * p.spec_stride + int64_t(col) * P,
+                     uint32_t(P * sizeof(C)), mbar);
         }
 
         // ---------------- phase A: stage w, x0, x1 rows (cp.async), weight, row FFTs
@@ -159,6 +294,8 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
         }
         __syncthreads();
 
+        prefetch_item<T>(p, s_cstart, s_next);
+
         // ---------------- phase B: column FFT, spectral product, inverse column FFT
         if (!mbar_wait_bounded(mbar, phase, kMbarLimit)) {
             atomicExch(p.ctrl + 2, 2);   // copy did not land; wait once more, then carry on
@@ -194,9 +331,11 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
         __syncthreads();
 
         // ---------------- ordered overlap-add: wait for lower colours
-        if (threadIdx.x == 0) {
-            for (int d = p.dep_start[ti]; d < p.dep_start[ti + 1]; ++d) {
-                const uint32_t *f = p.done + int64_t(p.dep[d]) * p.done_ld + pair;
+        // one thread per dependency flag, all polled concurrently
+        {
+            const int d0 = p.dep_start[ti], nd = p.dep_start[ti + 1] - d0;
+            for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+                const uint32_t *f = p.done + int64_t(p.dep[d0 + d]) * p.done_ld + pair;
                 long long spins = 0;
                 while (ld_acquire_u32(f) != p.epoch) {
                     if (++spins > kSpinLimit) {
@@ -205,8 +344,8 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
                     }
                     __nanosleep(64);
                 }
+                __threadfence();
             }
-            __threadfence();
         }
         __syncthreads();
 
@@ -215,6 +354,7 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
         // still sums in colour order)
         T *y0 = y + int64_t(b0) * p.ldy;
         T *y1 = has1 ? y0 + p.ldy : y0;
+        if (sizeof(T) == 4 && t == 0) fence_proxy_async_global();
         for (int n = line; n < L1; n += LINES) {
             const int oy = i0 - R + n;
             if (oy < 0 || oy >= p.n[0]) continue;
@@ -223,15 +363,14 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
             for (int j = 0; j < R1; ++j) a[j] = S[n * P + ((t + R2 * j) ^ swz(n))];
             RowScratch<P, C> scr{S, n};
             fft_line<P, true>(a, tw, t, scr, lmask);
-            const int64_t yr = int64_t(oy) * p.n[1];
-#pragma unroll
-            for (int j = 0; j < R1; ++j) {
-                const int m = t + R2 * j;
-                const int ox = j0 - R + m;
-                if (m < L2 && ox >= 0 && ox < p.n[1]) {
-                    atomicAdd(y0 + yr + ox, a[j].x);
-                    if (has1) atomicAdd(y1 + yr + ox, a[j].y);
-                }
+            add_row<T, P>(a, t, lmask, reinterpret_cast<float *>(SP) + line * L::STAGE,
+                          y0 + int64_t(oy) * p.n[1], y1 + int64_t(oy) * p.n[1], has1, j0 - R, L2, p.n[1]);
+        }
+        if constexpr (sizeof(T) == 4) {
+            // the line's bulk reductions are complete before the tile reports done
+            if (t == 0) {
+                bulk_wait_all();
+                fence_proxy_async_global();
             }
         }
         __syncthreads();

@@ -81,3 +81,24 @@ __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
 }
 
 }  // namespace pc
+
+namespace pc {
+
+// Bulk reduction shared -> global: dst[i] += src[i] (f32) for bytes/4 values,
+// performed by the asynchronous (TMA) unit.  16-byte aligned addresses, size a
+// multiple of 16.  Tracked by this thread's bulk async-groups.
+__device__ __forceinline__ void bulk_reduce_add_f32(float *dst, const float *src, uint32_t bytes) {
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst),
+                 "r"(smem_u32(src)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// this thread's bulk groups have finished reading their shared-memory sources
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// this thread's bulk groups are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+}  // namespace pc
