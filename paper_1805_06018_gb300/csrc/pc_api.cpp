@@ -205,14 +205,36 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     int P = tune && tune->fft_size ? tune->fft_size : (prec == PC_FP64 ? 64 : 128);
     if (prec == PC_FP64 && P != 64) return fail(ctx, PC_ERR_UNSUPPORTED, "FP64 operators use fft_size 64");
     if (prec == PC_FP32 && P != 64 && P != 128) return fail(ctx, PC_ERR_UNSUPPORTED, "FP32 2D fft_size must be 64 or 128");
-    if (2 * radius + 1 > P - 1) return fail(ctx, PC_ERR_UNSUPPORTED, "radius too large for the FFT size");
-    // input tiles: n + 2R <= P keeps the circular convolution linear; the kernel
-    // stages the weight and two right-hand-side rows of a tile in one workspace
-    // row of 2P reals, so also 3n <= 2P
-    int T = std::min(P - 2 * radius, (2 * P) / 3);
+    // Input tiles of extent n and kernel (sub-)windows of extent ws need
+    // n + ws - 1 <= P for the circular product to be the linear convolution;
+    // the kernel stages the weight and two right-hand-side rows of a tile in
+    // one workspace row of 2P reals, so also 3n <= 2P.  When the window
+    // 2R+1 leaves no room for a useful tile it is cut into nsub^2
+    // sub-windows (nsub chosen to minimise the FFT work per input pixel,
+    // nsub^2 / T^2).
+    const int Wfull = 2 * radius + 1;
+    const int cap = (2 * P) / 3;
+    pc::WindowSplit split;
+    int T = 0;
+    {
+        double best = 1e300;
+        for (int nsub = 1; nsub <= 8; ++nsub) {
+            const int ws = (Wfull + nsub - 1) / nsub;
+            const int t = std::min(P - ws + 1, cap);
+            if (t < 1 || (nsub == 1 && t < 16 && Wfull > 16)) continue;
+            const double cost = double(nsub) * nsub / (double(t) * t);
+            if (cost < best * 0.999) {
+                best = cost;
+                split.nsub = nsub;
+                split.ws = ws;
+                T = t;
+            }
+        }
+        if (T < 1) return fail(ctx, PC_ERR_UNSUPPORTED, "radius too large for the FFT size");
+    }
     if (tune && tune->tile) {
         if (tune->tile < 1 || tune->tile > T)
-            return fail(ctx, PC_ERR_ARG, "tile must be in [1, min(fft_size - 2R, 2 fft_size / 3)]");
+            return fail(ctx, PC_ERR_ARG, "tile must be in [1, min(fft_size - window + 1, 2 fft_size / 3)]");
         T = tune->tile;
     }
     DeviceGuard dg(ctx->device);
@@ -246,7 +268,7 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     pc::build_extension(g, radius, impulse, phiE);
     // schedule
     pc::Schedule sch;
-    pc::build_schedule(g, radius, T, woff, sch);
+    pc::build_schedule(g, radius, T, split, woff, sch);
 
     auto *op = new (std::nothrow) pc_operator;
     if (!op) return fail(ctx, PC_ERR_NOMEM, "out of host memory");
@@ -257,6 +279,7 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     op->R = radius;
     op->P = P;
     op->T = T;
+    op->split = split;
     op->r = r;
     op->prec = prec;
     op->elem = prec == PC_FP64 ? 8 : 4;
@@ -307,17 +330,35 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
         cudaFree(d_tw64);
         return bail(e, "twiddles");
     }
-    // spectra (FP64 on the device, rounded once)
+    // spectra (FP64 on the device, rounded once), one per (patch, sub-window):
+    // sub-window (s0, s1) of phi_k^E placed at [0, ws)^2, zero-padded
+    const int ns = split.nsub, ws = split.ws;
+    const int nspec = r * ns * ns;
+    std::vector<double> psi;
+    const double *psi_src = phiE.data();
+    if (ns > 1) {
+        psi.assign(size_t(nspec) * ws * ws, 0.0);
+        for (int k = 0; k < r; ++k)
+            for (int s0 = 0; s0 < ns; ++s0)
+                for (int s1 = 0; s1 < ns; ++s1) {
+                    double *dst = psi.data() + (size_t(k) * ns * ns + s0 * ns + s1) * ws * ws;
+                    for (int a = 0; a < ws && s0 * ws + a < Wfull; ++a)
+                        for (int b = 0; b < ws && s1 * ws + b < Wfull; ++b)
+                            dst[a * ws + b] = phiE[size_t(k) * wsz + (s0 * ws + a) * Wfull + (s1 * ws + b)];
+                }
+        psi_src = psi.data();
+    }
     op->spec_stride = int64_t(P / 2 + 1) * P;
-    op->spec_bytes = size_t(r) * op->spec_stride * 2 * op->elem;
+    op->spec_bytes = size_t(nspec) * op->spec_stride * 2 * op->elem;
     double *d_psi = nullptr;
+    const size_t psi_elems = size_t(nspec) * ws * ws;
     e = cudaMalloc(&op->d_spec, op->spec_bytes);
     if (e == cudaSuccess) {
         acct += op->spec_bytes;
-        e = cudaMalloc(&d_psi, sizeof(double) * phiE.size());
+        e = cudaMalloc(&d_psi, sizeof(double) * psi_elems);
     }
-    if (e == cudaSuccess) e = cudaMemcpy(d_psi, phiE.data(), sizeof(double) * phiE.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = pc::build_spectra_2d(d_psi, r, radius, P, prec, op->d_spec, d_tw64, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(d_psi, psi_src, sizeof(double) * psi_elems, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = pc::build_spectra_2d(d_psi, nspec, ws, P, prec, op->d_spec, d_tw64, nullptr);
     cudaFree(d_psi);
     cudaFree(d_tw64);
     if (e != cudaSuccess) return bail(e, "building spectra");

@@ -214,7 +214,6 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
     T *y = static_cast<T *>(p.y);
     const T *w = static_cast<const T *>(p.w);
     const C *spec = static_cast<const C *>(p.spec);
-    const int R = p.R;
     const C zero{T(0), T(0)};
     uint32_t phase = 0;
 
@@ -241,7 +240,8 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
         if (threadIdx.x == kThreads2d - 1) s_next = int64_t(atomicAdd(counter, 1ull));
         const int n1 = tile.in_ext[0], n2 = tile.in_ext[1];
         const int i0 = tile.in_lo[0], j0 = tile.in_lo[1];
-        const int L1 = n1 + 2 * R, L2 = n2 + 2 * R;
+        const int L1 = n1 + tile.kext[0] - 1, L2 = n2 + tile.kext[1] - 1;   // <= P
+        const int o0 = tile.out_lo[0], o1 = tile.out_lo[1];
         const int b0 = 2 * pair;
         const bool has1 = b0 + 1 < p.nrhs;
         const T *x0 = x + int64_t(b0) * p.ldx;
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
         if (threadIdx.x < H) {
             const int col = threadIdx.x;
             fence_proxy_async_smem();
-            bulk_g2s(SP + col * L::SPLD, spec + int64_t(tile.patch) * p.spec_stride + int64_t(col) * P,
+            bulk_g2s(SP + col * L::SPLD, spec + int64_t(tile.spec) * p.spec_stride + int64_t(col) * P,
                      uint32_t(P * sizeof(C)), mbar);
         }
 
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
         T *y1 = has1 ? y0 + p.ldy : y0;
         if (sizeof(T) == 4 && t == 0) fence_proxy_async_global();
         for (int n = line; n < L1; n += LINES) {
-            const int oy = i0 - R + n;
+            const int oy = o0 + n;
             if (oy < 0 || oy >= p.n[0]) continue;
             C a[R1];
 #pragma unroll
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
             RowScratch<P, C> scr{S, n};
             fft_line<P, true>(a, tw, t, scr, lmask);
             add_row<T, P>(a, t, lmask, reinterpret_cast<float *>(SP) + line * L::STAGE,
-                          y0 + int64_t(oy) * p.n[1], y1 + int64_t(oy) * p.n[1], has1, j0 - R, L2, p.n[1]);
+                          y0 + int64_t(oy) * p.n[1], y1 + int64_t(oy) * p.n[1], has1, o1, L2, p.n[1]);
         }
         if constexpr (sizeof(T) == 4) {
             // the line's bulk reductions are complete before the tile reports done

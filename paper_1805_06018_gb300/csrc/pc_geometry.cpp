@@ -238,8 +238,12 @@ void build_extension(const Geometry &g, int R, const double *phi, std::vector<do
     }
 }
 
-void build_schedule(const Geometry &g, int R, int T, const std::vector<int64_t> &w_off, Schedule &s) {
+void build_schedule(const Geometry &g, int R, int T, const WindowSplit &wsp, const std::vector<int64_t> &w_off,
+                    Schedule &s) {
     const int r = int(g.pts.size());
+    const int W = 2 * R + 1;
+    int nsubd = 1;
+    for (int a = 0; a < g.d; ++a) nsubd *= wsp.nsub;
     std::vector<Tile> tiles;
     for (int k = 0; k < r; ++k) {
         int64_t ext[3] = {1, 1, 1}, nt[3] = {1, 1, 1};
@@ -271,7 +275,24 @@ void build_schedule(const Geometry &g, int R, int T, const std::vector<int64_t> 
                         t.w_ld[1] = int32_t(e2);
                         t.w_base = w_off[k] + (rel[0] * e1 + rel[1]) * e2 + rel[2];
                     }
-                    tiles.push_back(t);
+                    // one work unit per kernel sub-window
+                    for (int sidx = 0; sidx < nsubd; ++sidx) {
+                        Tile u = t;
+                        u.spec = k * nsubd + sidx;
+                        int rest = sidx;
+                        for (int a = g.d - 1; a >= 0; --a) {
+                            const int sa = rest % wsp.nsub;
+                            rest /= wsp.nsub;
+                            const int o = sa * wsp.ws;
+                            u.kext[a] = std::min(wsp.ws, W - o);
+                            u.out_lo[a] = u.in_lo[a] - R + o;
+                        }
+                        for (int a = g.d; a < 3; ++a) {
+                            u.kext[a] = 1;
+                            u.out_lo[a] = 0;
+                        }
+                        tiles.push_back(u);
+                    }
                 }
     }
     const int nt = int(tiles.size());
@@ -279,9 +300,9 @@ void build_schedule(const Geometry &g, int R, int T, const std::vector<int64_t> 
     std::vector<std::array<int64_t, 6>> ob(nt);
     for (int i = 0; i < nt; ++i)
         for (int a = 0; a < 3; ++a) {
-            const int64_t rr = a < g.d ? R : 0;
-            ob[i][a] = std::max<int64_t>(0, tiles[i].in_lo[a] - rr);
-            ob[i][3 + a] = std::min<int64_t>(g.shape[a] - 1, tiles[i].in_lo[a] + tiles[i].in_ext[a] - 1 + rr);
+            ob[i][a] = std::max<int64_t>(0, tiles[i].out_lo[a]);
+            ob[i][3 + a] = std::min<int64_t>(g.shape[a] - 1,
+                                             int64_t(tiles[i].out_lo[a]) + tiles[i].in_ext[a] + tiles[i].kext[a] - 2);
         }
     auto overlap = [&](int i, int j) {
         for (int a = 0; a < 3; ++a)

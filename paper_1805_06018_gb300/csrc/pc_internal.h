@@ -52,12 +52,26 @@ void build_extension(const Geometry &g, int R, const double *phi, std::vector<do
 // ---------------------------------------------------------------------------
 // Device descriptors
 // ---------------------------------------------------------------------------
+// One unit of convolution work: an input tile of bbox(U_k) convolved with one
+// sub-window of phi_k^E.  When 2R+1 is too wide for the FFT size, the window
+// [-R, R]^d is cut into sub-windows with their own spectra; by linearity the
+// sum over sub-windows is the full convolution.
 struct Tile {
     int32_t patch;       // k
+    int32_t spec;        // spectrum index (patch * nsub^d + sub-window)
     int32_t in_lo[3];    // input tile origin in Omega
     int32_t in_ext[3];   // input tile extents (<= T)
+    int32_t out_lo[3];   // origin of the tile's linear-convolution output (may be < 0)
+    int32_t kext[3];     // sub-window extents: output extent = in_ext + kext - 1
     int32_t w_ld[2];     // strides of the patch weight window: 2D {ext1, 1}; 3D {ext1*ext2, ext2}
     int64_t w_base;      // element offset of the weight at in_lo
+};
+
+// Cut of the kernel window [-R, R] (per axis) into nsub sub-windows of
+// extent <= ws; sub-window s starts at -R + s * ws.
+struct WindowSplit {
+    int nsub = 1;
+    int ws = 1;
 };
 
 struct Schedule {
@@ -71,7 +85,8 @@ struct Schedule {
 // that tiles of one colour have disjoint output boxes (tile (+) [-R, R]^d,
 // clipped to Omega), and list for every tile the overlapping tiles of lower
 // colour.  Output pixels then receive their contributions in colour order.
-void build_schedule(const Geometry &g, int R, int T, const std::vector<int64_t> &w_off, Schedule &s);
+void build_schedule(const Geometry &g, int R, int T, const WindowSplit &ws, const std::vector<int64_t> &w_off,
+                    Schedule &s);
 
 // Kernel parameter block shared by the 2D and 3D fused kernels.
 struct ApplyParams {
@@ -113,6 +128,7 @@ struct pc_operator {
     pc::I3 shape{1, 1, 1};
     int64_t N = 0;
     int R = 0, P = 0, T = 0, r = 0;
+    pc::WindowSplit split;
     pc_precision prec = PC_FP32;
     int n_tiles = 0, n_colors = 0;
     size_t elem = 4;             // bytes of one real value
@@ -150,7 +166,8 @@ namespace pc {
 cudaError_t launch_zero(const ApplyParams &p, int64_t N, pc_precision prec, cudaStream_t s);
 cudaError_t launch_fft2d(const ApplyParams &p, int P, pc_precision prec, int ctas, cudaStream_t s);
 cudaError_t fft2d_configure(int P, pc_precision prec, int *ctas_per_sm, size_t *smem);
-cudaError_t build_spectra_2d(const double *d_psi, int r, int R, int P, pc_precision prec, void *d_spec,
+// d_psi: [nspec][W][W] FP64 windows placed at [0, W)^2; spectra [nspec][P/2+1][P]
+cudaError_t build_spectra_2d(const double *d_psi, int nspec, int W, int P, pc_precision prec, void *d_spec,
                              const double2 *d_tw64, cudaStream_t s);
 pc_status plain_apply(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
                       cudaStream_t s, std::string &err);

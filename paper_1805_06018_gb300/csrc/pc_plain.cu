@@ -39,7 +39,7 @@ __global__ void plain_product(float2 *freq, const Tile *tiles, const float2 *spe
     const int H = P / 2 + 1;
     const Tile t = tiles[blockIdx.x];
     float2 *f = freq + int64_t(blockIdx.x) * P * H;
-    const float2 *sp = spec + int64_t(t.patch) * spec_stride;
+    const float2 *sp = spec + int64_t(t.spec) * spec_stride;
     for (int i = threadIdx.x; i < P * H; i += blockDim.x) {
         const int k1 = i / H, k2 = i % H;
         const float2 a = f[i], s = sp[int64_t(k2) * P + k1];
@@ -48,7 +48,7 @@ __global__ void plain_product(float2 *freq, const Tile *tiles, const float2 *spe
 }
 
 __global__ void plain_add(float *y, const float *real, const Tile *tiles, const int32_t *blk_start,
-                          const int32_t *blk_tiles, int nb1, int n0, int n1, int R, int P) {
+                          const int32_t *blk_tiles, int nb1, int n0, int n1, int P) {
     const int i = blockIdx.y * 32 + threadIdx.y;
     const int j = blockIdx.x * 32 + threadIdx.x;
     if (i >= n0 || j >= n1) return;
@@ -57,8 +57,8 @@ __global__ void plain_add(float *y, const float *real, const Tile *tiles, const 
     for (int q = blk_start[blk]; q < blk_start[blk + 1]; ++q) {
         const int ti = blk_tiles[q];
         const Tile t = tiles[ti];
-        const int o0 = i - (t.in_lo[0] - R), o1 = j - (t.in_lo[1] - R);
-        if (o0 >= 0 && o0 < t.in_ext[0] + 2 * R && o1 >= 0 && o1 < t.in_ext[1] + 2 * R)
+        const int o0 = i - t.out_lo[0], o1 = j - t.out_lo[1];
+        if (o0 >= 0 && o0 < t.in_ext[0] + t.kext[0] - 1 && o1 >= 0 && o1 < t.in_ext[1] + t.kext[1] - 1)
             acc += real[(int64_t(ti) * P + o0) * P + o1];
     }
     y[int64_t(i) * n1 + j] = acc;
@@ -101,14 +101,14 @@ static pc_status plain_init(pc_operator *op, std::string &err) {
     }
     st->have_plans = true;
     // tiles covering each 32x32 output block
-    const int n0 = int(op->shape[0]), n1 = int(op->shape[1]), R = op->R;
+    const int n0 = int(op->shape[0]), n1 = int(op->shape[1]);
     st->nb0 = (n0 + 31) / 32;
     st->nb1 = (n1 + 31) / 32;
     std::vector<std::vector<int32_t>> lists(size_t(st->nb0) * st->nb1);
     for (int ti = 0; ti < nt; ++ti) {
         const Tile &t = op->tiles_h[ti];
-        const int a0 = std::max(0, t.in_lo[0] - R), a1 = std::min(n0 - 1, t.in_lo[0] + t.in_ext[0] - 1 + R);
-        const int b0 = std::max(0, t.in_lo[1] - R), b1 = std::min(n1 - 1, t.in_lo[1] + t.in_ext[1] - 1 + R);
+        const int a0 = std::max(0, t.out_lo[0]), a1 = std::min(n0 - 1, t.out_lo[0] + t.in_ext[0] + t.kext[0] - 2);
+        const int b0 = std::max(0, t.out_lo[1]), b1 = std::min(n1 - 1, t.out_lo[1] + t.in_ext[1] + t.kext[1] - 2);
         for (int bi = a0 / 32; bi <= a1 / 32; ++bi)
             for (int bj = b0 / 32; bj <= b1 / 32; ++bj) lists[size_t(bi) * st->nb1 + bj].push_back(ti);
     }
@@ -164,7 +164,7 @@ pc_status plain_apply(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx,
             return PC_ERR_CUDA;
         }
         plain_add<<<dim3(st->nb1, st->nb0), dim3(32, 32), 0, s>>>(yb, st->real, op->d_tiles, st->blk_start,
-                                                                st->blk_tiles, st->nb1, n0, n1, op->R, P);
+                                                                st->blk_tiles, st->nb1, n0, n1, P);
         launches += 3;
     }
     cudaError_t e = cudaGetLastError();

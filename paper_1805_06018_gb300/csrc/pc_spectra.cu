@@ -1,5 +1,6 @@
 // One-time FP64 construction of the patch spectra phi^_k = DFT_P(psi_k) / P^d,
-// psi_k[a] = phi_k^E[a - R] for a in [0, 2R]^d (zero elsewhere in [0, P)^d).
+// psi[a] = a window (phi_k^E or one sub-window of it) placed at [0, W)^d,
+// zero elsewhere in [0, P)^d.
 //
 // With this placement the linear convolution of a tile u (extent n per axis,
 // n + 2R <= P) with phi_k^E comes out of the circular product at output index
@@ -13,8 +14,8 @@
 namespace pc {
 
 // T1[k][a][c] = sum_b psi[k][a][b] W_P^{b c},  a in [0, 2R], c in [0, P/2]
-__global__ void spectra2d_stage1(const double *psi, int r0, int nr, int R, int P, const double2 *tw, double2 *T1) {
-    const int W = 2 * R + 1, H = P / 2 + 1;
+__global__ void spectra2d_stage1(const double *psi, int r0, int nr, int W, int P, const double2 *tw, double2 *T1) {
+    const int H = P / 2 + 1;
     const int64_t total = int64_t(nr) * W * H;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
         const int c = int(i % H);
@@ -33,8 +34,8 @@ __global__ void spectra2d_stage1(const double *psi, int r0, int nr, int R, int P
 
 // spec[k][c][k1] = (1/P^2) sum_a T1[k][a][c] W_P^{a k1}
 template <typename C>
-__global__ void spectra2d_stage2(const double2 *T1, int r0, int nr, int R, int P, const double2 *tw, C *spec) {
-    const int W = 2 * R + 1, H = P / 2 + 1;
+__global__ void spectra2d_stage2(const double2 *T1, int r0, int nr, int W, int P, const double2 *tw, C *spec) {
+    const int H = P / 2 + 1;
     const double scale = 1.0 / (double(P) * double(P));
     const int64_t total = int64_t(nr) * H * P;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
@@ -55,9 +56,9 @@ __global__ void spectra2d_stage2(const double2 *T1, int r0, int nr, int R, int P
     }
 }
 
-cudaError_t build_spectra_2d(const double *d_psi, int r, int R, int P, pc_precision prec, void *d_spec,
+cudaError_t build_spectra_2d(const double *d_psi, int r, int W, int P, pc_precision prec, void *d_spec,
                              const double2 *d_tw64, cudaStream_t s) {
-    const int W = 2 * R + 1, H = P / 2 + 1;
+    const int H = P / 2 + 1;
     const int chunk = 256;
     double2 *T1 = nullptr;
     cudaError_t e = cudaMalloc(&T1, sizeof(double2) * size_t(chunk) * W * H);
@@ -65,13 +66,13 @@ cudaError_t build_spectra_2d(const double *d_psi, int r, int R, int P, pc_precis
     for (int r0 = 0; r0 < r && e == cudaSuccess; r0 += chunk) {
         const int nr = std::min(chunk, r - r0);
         const int64_t n1 = int64_t(nr) * W * H, n2 = int64_t(nr) * H * P;
-        spectra2d_stage1<<<int(std::min<int64_t>((n1 + 255) / 256, 8192)), 256, 0, s>>>(d_psi, r0, nr, R, P, d_tw64, T1);
+        spectra2d_stage1<<<int(std::min<int64_t>((n1 + 255) / 256, 8192)), 256, 0, s>>>(d_psi, r0, nr, W, P, d_tw64, T1);
         if (prec == PC_FP64)
             spectra2d_stage2<double2><<<int(std::min<int64_t>((n2 + 255) / 256, 8192)), 256, 0, s>>>(
-                T1, r0, nr, R, P, d_tw64, static_cast<double2 *>(d_spec));
+                T1, r0, nr, W, P, d_tw64, static_cast<double2 *>(d_spec));
         else
             spectra2d_stage2<float2><<<int(std::min<int64_t>((n2 + 255) / 256, 8192)), 256, 0, s>>>(
-                T1, r0, nr, R, P, d_tw64, static_cast<float2 *>(d_spec));
+                T1, r0, nr, W, P, d_tw64, static_cast<float2 *>(d_spec));
         e = cudaGetLastError();
     }
     cudaError_t e2 = cudaStreamSynchronize(s);

@@ -171,3 +171,47 @@ def test_errors_are_returned():
         op.pc_apply_batched(1, x[0].data_ptr(), 5, x[1].data_ptr(), wl.n, s)
     op.pc_apply_batched(0, 0, 0, 0, 0, s)  # empty batch is a no-op
     op.check()
+
+
+# ------------------------------------------------------------------ adaptive grids, large radii
+
+from test_oracle_geometry import ADAPTIVE_CELLS, ADAPTIVE_SHAPE  # noqa: E402
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_hanging_nodes(precision):
+    kern = workloads.Skewed([0.4, -0.8], lambda x: 1.0 + 0.4 * np.cos(x[..., 1] / 5.0), 3)
+    op, orc = make_pair(ADAPTIVE_SHAPE, np.array(ADAPTIVE_CELLS), kern, precision)
+    x = workloads.rhs(31, 3, ADAPTIVE_SHAPE)
+    xin = x.astype(np.float64) if precision == "fp64" else x
+    err = rel_l2(run(op, xin), orc.apply(x))
+    assert np.all(err <= TOL[precision]), err
+
+
+@pytest.mark.parametrize("precision,R", [("fp32", 64), ("fp64", 64), ("fp32", 58)])
+def test_split_kernel_window(precision, R):
+    """2R+1 wider than the FFT allows: the window is cut into sub-windows with
+    their own spectra and the tiles shrink accordingly."""
+    shape = (150, 161)
+    cells = workloads.regular_grid(shape, (3, 3))
+    kern = workloads.HeavyTailed(lambda x: 2.0 + 3.0 * (x[..., 0] / 150.0), R)
+    op, orc = make_pair(shape, cells, kern, precision)
+    info = op.info()
+    assert info["num_tiles"] > orc.grid.r
+    x = workloads.rhs(41, 2, shape)
+    xin = x.astype(np.float64) if precision == "fp64" else x
+    err = rel_l2(run(op, xin), orc.apply(x))
+    assert np.all(err <= TOL[precision]), err
+
+
+def test_adaptive_workload_1024_sampled():
+    """The adaptive 1024^2 quadtree (r = 1579, hanging nodes, heavy-tailed
+    kernel, R = 64): 4 right-hand sides, 4096 seeded pixels each."""
+    wl = configs.adaptive_1024(4)
+    op, orc = make_pair(wl.shape, wl.cells, wl.kernel, "fp32")
+    x = workloads.rhs(wl.rhs_seed, 4, wl.shape)
+    y = run(op, x).reshape(4, -1)
+    pts = np.random.default_rng(9).choice(wl.n, 4096, replace=False)
+    ref = orc.apply(x, points=pts)
+    err = np.linalg.norm(y[:, pts] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert np.all(err <= TOL["fp32"]), err

@@ -108,3 +108,21 @@ def test_grid_validation(cells, why):
     with pytest.raises(pcb.PCError) as ei:
         pcb.pc_sample_points((10, 6), np.array(cells))
     assert ei.value.status == pcb.PC_ERR_GRID, why
+
+
+@pytest.mark.parametrize("which", ["small", "adaptive_1024"])
+def test_weights_match_oracle_with_hanging_nodes(which):
+    """The library solves hanging-node leaves by bilinear + per-edge separation
+    of variables; the oracle by a full sine-eigenbasis solve.  Both are exact
+    discrete harmonic extensions, so they agree to rounding."""
+    if which == "small":
+        shape, cells = ADAPTIVE_SHAPE, np.array(ADAPTIVE_CELLS)
+    else:
+        wl = configs.adaptive_1024()
+        shape, cells = wl.shape, wl.cells
+    g = Grid(shape, cells)
+    W = harmonic_weights(g)
+    lw = pcb.pc_harmonic_weights(shape, cells)
+    ref = np.concatenate([w.ravel() for w in W])
+    assert lw.size == ref.size
+    assert np.max(np.abs(lw - ref)) < 1e-12
