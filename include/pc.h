@@ -108,6 +108,36 @@ typedef struct {
 
 typedef struct pc_context pc_context;
 typedef struct pc_operator pc_operator;
+typedef struct pc_server pc_server;
+
+/* Serving configuration (pc_serve_create). */
+typedef struct {
+    int64_t hbm_budget_bytes;   /* device bytes the server may hold for resident operators
+                                   (counted while they have work in flight) plus request scratch */
+    int32_t max_inflight;       /* requests admitted but not finished, <= 1024 */
+    int32_t streams;            /* concurrent launch slots (1..4); launches on different slots overlap */
+    int32_t max_requests_per_launch;   /* <= 64 */
+    int32_t reserved[3];
+} pc_serve_config;
+
+/* Completion record of a served request (pc_serve_poll). Times are seconds
+ * on the server's steady clock. */
+typedef struct {
+    double submit_s, launch_s, finish_s;
+    int32_t nrhs;
+    int32_t launch_requests;    /* requests that shared its launch */
+    int32_t status;             /* pc_status of the request */
+    int32_t reserved;
+} pc_request_info;
+
+/* Aggregate serving statistics since pc_serve_create. */
+typedef struct {
+    int64_t completed, rhs_completed, launches;
+    double p50_latency_s, p99_latency_s, mean_latency_s;
+    double busy_s;              /* first submit to last completion */
+    double rhs_per_s;
+    int64_t peak_bytes;         /* peak budgeted bytes */
+} pc_serve_stats;
 
 /* Create a library context bound to CUDA device `device`.  *ctx receives a
  * handle that the caller releases with pc_context_destroy.  Fails with
@@ -225,6 +255,53 @@ pc_status pc_apply_plain(pc_operator *op, int32_t nrhs, const void *x, int64_t l
  *     pc_apply_batched with pc_operator_check for that). */
 pc_status pc_apply_batched_noalloc(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx,
                                    void *y, int64_t ldy, pc_stream stream);
+
+/* ---------------------------------------------------------------------
+ * Serving.  The paper's use of A~ is many applications to vectors that
+ * arrive over time: preconditioner applications inside Krylov solves
+ * (Section 5.2) and the random probes Y~ = A~* Z of the a-posteriori
+ * estimator (Section 2.6, Algorithm 1).  A server keeps operators
+ * resident, admits requests against a device-memory budget, and batches
+ * the requests waiting at each moment - any operators, uneven right-hand
+ * side counts - into one persistent launch of the fused kernel, replayed
+ * from a CUDA graph captured at creation.  Launch slots run on separate
+ * streams, so a new launch starts while earlier ones finish.  Each request
+ * is computed exactly as pc_apply_batched would compute it alone.
+ * Supported operators: 2D, PC_FP32, fft_size 128.
+ * --------------------------------------------------------------------- */
+
+/* Create a server on ctx's device: a scheduler thread, `streams` launch
+ * slots (each with its captured graph, a pinned launch descriptor, ordering
+ * flags for up to 2^22 (tile, pair) units) and mapped completion flags. */
+pc_status pc_serve_create(pc_context *ctx, const pc_serve_config *cfg, pc_server **srv);
+
+/* Queue Y = A~ X for nrhs vectors: x and y are device arrays [nrhs][N] of
+ * float (contiguous), owned by the caller and kept alive until pc_serve_poll
+ * returns PC_OK for the ticket.  Returns at once with *ticket.  Errors:
+ * PC_ERR_UNSUPPORTED for operators the server cannot launch, PC_ERR_BUDGET
+ * if the operator and request alone exceed the budget, PC_ERR_ARG for bad
+ * arguments.  flags: reserved, pass 0. */
+pc_status pc_serve_submit(pc_server *srv, pc_operator *op, int32_t nrhs, const void *x, void *y, uint32_t flags,
+                          uint64_t *ticket);
+
+/* PC_ERR_NOT_READY while the request is queued or running; PC_OK (and
+ * *info, if not NULL) once y holds the result - the record is then
+ * released; PC_ERR_TIMEOUT / PC_ERR_CUDA if its launch failed; PC_ERR_ARG
+ * for an unknown ticket. */
+pc_status pc_serve_poll(pc_server *srv, uint64_t ticket, pc_request_info *info);
+
+pc_status pc_serve_stats_get(pc_server *srv, pc_serve_stats *stats);
+
+/* Waits for every admitted request, then stops the scheduler and frees the
+ * server's resources.  Requests still queued are dropped. */
+pc_status pc_serve_destroy(pc_server *srv);
+
+/* Autotuner: builds candidate launch shapes of the operator (FFT size,
+ * tile extent), times a batch of nrhs vectors on each with CUDA events, and
+ * writes the fastest into *best (*best_ms: its time per batch).  Same
+ * operator arguments as pc_build_spectra. */
+pc_status pc_autotune(pc_context *ctx, const pc_box *box, const pc_grid *grid, int32_t radius, const double *impulse,
+                      const double *weights, pc_precision prec, int32_t nrhs, pc_tuning *best, double *best_ms);
 
 /* Synchronise the operator's last stream and report device-side status:
  * PC_ERR_TIMEOUT if a bounded wait inside a kernel gave up since the last

@@ -56,6 +56,24 @@ class pc_operator_info(ctypes.Structure):
                 ("build_seconds", ctypes.c_double)]
 
 
+class pc_serve_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32), ("streams", ctypes.c_int32),
+                ("max_requests_per_launch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class pc_request_info(ctypes.Structure):
+    _fields_ = [("submit_s", ctypes.c_double), ("launch_s", ctypes.c_double), ("finish_s", ctypes.c_double),
+                ("nrhs", ctypes.c_int32), ("launch_requests", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class pc_serve_stats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("rhs_completed", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("p50_latency_s", ctypes.c_double), ("p99_latency_s", ctypes.c_double),
+                ("mean_latency_s", ctypes.c_double), ("busy_s", ctypes.c_double), ("rhs_per_s", ctypes.c_double),
+                ("peak_bytes", ctypes.c_int64)]
+
+
 # every entry point of include/pc.h: name -> (restype, argtypes)
 _VP = ctypes.c_void_p
 _PROTOS = {
@@ -81,6 +99,15 @@ _PROTOS = {
     "pc_operator_kernel_time": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
     "pc_operator_launches": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     "pc_operator_destroy": (ctypes.c_int, [_VP]),
+    "pc_serve_create": (ctypes.c_int, [_VP, ctypes.POINTER(pc_serve_config), ctypes.POINTER(_VP)]),
+    "pc_serve_submit": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _VP, _VP, ctypes.c_uint32,
+                                       ctypes.POINTER(ctypes.c_uint64)]),
+    "pc_serve_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(pc_request_info)]),
+    "pc_serve_stats_get": (ctypes.c_int, [_VP, ctypes.POINTER(pc_serve_stats)]),
+    "pc_serve_destroy": (ctypes.c_int, [_VP]),
+    "pc_autotune": (ctypes.c_int, [_VP, ctypes.POINTER(pc_box), ctypes.POINTER(pc_grid), ctypes.c_int32, _VP, _VP,
+                                   ctypes.c_int, ctypes.c_int32, ctypes.POINTER(pc_tuning),
+                                   ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None
@@ -281,6 +308,76 @@ class Operator:
         if getattr(self, "handle", None):
             lib().pc_operator_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pc_autotune(ctx: Context, shape, cells, radius: int, impulse: np.ndarray, precision: str = "fp32",
+                nrhs: int = 8, weights: Optional[np.ndarray] = None):
+    """Fastest launch shape (dict of pc_tuning fields) and its ms per batch of nrhs."""
+    b = _box(shape)
+    g, keep = _grid(cells)
+    imp = np.ascontiguousarray(impulse, dtype=np.float64)
+    wts = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    best = pc_tuning()
+    ms = ctypes.c_double()
+    _check(lib().pc_autotune(ctx.handle, ctypes.byref(b), ctypes.byref(g), ctypes.c_int32(radius), _ptr(imp),
+                             _ptr(wts), PRECISIONS[precision], ctypes.c_int32(nrhs), ctypes.byref(best),
+                             ctypes.byref(ms)), ctx.handle)
+    del keep
+    return {"fft_size": best.fft_size, "tile": best.tile, "ctas_per_sm": best.ctas_per_sm}, ms.value
+
+
+class Server:
+    """pc_serve_*: batched serving of apply requests on resident operators."""
+
+    def __init__(self, ctx: Context, budget_bytes: int, max_inflight: int = 256, streams: int = 2,
+                 max_requests_per_launch: int = 32):
+        self.ctx = ctx
+        cfg = pc_serve_config()
+        cfg.hbm_budget_bytes = int(budget_bytes)
+        cfg.max_inflight = max_inflight
+        cfg.streams = streams
+        cfg.max_requests_per_launch = max_requests_per_launch
+        h = _VP()
+        _check(lib().pc_serve_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)), ctx.handle)
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, op: "Operator", x, y) -> int:
+        """Queue y = A~ x (x, y: contiguous float32 CUDA tensors [nrhs, *box]).
+        The tensors are kept alive until poll() reports the ticket done."""
+        nrhs = x.numel() // op.N
+        t = ctypes.c_uint64()
+        _check(lib().pc_serve_submit(self.handle, op.handle, ctypes.c_int32(nrhs), _VP(x.data_ptr()),
+                                     _VP(y.data_ptr()), ctypes.c_uint32(0), ctypes.byref(t)), self.ctx.handle)
+        self._keep[t.value] = (x, y)
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while not ready, else the completion record (dict)."""
+        info = pc_request_info()
+        st = lib().pc_serve_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(info))
+        if st == PC_ERR_NOT_READY:
+            return None
+        self._keep.pop(ticket, None)
+        _check(st, self.ctx.handle)
+        return {f: getattr(info, f) for f, _ in info._fields_ if f != "reserved"}
+
+    def stats(self) -> dict:
+        st = pc_serve_stats()
+        _check(lib().pc_serve_stats_get(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pc_serve_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
 
     def __del__(self):
         try:

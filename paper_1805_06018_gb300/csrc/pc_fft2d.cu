@@ -186,7 +186,7 @@ __device__ __forceinline__ void add_row(const C *a, int t, unsigned lmask, float
 }
 
 template <typename T, int P>
-__global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams p) {
+__global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const LaunchParams lp) {
     using C = typename Cx<T>::type;
     using L = Smem2d<T, P>;
     constexpr int R1 = FftShape<P>::R1, R2 = FftShape<P>::R2;
@@ -198,24 +198,24 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
     C *SP = reinterpret_cast<C *>(smem_raw + L::ws);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw + L::ws + L::sp);
     __shared__ int64_t s_next;
+    __shared__ int s_segidx;
+    __shared__ __align__(16) Segment s_seg;          // the current item's request
     __shared__ int s_cstart_buf[kMaxColorsCached + 1];
-    const int *s_cstart = p.n_colors <= kMaxColorsCached ? s_cstart_buf : p.color_start;
-    for (int c = threadIdx.x; c <= p.n_colors && c <= kMaxColorsCached; c += blockDim.x) s_cstart_buf[c] = p.color_start[c];
 
+    const int nseg = lp.desc ? lp.desc->nseg : 1;
+    const int64_t total = lp.desc ? lp.desc->total_items : lp.one.p.total_items;
     const int t = threadIdx.x % R2;
     const int line = threadIdx.x / R2;
     const unsigned lmask = FftShape<P>::line_mask();
-    const C *twg = static_cast<const C *>(p.tw);
+    // every operator of a launch shares P, so the twiddle values W_P^k are the same
+    const C *twg = static_cast<const C *>(lp.desc ? lp.desc->seg[0].p.tw : lp.one.p.tw);
     C tw[R1];
 #pragma unroll
     for (int m = 0; m < R1; ++m) tw[m] = twg[(t * m) & (P - 1)];
-
-    const T *x = static_cast<const T *>(p.x);
-    T *y = static_cast<T *>(p.y);
-    const T *w = static_cast<const T *>(p.w);
-    const C *spec = static_cast<const C *>(p.spec);
     const C zero{T(0), T(0)};
     uint32_t phase = 0;
+    int cur_seg = -1;
+    const int *s_cstart = s_cstart_buf;
 
     if (threadIdx.x == 0) {
         mbar_init(mbar, 1);
@@ -226,12 +226,42 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
     // claimed so its input rows can be pulled into L2.  Claims still happen in
     // increasing order, and the lowest unfinished item is always one that a
     // CTA is working on, so every dependency wait ends.
-    unsigned long long *counter = reinterpret_cast<unsigned long long *>(p.ctrl);
+    unsigned long long *counter = lp.counter;
     if (threadIdx.x == 0) s_next = int64_t(atomicAdd(counter, 1ull));
     for (;;) {
         __syncthreads();
-        const int64_t item = s_next;
-        if (item >= p.total_items) break;
+        const int64_t gitem = s_next;
+        if (gitem >= total) break;
+        // the request (segment) this item belongs to
+        if (threadIdx.x == 0) {
+            int sx = 0;
+            if (lp.desc)
+                while (sx + 1 < nseg && lp.desc->seg[sx + 1].item_begin <= gitem) ++sx;
+            s_segidx = sx;
+        }
+        __syncthreads();
+        if (s_segidx != cur_seg) {
+            cur_seg = s_segidx;
+            if (lp.desc) {
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(lp.desc->seg + cur_seg);
+                for (int q = threadIdx.x; q < int(sizeof(Segment) / 4); q += blockDim.x)
+                    reinterpret_cast<uint32_t *>(&s_seg)[q] = src[q];
+            } else if (threadIdx.x == 0) {
+                s_seg = lp.one;
+            }
+            __syncthreads();
+            const int nc = s_seg.p.n_colors;
+            s_cstart = nc <= kMaxColorsCached ? s_cstart_buf : s_seg.p.color_start;
+            for (int c = threadIdx.x; c <= nc && c <= kMaxColorsCached; c += blockDim.x)
+                s_cstart_buf[c] = s_seg.p.color_start[c];
+            __syncthreads();
+        }
+        const ApplyParams &p = s_seg.p;
+        const int64_t item = gitem - s_seg.item_begin;
+        const T *x = static_cast<const T *>(p.x);
+        T *y = static_cast<T *>(p.y);
+        const T *w = static_cast<const T *>(p.w);
+        const C *spec = static_cast<const C *>(p.spec);
         int ti, pair;
         decode_item(p, s_cstart, item, ti, pair);
         const Tile tile = p.tiles[ti];
@@ -294,11 +324,11 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
         }
         __syncthreads();
 
-        prefetch_item<T>(p, s_cstart, s_next);
+        if (s_next - s_seg.item_begin < p.total_items) prefetch_item<T>(p, s_cstart, s_next - s_seg.item_begin);
 
         // ---------------- phase B: column FFT, spectral product, inverse column FFT
         if (!mbar_wait_bounded(mbar, phase, kMbarLimit)) {
-            atomicExch(p.ctrl + 2, 2);   // copy did not land; wait once more, then carry on
+            atomicExch(lp.status, 2);   // copy did not land; wait once more, then carry on
             mbar_wait_bounded(mbar, phase, kMbarLimit);
         }
         phase ^= 1u;
@@ -339,7 +369,7 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
                 long long spins = 0;
                 while (ld_acquire_u32(f) != p.epoch) {
                     if (++spins > kSpinLimit) {
-                        atomicExch(p.ctrl + 2, 1);   // timeout flag; result of this apply is invalid
+                        atomicExch(lp.status, 1);   // timeout flag; result of this apply is invalid
                         break;
                     }
                     __nanosleep(64);
@@ -377,6 +407,14 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const ApplyParams 
         if (threadIdx.x == 0) {
             __threadfence();
             st_release_u32(p.done + int64_t(ti) * p.done_ld + pair, p.epoch);
+            if (lp.seg_done) {
+                // the request's last item raises its completion flag in host memory
+                const uint32_t before = atomicAdd(lp.seg_done + cur_seg, 1u);
+                if (int64_t(before) + 1 == p.total_items && s_seg.slot >= 0 && lp.host_flags) {
+                    __threadfence_system();
+                    st_release_sys_u32(lp.host_flags + s_seg.slot, 1u);
+                }
+            }
         }
     }
 }
@@ -430,12 +468,55 @@ cudaError_t launch_fft2d(const ApplyParams &p, int P, pc_precision prec, int cta
     size_t smem = 0;
     cudaError_t e = fft2d_configure(P, prec, nullptr, &smem);
     if (e != cudaSuccess) return e;
+    LaunchParams lp{};
+    lp.desc = nullptr;
+    lp.one.p = p;
+    lp.one.item_begin = 0;
+    lp.one.slot = -1;
+    lp.counter = reinterpret_cast<unsigned long long *>(p.ctrl);
+    lp.status = p.ctrl + 2;
     if (prec == PC_FP64)
-        fft2d_kernel<double, 64><<<ctas, kThreads2d, smem, s>>>(p);
+        fft2d_kernel<double, 64><<<ctas, kThreads2d, smem, s>>>(lp);
     else if (P == 64)
-        fft2d_kernel<float, 64><<<ctas, kThreads2d, smem, s>>>(p);
+        fft2d_kernel<float, 64><<<ctas, kThreads2d, smem, s>>>(lp);
     else
-        fft2d_kernel<float, 128><<<ctas, kThreads2d, smem, s>>>(p);
+        fft2d_kernel<float, 128><<<ctas, kThreads2d, smem, s>>>(lp);
+    return cudaGetLastError();
+}
+
+// Multi-request launch: every segment's y zeroed, its ordering flags and
+// finished-item counter cleared, the claim counter reset.
+__global__ void round_prepare(const LaunchDesc *d, unsigned long long *counter, uint32_t *seg_done) {
+    const int nseg = d->nseg;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0ull;
+    if (blockIdx.x == 0)
+        for (int q = threadIdx.x; q < nseg; q += blockDim.x) seg_done[q] = 0u;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int sx = 0; sx < nseg; ++sx) {
+        const ApplyParams &p = d->seg[sx].p;
+        const int64_t N = int64_t(p.n[0]) * p.n[1] * p.n[2];
+        float *y = static_cast<float *>(p.y);
+        const int64_t tot = int64_t(p.nrhs) * N;
+        for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < tot; q += stride) {
+            const int64_t b = q / N, e = q - b * N;
+            y[b * p.ldy + e] = 0.0f;
+        }
+        const int64_t nf = int64_t(p.color_start[p.n_colors]) * p.done_ld;
+        for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < nf; q += stride) p.done[q] = 0u;
+    }
+}
+
+cudaError_t launch_round(const LaunchDesc *d_desc, unsigned long long *counter, int32_t *status, uint32_t *seg_done,
+                         uint32_t *host_flags, int ctas, size_t smem, cudaStream_t s) {
+    round_prepare<<<1024, 256, 0, s>>>(d_desc, counter, seg_done);
+    LaunchParams lp{};
+    lp.desc = d_desc;
+    lp.one.slot = -1;
+    lp.counter = counter;
+    lp.status = status;
+    lp.seg_done = seg_done;
+    lp.host_flags = host_flags;
+    fft2d_kernel<float, 128><<<ctas, kThreads2d, smem, s>>>(lp);
     return cudaGetLastError();
 }
 

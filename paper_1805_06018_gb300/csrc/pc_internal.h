@@ -112,6 +112,33 @@ struct ApplyParams {
     int64_t total_items;
 };
 
+// One request on one operator inside a launch.
+struct Segment {
+    ApplyParams p;          // operator data, the request's x/y/nrhs, its ordering flags; p.total_items = its items
+    int64_t item_begin;     // first launch-wide item index of the segment
+    int32_t slot;           // completion slot in the host flag array, or -1
+    int32_t pad_;
+};
+
+constexpr int kMaxSegments = 64;
+
+// Device-resident descriptor of a launch that serves several requests.
+struct LaunchDesc {
+    int32_t nseg;
+    int32_t pad_;
+    int64_t total_items;
+    Segment seg[kMaxSegments];
+};
+
+struct LaunchParams {
+    const LaunchDesc *desc;         // nullptr: the single inline segment `one`
+    Segment one;
+    unsigned long long *counter;    // claim counter, zero at launch
+    int32_t *status;                // [0] timeout flag
+    uint32_t *seg_done;             // per-segment finished-item counters (descriptor launches)
+    uint32_t *host_flags;           // mapped host memory: host_flags[slot] = 1 once a segment is complete
+};
+
 }  // namespace pc
 
 struct pc_context {
@@ -165,6 +192,10 @@ namespace pc {
 // kernels (pc_fft2d.cu, pc_spectra.cu, pc_plain.cu)
 cudaError_t launch_zero(const ApplyParams &p, int64_t N, pc_precision prec, cudaStream_t s);
 cudaError_t launch_fft2d(const ApplyParams &p, int P, pc_precision prec, int ctas, cudaStream_t s);
+// multi-request launch (FP32, P = 128): y zero-fill + claim reset, then the fused kernel
+// (fft2d_configure(128, PC_FP32, ...) must have been called; capturable)
+cudaError_t launch_round(const LaunchDesc *d_desc, unsigned long long *counter, int32_t *status, uint32_t *seg_done,
+                         uint32_t *host_flags, int ctas, size_t smem, cudaStream_t s);
 cudaError_t fft2d_configure(int P, pc_precision prec, int *ctas_per_sm, size_t *smem);
 // d_psi: [nspec][W][W] FP64 windows placed at [0, W)^2; spectra [nspec][P/2+1][P]
 cudaError_t build_spectra_2d(const double *d_psi, int nspec, int W, int P, pc_precision prec, void *d_spec,

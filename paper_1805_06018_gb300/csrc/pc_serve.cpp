@@ -1,0 +1,510 @@
+// Serving loop and autotuner.
+//
+// A scheduler thread owns the device work.  Submitted requests wait in a
+// FIFO queue.  Whenever a launch slot is free it takes the longest prefix of
+// the queue that fits the slot (at most max_requests_per_launch requests and
+// the slot's ordering-flag arena), the in-flight limit and the memory budget,
+// writes one launch descriptor (one segment per request) into the slot's
+// pinned buffer and replays the slot's captured graph: descriptor copy,
+// zero-fill, persistent fused kernel.  The kernel raises a flag in mapped host
+// memory when a request's last work item is done; the scheduler turns flags
+// into completions (timestamps, budget release).  Slots live on separate
+// streams, so the next launch is already running while the previous one
+// drains: requests that arrive while others run are admitted as soon as a
+// slot and memory free up.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "pc_internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+constexpr int64_t kFlagArenaWords = int64_t(1) << 22;   // ordering flags per launch slot
+constexpr int kMaxInflightCap = 1024;
+
+struct Request {
+    uint64_t ticket = 0;
+    pc_operator *op = nullptr;
+    int32_t nrhs = 0;
+    const void *x = nullptr;
+    void *y = nullptr;
+    int64_t flag_words = 0;
+    int64_t scratch_bytes = 0;
+    double submit_s = 0, launch_s = 0, finish_s = 0;
+    int state = 0;      // 0 queued, 1 launched, 2 done, 3 failed
+    int status = PC_OK;
+    int hslot = -1;     // host completion flag index
+    int launch_requests = 0;
+};
+
+struct LaunchSlot {
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    pc::LaunchDesc *h_desc = nullptr;   // pinned
+    pc::LaunchDesc *d_desc = nullptr;
+    uint32_t *d_flags = nullptr;
+    uint32_t *d_seg_done = nullptr;
+    unsigned long long *d_counter = nullptr;
+    int32_t *d_status = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    std::vector<Request *> reqs;
+};
+
+}  // namespace
+
+struct pc_server {
+    pc_context *ctx = nullptr;
+    pc_serve_config cfg{};
+    std::mutex mu;
+    std::condition_variable cv;
+    std::thread th;
+    bool stop = false;
+    std::string fatal;
+    std::deque<Request *> queue;
+    std::unordered_map<uint64_t, Request *> all;
+    uint64_t next_ticket = 1;
+    std::vector<LaunchSlot> slots;
+    uint32_t *h_flags = nullptr;        // mapped pinned host memory
+    uint32_t *d_hflags = nullptr;
+    std::vector<int> free_hslots;
+    int64_t budget_used = 0, budget_peak = 0;
+    std::unordered_map<pc_operator *, int> op_inflight;
+    int inflight = 0;
+    std::vector<double> latencies;
+    int64_t rhs_done = 0, launches = 0;
+    double first_submit = -1.0, last_finish = 0.0;
+    Clock::time_point t0;
+    int ctas = 0;
+    size_t smem = 0;
+
+    double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+};
+
+namespace {
+
+pc_status srv_fail(pc_server *s, pc_status st, const std::string &msg) {
+    if (s && s->ctx) s->ctx->last_error = msg;
+    return st;
+}
+
+void release_budget(pc_server *s, Request *r) {
+    s->budget_used -= r->scratch_bytes;
+    auto it = s->op_inflight.find(r->op);
+    if (it != s->op_inflight.end() && --it->second == 0) {
+        s->budget_used -= int64_t(r->op->device_bytes);
+        s->op_inflight.erase(it);
+    }
+    --s->inflight;
+    if (r->hslot >= 0) s->free_hslots.push_back(r->hslot);
+    r->hslot = -1;
+}
+
+// Bytes the request adds to the budget if admitted now.
+int64_t admission_bytes(pc_server *s, const Request *r) {
+    return r->scratch_bytes + (s->op_inflight.count(r->op) ? 0 : int64_t(r->op->device_bytes));
+}
+
+void reap(pc_server *s) {
+    for (auto &sl : s->slots) {
+        if (!sl.busy) continue;
+        const double t = s->now();
+        for (Request *r : sl.reqs) {
+            if (r->state != 1) continue;
+            if (reinterpret_cast<volatile uint32_t *>(s->h_flags)[r->hslot] != 0u) {
+                r->state = 2;
+                r->finish_s = t;
+                s->latencies.push_back(r->finish_s - r->submit_s);
+                s->rhs_done += r->nrhs;
+                s->last_finish = t;
+                release_budget(s, r);
+            }
+        }
+        const cudaError_t q = cudaEventQuery(sl.done);
+        if (q == cudaErrorNotReady) continue;
+        // the launch has ended: anything not flagged failed
+        int32_t status = 0;
+        if (q == cudaSuccess &&
+            cudaMemcpyAsync(&status, sl.d_status, sizeof(status), cudaMemcpyDeviceToHost, sl.stream) == cudaSuccess)
+            cudaStreamSynchronize(sl.stream);
+        for (Request *r : sl.reqs) {
+            if (r->state != 1) continue;
+            if (reinterpret_cast<volatile uint32_t *>(s->h_flags)[r->hslot] != 0u && q == cudaSuccess && !status) {
+                r->state = 2;
+                r->finish_s = s->now();
+                s->latencies.push_back(r->finish_s - r->submit_s);
+                s->rhs_done += r->nrhs;
+                s->last_finish = r->finish_s;
+            } else {
+                r->state = 3;
+                r->status = q != cudaSuccess ? PC_ERR_CUDA : PC_ERR_TIMEOUT;
+            }
+            release_budget(s, r);
+        }
+        if (status) cudaMemsetAsync(sl.d_status, 0, sizeof(int32_t), sl.stream);
+        sl.reqs.clear();
+        sl.busy = false;
+    }
+}
+
+void try_launch(pc_server *s) {
+    for (auto &sl : s->slots) {
+        if (sl.busy || s->queue.empty()) continue;
+        std::vector<Request *> take;
+        int64_t words = 0, extra = 0;
+        std::unordered_map<pc_operator *, int> seen;
+        for (Request *r : s->queue) {
+            if (int(take.size()) >= s->cfg.max_requests_per_launch) break;
+            if (s->inflight + int(take.size()) >= s->cfg.max_inflight) break;
+            if (s->free_hslots.size() <= take.size()) break;
+            if (words + r->flag_words > kFlagArenaWords) break;
+            int64_t add = r->scratch_bytes;
+            if (!s->op_inflight.count(r->op) && !seen.count(r->op)) add += int64_t(r->op->device_bytes);
+            if (s->budget_used + extra + add > s->cfg.hbm_budget_bytes) break;   // FIFO: no overtaking
+            take.push_back(r);
+            seen[r->op] = 1;
+            words += r->flag_words;
+            extra += add;
+        }
+        if (take.empty()) return;
+        pc::LaunchDesc &d = *sl.h_desc;
+        std::memset(&d, 0, sizeof(pc::LaunchDesc));
+        int64_t items = 0, woff = 0;
+        const double t = s->now();
+        for (size_t q = 0; q < take.size(); ++q) {
+            Request *r = take[q];
+            pc_operator *op = r->op;
+            pc::Segment &sg = d.seg[q];
+            const int32_t npairs = (r->nrhs + 1) / 2;
+            pc::ApplyParams &p = sg.p;
+            p.x = r->x;
+            p.y = r->y;
+            p.ldx = op->N;
+            p.ldy = op->N;
+            p.nrhs = r->nrhs;
+            p.npairs = npairs;
+            p.n[0] = int32_t(op->shape[0]);
+            p.n[1] = int32_t(op->shape[1]);
+            p.n[2] = int32_t(op->shape[2]);
+            p.R = op->R;
+            p.tiles = op->d_tiles;
+            p.color_start = op->d_color_start;
+            p.n_colors = op->n_colors;
+            p.dep_start = op->d_dep_start;
+            p.dep = op->d_dep;
+            p.done = sl.d_flags + woff;
+            p.done_ld = npairs;
+            p.epoch = 1u;
+            p.ctrl = nullptr;
+            p.spec = op->d_spec;
+            p.spec_stride = op->spec_stride;
+            p.w = op->d_w;
+            p.tw = op->d_tw;
+            p.total_items = int64_t(op->n_tiles) * npairs;
+            sg.item_begin = items;
+            r->hslot = s->free_hslots.back();
+            s->free_hslots.pop_back();
+            reinterpret_cast<volatile uint32_t *>(s->h_flags)[r->hslot] = 0u;
+            sg.slot = r->hslot;
+            items += p.total_items;
+            woff += r->flag_words;
+            // admit
+            if (!s->op_inflight.count(op)) s->budget_used += int64_t(op->device_bytes);
+            s->op_inflight[op]++;
+            s->budget_used += r->scratch_bytes;
+            ++s->inflight;
+            r->state = 1;
+            r->launch_s = t;
+            r->launch_requests = int(take.size());
+        }
+        d.nseg = int32_t(take.size());
+        d.total_items = items;
+        s->budget_peak = std::max(s->budget_peak, s->budget_used);
+        for (size_t q = 0; q < take.size(); ++q) s->queue.pop_front();
+        cudaError_t e = cudaGraphLaunch(sl.exec, sl.stream);
+        if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
+        sl.reqs = take;
+        sl.busy = true;
+        ++s->launches;
+        if (e != cudaSuccess) s->fatal = std::string("graph launch: ") + cudaGetErrorString(e);
+    }
+}
+
+void scheduler(pc_server *s) {
+    cudaSetDevice(s->ctx->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        reap(s);
+        if (!s->stop) try_launch(s);
+        bool busy = false;
+        for (auto &sl : s->slots) busy = busy || sl.busy;
+        if (s->stop && !busy) break;
+        if (!busy && s->queue.empty()) {
+            s->cv.wait_for(lk, std::chrono::milliseconds(50));
+        } else {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(10));
+            lk.lock();
+        }
+    }
+}
+
+void free_server(pc_server *s) {
+    for (auto &sl : s->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.exec) cudaGraphExecDestroy(sl.exec);
+        if (sl.graph) cudaGraphDestroy(sl.graph);
+        if (sl.h_desc) cudaFreeHost(sl.h_desc);
+        cudaFree(sl.d_desc);
+        cudaFree(sl.d_flags);
+        cudaFree(sl.d_seg_done);
+        cudaFree(sl.d_counter);
+        cudaFree(sl.d_status);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+    }
+    if (s->h_flags) cudaFreeHost(s->h_flags);
+    for (auto &kv : s->all) delete kv.second;
+    delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+pc_status pc_serve_create(pc_context *ctx, const pc_serve_config *cfg, pc_server **out) {
+    if (!ctx || !cfg || !out) return PC_ERR_ARG;
+    *out = nullptr;
+    if (cfg->hbm_budget_bytes <= 0 || cfg->max_inflight < 1 || cfg->max_inflight > kMaxInflightCap ||
+        cfg->streams < 1 || cfg->streams > 4 || cfg->max_requests_per_launch < 1 ||
+        cfg->max_requests_per_launch > pc::kMaxSegments) {
+        ctx->last_error = "invalid serving configuration";
+        return PC_ERR_ARG;
+    }
+    if (cudaSetDevice(ctx->device) != cudaSuccess) {
+        ctx->last_error = "cannot select the context's device";
+        return PC_ERR_CUDA;
+    }
+    auto *s = new pc_server;
+    s->ctx = ctx;
+    s->cfg = *cfg;
+    s->t0 = Clock::now();
+    int per_sm = 0;
+    cudaError_t e = pc::fft2d_configure(128, PC_FP32, &per_sm, &s->smem);
+    s->ctas = ctx->num_sms * std::max(per_sm, 1);
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&s->h_flags), sizeof(uint32_t) * kMaxInflightCap,
+                                            cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&s->d_hflags), s->h_flags, 0);
+    if (e == cudaSuccess) std::memset(s->h_flags, 0, sizeof(uint32_t) * kMaxInflightCap);
+    for (int q = kMaxInflightCap - 1; q >= 0; --q) s->free_hslots.push_back(q);
+    s->slots.resize(cfg->streams);
+    for (auto &sl : s->slots) {
+        if (e != cudaSuccess) break;
+        e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&sl.h_desc), sizeof(pc::LaunchDesc), 0);
+        if (e == cudaSuccess) e = cudaMalloc(&sl.d_desc, sizeof(pc::LaunchDesc));
+        if (e == cudaSuccess) e = cudaMalloc(&sl.d_flags, sizeof(uint32_t) * kFlagArenaWords);
+        if (e == cudaSuccess) e = cudaMalloc(&sl.d_seg_done, sizeof(uint32_t) * pc::kMaxSegments);
+        if (e == cudaSuccess) e = cudaMalloc(&sl.d_counter, sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMalloc(&sl.d_status, sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMemset(sl.d_status, 0, sizeof(int32_t));
+        if (e == cudaSuccess) std::memset(sl.h_desc, 0, sizeof(pc::LaunchDesc));
+        // capture: descriptor upload, zero-fill, persistent fused kernel
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = cudaMemcpyAsync(sl.d_desc, sl.h_desc, sizeof(pc::LaunchDesc), cudaMemcpyHostToDevice,
+                                             sl.stream);
+            cudaError_t e2 = e1 == cudaSuccess ? pc::launch_round(sl.d_desc, sl.d_counter, sl.d_status, sl.d_seg_done,
+                                                                  s->d_hflags, s->ctas, s->smem, sl.stream)
+                                               : e1;
+            e = cudaStreamEndCapture(sl.stream, &sl.graph);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&sl.exec, sl.graph, 0);
+    }
+    if (e != cudaSuccess) {
+        ctx->last_error = std::string("pc_serve_create: ") + cudaGetErrorString(e);
+        free_server(s);
+        return e == cudaErrorMemoryAllocation ? PC_ERR_NOMEM : PC_ERR_CUDA;
+    }
+    s->th = std::thread(scheduler, s);
+    *out = s;
+    return PC_OK;
+}
+
+pc_status pc_serve_submit(pc_server *s, pc_operator *op, int32_t nrhs, const void *x, void *y, uint32_t flags,
+                          uint64_t *ticket) {
+    if (!s || !ticket) return PC_ERR_ARG;
+    if (!op || nrhs < 1 || !x || !y || flags != 0) return srv_fail(s, PC_ERR_ARG, "bad request arguments");
+    if (op->ctx->device != s->ctx->device) return srv_fail(s, PC_ERR_ARG, "operator lives on another device");
+    if (op->d != 2 || op->prec != PC_FP32 || op->P != 128)
+        return srv_fail(s, PC_ERR_UNSUPPORTED, "served operators are 2D, FP32, fft_size 128");
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) % 4)
+        return srv_fail(s, PC_ERR_ARG, "x and y must be 4-byte aligned");
+    auto *r = new Request;
+    r->op = op;
+    r->nrhs = nrhs;
+    r->x = x;
+    r->y = y;
+    r->flag_words = int64_t(op->n_tiles) * ((nrhs + 1) / 2);
+    r->scratch_bytes = r->flag_words * 4;
+    if (r->flag_words > kFlagArenaWords) {
+        delete r;
+        return srv_fail(s, PC_ERR_BUDGET, "request needs more ordering flags than a launch slot holds; split it");
+    }
+    if (int64_t(op->device_bytes) + r->scratch_bytes > s->cfg.hbm_budget_bytes) {
+        delete r;
+        return srv_fail(s, PC_ERR_BUDGET, "operator and request exceed the serving budget");
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) {
+            delete r;
+            return srv_fail(s, PC_ERR_ARG, "server is stopping");
+        }
+        r->ticket = s->next_ticket++;
+        r->submit_s = s->now();
+        if (s->first_submit < 0) s->first_submit = r->submit_s;
+        s->queue.push_back(r);
+        s->all[r->ticket] = r;
+        *ticket = r->ticket;
+    }
+    s->cv.notify_one();
+    return PC_OK;
+}
+
+pc_status pc_serve_poll(pc_server *s, uint64_t ticket, pc_request_info *info) {
+    if (!s) return PC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!s->fatal.empty()) s->ctx->last_error = s->fatal;
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return srv_fail(s, PC_ERR_ARG, "unknown ticket");
+    Request *r = it->second;
+    if (r->state < 2) return PC_ERR_NOT_READY;
+    if (info) {
+        info->submit_s = r->submit_s;
+        info->launch_s = r->launch_s;
+        info->finish_s = r->finish_s;
+        info->nrhs = r->nrhs;
+        info->launch_requests = r->launch_requests;
+        info->status = r->state == 2 ? PC_OK : r->status;
+    }
+    const pc_status st = r->state == 2 ? PC_OK : pc_status(r->status);
+    s->all.erase(it);
+    delete r;
+    if (st != PC_OK) return srv_fail(s, st, "the request's launch failed");
+    return PC_OK;
+}
+
+pc_status pc_serve_stats_get(pc_server *s, pc_serve_stats *st) {
+    if (!s || !st) return PC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memset(st, 0, sizeof(*st));
+    st->completed = int64_t(s->latencies.size());
+    st->rhs_completed = s->rhs_done;
+    st->launches = s->launches;
+    st->peak_bytes = s->budget_peak;
+    if (!s->latencies.empty()) {
+        std::vector<double> v = s->latencies;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) { return v[std::min(v.size() - 1, size_t(q * double(v.size() - 1) + 0.5))]; };
+        st->p50_latency_s = pct(0.50);
+        st->p99_latency_s = pct(0.99);
+        double sum = 0;
+        for (double x : v) sum += x;
+        st->mean_latency_s = sum / double(v.size());
+        st->busy_s = s->last_finish - s->first_submit;
+        st->rhs_per_s = st->busy_s > 0 ? double(s->rhs_done) / st->busy_s : 0.0;
+    }
+    return PC_OK;
+}
+
+pc_status pc_serve_destroy(pc_server *s) {
+    if (!s) return PC_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_one();
+    if (s->th.joinable()) s->th.join();
+    free_server(s);
+    return PC_OK;
+}
+
+pc_status pc_autotune(pc_context *ctx, const pc_box *box, const pc_grid *grid, int32_t radius, const double *impulse,
+                      const double *weights, pc_precision prec, int32_t nrhs, pc_tuning *best, double *best_ms) {
+    if (!ctx || !best || nrhs < 1) return PC_ERR_ARG;
+    std::vector<pc_tuning> cands;
+    for (int P : {64, 128}) {
+        if (prec == PC_FP64 && P != 64) continue;
+        const int Wfull = 2 * radius + 1;
+        if (Wfull + 15 > P && P == 64) continue;   // no useful tile without splitting at P = 64
+        for (int frac : {4, 3}) {
+            pc_tuning t{};
+            t.fft_size = P;
+            const int tmax = std::min(P - Wfull + 1, (2 * P) / 3);
+            t.tile = frac == 4 ? 0 : std::max(8, tmax * 3 / 4);
+            if (frac == 3 && (tmax < 16 || t.tile >= tmax)) continue;
+            cands.push_back(t);
+        }
+    }
+    double bms = 1e300;
+    pc_tuning bt{};
+    std::string last_err;
+    void *x = nullptr, *y = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaSetDevice(ctx->device);
+    for (const pc_tuning &t : cands) {
+        pc_operator *op = nullptr;
+        if (pc_build_spectra(ctx, box, grid, radius, impulse, weights, prec, &t, &op) != PC_OK) {
+            last_err = ctx->last_error;
+            continue;
+        }
+        const size_t bytes = size_t(nrhs) * op->N * op->elem;
+        if (!x) {
+            if (cudaMalloc(&x, bytes) != cudaSuccess || cudaMalloc(&y, bytes) != cudaSuccess ||
+                cudaMemset(x, 0, bytes) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+                cudaEventCreate(&e1) != cudaSuccess) {
+                pc_operator_destroy(op);
+                break;
+            }
+        }
+        for (int q = 0; q < 2; ++q) pc_apply_batched(op, nrhs, x, op->N, y, op->N, nullptr);
+        cudaEventRecord(e0, nullptr);
+        const int reps = 5;
+        for (int q = 0; q < reps; ++q) pc_apply_batched(op, nrhs, x, op->N, y, op->N, nullptr);
+        cudaEventRecord(e1, nullptr);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = double(ms) / reps;
+        if (per < bms) {
+            bms = per;
+            bt = t;
+        }
+        pc_operator_destroy(op);
+    }
+    cudaFree(x);
+    cudaFree(y);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (bms >= 1e300) {
+        ctx->last_error = "no candidate launch shape could be built: " + last_err;
+        return PC_ERR_UNSUPPORTED;
+    }
+    *best = bt;
+    if (best_ms) *best_ms = bms;
+    return PC_OK;
+}
+
+}  // extern "C"

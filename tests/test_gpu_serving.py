@@ -1,0 +1,115 @@
+"""Serving loop (pc_serve_*): requests over several resident operators with
+uneven right-hand-side counts are batched into shared persistent launches;
+each result equals the same request applied alone (pc_apply_batched), within
+the FP32 tolerance and in fact bit for bit."""
+import time
+
+import numpy as np
+import pytest
+
+import workloads
+from workloads import configs
+
+from gpu_common import context, make_pair, rel_l2
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ops():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    context()
+    out = []
+    wl = configs.fp32_512(1)
+    out.append(make_pair(wl.shape, wl.cells, wl.kernel, "fp32")[0])
+    for shape, npts, R in [((256, 256), (9, 9), 24), ((200, 300), (4, 6), 12)]:
+        cells = workloads.regular_grid(shape, npts)
+        kern = workloads.GaussianAniso2D(lambda x: 2.0 + 0 * x[..., 0], lambda x: 3.0 + np.sin(x[..., 0] / 30.0),
+                                         lambda x: 0.4 + 0 * x[..., 0], R)
+        out.append(make_pair(shape, cells, kern, "fp32", fft_size=128)[0])
+    return out
+
+
+def _wait(srv, tickets, timeout=60.0):
+    done = {}
+    t0 = time.time()
+    while len(done) < len(tickets):
+        for t in tickets:
+            if t not in done:
+                r = srv.poll(t)
+                if r is not None:
+                    done[t] = r
+        assert time.time() - t0 < timeout, "requests did not finish"
+        time.sleep(0.001)
+    return done
+
+
+def test_mixed_requests_match_alone(ops):
+    import paper_1805_06018_gb300 as pcg
+    srv = pcg.Server(context(), budget_bytes=8 << 30, streams=2, max_requests_per_launch=16)
+    rng = np.random.default_rng(0)
+    prepared = []
+    for q in range(24):
+        op = ops[q % len(ops)]
+        nrhs = int(rng.integers(1, 8))
+        x = torch.from_numpy(workloads.rhs(500 + q, nrhs, op.shape)).cuda()
+        prepared.append((op, x, torch.full_like(x, float("nan"))))
+    torch.cuda.synchronize()
+    # submitted back to back: requests queue behind the busy launch slots
+    jobs = [(op, x, y, srv.submit(op, x, y)) for op, x, y in prepared]
+    done = _wait(srv, [j[3] for j in jobs])
+    for op, x, y, t in jobs:
+        alone = op.apply(x)
+        torch.cuda.synchronize()
+        assert np.all(rel_l2(y.cpu().numpy(), alone.cpu().numpy()) <= 1e-5)
+        assert torch.equal(y, alone)
+        assert done[t]["status"] == 0 and done[t]["finish_s"] >= done[t]["launch_s"] >= done[t]["submit_s"]
+    st = srv.stats()
+    assert st["completed"] == 24
+    assert st["launches"] < 24                        # requests shared launches
+    assert max(d["launch_requests"] for d in done.values()) > 1
+    assert st["p99_latency_s"] >= st["p50_latency_s"] > 0
+    srv.close()
+
+
+def test_budget_admission(ops):
+    import paper_1805_06018_gb300 as pcg
+    big = max(op.info()["device_bytes"] for op in ops)
+    # room for one operator at a time: requests on different operators serialise
+    srv = pcg.Server(context(), budget_bytes=big + (4 << 20), streams=2)
+    tickets, jobs = [], []
+    for q in range(6):
+        op = ops[q % len(ops)]
+        x = torch.from_numpy(workloads.rhs(900 + q, 3, op.shape)).cuda()
+        y = torch.empty_like(x)
+        tickets.append(srv.submit(op, x, y))
+        jobs.append((op, x, y))
+    _wait(srv, tickets)
+    for op, x, y in jobs:
+        assert torch.equal(y, op.apply(x))
+    st = srv.stats()
+    assert st["peak_bytes"] <= big + (4 << 20)
+    srv.close()
+    small = pcg.Server(context(), budget_bytes=1 << 20)
+    x = torch.zeros(1, *ops[0].shape, device="cuda")
+    with pytest.raises(pcg.PCError) as e:
+        small.submit(ops[0], x, torch.empty_like(x))
+    assert e.value.status == pcg.binding.PC_ERR_BUDGET
+    with pytest.raises(pcg.PCError):
+        small.poll(12345)
+    small.close()
+
+
+def test_autotune_picks_a_valid_shape():
+    import paper_1805_06018_gb300 as pcg
+    wl = configs.fp32_512(1)
+    pts = pcg.pc_sample_points(wl.shape, wl.cells)
+    phi = workloads.impulse_windows(wl.shape, pts, wl.kernel)
+    best, ms = pcg.pc_autotune(context(), wl.shape, wl.cells, wl.radius, phi, "fp32", nrhs=8)
+    assert best["fft_size"] in (64, 128) and ms > 0
+    op, orc = make_pair(wl.shape, wl.cells, wl.kernel, "fp32", fft_size=best["fft_size"], tile=best["tile"])
+    x = workloads.rhs(3, 2, wl.shape)
+    y = op.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert np.all(rel_l2(y, orc.apply(x)) <= 1e-5)
