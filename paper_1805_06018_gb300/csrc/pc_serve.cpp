@@ -13,6 +13,7 @@
 // drains: requests that arrive while others run are admitted as soon as a
 // slot and memory free up.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -43,6 +44,7 @@ struct Request {
     int status = PC_OK;
     int hslot = -1;     // host completion flag index
     int launch_requests = 0;
+    std::string error;
 };
 
 struct LaunchSlot {
@@ -138,7 +140,9 @@ void reap(pc_server *s) {
             cudaStreamSynchronize(sl.stream);
         for (Request *r : sl.reqs) {
             if (r->state != 1) continue;
-            if (reinterpret_cast<volatile uint32_t *>(s->h_flags)[r->hslot] != 0u && q == cudaSuccess && !status) {
+            // a launch that ended with a clean status has finished every item of
+            // every request in it; the mapped-memory flags only report earlier
+            if (q == cudaSuccess && !status) {
                 r->state = 2;
                 r->finish_s = s->now();
                 s->latencies.push_back(r->finish_s - r->submit_s);
@@ -146,7 +150,14 @@ void reap(pc_server *s) {
                 s->last_finish = r->finish_s;
             } else {
                 r->state = 3;
-                r->status = q != cudaSuccess ? PC_ERR_CUDA : PC_ERR_TIMEOUT;
+                if (q != cudaSuccess) {
+                    r->status = PC_ERR_CUDA;
+                    r->error = std::string("launch failed: ") + cudaGetErrorString(q);
+                } else if (status) {
+                    r->status = PC_ERR_TIMEOUT;
+                    r->error = status == 1 ? "a bounded overlap-order wait gave up"
+                                           : "a bounded spectrum-copy wait gave up";
+                }
             }
             release_budget(s, r);
         }
@@ -226,16 +237,26 @@ void try_launch(pc_server *s) {
             r->launch_s = t;
             r->launch_requests = int(take.size());
         }
+        std::atomic_thread_fence(std::memory_order_seq_cst);   // flag resets land before the launch
         d.nseg = int32_t(take.size());
         d.total_items = items;
         s->budget_peak = std::max(s->budget_peak, s->budget_used);
         for (size_t q = 0; q < take.size(); ++q) s->queue.pop_front();
         cudaError_t e = cudaGraphLaunch(sl.exec, sl.stream);
         if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
+        if (e != cudaSuccess) {
+            s->fatal = std::string("graph launch: ") + cudaGetErrorString(e);
+            for (Request *r : take) {
+                r->state = 3;
+                r->status = PC_ERR_CUDA;
+                r->error = s->fatal;
+                release_budget(s, r);
+            }
+            continue;
+        }
         sl.reqs = take;
         sl.busy = true;
         ++s->launches;
-        if (e != cudaSuccess) s->fatal = std::string("graph launch: ") + cudaGetErrorString(e);
     }
 }
 
@@ -400,9 +421,10 @@ pc_status pc_serve_poll(pc_server *s, uint64_t ticket, pc_request_info *info) {
         info->status = r->state == 2 ? PC_OK : r->status;
     }
     const pc_status st = r->state == 2 ? PC_OK : pc_status(r->status);
+    const std::string msg = r->error;
     s->all.erase(it);
     delete r;
-    if (st != PC_OK) return srv_fail(s, st, "the request's launch failed");
+    if (st != PC_OK) return srv_fail(s, st, msg);
     return PC_OK;
 }
 
