@@ -85,7 +85,8 @@ typedef struct {
 /* Launch-shape knobs; a NULL pc_tuning, or a field of 0, means "choose". */
 typedef struct {
     int32_t fft_size;        /* padded FFT extent P per axis: 64, 128 (2D) */
-    int32_t tile;            /* input tile extent T <= min(P - 2R, 2P/3) (0: that bound) */
+    int32_t tile;            /* input tile extent T <= min(P - W + 1, 2P/3), W the kernel
+                                (sub-)window extent (2R+1 unless split) (0: that bound) */
     int32_t ctas_per_sm;     /* persistent CTAs per SM (0: occupancy limit) */
     int32_t reserved[5];
 } pc_tuning;

@@ -208,7 +208,7 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     // Input tiles of extent n and kernel (sub-)windows of extent ws need
     // n + ws - 1 <= P for the circular product to be the linear convolution;
     // the kernel stages the weight and two right-hand-side rows of a tile in
-    // one workspace row of 2P reals, so also 3n <= 2P.  When the window
+    // one workspace row of 2P reals (3n <= 2P).  When the window
     // 2R+1 leaves no room for a useful tile it is cut into nsub^2
     // sub-windows (nsub chosen to minimise the FFT work per input pixel,
     // nsub^2 / T^2).

@@ -29,6 +29,13 @@
 namespace pc {
 
 constexpr int kThreads2d = 512;
+// Threads per CTA.  16 warps with 128 registers keep a line's 16 values and
+// its 16 twiddles in registers; 32 warps at 64 registers (one line per
+// column) spilled and measured slower on GB300 (1.22 ms vs 1.07 ms for the
+// 512^2 x 64 workload).
+template <typename T, int P> struct KCfg {
+    static constexpr int threads = kThreads2d;
+};
 constexpr long long kSpinLimit = 1ll << 24;   // x >= 64 ns per spin: about a second at least
 constexpr long long kMbarLimit = 1ll << 24;   // try_wait rounds for the spectrum copy
 
@@ -51,11 +58,13 @@ template <typename T, int P> struct Smem2d {
     using C = typename Cx<T>::type;
     static constexpr int SPLD = P + 8;
     // phase C reuses the spectrum region as one FP32 staging row per line:
-    // re part [0, P+4), im part [P+8, 2P+12) floats
-    static constexpr int STAGE = 2 * (P + 8);
+    // re part [0, P+4), im part [P+12, 2P+16); the stride 2P+24 is 24 banks
+    // mod 32, so the four lines of a warp write disjoint banks
+    static constexpr int STAGE = 2 * P + 24;
+    static constexpr int IMOFF = P + 12;
     static constexpr size_t ws = size_t(P) * P * sizeof(C);
     static constexpr size_t spec = size_t(P / 2 + 1) * SPLD * sizeof(C);
-    static constexpr size_t stage = size_t(kThreads2d / FftShape<P>::R2) * STAGE * sizeof(float);
+    static constexpr size_t stage = size_t(KCfg<T, P>::threads / FftShape<P>::R2) * STAGE * sizeof(float);
     static constexpr size_t sp = spec > stage ? spec : stage;
     static constexpr size_t bytes = ws + sp + 16;
 };
@@ -142,7 +151,7 @@ __device__ __forceinline__ void add_row(const C *a, int t, unsigned lmask, float
             }
         }
     } else {
-        constexpr int IMOFF = P + 8;
+        constexpr int IMOFF = Smem2d<T, P>::IMOFF;
         // y row alignment (in elements, mod 4) and the aligned origin q <= lo of each part
         const int off0 = int((reinterpret_cast<uintptr_t>(y0) >> 2) & 3);
         const int off1 = int((reinterpret_cast<uintptr_t>(y1) >> 2) & 3);
@@ -186,11 +195,12 @@ __device__ __forceinline__ void add_row(const C *a, int t, unsigned lmask, float
 }
 
 template <typename T, int P>
-__global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const LaunchParams lp) {
+__global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const LaunchParams lp) {
     using C = typename Cx<T>::type;
     using L = Smem2d<T, P>;
     constexpr int R1 = FftShape<P>::R1, R2 = FftShape<P>::R2;
-    constexpr int LINES = kThreads2d / R2;
+    constexpr int NT = KCfg<T, P>::threads;
+    constexpr int LINES = NT / R2;
     constexpr int H = P / 2 + 1;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     C *S = reinterpret_cast<C *>(smem_raw);
@@ -209,7 +219,7 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const LaunchParams
     const unsigned lmask = FftShape<P>::line_mask();
     // every operator of a launch shares P, so the twiddle values W_P^k are the same
     const C *twg = static_cast<const C *>(lp.desc ? lp.desc->seg[0].p.tw : lp.one.p.tw);
-    C tw[R1];
+    C tw[R1];   // W_P^{t m} for this thread's t
 #pragma unroll
     for (int m = 0; m < R1; ++m) tw[m] = twg[(t * m) & (P - 1)];
     const C zero{T(0), T(0)};
@@ -267,7 +277,7 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const LaunchParams
         const Tile tile = p.tiles[ti];
         if (threadIdx.x == 0) mbar_arrive_expect_tx(mbar, uint32_t(H * P * sizeof(C)));
         __syncthreads();   // everyone has read s_next; the spectrum copy is announced
-        if (threadIdx.x == kThreads2d - 1) s_next = int64_t(atomicAdd(counter, 1ull));
+        if (threadIdx.x == NT - 1) s_next = int64_t(atomicAdd(counter, 1ull));
         const int n1 = tile.in_ext[0], n2 = tile.in_ext[1];
         const int i0 = tile.in_lo[0], j0 = tile.in_lo[1];
         const int L1 = n1 + tile.kext[0] - 1, L2 = n2 + tile.kext[1] - 1;   // <= P
@@ -288,8 +298,11 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const LaunchParams
         }
 
         // ---------------- phase A: stage w, x0, x1 rows (cp.async), weight, row FFTs
+        // rows of one warp sit 2P reals apart (same banks): shift each row's staging
+        // by (row & 3) * 8 reals when the three arrays leave room
+        const int shmul = 3 * n2 + 24 <= 2 * P ? 8 : 0;
         for (int i = line; i < n1; i += LINES) {
-            T *row = Sf + i * 2 * P;
+            T *row = Sf + i * 2 * P + (i & 3) * shmul;
             const int64_t xr = int64_t(i0 + i) * p.n[1] + j0;
             const T *wr = wt + int64_t(i) * tile.w_ld[0];
 #pragma unroll
@@ -305,7 +318,7 @@ __global__ void __launch_bounds__(kThreads2d, 1) fft2d_kernel(const LaunchParams
         cp_async_wait_all();
         __syncwarp(lmask);
         for (int i = line; i < n1; i += LINES) {
-            const T *row = Sf + i * 2 * P;
+            const T *row = Sf + i * 2 * P + (i & 3) * shmul;
             C a[R1];
 #pragma unroll
             for (int j = 0; j < R1; ++j) {
@@ -447,7 +460,7 @@ static cudaError_t configure_one(int *ctas_per_sm, size_t *smem) {
     cudaError_t e = cudaFuncSetAttribute(fft2d_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
     if (e != cudaSuccess) return e;
     int n = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fft2d_kernel<T, P>, kThreads2d, bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fft2d_kernel<T, P>, KCfg<T, P>::threads, bytes);
     if (e != cudaSuccess) return e;
     if (ctas_per_sm) *ctas_per_sm = n;
     if (smem) *smem = bytes;
@@ -476,11 +489,11 @@ cudaError_t launch_fft2d(const ApplyParams &p, int P, pc_precision prec, int cta
     lp.counter = reinterpret_cast<unsigned long long *>(p.ctrl);
     lp.status = p.ctrl + 2;
     if (prec == PC_FP64)
-        fft2d_kernel<double, 64><<<ctas, kThreads2d, smem, s>>>(lp);
+        fft2d_kernel<double, 64><<<ctas, KCfg<double, 64>::threads, smem, s>>>(lp);
     else if (P == 64)
-        fft2d_kernel<float, 64><<<ctas, kThreads2d, smem, s>>>(lp);
+        fft2d_kernel<float, 64><<<ctas, KCfg<float, 64>::threads, smem, s>>>(lp);
     else
-        fft2d_kernel<float, 128><<<ctas, kThreads2d, smem, s>>>(lp);
+        fft2d_kernel<float, 128><<<ctas, KCfg<float, 128>::threads, smem, s>>>(lp);
     return cudaGetLastError();
 }
 
@@ -516,7 +529,7 @@ cudaError_t launch_round(const LaunchDesc *d_desc, unsigned long long *counter, 
     lp.status = status;
     lp.seg_done = seg_done;
     lp.host_flags = host_flags;
-    fft2d_kernel<float, 128><<<ctas, kThreads2d, smem, s>>>(lp);
+    fft2d_kernel<float, 128><<<ctas, KCfg<float, 128>::threads, smem, s>>>(lp);
     return cudaGetLastError();
 }
 
