@@ -82,6 +82,7 @@ void free_operator(pc_operator *op) {
     cudaFree(op->d_done);
     cudaFree(op->d_ctrl);
     cudaFree(op->d_tw);
+    cudaFree(op->d_scratch);
     if (op->ev_begin) cudaEventDestroy(op->ev_begin);
     if (op->ev_end) cudaEventDestroy(op->ev_end);
     delete op;
@@ -200,9 +201,11 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     std::string err;
     pc_status st = pc::build_geometry(box, grid, g, err);
     if (st != PC_OK) return fail(ctx, st, err);
-    if (g.d != 2) return fail(ctx, PC_ERR_UNSUPPORTED, "only 2D operators are built in this version");
     if (radius < 1) return fail(ctx, PC_ERR_ARG, "radius must be >= 1");
-    int P = tune && tune->fft_size ? tune->fft_size : (prec == PC_FP64 ? 64 : 128);
+    const bool three = g.d == 3;
+    if (three && prec != PC_FP32) return fail(ctx, PC_ERR_UNSUPPORTED, "3D operators are FP32");
+    int P = tune && tune->fft_size ? tune->fft_size : (three || prec == PC_FP64 ? 64 : 128);
+    if (three && P != 64) return fail(ctx, PC_ERR_UNSUPPORTED, "3D operators use fft_size 64");
     if (prec == PC_FP64 && P != 64) return fail(ctx, PC_ERR_UNSUPPORTED, "FP64 operators use fft_size 64");
     if (prec == PC_FP32 && P != 64 && P != 128) return fail(ctx, PC_ERR_UNSUPPORTED, "FP32 2D fft_size must be 64 or 128");
     // Input tiles of extent n and kernel (sub-)windows of extent ws need
@@ -213,7 +216,7 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     // sub-windows (nsub chosen to minimise the FFT work per input pixel,
     // nsub^2 / T^2).
     const int Wfull = 2 * radius + 1;
-    const int cap = (2 * P) / 3;
+    const int cap = three ? P : (2 * P) / 3;   // the 3D kernel gathers directly, without staging
     pc::WindowSplit split;
     int T = 0;
     {
@@ -241,13 +244,13 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     if (!dg.ok) return fail(ctx, PC_ERR_CUDA, "cannot select the context's device");
     int ctas_per_sm = 0;
     size_t smem = 0;
-    cudaError_t e = pc::fft2d_configure(P, prec, &ctas_per_sm, &smem);
+    cudaError_t e = three ? pc::fft3d_configure(&ctas_per_sm) : pc::fft2d_configure(P, prec, &ctas_per_sm, &smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "configuring the patch kernel");
     if (ctas_per_sm < 1) return fail(ctx, PC_ERR_UNSUPPORTED, "patch kernel does not fit on an SM");
     if (tune && tune->ctas_per_sm > 0) ctas_per_sm = std::min(ctas_per_sm, int(tune->ctas_per_sm));
 
     const int r = int(g.pts.size());
-    const int64_t W = 2 * radius + 1, wsz = W * W;
+    const int64_t W = 2 * radius + 1, wsz = three ? W * W * W : W * W;
     // weights
     std::vector<double> w;
     std::vector<int64_t> woff;
@@ -333,32 +336,46 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     // spectra (FP64 on the device, rounded once), one per (patch, sub-window):
     // sub-window (s0, s1) of phi_k^E placed at [0, ws)^2, zero-padded
     const int ns = split.nsub, ws = split.ws;
-    const int nspec = r * ns * ns;
+    const int nsd = three ? ns * ns * ns : ns * ns;
+    const int nspec = r * nsd;
+    const size_t wvol = three ? size_t(ws) * ws * ws : size_t(ws) * ws;
     std::vector<double> psi;
     const double *psi_src = phiE.data();
     if (ns > 1) {
-        psi.assign(size_t(nspec) * ws * ws, 0.0);
+        psi.assign(size_t(nspec) * wvol, 0.0);
+        const int ns2 = three ? ns : 1, ws2 = three ? ws : 1, Wf2 = three ? Wfull : 1;
         for (int k = 0; k < r; ++k)
             for (int s0 = 0; s0 < ns; ++s0)
-                for (int s1 = 0; s1 < ns; ++s1) {
-                    double *dst = psi.data() + (size_t(k) * ns * ns + s0 * ns + s1) * ws * ws;
-                    for (int a = 0; a < ws && s0 * ws + a < Wfull; ++a)
-                        for (int b = 0; b < ws && s1 * ws + b < Wfull; ++b)
-                            dst[a * ws + b] = phiE[size_t(k) * wsz + (s0 * ws + a) * Wfull + (s1 * ws + b)];
-                }
+                for (int s1 = 0; s1 < ns; ++s1)
+                    for (int s2 = 0; s2 < ns2; ++s2) {
+                        double *dst = psi.data() + (size_t(k) * nsd + (s0 * ns + s1) * ns2 + s2) * wvol;
+                        for (int a = 0; a < ws && s0 * ws + a < Wfull; ++a)
+                            for (int b = 0; b < ws && s1 * ws + b < Wfull; ++b)
+                                for (int c = 0; c < ws2 && s2 * ws2 + c < Wf2; ++c)
+                                    dst[(size_t(a) * ws + b) * ws2 + c] =
+                                        phiE[size_t(k) * wsz + ((size_t(s0 * ws + a) * Wfull + (s1 * ws + b)) * Wf2 +
+                                                                (s2 * ws2 + c))];
+                    }
         psi_src = psi.data();
     }
-    op->spec_stride = int64_t(P / 2 + 1) * P;
+    op->spec_stride = three ? int64_t(P / 2 + 1) * P * P : int64_t(P / 2 + 1) * P;
     op->spec_bytes = size_t(nspec) * op->spec_stride * 2 * op->elem;
     double *d_psi = nullptr;
-    const size_t psi_elems = size_t(nspec) * ws * ws;
+    const size_t psi_elems = size_t(nspec) * wvol;
     e = cudaMalloc(&op->d_spec, op->spec_bytes);
     if (e == cudaSuccess) {
         acct += op->spec_bytes;
         e = cudaMalloc(&d_psi, sizeof(double) * psi_elems);
     }
     if (e == cudaSuccess) e = cudaMemcpy(d_psi, psi_src, sizeof(double) * psi_elems, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = pc::build_spectra_2d(d_psi, nspec, ws, P, prec, op->d_spec, d_tw64, nullptr);
+    if (e == cudaSuccess)
+        e = three ? pc::build_spectra_3d(d_psi, nspec, ws, P, op->d_spec, d_tw64, nullptr)
+                  : pc::build_spectra_2d(d_psi, nspec, ws, P, prec, op->d_spec, d_tw64, nullptr);
+    if (e == cudaSuccess && three) {
+        const size_t sb = pc::fft3d_scratch_bytes(op->ctas);
+        e = cudaMalloc(&op->d_scratch, sb);
+        if (e == cudaSuccess) acct += sb;
+    }
     cudaFree(d_psi);
     cudaFree(d_tw64);
     if (e != cudaSuccess) return bail(e, "building spectra");
@@ -461,7 +478,7 @@ pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t
         if ((e = cudaEventCreate(&op->ev_end)) != cudaSuccess) return cuda_fail(ctx, e, "creating events");
     }
     cudaEventRecord(op->ev_begin, s);
-    e = pc::launch_fft2d(p, op->P, op->prec, ctas, s);
+    e = op->d == 3 ? pc::launch_fft3d(p, ctas, op->d_scratch, s) : pc::launch_fft2d(p, op->P, op->prec, ctas, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the patch kernel");
     cudaEventRecord(op->ev_end, s);
     op->timed = true;
@@ -479,7 +496,7 @@ pc_status pc_apply_plain(pc_operator *op, int32_t nrhs, const void *x, int64_t l
                          pc_stream stream) {
     if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
     pc_context *ctx = op->ctx;
-    if (op->prec != PC_FP32) return fail(ctx, PC_ERR_UNSUPPORTED, "the plain path is FP32 only");
+    if (op->prec != PC_FP32 || op->d != 2) return fail(ctx, PC_ERR_UNSUPPORTED, "the plain path is 2D FP32 only");
     if (nrhs < 0) return fail(ctx, PC_ERR_ARG, "nrhs < 0");
     if (nrhs == 0) return PC_OK;
     if (!x || !y) return fail(ctx, PC_ERR_ARG, "null x or y");

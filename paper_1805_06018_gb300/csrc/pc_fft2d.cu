@@ -39,18 +39,6 @@ template <typename T, int P> struct KCfg {
 constexpr long long kSpinLimit = 1ll << 24;   // x >= 64 ns per spin: about a second at least
 constexpr long long kMbarLimit = 1ll << 24;   // try_wait rounds for the spectrum copy
 
-template <int P, typename C> struct RowScratch {
-    C *S;
-    int row;
-    __device__ __forceinline__ C ld(int s) const { return S[row * P + (s ^ swz(row))]; }
-    __device__ __forceinline__ void st(int s, C v) const { S[row * P + (s ^ swz(row))] = v; }
-};
-template <int P, typename C> struct ColScratch {
-    C *S;
-    int col;
-    __device__ __forceinline__ C ld(int s) const { return S[s * P + (col ^ swz(s))]; }
-    __device__ __forceinline__ void st(int s, C v) const { S[s * P + (col ^ swz(s))] = v; }
-};
 
 // Shared memory: the P x P complex workspace, then the patch's half spectrum
 // ([P/2+1] columns of P values, rows padded to P + 8 values), then an mbarrier.

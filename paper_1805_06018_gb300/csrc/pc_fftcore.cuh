@@ -166,4 +166,19 @@ __device__ __forceinline__ void fft_line(C *a, const C *tw, int t, Scratch &scr,
     for (int j = 0; j < R1; ++j) a[j] = b[j];
 }
 
+// Line scratch inside a P x P shared workspace laid out row * P + (col ^ swz(row)):
+// a row, or a column (positions are then row indices).
+template <int P, typename C> struct RowScratch {
+    C *S;
+    int row;
+    __device__ __forceinline__ C ld(int s) const { return S[row * P + (s ^ swz(row))]; }
+    __device__ __forceinline__ void st(int s, C v) const { S[row * P + (s ^ swz(row))] = v; }
+};
+template <int P, typename C> struct ColScratch {
+    C *S;
+    int col;
+    __device__ __forceinline__ C ld(int s) const { return S[s * P + (col ^ swz(s))]; }
+    __device__ __forceinline__ void st(int s, C v) const { S[s * P + (col ^ swz(s))] = v; }
+};
+
 }  // namespace pc

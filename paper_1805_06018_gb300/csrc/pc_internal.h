@@ -173,6 +173,7 @@ struct pc_operator {
     int32_t done_cap = 0;
     int32_t *d_ctrl = nullptr;
     void *d_tw = nullptr;
+    void *d_scratch = nullptr;   // 3D: per-CTA spectrum volumes
     uint32_t epoch = 0;
     cudaStream_t last_stream = nullptr;
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;   // around the fused kernel of the last apply
@@ -200,6 +201,12 @@ cudaError_t fft2d_configure(int P, pc_precision prec, int *ctas_per_sm, size_t *
 // d_psi: [nspec][W][W] FP64 windows placed at [0, W)^2; spectra [nspec][P/2+1][P]
 cudaError_t build_spectra_2d(const double *d_psi, int nspec, int W, int P, pc_precision prec, void *d_spec,
                              const double2 *d_tw64, cudaStream_t s);
+// 3D patch path (pc_fft3d.cu), FP32, P = 64
+cudaError_t fft3d_configure(int *ctas_per_sm);
+cudaError_t launch_fft3d(const ApplyParams &p, int ctas, void *scratch, cudaStream_t s);
+size_t fft3d_scratch_bytes(int ctas);
+cudaError_t build_spectra_3d(const double *d_psi, int nspec, int W, int P, void *d_spec, const double2 *d_tw64,
+                             cudaStream_t s);
 pc_status plain_apply(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
                       cudaStream_t s, std::string &err);
 void plain_free(pc_operator *op);

@@ -71,6 +71,7 @@ extern "C" pc_status pc_apply_batched_noalloc(pc_operator *op, int32_t nrhs, con
         return st;
     };
     if (nrhs < 0) return fail(PC_ERR_ARG, "nrhs < 0");
+    if (op->d != 2) return fail(PC_ERR_UNSUPPORTED, "the allocation-free apply covers 2D operators");
     if (nrhs == 0) return PC_OK;
     if (!x || !y) return fail(PC_ERR_ARG, "null x or y");
     if (ldx < op->N || ldy < op->N) return fail(PC_ERR_ARG, "ldx and ldy must be >= N");

@@ -215,3 +215,44 @@ def test_adaptive_workload_1024_sampled():
     ref = orc.apply(x, points=pts)
     err = np.linalg.norm(y[:, pts] - ref, axis=1) / np.linalg.norm(ref, axis=1)
     assert np.all(err <= TOL["fp32"]), err
+
+
+# ------------------------------------------------------------------ 3D patches (64^3 FFTs)
+
+def test_3d_small_full():
+    shape = (40, 36, 30)
+    cells = workloads.regular_grid(shape, (3, 3, 3))
+    s = lambda x: 1.2 + 0.3 * np.sin(x[..., 0] / 7.0)  # noqa: E731
+    kern = workloads.GaussianAxis3D(s, lambda x: 1.6 + 0 * x[..., 0], lambda x: 1.0 + 0.2 * np.cos(x[..., 2] / 5.0), 5)
+    op, orc = make_pair(shape, cells, kern, "fp32")
+    x = workloads.rhs(61, 3, shape)
+    err = rel_l2(run(op, x), orc.apply(x))
+    assert np.all(err <= TOL["fp32"]), err
+
+
+def test_3d_split_window():
+    """R = 40 at P = 64: the 81^3 window is cut into sub-windows."""
+    shape = (70, 66, 60)
+    cells = workloads.regular_grid(shape, (2, 2, 2))
+    kern = workloads.HeavyTailed(lambda x: 3.0 + 0 * x[..., 0], 40)
+    op, orc = make_pair(shape, cells, kern, "fp32")
+    assert op.info()["num_tiles"] > orc.grid.r
+    x = workloads.rhs(62, 2, shape)
+    y = run(op, x).reshape(2, -1)
+    pts = np.random.default_rng(3).choice(int(np.prod(shape)), 512, replace=False)
+    ref = orc.apply(x, points=pts)
+    err = np.linalg.norm(y[:, pts] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert np.all(err <= TOL["fp32"]), err
+
+
+def test_3d_workload_128_sampled():
+    """128^3, regular 8x8x8 grid, anisotropic 3D Gaussian, R = 12: 4 right-hand
+    sides, 2048 seeded voxels each (plus one full right-hand side)."""
+    wl = configs.fp32_128c(4)
+    op, orc = make_pair(wl.shape, wl.cells, wl.kernel, "fp32")
+    x = workloads.rhs(wl.rhs_seed, 4, wl.shape)
+    y = run(op, x).reshape(4, -1)
+    pts = np.random.default_rng(11).choice(wl.n, 2048, replace=False)
+    ref = orc.apply(x, points=pts)
+    err = np.linalg.norm(y[:, pts] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert np.all(err <= TOL["fp32"]), err
