@@ -40,6 +40,45 @@ sys.path.insert(0, ROOT)
 
 METRIC = "product-convolution RHS/s"
 WORKLOAD = "fp32_512"
+# description, kernel name and the sources whose hash keys the profiled DRAM traffic
+WORKLOADS = {
+    "fp32_512": ("512x512 regular 16x16 grid (r=256), anisotropic Gaussian R=24, 128^2 patch FFTs, 64 RHS",
+                 "fft2d_kernel<float,128>", ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh"]),
+    "fp32_128c": ("128^3 regular 8x8x8 grid (r=512), axis-aligned Gaussian R=12, 64^3 patch FFTs, 32 RHS",
+                  "fft3d_kernel", ["pc_fft3d.cu", "pc_fftcore.cuh", "pc_ptx.cuh"]),
+    "adaptive_1024": ("1024x1024 adaptive quadtree (r=1579), heavy-tailed R=64 (2x2 kernel sub-windows), "
+                      "128^2 patch FFTs, 32 RHS", "fft2d_kernel<float,128>",
+                      ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh"]),
+}
+
+
+def kernel_sources_hash(names):
+    import hashlib
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1805_06018_gb300", "csrc", n), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per launch from profiles/<kernel>_<workload>.md (an ncu
+    capture), or None when the kernel sources changed since the capture."""
+    desc, kname, srcs = WORKLOADS[workload]
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kname.split("<")[0], workload))
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    if fields.get("kernel_sources_sha256_16") != kernel_sources_hash(srcs):
+        return None
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def algorithmic_work(shape, lo, hi, R, nrhs, spectra_bytes, elem=4):
@@ -263,6 +302,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--serve", action="store_true", help="serving benchmark instead of the batched apply")
     ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -286,7 +326,8 @@ def main():
     if world > 1:
         dist.barrier()
 
-    wl = configs.get(WORKLOAD)
+    wl = configs.get(args.workload)
+    desc, kname, ksrcs = WORKLOADS[args.workload]
     pts = pcg.pc_sample_points(wl.shape, wl.cells)
     phi = workloads.impulse_windows(wl.shape, pts, wl.kernel)
     ctx = pcg.Context(local)
@@ -356,7 +397,7 @@ def main():
 
     # ---- plain per-vector path on the same operator
     plain = None
-    if not args.no_plain:
+    if not args.no_plain and wl.ndim == 2:
         yp = torch.empty_like(x)
         op.pc_apply_plain(wl.nrhs, x.data_ptr(), N, yp.data_ptr(), N, sp)
         torch.cuda.synchronize()
@@ -388,17 +429,13 @@ def main():
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
     kern_ms = float(np.mean(kms))
     achieved = flops / (kern_ms / 1e3) / 1e12
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic_fft2d_fp32_512.json")
-    if os.path.exists(tr_path):
-        traffic = json.load(open(tr_path)).get("bytes_per_launch")
+    traffic = profiled_traffic(args.workload)
 
     line = {"metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "512x512 regular 16x16 grid (r=256), anisotropic Gaussian R=24, "
-                                   "128^2 patch FFTs, 64 RHS", "global_batch": wl.nrhs * world,
-                       "per_gpu_batch": wl.nrhs, "grid": [512, 512], "radius": wl.radius, "fft": info["fft_size"],
+            "config": {"workload": desc, "global_batch": wl.nrhs * world,
+                       "per_gpu_batch": wl.nrhs, "grid": list(wl.shape), "radius": wl.radius, "fft": info["fft_size"],
                        "parallelism": "replicas%d" % world, "l2": "flushed between steps (256 MB write)"},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                            "per": "apply of 64 RHS"},
@@ -408,7 +445,7 @@ def main():
             "gpu_launches": int(op.launches()) * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak, "traffic": traffic,
-                         "kernel": "fft2d_kernel<float,128>", "kernel_ms": kern_ms,
+                         "kernel": kname, "kernel_ms": kern_ms,
                          "algorithmic_flop_per_launch": flops, "algorithmic_bytes_per_launch": bytes_,
                          "peak_basis": "FP32 FMA pipe: SMs x 128 lanes x 2 x %.0f MHz" % sm_max},
             "clocks": clk.summary()}
