@@ -46,10 +46,16 @@ WORKLOADS = {
                  "fft2d_kernel<float,128>", ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh"]),
     "fp32_128c": ("128^3 regular 8x8x8 grid (r=512), axis-aligned Gaussian R=12, 64^3 patch FFTs, 32 RHS",
                   "fft3d_kernel", ["pc_fft3d.cu", "pc_fftcore.cuh", "pc_ptx.cuh"]),
+    "bf16x3_128c": ("128^3 regular 8x8x8 grid (r=512), axis-aligned Gaussian R=12, 64^3 patches: plane FFTs in "
+                    "FP32, first-axis DFTs as split-BF16 tensor-core GEMMs, 32 RHS",
+                    "tc3d_axis0_kernel", ["pc_tc3d.cu", "pc_tc.cuh", "pc_ptx.cuh"]),
     "adaptive_1024": ("1024x1024 adaptive quadtree (r=1579), heavy-tailed R=64 (2x2 kernel sub-windows), "
                       "128^2 patch FFTs, 32 RHS", "fft2d_kernel<float,128>",
                       ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh"]),
 }
+# workload name -> (operator configuration, precision)
+WORKLOAD_OPERATOR = {"fp32_512": ("fp32_512", "fp32"), "fp32_128c": ("fp32_128c", "fp32"),
+                     "bf16x3_128c": ("fp32_128c", "bf16x3"), "adaptive_1024": ("adaptive_1024", "fp32")}
 
 
 def kernel_sources_hash(names):
@@ -170,7 +176,7 @@ def run_reference(args, rank, world):
     from workloads import configs
     from oracle import build as obuild
     obuild.build()
-    wl = configs.get(WORKLOAD)
+    wl = configs.get(WORKLOAD_OPERATOR[args.workload][0])
     x = workloads.rhs(wl.rhs_seed, wl.nrhs, wl.shape)
     from oracle import PCOracle
     orc = PCOracle.from_workload(wl)
@@ -190,7 +196,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "512x512 r=256 anisotropic Gaussian R=24, 64 RHS",
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][0],
                                             "global_batch": wl.nrhs, "parallelism": "cpu"},
             "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": sample},
@@ -326,12 +332,14 @@ def main():
     if world > 1:
         dist.barrier()
 
-    wl = configs.get(args.workload)
+    cfg_name, precision = WORKLOAD_OPERATOR[args.workload]
+    wl = configs.get(cfg_name)
     desc, kname, ksrcs = WORKLOADS[args.workload]
     pts = pcg.pc_sample_points(wl.shape, wl.cells)
     phi = workloads.impulse_windows(wl.shape, pts, wl.kernel)
     ctx = pcg.Context(local)
-    op = pcg.Operator(ctx, wl.shape, wl.cells, wl.radius, phi, precision="fp32")
+    op = pcg.Operator(ctx, wl.shape, wl.cells, wl.radius, phi, precision=precision)
+    staged = precision == "bf16x3"
     info = op.info()
     x_host = workloads.rhs(wl.rhs_seed, wl.nrhs, wl.shape)
     x = torch.from_numpy(x_host).cuda()
@@ -362,7 +370,7 @@ def main():
             ev0[i].record(stream)
             step()
             ev1[i].record(stream)
-            kms.append(op.kernel_ms())
+            kms.append([op.stage_ms(k) for k in range(3)] if staged else op.kernel_ms())
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -427,9 +435,51 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
-    kern_ms = float(np.mean(kms))
-    achieved = flops / (kern_ms / 1e3) / 1e12
-    traffic = profiled_traffic(args.workload)
+    roof_tensor = None
+    if staged:
+        # three kernels per chunk; nominal flops split by transform axis:
+        # phase 1 = forward axes 1, 2; tensor stage = axis 0 forward + inverse
+        # + product; phase 3 = inverse axes 1, 2.  Executed tensor-core flops
+        # count the MMAs the tensor stage issues (3 split products per step).
+        stage_names = ["fft3d_phase1_kernel", "tc3d_axis0_kernel", "fft3d_phase3_kernel"]
+        st_ms = np.mean(np.array(kms), axis=0)
+        npairs = (wl.nrhs + 1) // 2
+        f_stage = [0.0, 0.0, 0.0]
+        mma_flops = 0.0
+        assert info["num_tiles"] == len(lo), "one tile per patch expected"
+        for a, b in zip(lo, hi):
+            n = [bb - aa + 1 for aa, bb in zip(a, b)]
+            Ls = [v + 2 * wl.radius for v in n]
+            L = float(np.prod(Ls))
+            f_stage[0] += 2.5 * L * (math.log2(Ls[1]) + math.log2(Ls[2]))
+            f_stage[1] += 5.0 * L * math.log2(Ls[0]) + 3.0 * L
+            f_stage[2] += 2.5 * L * (math.log2(Ls[1]) + math.log2(Ls[2]))
+            mma_flops += npairs * 32 * 3 * ((2 * n[0] + 15) // 16 + 8) * 2.0 * 128 * 128 * 16
+        f_stage = [f * wl.nrhs for f in f_stage]
+        bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+        tc_ach = mma_flops / (st_ms[1] / 1e3) / 1e12
+        roof_tensor = {"bound": "tensor", "kernel": stage_names[1], "kernel_ms": float(st_ms[1]),
+                       "executed_mma_flop_per_apply": mma_flops, "achieved": tc_ach, "peak": bf16_peak,
+                       "unit": "TFLOP/s", "frac": tc_ach / bf16_peak,
+                       "peak_basis": "measured cuBLAS bf16 GEMM (burst)",
+                       "nominal_fft_tflops": f_stage[1] / (st_ms[1] / 1e3) / 1e12,
+                       "stage_ms": {nm: float(t) for nm, t in zip(stage_names, st_ms)}}
+        dom = int(np.argmax(st_ms))
+        kname = stage_names[dom]
+        kern_ms = float(st_ms[dom])
+        if dom == 1:
+            achieved, peak, bound, basis = tc_ach, bf16_peak, "tensor", roof_tensor["peak_basis"]
+            work = mma_flops
+        else:
+            achieved = f_stage[dom] / (kern_ms / 1e3) / 1e12
+            peak, bound = fp32_peak, "alu"
+            basis = "FP32 FMA pipe: SMs x 128 lanes x 2 x %.0f MHz" % sm_max
+            work = f_stage[dom]
+    else:
+        kern_ms = float(np.mean(kms))
+        achieved, peak, bound, work = flops / (kern_ms / 1e3) / 1e12, fp32_peak, "alu", flops
+        basis = "FP32 FMA pipe: SMs x 128 lanes x 2 x %.0f MHz" % sm_max
+    traffic = profiled_traffic(args.workload) if kname == WORKLOADS[args.workload][1] else None
 
     line = {"metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
@@ -438,21 +488,24 @@ def main():
                        "per_gpu_batch": wl.nrhs, "grid": list(wl.shape), "radius": wl.radius, "fft": info["fft_size"],
                        "parallelism": "replicas%d" % world, "l2": "flushed between steps (256 MB write)"},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
-                           "per": "apply of 64 RHS"},
+                           "per": "apply of %d RHS" % wl.nrhs},
             "plain_gpu": plain,
             "e2e": {"value": e2e_value, "unit": "RHS/s", "h2d_bytes_per_step": int(x_host.nbytes),
                     "d2h_bytes_per_step": int(x_host.nbytes)},
             "gpu_launches": int(op.launches()) * args.steps,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp32_peak, "traffic": traffic,
+            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic,
                          "kernel": kname, "kernel_ms": kern_ms,
-                         "algorithmic_flop_per_launch": flops, "algorithmic_bytes_per_launch": bytes_,
-                         "peak_basis": "FP32 FMA pipe: SMs x 128 lanes x 2 x %.0f MHz" % sm_max},
+                         "algorithmic_flop_per_launch": work, "algorithmic_bytes_per_launch": bytes_,
+                         "peak_basis": basis},
             "clocks": clk.summary()}
+    if roof_tensor is not None:
+        line["roofline_tensor"] = roof_tensor
+        line["dtype"] = "f32+bf16x3"
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
         rate, pix, cores, el = cpu_oracle_rate(wl, x_host, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "RHS/s", "cores": cores, "kind": "oracle",
-                                "sample": "%d random output pixels x 64 RHS in %.1f s" % (pix, el)}
+                                "sample": "%d random output pixels x %d RHS in %.1f s" % (pix, wl.nrhs, el)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     op.close()

@@ -60,8 +60,10 @@ typedef enum {
 typedef enum {
     PC_FP64 = 0,             /* FP64 data, FP64 FFTs (correctness configuration) */
     PC_FP32 = 1,             /* FP32 data, FP32 FFTs, spectra built in FP64 and rounded once */
-    PC_BF16X3 = 2,           /* reserved: tensor-core DFT with split BF16 operands */
-    PC_TF32X3 = 3            /* reserved: tensor-core DFT with split TF32 operands */
+    PC_BF16X3 = 2,           /* 3D operators: FP32 data and plane FFTs; the first-axis DFTs are
+                                tensor-core GEMMs with split BF16 operands, a = a_hi + a_lo,
+                                products a_lo b_hi + a_hi b_lo + a_hi b_hi accumulated in FP32 */
+    PC_TF32X3 = 3            /* reserved (not built): split TF32 operands */
 } pc_precision;
 
 typedef void *pc_stream;     /* cudaStream_t */
@@ -199,7 +201,9 @@ pc_status pc_extend_impulse(const pc_box *box, const pc_grid *grid, int32_t radi
  *            Otherwise host FP64, w_k on bbox(U_k) (pc_neighbourhood_boxes),
  *            C order, concatenated for k = 0..r-1; entries outside U_k must
  *            be 0.
- *   prec     PC_FP64 or PC_FP32.
+ *   prec     PC_FP64 (2D), PC_FP32, or PC_BF16X3 (3D only; the first-axis
+ *            transform of each patch runs as split-BF16 tensor-core GEMMs,
+ *            relative error of the result about 1e-5 against FP64).
  *   tune     NULL or knobs (see pc_tuning).
  * The operator owns its device memory until pc_operator_destroy.  The call
  * synchronises the device. */
@@ -315,6 +319,15 @@ pc_status pc_operator_check(pc_operator *op);
  * zero-fill of y is outside the pair).  Waits for the end event.
  * PC_ERR_NOT_READY if no apply has been issued. */
 pc_status pc_operator_kernel_time(pc_operator *op, float *ms);
+
+/* Device time of one stage of the most recent apply of a 3D PC_BF16X3
+ * operator, summed over its chunks of work items (milliseconds, CUDA events
+ * on the caller's stream): stage 0 = input-plane 2D FFTs, 1 = tensor-core
+ * first-axis DFT, spectral product and inverse DFT, 2 = inverse plane FFTs
+ * and the ordered overlap-add.  Waits for the apply's end event.  The paper
+ * has no counterpart (measurement helper).  PC_ERR_NOT_READY if the last
+ * apply was not of that kind; PC_ERR_ARG if stage is not 0, 1 or 2. */
+pc_status pc_operator_stage_time(pc_operator *op, int32_t stage, float *ms);
 
 /* Counters of the operator's most recent apply (host): kernels launched. */
 pc_status pc_operator_launches(const pc_operator *op, int64_t *kernels_last_apply);

@@ -98,6 +98,7 @@ _PROTOS = {
     "pc_operator_check": (ctypes.c_int, [_VP]),
     "pc_operator_kernel_time": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
     "pc_operator_launches": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
+    "pc_operator_stage_time": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
     "pc_operator_destroy": (ctypes.c_int, [_VP]),
     "pc_serve_create": (ctypes.c_int, [_VP, ctypes.POINTER(pc_serve_config), ctypes.POINTER(_VP)]),
     "pc_serve_submit": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _VP, _VP, ctypes.c_uint32,
@@ -272,6 +273,13 @@ class Operator:
         """Device time of the fused kernel of the last apply (waits for it)."""
         ms = ctypes.c_float()
         _check(lib().pc_operator_kernel_time(self.handle, ctypes.byref(ms)), self.ctx.handle)
+        return ms.value
+
+    def stage_ms(self, stage: int) -> float:
+        """3D BF16X3 operators: device time of stage 0 (plane FFTs), 1 (tensor-core
+        first-axis DFTs) or 2 (inverse plane FFTs + overlap-add) of the last apply."""
+        ms = ctypes.c_float()
+        _check(lib().pc_operator_stage_time(self.handle, ctypes.c_int32(stage), ctypes.byref(ms)), self.ctx.handle)
         return ms.value
 
     def launches(self) -> int:

@@ -83,6 +83,8 @@ void free_operator(pc_operator *op) {
     cudaFree(op->d_ctrl);
     cudaFree(op->d_tw);
     cudaFree(op->d_scratch);
+    cudaFree(op->d_tc_ops);
+    for (cudaEvent_t ev : op->stage_ev) cudaEventDestroy(ev);
     if (op->ev_begin) cudaEventDestroy(op->ev_begin);
     if (op->ev_end) cudaEventDestroy(op->ev_end);
     delete op;
@@ -195,15 +197,17 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     if (!ctx) return fail(nullptr, PC_ERR_ARG, "ctx is null");
     if (!out || !impulse) return fail(ctx, PC_ERR_ARG, "null impulse or output handle");
     *out = nullptr;
-    if (prec != PC_FP32 && prec != PC_FP64)
-        return fail(ctx, PC_ERR_UNSUPPORTED, "precision not built: use PC_FP32 or PC_FP64");
+    if (prec != PC_FP32 && prec != PC_FP64 && prec != PC_BF16X3)
+        return fail(ctx, PC_ERR_UNSUPPORTED, "precision not built: use PC_FP32, PC_FP64 or (3D) PC_BF16X3");
     pc::Geometry g;
     std::string err;
     pc_status st = pc::build_geometry(box, grid, g, err);
     if (st != PC_OK) return fail(ctx, st, err);
     if (radius < 1) return fail(ctx, PC_ERR_ARG, "radius must be >= 1");
     const bool three = g.d == 3;
-    if (three && prec != PC_FP32) return fail(ctx, PC_ERR_UNSUPPORTED, "3D operators are FP32");
+    if (three && prec == PC_FP64) return fail(ctx, PC_ERR_UNSUPPORTED, "3D operators are FP32 or BF16X3");
+    if (!three && prec == PC_BF16X3)
+        return fail(ctx, PC_ERR_UNSUPPORTED, "PC_BF16X3 (tensor-core first-axis DFTs) covers 3D operators");
     int P = tune && tune->fft_size ? tune->fft_size : (three || prec == PC_FP64 ? 64 : 128);
     if (three && P != 64) return fail(ctx, PC_ERR_UNSUPPORTED, "3D operators use fft_size 64");
     if (prec == PC_FP64 && P != 64) return fail(ctx, PC_ERR_UNSUPPORTED, "FP64 operators use fft_size 64");
@@ -371,10 +375,17 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     if (e == cudaSuccess)
         e = three ? pc::build_spectra_3d(d_psi, nspec, ws, P, op->d_spec, d_tw64, nullptr)
                   : pc::build_spectra_2d(d_psi, nspec, ws, P, prec, op->d_spec, d_tw64, nullptr);
-    if (e == cudaSuccess && three) {
+    if (e == cudaSuccess && three && prec == PC_FP32) {
         const size_t sb = pc::fft3d_scratch_bytes(op->ctas);
         e = cudaMalloc(&op->d_scratch, sb);
         if (e == cudaSuccess) acct += sb;
+    }
+    if (e == cudaSuccess && three && prec == PC_BF16X3) {
+        // the chunk scratch volumes are allocated by the first apply (their
+        // number depends on the batch)
+        e = pc::tc3d_configure();
+        if (e == cudaSuccess) e = pc::tc3d_build_operands(&op->d_tc_ops);
+        if (e == cudaSuccess) acct += 4 * 32768;
     }
     cudaFree(d_psi);
     cudaFree(d_tw64);
@@ -425,6 +436,58 @@ static pc_status ensure_done_capacity(pc_operator *op, int32_t npairs) {
     return PC_OK;
 }
 
+// 3D, BF16x3: the items run in chunks of at most kTc3dChunkItems through
+// three kernels (phase 1 -> tensor-core first-axis transform -> phase 3),
+// each item with its own scratch volume; stream-ordered like the fused path.
+static pc_status apply_split3d(pc_operator *op, const pc::ApplyParams &p, cudaStream_t s) {
+    pc_context *ctx = op->ctx;
+    const int64_t total = p.total_items;
+    const int64_t chunk = std::min<int64_t>(total, pc::kTc3dChunkItems);
+    cudaError_t e = cudaSuccess;
+    if (op->scratch_items < chunk) {
+        if (op->d_scratch && (e = cudaDeviceSynchronize()) != cudaSuccess)
+            return cuda_fail(ctx, e, "synchronising before growing the scratch volumes");
+        cudaFree(op->d_scratch);
+        op->d_scratch = nullptr;
+        op->scratch_items = 0;
+        if ((e = cudaMalloc(&op->d_scratch, size_t(chunk) * pc::fft3d_scratch_bytes(1))) != cudaSuccess)
+            return cuda_fail(ctx, e, "allocating the 3D scratch volumes");
+        op->scratch_items = chunk;
+    }
+    const int nchunks = int((total + chunk - 1) / chunk);
+    while (op->stage_ev.size() < size_t(nchunks) * 6) {
+        cudaEvent_t ev = nullptr;
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(ctx, e, "creating events");
+        op->stage_ev.push_back(ev);
+    }
+    if ((e = pc::launch_zero(p, op->N, op->prec, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "launching the zero kernel");
+    cudaEventRecord(op->ev_begin, s);
+    for (int c = 0; c < nchunks && e == cudaSuccess; ++c) {
+        const int64_t c0 = int64_t(c) * chunk, c1 = std::min<int64_t>(total, c0 + chunk);
+        const int ctas = int(std::min<int64_t>(op->ctas, c1 - c0));
+        cudaEvent_t *ev = &op->stage_ev[size_t(c) * 6];
+        cudaEventRecord(ev[0], s);
+        e = pc::launch_fft3d_phase1(p, ctas, op->d_scratch, c0, c1, s);
+        cudaEventRecord(ev[1], s);
+        if (e != cudaSuccess) break;
+        cudaEventRecord(ev[2], s);
+        e = pc::launch_tc3d_axis0(p, ctx->num_sms, op->d_scratch, c0, c1, op->d_tc_ops, s);
+        cudaEventRecord(ev[3], s);
+        if (e != cudaSuccess) break;
+        cudaEventRecord(ev[4], s);
+        e = pc::launch_fft3d_phase3(p, ctas, op->d_scratch, c0, c1, s);
+        cudaEventRecord(ev[5], s);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the 3D split path");
+    cudaEventRecord(op->ev_end, s);
+    op->stage_chunks = nchunks;
+    op->timed = true;
+    op->last_stream = s;
+    op->launches_last = 1 + 3 * int64_t(nchunks);
+    return PC_OK;
+}
+
 pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
                            pc_stream stream) {
     if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
@@ -470,13 +533,15 @@ pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t
     p.w = op->d_w;
     p.tw = op->d_tw;
     p.total_items = int64_t(op->n_tiles) * npairs;
+    if (!op->ev_begin) {
+        cudaError_t e = cudaEventCreate(&op->ev_begin);
+        if (e == cudaSuccess) e = cudaEventCreate(&op->ev_end);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "creating events");
+    }
+    if (op->d == 3 && op->prec == PC_BF16X3) return apply_split3d(op, p, s);
     cudaError_t e = pc::launch_zero(p, op->N, op->prec, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the zero kernel");
     const int ctas = int(std::min<int64_t>(op->ctas, p.total_items));
-    if (!op->ev_begin) {
-        if ((e = cudaEventCreate(&op->ev_begin)) != cudaSuccess) return cuda_fail(ctx, e, "creating events");
-        if ((e = cudaEventCreate(&op->ev_end)) != cudaSuccess) return cuda_fail(ctx, e, "creating events");
-    }
     cudaEventRecord(op->ev_begin, s);
     e = op->d == 3 ? pc::launch_fft3d(p, ctas, op->d_scratch, s) : pc::launch_fft2d(p, op->P, op->prec, ctas, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the patch kernel");
@@ -532,6 +597,24 @@ pc_status pc_operator_kernel_time(pc_operator *op, float *ms) {
     cudaError_t e = cudaEventSynchronize(op->ev_end);
     if (e == cudaSuccess) e = cudaEventElapsedTime(ms, op->ev_begin, op->ev_end);
     if (e != cudaSuccess) return cuda_fail(op->ctx, e, "reading kernel events");
+    return PC_OK;
+}
+
+pc_status pc_operator_stage_time(pc_operator *op, int32_t stage, float *ms) {
+    if (!op || !ms) return fail(nullptr, PC_ERR_ARG, "null argument");
+    if (stage < 0 || stage > 2) return fail(op->ctx, PC_ERR_ARG, "stage must be 0, 1 or 2");
+    if (!op->timed || op->stage_chunks == 0)
+        return fail(op->ctx, PC_ERR_NOT_READY, "no staged (3D BF16X3) apply has been issued");
+    DeviceGuard dg(op->ctx->device);
+    cudaError_t e = cudaEventSynchronize(op->ev_end);
+    float sum = 0.0f;
+    for (int c = 0; c < op->stage_chunks && e == cudaSuccess; ++c) {
+        float t = 0.0f;
+        e = cudaEventElapsedTime(&t, op->stage_ev[size_t(c) * 6 + 2 * stage], op->stage_ev[size_t(c) * 6 + 2 * stage + 1]);
+        sum += t;
+    }
+    if (e != cudaSuccess) return cuda_fail(op->ctx, e, "reading stage events");
+    *ms = sum;
     return PC_OK;
 }
 

@@ -15,7 +15,9 @@
 //            rows) and the overlap-add of its L1 x L2 box into y
 //
 // Overlap-add order, termination and determinism are those of the 2D kernel:
-// colour-ordered tiles, claims in increasing order, bounded waits.  Scratch
+// colour-ordered tiles, claims in increasing order, bounded waits.  The same
+// phases also run as separate kernels over chunks of items (phase 1, then the
+// tensor-core first-axis transform of pc_tc3d.cu, then phase 3).  Scratch
 // traffic is about 6.7 MB per item; the line FFTs (about 20,000 of length 64
 // per item) dominate the time.
 #include "pc_fftcore.cuh"
@@ -28,188 +30,267 @@ constexpr int kThreads3d = 256;
 constexpr int kP3 = 64;
 constexpr long long kSpinLimit3 = 1ll << 24;
 
-__global__ void __launch_bounds__(kThreads3d, 3) fft3d_kernel(const ApplyParams p, float2 *scratch) {
-    using C = float2;
-    constexpr int P = kP3;
-    constexpr int R1 = FftShape<P>::R1, R2 = FftShape<P>::R2;
-    constexpr int LINES = kThreads3d / R2;
-    constexpr int PP = P * P;
-    __shared__ __align__(16) C S[P * P];
-    __shared__ int64_t s_item;
+// One work item: tile `ti` of the schedule and right-hand-side pair `pair`
+// (columns 2 pair and 2 pair + 1 packed as the real and imaginary parts).
+struct Item3 {
+    int ti, pair;
+    Tile tile;
+};
 
-    const int t = threadIdx.x % R2;
-    const int line = threadIdx.x / R2;
-    const unsigned lmask = FftShape<P>::line_mask();
-    const C *twg = static_cast<const C *>(p.tw);
-    C tw[R1];
+__device__ __forceinline__ Item3 decode_item3(const ApplyParams &p, int64_t item) {
+    int c = 0;
+    while (int64_t(p.color_start[c + 1]) * p.npairs <= item) ++c;
+    const int64_t base = int64_t(p.color_start[c]) * p.npairs;
+    const int ntc = p.color_start[c + 1] - p.color_start[c];
+    Item3 it;
+    it.pair = int((item - base) / ntc);
+    it.ti = p.color_start[c] + int((item - base) % ntc);
+    it.tile = p.tiles[it.ti];
+    return it;
+}
+
+// Per-thread constants of the line FFTs (R2 = 8 threads per line of 64).
+struct Lines3 {
+    static constexpr int P = kP3;
+    static constexpr int R1 = FftShape<P>::R1, R2 = FftShape<P>::R2;
+    static constexpr int LINES = kThreads3d / R2;
+    static constexpr int PP = P * P;
+    int t, line;
+    unsigned lmask;
+    float2 tw[R1];
+    __device__ __forceinline__ explicit Lines3(const float2 *twg) {
+        t = threadIdx.x % R2;
+        line = threadIdx.x / R2;
+        lmask = FftShape<P>::line_mask();
 #pragma unroll
-    for (int m = 0; m < R1; ++m) tw[m] = twg[(t * m) & (P - 1)];
-    const float *x = static_cast<const float *>(p.x);
-    float *y = static_cast<float *>(p.y);
-    const float *w = static_cast<const float *>(p.w);
-    const C *spec = static_cast<const C *>(p.spec);
-    C *G = scratch + int64_t(blockIdx.x) * P * PP;
-    const C zero{0.0f, 0.0f};
-    const int n1box = p.n[1], n2box = p.n[2];
-    const int64_t plane_box = int64_t(n1box) * n2box;
+        for (int m = 0; m < R1; ++m) tw[m] = twg[(t * m) & (P - 1)];
+    }
+};
 
+// phase 1: 2D FFT of each of the n0 non-zero input planes -> G[i0][k2][k1]
+__device__ __forceinline__ void phase1_3d(const ApplyParams &p, const Item3 &it, float2 *G, float2 *S,
+                                          const Lines3 &L) {
+    using C = float2;
+    constexpr int P = Lines3::P, R1 = Lines3::R1, R2 = Lines3::R2, LINES = Lines3::LINES, PP = Lines3::PP;
+    const C zero{0.0f, 0.0f};
+    const Tile &tile = it.tile;
+    const int n0 = tile.in_ext[0], n1 = tile.in_ext[1], n2 = tile.in_ext[2];
+    const int b0 = 2 * it.pair;
+    const bool has1 = b0 + 1 < p.nrhs;
+    const float *x0 = static_cast<const float *>(p.x) + int64_t(b0) * p.ldx;
+    const float *x1 = has1 ? x0 + p.ldx : x0;
+    const float *wt = static_cast<const float *>(p.w) + tile.w_base;
+    const int64_t plane_box = int64_t(p.n[1]) * p.n[2];
+    for (int i0 = 0; i0 < n0; ++i0) {
+        const float *wp = wt + int64_t(i0) * tile.w_ld[0];
+        const int64_t xp = int64_t(tile.in_lo[0] + i0) * plane_box;
+        for (int r = L.line; r < n1; r += LINES) {
+            C a[R1];
+            const int64_t xr = xp + int64_t(tile.in_lo[1] + r) * p.n[2] + tile.in_lo[2];
+            const float *wr = wp + int64_t(r) * tile.w_ld[1];
+#pragma unroll
+            for (int j = 0; j < R1; ++j) {
+                const int col = L.t + R2 * j;
+                if (col < n2) {
+                    const float wv = __ldg(wr + col);
+                    a[j] = C{wv * __ldg(x0 + xr + col), has1 ? wv * __ldg(x1 + xr + col) : 0.0f};
+                } else {
+                    a[j] = zero;
+                }
+            }
+            RowScratch<P, C> scr{S, r};
+            fft_line<P, false>(a, L.tw, L.t, scr, L.lmask);
+#pragma unroll
+            for (int j = 0; j < R1; ++j) S[r * P + ((L.t + R2 * j) ^ swz(r))] = a[j];
+        }
+        __syncthreads();
+        for (int k2 = L.line; k2 < P; k2 += LINES) {
+            C a[R1];
+#pragma unroll
+            for (int j = 0; j < R1; ++j) {
+                const int row = L.t + R2 * j;
+                a[j] = row < n1 ? S[row * P + (k2 ^ swz(row))] : zero;
+            }
+            ColScratch<P, C> scr{S, k2};
+            fft_line<P, false>(a, L.tw, L.t, scr, L.lmask);
+            C *g = G + int64_t(i0) * PP + k2 * P;
+#pragma unroll
+            for (int j = 0; j < R1; ++j) __stcg(g + L.t + R2 * j, a[j]);
+        }
+        __syncthreads();
+    }
+}
+
+// phase 2 (FP32 line FFTs): per (k1, k2) line, FFT along the first axis over
+// the n0 non-zero planes, product with the stored spectrum, inverse FFT,
+// keeping the L0 needed output planes.  Stored spectrum: Hermitian half in
+// k2, layout [k2 <= P/2][k1][k0].
+__device__ __forceinline__ void phase2_3d(const ApplyParams &p, const Item3 &it, float2 *G, float2 *S,
+                                          const Lines3 &L) {
+    using C = float2;
+    constexpr int P = Lines3::P, R1 = Lines3::R1, R2 = Lines3::R2, LINES = Lines3::LINES, PP = Lines3::PP;
+    const C zero{0.0f, 0.0f};
+    const int n0 = it.tile.in_ext[0], L0 = n0 + it.tile.kext[0] - 1;
+    const C *sp = static_cast<const C *>(p.spec) + int64_t(it.tile.spec) * p.spec_stride;
+    for (int l = L.line; l < PP; l += LINES) {
+        const int k2 = l / P, k1 = l % P;
+        C a[R1];
+        C *g = G + k2 * P + k1;
+#pragma unroll
+        for (int j = 0; j < R1; ++j) {
+            const int i0 = L.t + R2 * j;
+            a[j] = i0 < n0 ? __ldcg(g + int64_t(i0) * PP) : zero;
+        }
+        // S is idle in this phase: row `line` is the line's transpose scratch
+        RowScratch<P, C> scr{S, L.line};
+        fft_line<P, false>(a, L.tw, L.t, scr, L.lmask);
+        if (k2 <= P / 2) {
+            const C *sc = sp + (int64_t(k2) * P + k1) * P;
+#pragma unroll
+            for (int j = 0; j < R1; ++j) a[j] = cmul(a[j], __ldg(sc + L.t + R2 * j));
+        } else {
+            const C *sc = sp + (int64_t(P - k2) * P + ((P - k1) & (P - 1))) * P;
+#pragma unroll
+            for (int j = 0; j < R1; ++j) a[j] = cmulc(a[j], __ldg(sc + ((P - (L.t + R2 * j)) & (P - 1))));
+        }
+        fft_line<P, true>(a, L.tw, L.t, scr, L.lmask);
+#pragma unroll
+        for (int j = 0; j < R1; ++j) {
+            const int o0 = L.t + R2 * j;
+            if (o0 < L0) __stcg(g + int64_t(o0) * PP, a[j]);
+        }
+    }
+    __syncthreads();
+}
+
+// ordered overlap-add: wait (bounded) until every overlapping tile of a lower
+// colour has published its contribution for this pair
+__device__ __forceinline__ void wait_deps_3d(const ApplyParams &p, const Item3 &it) {
+    const int d0 = p.dep_start[it.ti], nd = p.dep_start[it.ti + 1] - d0;
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+        const uint32_t *f = p.done + int64_t(p.dep[d0 + d]) * p.done_ld + it.pair;
+        long long spins = 0;
+        while (ld_acquire_u32(f) != p.epoch) {
+            if (++spins > kSpinLimit3) {
+                atomicExch(p.ctrl + 2, 1);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// phase 3: inverse 2D FFT of each needed output plane and the overlap-add of
+// its L1 x L2 box into y; then publish this item's flag
+__device__ __forceinline__ void phase3_3d(const ApplyParams &p, const Item3 &it, const float2 *G, float2 *S,
+                                          const Lines3 &L) {
+    using C = float2;
+    constexpr int P = Lines3::P, R1 = Lines3::R1, R2 = Lines3::R2, LINES = Lines3::LINES, PP = Lines3::PP;
+    const Tile &tile = it.tile;
+    const int n0 = tile.in_ext[0], n1 = tile.in_ext[1], n2 = tile.in_ext[2];
+    const int L0 = n0 + tile.kext[0] - 1, L1 = n1 + tile.kext[1] - 1, L2 = n2 + tile.kext[2] - 1;
+    const int b0 = 2 * it.pair;
+    const bool has1 = b0 + 1 < p.nrhs;
+    float *y0 = static_cast<float *>(p.y) + int64_t(b0) * p.ldy;
+    float *y1 = has1 ? y0 + p.ldy : y0;
+    const int n2box = p.n[2];
+    const int64_t plane_box = int64_t(p.n[1]) * n2box;
+    for (int o0 = 0; o0 < L0; ++o0) {
+        const int gy0 = tile.out_lo[0] + o0;
+        if (gy0 < 0 || gy0 >= p.n[0]) continue;   // uniform across the CTA
+        // inverse along k1 for each k2: rows o1 of S
+        const C *gp = G + int64_t(o0) * PP;
+        for (int k2 = L.line; k2 < P; k2 += LINES) {
+            C a[R1];
+#pragma unroll
+            for (int j = 0; j < R1; ++j) a[j] = __ldcg(gp + k2 * P + L.t + R2 * j);
+            ColScratch<P, C> scr{S, k2};
+            fft_line<P, true>(a, L.tw, L.t, scr, L.lmask);
+#pragma unroll
+            for (int j = 0; j < R1; ++j) {
+                const int o1 = L.t + R2 * j;
+                if (o1 < L1) S[o1 * P + (k2 ^ swz(o1))] = a[j];
+            }
+        }
+        __syncthreads();
+        for (int o1 = L.line; o1 < L1; o1 += LINES) {
+            const int gy1 = tile.out_lo[1] + o1;
+            if (gy1 < 0 || gy1 >= p.n[1]) continue;
+            C a[R1];
+#pragma unroll
+            for (int j = 0; j < R1; ++j) a[j] = S[o1 * P + ((L.t + R2 * j) ^ swz(o1))];
+            RowScratch<P, C> scr{S, o1};
+            fft_line<P, true>(a, L.tw, L.t, scr, L.lmask);
+            const int64_t yr = int64_t(gy0) * plane_box + int64_t(gy1) * n2box;
+#pragma unroll
+            for (int j = 0; j < R1; ++j) {
+                const int o2 = L.t + R2 * j;
+                const int gy2 = tile.out_lo[2] + o2;
+                if (o2 < L2 && gy2 >= 0 && gy2 < n2box) {
+                    atomicAdd(y0 + yr + gy2, a[j].x);
+                    if (has1) atomicAdd(y1 + yr + gy2, a[j].y);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st_release_u32(p.done + int64_t(it.ti) * p.done_ld + it.pair, p.epoch);
+    }
+}
+
+// The fused FP32 kernel: persistent CTAs claim items in increasing order and
+// run the three phases through their own scratch volume.
+__global__ void __launch_bounds__(kThreads3d, 3) fft3d_kernel(const ApplyParams p, float2 *scratch) {
+    __shared__ __align__(16) float2 S[kP3 * kP3];
+    __shared__ int64_t s_item;
+    const Lines3 L(static_cast<const float2 *>(p.tw));
+    float2 *G = scratch + int64_t(blockIdx.x) * kP3 * kP3 * kP3;
     for (;;) {
         if (threadIdx.x == 0) s_item = int64_t(atomicAdd(reinterpret_cast<unsigned long long *>(p.ctrl), 1ull));
         __syncthreads();
         const int64_t item = s_item;
         if (item >= p.total_items) break;
-        int c = 0;
-        while (int64_t(p.color_start[c + 1]) * p.npairs <= item) ++c;
-        const int64_t base = int64_t(p.color_start[c]) * p.npairs;
-        const int ntc = p.color_start[c + 1] - p.color_start[c];
-        const int pair = int((item - base) / ntc);
-        const int ti = p.color_start[c] + int((item - base) % ntc);
-        const Tile tile = p.tiles[ti];
-        const int n0 = tile.in_ext[0], n1 = tile.in_ext[1], n2 = tile.in_ext[2];
-        const int L0 = n0 + tile.kext[0] - 1, L1 = n1 + tile.kext[1] - 1, L2 = n2 + tile.kext[2] - 1;
-        const int b0 = 2 * pair;
-        const bool has1 = b0 + 1 < p.nrhs;
-        const float *x0 = x + int64_t(b0) * p.ldx;
-        const float *x1 = has1 ? x0 + p.ldx : x0;
-        const float *wt = w + tile.w_base;
-        const C *sp = spec + int64_t(tile.spec) * p.spec_stride;
+        const Item3 it = decode_item3(p, item);
+        phase1_3d(p, it, G, S, L);
+        phase2_3d(p, it, G, S, L);
+        wait_deps_3d(p, it);
+        phase3_3d(p, it, G, S, L);
+    }
+}
 
-        // ---------------- phase 1: 2D FFT of each non-zero input plane -> G[i0][k2][k1]
-        for (int i0 = 0; i0 < n0; ++i0) {
-            const float *wp = wt + int64_t(i0) * tile.w_ld[0];
-            const int64_t xp = int64_t(tile.in_lo[0] + i0) * plane_box;
-            for (int r = line; r < n1; r += LINES) {
-                C a[R1];
-                const int64_t xr = xp + int64_t(tile.in_lo[1] + r) * n2box + tile.in_lo[2];
-                const float *wr = wp + int64_t(r) * tile.w_ld[1];
-#pragma unroll
-                for (int j = 0; j < R1; ++j) {
-                    const int col = t + R2 * j;
-                    if (col < n2) {
-                        const float wv = __ldg(wr + col);
-                        a[j] = C{wv * __ldg(x0 + xr + col), has1 ? wv * __ldg(x1 + xr + col) : 0.0f};
-                    } else {
-                        a[j] = zero;
-                    }
-                }
-                RowScratch<P, C> scr{S, r};
-                fft_line<P, false>(a, tw, t, scr, lmask);
-#pragma unroll
-                for (int j = 0; j < R1; ++j) S[r * P + ((t + R2 * j) ^ swz(r))] = a[j];
-            }
-            __syncthreads();
-            for (int k2 = line; k2 < P; k2 += LINES) {
-                C a[R1];
-#pragma unroll
-                for (int j = 0; j < R1; ++j) {
-                    const int row = t + R2 * j;
-                    a[j] = row < n1 ? S[row * P + (k2 ^ swz(row))] : zero;
-                }
-                ColScratch<P, C> scr{S, k2};
-                fft_line<P, false>(a, tw, t, scr, lmask);
-                C *g = G + int64_t(i0) * PP + k2 * P;
-#pragma unroll
-                for (int j = 0; j < R1; ++j) __stcg(g + t + R2 * j, a[j]);
-            }
-            __syncthreads();
-        }
+// Split form used with the tensor-core first-axis transform: items
+// [c0, c1) of one chunk, each with its own scratch volume G[item - c0].
+// Phase 1 needs no ordering.
+__global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase1_kernel(const ApplyParams p, float2 *scratch,
+                                                                     int64_t c0, int64_t c1) {
+    __shared__ __align__(16) float2 S[kP3 * kP3];
+    const Lines3 L(static_cast<const float2 *>(p.tw));
+    for (int64_t item = c0 + blockIdx.x; item < c1; item += gridDim.x) {
+        const Item3 it = decode_item3(p, item);
+        phase1_3d(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L);
+    }
+}
 
-        // ---------------- phase 2: first-axis FFT, spectral product, inverse, per (k1, k2)
-        // stored spectrum: Hermitian half in k2, layout [k2 <= P/2][k1][k0]
-        for (int l = line; l < PP; l += LINES) {
-            const int k2 = l / P, k1 = l % P;
-            C a[R1];
-            C *g = G + k2 * P + k1;
-#pragma unroll
-            for (int j = 0; j < R1; ++j) {
-                const int i0 = t + R2 * j;
-                a[j] = i0 < n0 ? __ldcg(g + int64_t(i0) * PP) : zero;
-            }
-            // S is idle in this phase: row `line` is the line's transpose scratch
-            RowScratch<P, C> scr{S, line};
-            fft_line<P, false>(a, tw, t, scr, lmask);
-            if (k2 <= P / 2) {
-                const C *sc = sp + (int64_t(k2) * P + k1) * P;
-#pragma unroll
-                for (int j = 0; j < R1; ++j) a[j] = cmul(a[j], __ldg(sc + t + R2 * j));
-            } else {
-                const C *sc = sp + (int64_t(P - k2) * P + ((P - k1) & (P - 1))) * P;
-#pragma unroll
-                for (int j = 0; j < R1; ++j) a[j] = cmulc(a[j], __ldg(sc + ((P - (t + R2 * j)) & (P - 1))));
-            }
-            fft_line<P, true>(a, tw, t, scr, lmask);
-#pragma unroll
-            for (int j = 0; j < R1; ++j) {
-                const int o0 = t + R2 * j;
-                if (o0 < L0) __stcg(g + int64_t(o0) * PP, a[j]);
-            }
-        }
+// Phase 3 claims the chunk's items in increasing order (claim counter reset
+// to 0 before the launch) so that the overlap-add order is the fused kernel's.
+__global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase3_kernel(const ApplyParams p, const float2 *scratch,
+                                                                     int64_t c0, int64_t c1) {
+    __shared__ __align__(16) float2 S[kP3 * kP3];
+    __shared__ int64_t s_item;
+    const Lines3 L(static_cast<const float2 *>(p.tw));
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_item = c0 + int64_t(atomicAdd(reinterpret_cast<unsigned long long *>(p.ctrl), 1ull));
         __syncthreads();
-
-        // ---------------- ordered overlap-add: wait for lower colours
-        {
-            const int d0 = p.dep_start[ti], nd = p.dep_start[ti + 1] - d0;
-            for (int d = threadIdx.x; d < nd; d += blockDim.x) {
-                const uint32_t *f = p.done + int64_t(p.dep[d0 + d]) * p.done_ld + pair;
-                long long spins = 0;
-                while (ld_acquire_u32(f) != p.epoch) {
-                    if (++spins > kSpinLimit3) {
-                        atomicExch(p.ctrl + 2, 1);
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-                __threadfence();
-            }
-        }
-        __syncthreads();
-
-        // ---------------- phase 3: inverse 2D FFT of each output plane, overlap-add
-        float *y0 = y + int64_t(b0) * p.ldy;
-        float *y1 = has1 ? y0 + p.ldy : y0;
-        for (int o0 = 0; o0 < L0; ++o0) {
-            const int gy0 = tile.out_lo[0] + o0;
-            if (gy0 < 0 || gy0 >= p.n[0]) continue;   // uniform across the CTA
-            // inverse along k1 for each k2: rows o1 of S
-            const C *gp = G + int64_t(o0) * PP;
-            for (int k2 = line; k2 < P; k2 += LINES) {
-                C a[R1];
-#pragma unroll
-                for (int j = 0; j < R1; ++j) a[j] = __ldcg(gp + k2 * P + t + R2 * j);
-                ColScratch<P, C> scr{S, k2};
-                fft_line<P, true>(a, tw, t, scr, lmask);
-#pragma unroll
-                for (int j = 0; j < R1; ++j) {
-                    const int o1 = t + R2 * j;
-                    if (o1 < L1) S[o1 * P + (k2 ^ swz(o1))] = a[j];
-                }
-            }
-            __syncthreads();
-            for (int o1 = line; o1 < L1; o1 += LINES) {
-                const int gy1 = tile.out_lo[1] + o1;
-                if (gy1 < 0 || gy1 >= p.n[1]) continue;
-                C a[R1];
-#pragma unroll
-                for (int j = 0; j < R1; ++j) a[j] = S[o1 * P + ((t + R2 * j) ^ swz(o1))];
-                RowScratch<P, C> scr{S, o1};
-                fft_line<P, true>(a, tw, t, scr, lmask);
-                const int64_t yr = int64_t(gy0) * plane_box + int64_t(gy1) * n2box;
-#pragma unroll
-                for (int j = 0; j < R1; ++j) {
-                    const int o2 = t + R2 * j;
-                    const int gy2 = tile.out_lo[2] + o2;
-                    if (o2 < L2 && gy2 >= 0 && gy2 < n2box) {
-                        atomicAdd(y0 + yr + gy2, a[j].x);
-                        if (has1) atomicAdd(y1 + yr + gy2, a[j].y);
-                    }
-                }
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            __threadfence();
-            st_release_u32(p.done + int64_t(ti) * p.done_ld + pair, p.epoch);
-        }
+        const int64_t item = s_item;
+        if (item >= c1) break;
+        const Item3 it = decode_item3(p, item);
+        wait_deps_3d(p, it);
+        phase3_3d(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L);
     }
 }
 
@@ -226,6 +307,21 @@ cudaError_t launch_fft3d(const ApplyParams &p, int ctas, void *scratch, cudaStre
 }
 
 size_t fft3d_scratch_bytes(int ctas) { return size_t(ctas) * kP3 * kP3 * kP3 * sizeof(float2); }
+
+cudaError_t launch_fft3d_phase1(const ApplyParams &p, int ctas, void *scratch, int64_t c0, int64_t c1,
+                                cudaStream_t s) {
+    fft3d_phase1_kernel<<<ctas, kThreads3d, 0, s>>>(p, static_cast<float2 *>(scratch), c0, c1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fft3d_phase3(const ApplyParams &p, int ctas, const void *scratch, int64_t c0, int64_t c1,
+                                cudaStream_t s) {
+    // claim counter of this chunk
+    cudaError_t e = cudaMemsetAsync(p.ctrl, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    fft3d_phase3_kernel<<<ctas, kThreads3d, 0, s>>>(p, static_cast<const float2 *>(scratch), c0, c1);
+    return cudaGetLastError();
+}
 
 // ---------------------------------------------------------------------------
 // FP64 3D spectra: windows psi [nspec][W][W][W] at [0, W)^3, stored Hermitian

@@ -173,7 +173,11 @@ struct pc_operator {
     int32_t done_cap = 0;
     int32_t *d_ctrl = nullptr;
     void *d_tw = nullptr;
-    void *d_scratch = nullptr;   // 3D: per-CTA spectrum volumes
+    void *d_scratch = nullptr;   // 3D: per-CTA spectrum volumes (FP32) or per-item volumes of a chunk (BF16x3)
+    int64_t scratch_items = 0;   // BF16x3 3D: items d_scratch holds
+    void *d_tc_ops = nullptr;    // BF16x3 3D: DFT operand tiles for the tensor cores
+    std::vector<cudaEvent_t> stage_ev;   // BF16x3 3D: [chunk][stage][begin, end] of the last apply
+    int stage_chunks = 0;
     uint32_t epoch = 0;
     cudaStream_t last_stream = nullptr;
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;   // around the fused kernel of the last apply
@@ -207,6 +211,18 @@ cudaError_t launch_fft3d(const ApplyParams &p, int ctas, void *scratch, cudaStre
 size_t fft3d_scratch_bytes(int ctas);
 cudaError_t build_spectra_3d(const double *d_psi, int nspec, int W, int P, void *d_spec, const double2 *d_tw64,
                              cudaStream_t s);
+// split 3D path: phase 1 and phase 3 over items [c0, c1), scratch volume of
+// item i at scratch + (i - c0) * fft3d_scratch_bytes(1)
+cudaError_t launch_fft3d_phase1(const ApplyParams &p, int ctas, void *scratch, int64_t c0, int64_t c1,
+                                cudaStream_t s);
+cudaError_t launch_fft3d_phase3(const ApplyParams &p, int ctas, const void *scratch, int64_t c0, int64_t c1,
+                                cudaStream_t s);
+// tensor-core first-axis transform (pc_tc3d.cu), one CTA per SM
+constexpr int64_t kTc3dChunkItems = 4096;
+cudaError_t tc3d_build_operands(void **d_ops);
+cudaError_t tc3d_configure();
+cudaError_t launch_tc3d_axis0(const ApplyParams &p, int ctas, void *scratch, int64_t c0, int64_t c1,
+                              const void *ops, cudaStream_t s);
 pc_status plain_apply(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
                       cudaStream_t s, std::string &err);
 void plain_free(pc_operator *op);
