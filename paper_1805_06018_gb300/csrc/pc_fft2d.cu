@@ -24,6 +24,7 @@
 // earlier by running CTAs: the wait always ends.
 #include "pc_fftcore.cuh"
 #include "pc_internal.h"
+#include "pc_overlap.cuh"
 #include "pc_ptx.cuh"
 
 namespace pc {
@@ -103,32 +104,16 @@ __device__ __forceinline__ void prefetch_item(const ApplyParams &p, const int *c
     }
 }
 
-__device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float c, float d) {
-    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c),
-                 "f"(d)
-                 : "memory");
-}
-
 // Overlap-add of one output row of a line: value m (< L2) goes to y[g0 + m]
-// when 0 <= g0 + m < width.
-//
-// FP32: the values are laid out in the line's staging row `st` (re part, then
-// im part, each shifted so that a 16-byte aligned y address meets a 16-byte
-// aligned staging address), then lane 0 of the line hands the aligned
-// interior of each part to the TMA unit as one bulk add-reduction; the at most
-// three ragged values at either end are added by single atomics.  The
-// reductions stay asynchronous until the end of phase C.  FP64 adds element
-// by element.
+// when 0 <= g0 + m < width.  FP32 stages the row and hands its aligned
+// interior to bulk add-reductions (add_row_f32); FP64 adds element by element.
 template <typename T, int P, typename C>
 __device__ __forceinline__ void add_row(const C *a, int t, unsigned lmask, float *st, T *y0, T *y1, bool has1, int g0,
                                         int L2, int width) {
     constexpr int R1 = FftShape<P>::R1, R2 = FftShape<P>::R2;
-    const int lo = max(g0, 0), hi = min(g0 + L2, width);   // [lo, hi) in y coordinates
     if constexpr (sizeof(T) == 8) {
         (void)st;
         (void)lmask;
-        (void)lo;
-        (void)hi;
 #pragma unroll
         for (int j = 0; j < R1; ++j) {
             const int m = t + R2 * j;
@@ -139,46 +124,7 @@ __device__ __forceinline__ void add_row(const C *a, int t, unsigned lmask, float
             }
         }
     } else {
-        constexpr int IMOFF = Smem2d<T, P>::IMOFF;
-        // y row alignment (in elements, mod 4) and the aligned origin q <= lo of each part
-        const int off0 = int((reinterpret_cast<uintptr_t>(y0) >> 2) & 3);
-        const int off1 = int((reinterpret_cast<uintptr_t>(y1) >> 2) & 3);
-        const int q0 = ((lo + off0) & ~3) - off0, q1 = ((lo + off1) & ~3) - off1;
-        // the previous row's bulk reductions have finished reading `st`
-        if (t == 0) bulk_wait_read();
-        __syncwarp(lmask);
-#pragma unroll
-        for (int j = 0; j < R1; ++j) {
-            const int gx = g0 + t + R2 * j;
-            if (gx >= lo && gx < hi) {
-                st[gx - q0] = a[j].x;
-                st[IMOFF + gx - q1] = a[j].y;
-            }
-        }
-        fence_proxy_async_smem();   // these generic writes are read by the bulk (async-proxy) reductions
-        __syncwarp(lmask);
-        // aligned interior [a, b) of each part; ragged ends by atomics
-        const int a0 = lo == q0 ? q0 : q0 + 4, b0 = q0 + ((hi - q0) & ~3);
-        const int a1 = lo == q1 ? q1 : q1 + 4, b1 = q1 + ((hi - q1) & ~3);
-        if (t == 0) {
-            if (b0 > a0) bulk_reduce_add_f32(y0 + a0, st + (a0 - q0), uint32_t(b0 - a0) * 4u);
-            if (has1 && b1 > a1) bulk_reduce_add_f32(y1 + a1, st + IMOFF + (a1 - q1), uint32_t(b1 - a1) * 4u);
-            bulk_commit();
-        }
-        if (b0 > a0) {
-            for (int gx = lo + t; gx < a0; gx += R2) atomicAdd(y0 + gx, st[gx - q0]);
-            for (int gx = b0 + t; gx < hi; gx += R2) atomicAdd(y0 + gx, st[gx - q0]);
-        } else {
-            for (int gx = lo + t; gx < hi; gx += R2) atomicAdd(y0 + gx, st[gx - q0]);
-        }
-        if (has1) {
-            if (b1 > a1) {
-                for (int gx = lo + t; gx < a1; gx += R2) atomicAdd(y1 + gx, st[IMOFF + gx - q1]);
-                for (int gx = b1 + t; gx < hi; gx += R2) atomicAdd(y1 + gx, st[IMOFF + gx - q1]);
-            } else {
-                for (int gx = lo + t; gx < hi; gx += R2) atomicAdd(y1 + gx, st[IMOFF + gx - q1]);
-            }
-        }
+        add_row_f32<P>(a, t, lmask, st, Smem2d<T, P>::IMOFF, y0, y1, has1, g0, L2, width);
     }
 }
 

@@ -29,6 +29,7 @@ namespace pc {
 constexpr int kThreads3d = 256;
 constexpr int kP3 = 64;
 constexpr long long kSpinLimit3 = 1ll << 24;
+constexpr int kSmem3 = kP3 * kP3 * int(sizeof(float2));
 
 // One work item: tile `ti` of the schedule and right-hand-side pair `pair`
 // (columns 2 pair and 2 pair + 1 packed as the real and imaginary parts).
@@ -224,6 +225,8 @@ __device__ __forceinline__ void phase3_3d(const ApplyParams &p, const Item3 &it,
             RowScratch<P, C> scr{S, o1};
             fft_line<P, true>(a, L.tw, L.t, scr, L.lmask);
             const int64_t yr = int64_t(gy0) * plane_box + int64_t(gy1) * n2box;
+            // a warp's atomics land in 32-byte sectors of four output rows;
+            // staging the row for vector or bulk reductions measured slower
 #pragma unroll
             for (int j = 0; j < R1; ++j) {
                 const int o2 = L.t + R2 * j;
@@ -245,7 +248,8 @@ __device__ __forceinline__ void phase3_3d(const ApplyParams &p, const Item3 &it,
 // The fused FP32 kernel: persistent CTAs claim items in increasing order and
 // run the three phases through their own scratch volume.
 __global__ void __launch_bounds__(kThreads3d, 3) fft3d_kernel(const ApplyParams p, float2 *scratch) {
-    __shared__ __align__(16) float2 S[kP3 * kP3];
+    extern __shared__ __align__(16) unsigned char smem3[];
+    float2 *S = reinterpret_cast<float2 *>(smem3);
     __shared__ int64_t s_item;
     const Lines3 L(static_cast<const float2 *>(p.tw));
     float2 *G = scratch + int64_t(blockIdx.x) * kP3 * kP3 * kP3;
@@ -279,7 +283,8 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase1_kernel(const Apply
 // to 0 before the launch) so that the overlap-add order is the fused kernel's.
 __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase3_kernel(const ApplyParams p, const float2 *scratch,
                                                                      int64_t c0, int64_t c1) {
-    __shared__ __align__(16) float2 S[kP3 * kP3];
+    extern __shared__ __align__(16) unsigned char smem3[];
+    float2 *S = reinterpret_cast<float2 *>(smem3);
     __shared__ int64_t s_item;
     const Lines3 L(static_cast<const float2 *>(p.tw));
     for (;;) {
@@ -295,14 +300,17 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase3_kernel(const Apply
 }
 
 cudaError_t fft3d_configure(int *ctas_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(fft3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fft3d_phase3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
     int n = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fft3d_kernel, kThreads3d, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fft3d_kernel, kThreads3d, kSmem3);
     if (ctas_per_sm) *ctas_per_sm = n;
     return e;
 }
 
 cudaError_t launch_fft3d(const ApplyParams &p, int ctas, void *scratch, cudaStream_t s) {
-    fft3d_kernel<<<ctas, kThreads3d, 0, s>>>(p, static_cast<float2 *>(scratch));
+    fft3d_kernel<<<ctas, kThreads3d, kSmem3, s>>>(p, static_cast<float2 *>(scratch));
     return cudaGetLastError();
 }
 
@@ -319,7 +327,7 @@ cudaError_t launch_fft3d_phase3(const ApplyParams &p, int ctas, const void *scra
     // claim counter of this chunk
     cudaError_t e = cudaMemsetAsync(p.ctrl, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    fft3d_phase3_kernel<<<ctas, kThreads3d, 0, s>>>(p, static_cast<const float2 *>(scratch), c0, c1);
+    fft3d_phase3_kernel<<<ctas, kThreads3d, kSmem3, s>>>(p, static_cast<const float2 *>(scratch), c0, c1);
     return cudaGetLastError();
 }
 

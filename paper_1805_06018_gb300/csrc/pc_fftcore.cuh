@@ -33,6 +33,28 @@ template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {  // a * con
     return C{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
 }
 
+// Butterfly sum and difference.  For FP32 both components go through one
+// packed two-lane instruction (add/sub.rn.f32x2, round-to-nearest per lane,
+// the same result as two scalar operations); FP64 stays scalar.
+template <typename C> __device__ __forceinline__ C badd(C a, C b) { return cadd(a, b); }
+template <typename C> __device__ __forceinline__ C bsub(C a, C b) { return csub(a, b); }
+template <> __device__ __forceinline__ float2 badd<float2>(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "add.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+template <> __device__ __forceinline__ float2 bsub<float2>(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "sub.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
 // cos and sin of 2*pi*e/16 for e = 0..15 (exact values of the regular
 // 16-gon: cos(pi/8) = sqrt(2 + sqrt 2)/2, sin(pi/8) = sqrt(2 - sqrt 2)/2).
 __host__ __device__ constexpr double kC16(int e) {
@@ -94,10 +116,18 @@ __device__ __forceinline__ void dit_stage(C *a) {
     if constexpr (B < N / 2) {
         constexpr int half = LEN / 2, blk = B / half, k = B % half;
         constexpr int i0 = blk * LEN + k, i1 = i0 + half;
+        constexpr int e = (k * (16 / LEN)) & 15;   // W_LEN^k = W_16^(16k/LEN)
         const C u = a[i0];
-        const C v = tw16<k * (16 / LEN), INV>(a[i1]);   // W_LEN^k = W_16^(16k/LEN)
-        a[i0] = cadd(u, v);
-        a[i1] = csub(u, v);
+        if constexpr (e == 4 || e == 12) {
+            // +-i: a swap of components, cheaper as scalar operations
+            const C v = tw16<e, INV>(a[i1]);
+            a[i0] = cadd(u, v);
+            a[i1] = csub(u, v);
+        } else {
+            const C v = tw16<e, INV>(a[i1]);
+            a[i0] = badd(u, v);
+            a[i1] = bsub(u, v);
+        }
         dit_stage<N, INV, LEN, B + 1>(a);
     }
 }

@@ -80,6 +80,64 @@ __device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const uint8_t *a_til
     }
 }
 
+// One unit: 128 consecutive (k2, k1) lines of one work item.
+struct Unit {
+    int line0, n0, L0, steps1, spec;
+    float2 *G;   // the item's scratch volume [plane][k2][k1]
+};
+
+__device__ __forceinline__ Unit unit_of(const ApplyParams &p, float2 *scratch, int64_t c0, int64_t nitems,
+                                        int64_t u) {
+    // block index major, so that the items of one tile (all pairs) read the
+    // same 64 KB spectrum block close together in time
+    const int blk = int(u / nitems);
+    const int64_t item = c0 + (u - int64_t(blk) * nitems);
+    int c = 0;
+    while (int64_t(p.color_start[c + 1]) * p.npairs <= item) ++c;
+    const int64_t cbase = int64_t(p.color_start[c]) * p.npairs;
+    const int ntc = p.color_start[c + 1] - p.color_start[c];
+    const Tile &tile = p.tiles[p.color_start[c] + int((item - cbase) % ntc)];
+    Unit x;
+    x.n0 = tile.in_ext[0];
+    x.L0 = x.n0 + tile.kext[0] - 1;
+    x.steps1 = (2 * x.n0 + 15) / 16;
+    x.spec = tile.spec;
+    x.G = scratch + (item - c0) * int64_t(kP) * kPlane;
+    x.line0 = blk * kBlock;
+    return x;
+}
+
+// The GEMM-1 input of a unit: thread (m = tid % 128, h = tid / 128) holds
+// groups g = h + 2 e of 4 planes (8 K values) of line line0 + m.  All loads
+// are issued before any is used.
+__device__ __forceinline__ void stage_load(const Unit &x, int tid, float2 (&z)[32]) {
+    const int m = tid & (kBlock - 1), h = tid >> 7;
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i0 = 4 * (h + 2 * e) + q;
+            z[4 * e + q] = i0 < x.n0 ? __ldcg(x.G + int64_t(i0) * kPlane + x.line0 + m) : make_float2(0.f, 0.f);
+        }
+}
+
+__device__ __forceinline__ void stage_store(const Unit &x, int tid, const float2 (&z)[32], uint8_t *sA) {
+    const int m = tid & (kBlock - 1), h = tid >> 7;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int g = h + 2 * e;
+        if (g < 2 * x.steps1) {
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                v[2 * q] = z[4 * e + q].x;
+                v[2 * q + 1] = z[4 * e + q].y;
+            }
+            split8_store(sA, tc::kmajor_offset(m, 8 * g, kK, 2), v);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     tc3d_axis0_kernel(const ApplyParams p, float2 *scratch, int64_t c0, int64_t c1, const uint8_t *ops) {
     extern __shared__ __align__(1024) uint8_t sm[];
@@ -118,78 +176,65 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int erow = 32 * quarter + lane;
     const float2 *spec_all = static_cast<const float2 *>(p.spec);
 
-    for (int64_t u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
-        // unit order: block index major, so that the items of one tile (all
-        // pairs) read the same 64 KB spectrum block close together in time
-        const int blk = int(u / nitems);
-        const int64_t item = c0 + (u - int64_t(blk) * nitems);
-        int c = 0;
-        while (int64_t(p.color_start[c + 1]) * p.npairs <= item) ++c;
-        const int64_t cbase = int64_t(p.color_start[c]) * p.npairs;
-        const int ntc = p.color_start[c + 1] - p.color_start[c];
-        const int ti = p.color_start[c] + int((item - cbase) % ntc);
-        const Tile &tile = p.tiles[ti];
-        const int n0 = tile.in_ext[0];
-        const int L0 = n0 + tile.kext[0] - 1;
-        const int steps1 = (2 * n0 + 15) / 16;
-        float2 *G = scratch + (item - c0) * int64_t(kP) * kPlane;
-        const int line0 = blk * kBlock;
-
-        // ---- A = split(U): row m = line0 + m, K = (i0, re|im), groups of 4 planes
-        {
-            const int m = tid & (kBlock - 1), h = tid >> 7;
-            for (int g = h; g < 2 * steps1; g += 2) {
-                float v[8];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int i0 = 4 * g + q;
-                    const float2 z = i0 < n0 ? __ldcg(G + int64_t(i0) * kPlane + line0 + m) : make_float2(0.f, 0.f);
-                    v[2 * q] = z.x;
-                    v[2 * q + 1] = z.y;
-                }
-                split8_store(sA, tc::kmajor_offset(m, 8 * g, kK, 2), v);
-            }
-        }
+    // software pipeline: the next unit's input is loaded while GEMM 2 runs,
+    // the spectrum while GEMM 1 runs
+    float2 z[32];
+    int64_t u = blockIdx.x;
+    Unit cur{};
+    if (ok && u < nunits) {
+        cur = unit_of(p, scratch, c0, nitems, u);
+        stage_load(cur, tid, z);
+    }
+    for (; ok && u < nunits; u += gridDim.x) {
+        // ---- A = split(U): rows = lines, K = (i0, re|im)
+        stage_store(cur, tid, z, sA);
         fence_proxy_async_smem();
         tc::fence_before_sync();
         __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
-            issue_gemm(tmem, sA, sF1, steps1);
+            issue_gemm(tmem, sA, sF1, cur.steps1);
             tc::mma_commit(bar_mma);
         }
         mma_pending = true;
+        // spectrum of this thread's line, k0 = 32 half ... 32 half + 31
+        // (Hermitian mirror for k2 > P/2)
+        float2 f[32];
+        {
+            const int line = cur.line0 + erow, k2 = line / kP, k1 = line % kP;
+            const bool mirror = k2 > kP / 2;
+            const float2 *sp = spec_all + int64_t(cur.spec) * p.spec_stride +
+                               (mirror ? (int64_t(kP - k2) * kP + ((kP - k1) & (kP - 1))) * kP
+                                       : (int64_t(k2) * kP + k1) * kP);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int k0 = 32 * half + j;
+                f[j] = __ldg(sp + (mirror ? ((kP - k0) & (kP - 1)) : k0));
+                if (mirror) f[j].y = -f[j].y;
+            }
+        }
         ok = __syncthreads_and(mbar_wait_bounded(bar_mma, phase, kSpin));
         if (!ok) break;
         mma_pending = false;
         phase ^= 1u;
         tc::fence_after_sync();
 
-        // ---- V^ = D1 * phi^ (Hermitian mirror for k2 > P/2), split into A
-        {
-            const int line = line0 + erow, k2 = line / kP, k1 = line % kP;
-            const bool mirror = k2 > kP / 2;
-            const float2 *sp = spec_all + int64_t(tile.spec) * p.spec_stride +
-                               (mirror ? (int64_t(kP - k2) * kP + ((kP - k1) & (kP - 1))) * kP
-                                       : (int64_t(k2) * kP + k1) * kP);
-#pragma unroll 1
-            for (int cc = 0; cc < 2; ++cc) {
-                float v[32];
-                tc::tmem_ld32(tmem + (uint32_t(32 * quarter) << 16) + uint32_t(64 * half + 32 * cc), v);
+        // ---- V^ = D1 * phi^, split into A (K = (k0, re|im))
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int k0 = 32 * half + 16 * cc + j;
-                    float2 f = __ldg(sp + (mirror ? ((kP - k0) & (kP - 1)) : k0));
-                    if (mirror) f.y = -f.y;
-                    const float re = v[2 * j] * f.x - v[2 * j + 1] * f.y;
-                    const float im = v[2 * j] * f.y + v[2 * j + 1] * f.x;
-                    v[2 * j] = re;
-                    v[2 * j + 1] = im;
-                }
+        for (int cc = 0; cc < 2; ++cc) {
+            float v[32];
+            tc::tmem_ld32(tmem + (uint32_t(32 * quarter) << 16) + uint32_t(64 * half + 32 * cc), v);
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
-                    split8_store(sA, tc::kmajor_offset(erow, 64 * half + 32 * cc + 8 * r, kK, 2), v + 8 * r);
+            for (int j = 0; j < 16; ++j) {
+                const float2 w = f[16 * cc + j];
+                const float re = v[2 * j] * w.x - v[2 * j + 1] * w.y;
+                const float im = v[2 * j] * w.y + v[2 * j + 1] * w.x;
+                v[2 * j] = re;
+                v[2 * j + 1] = im;
             }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                split8_store(sA, tc::kmajor_offset(erow, 64 * half + 32 * cc + 8 * r, kK, 2), v + 8 * r);
         }
         fence_proxy_async_smem();
         tc::fence_before_sync();
@@ -200,6 +245,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::mma_commit(bar_mma);
         }
         mma_pending = true;
+        Unit nxt = cur;
+        if (u + gridDim.x < nunits) {
+            nxt = unit_of(p, scratch, c0, nitems, u + gridDim.x);
+            stage_load(nxt, tid, z);
+        }
         ok = __syncthreads_and(mbar_wait_bounded(bar_mma, phase, kSpin));
         if (!ok) break;
         mma_pending = false;
@@ -208,20 +258,21 @@ __global__ void __launch_bounds__(kThreads, 1)
 
         // ---- output planes o0 < L0 back into G (in place: this unit's lines only)
         {
-            float2 *g = G + line0 + erow;
-#pragma unroll 1
+            float2 *g = cur.G + cur.line0 + erow;
+#pragma unroll
             for (int cc = 0; cc < 2; ++cc) {
                 float v[32];
                 tc::tmem_ld32(tmem + (uint32_t(32 * quarter) << 16) + uint32_t(64 * half + 32 * cc), v);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int o0 = 32 * half + 16 * cc + j;
-                    if (o0 < L0) __stcg(g + int64_t(o0) * kPlane, make_float2(v[2 * j], v[2 * j + 1]));
+                    if (o0 < cur.L0) __stcg(g + int64_t(o0) * kPlane, make_float2(v[2 * j], v[2 * j + 1]));
                 }
             }
         }
         tc::fence_before_sync();
         __syncthreads();
+        cur = nxt;
     }
     if (!ok) {
         if (tid == 0) atomicExch(p.ctrl + 2, 1);
