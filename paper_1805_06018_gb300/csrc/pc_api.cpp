@@ -84,6 +84,7 @@ void free_operator(pc_operator *op) {
     cudaFree(op->d_tw);
     cudaFree(op->d_scratch);
     cudaFree(op->d_tc_ops);
+    cudaFree(op->d_tc_order);
     for (cudaEvent_t ev : op->stage_ev) cudaEventDestroy(ev);
     if (op->ev_begin) cudaEventDestroy(op->ev_begin);
     if (op->ev_end) cudaEventDestroy(op->ev_end);
@@ -220,7 +221,9 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     // sub-windows (nsub chosen to minimise the FFT work per input pixel,
     // nsub^2 / T^2).
     const int Wfull = 2 * radius + 1;
-    const int cap = three ? P : (2 * P) / 3;   // the 3D kernel gathers directly, without staging
+    // the 3D kernels gather directly, without staging; the tensor-core path
+    // keeps GEMM-1 operands of K <= 2 kTc3dMaxTile in shared memory
+    const int cap = three ? (prec == PC_BF16X3 ? pc::kTc3dMaxTile : P) : (2 * P) / 3;
     pc::WindowSplit split;
     int T = 0;
     {
@@ -383,9 +386,10 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     if (e == cudaSuccess && three && prec == PC_BF16X3) {
         // the chunk scratch volumes are allocated by the first apply (their
         // number depends on the batch)
+        op->tc_k1cap = pc::tc3d_k1cap(T);
         e = pc::tc3d_configure();
-        if (e == cudaSuccess) e = pc::tc3d_build_operands(&op->d_tc_ops);
-        if (e == cudaSuccess) acct += 4 * 32768;
+        if (e == cudaSuccess) e = pc::tc3d_build_operands(op->tc_k1cap, &op->d_tc_ops);
+        if (e == cudaSuccess) acct += size_t(op->tc_k1cap) * 512 + 65536;
     }
     cudaFree(d_psi);
     cudaFree(d_tw64);
@@ -455,6 +459,38 @@ static pc_status apply_split3d(pc_operator *op, const pc::ApplyParams &p, cudaSt
         op->scratch_items = chunk;
     }
     const int nchunks = int((total + chunk - 1) / chunk);
+    if (op->tc_order_npairs != p.npairs) {
+        // items of each chunk sorted by (tile, pair): the tensor stage then
+        // visits the pairs of one tile and line block back to back
+        const int32_t np = p.npairs;
+        std::vector<int32_t> order(static_cast<size_t>(total));
+        std::vector<std::pair<int64_t, int32_t>> key;
+        for (int c = 0; c < nchunks; ++c) {
+            const int64_t c0 = int64_t(c) * chunk, c1 = std::min<int64_t>(total, c0 + chunk);
+            key.clear();
+            for (int64_t item = c0; item < c1; ++item) {
+                int col = 0;
+                while (int64_t(op->color_start_h[col + 1]) * np <= item) ++col;
+                const int64_t base = int64_t(op->color_start_h[col]) * np;
+                const int ntc = op->color_start_h[col + 1] - op->color_start_h[col];
+                const int64_t ti = op->color_start_h[col] + (item - base) % ntc, pair = (item - base) / ntc;
+                key.emplace_back(ti * np + pair, int32_t(item));
+            }
+            std::sort(key.begin(), key.end());
+            for (size_t i = 0; i < key.size(); ++i) order[size_t(c0) + i] = key[i].second;
+        }
+        if (op->d_tc_order && (e = cudaDeviceSynchronize()) != cudaSuccess)
+            return cuda_fail(ctx, e, "synchronising before replacing the unit order");
+        cudaFree(op->d_tc_order);
+        op->d_tc_order = nullptr;
+        op->tc_order_npairs = 0;
+        if ((e = cudaMalloc(&op->d_tc_order, order.size() * sizeof(int32_t))) != cudaSuccess)
+            return cuda_fail(ctx, e, "allocating the unit order");
+        if ((e = cudaMemcpy(op->d_tc_order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            return cuda_fail(ctx, e, "uploading the unit order");
+        op->tc_order_npairs = np;
+    }
     while (op->stage_ev.size() < size_t(nchunks) * 6) {
         cudaEvent_t ev = nullptr;
         if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(ctx, e, "creating events");
@@ -472,7 +508,8 @@ static pc_status apply_split3d(pc_operator *op, const pc::ApplyParams &p, cudaSt
         cudaEventRecord(ev[1], s);
         if (e != cudaSuccess) break;
         cudaEventRecord(ev[2], s);
-        e = pc::launch_tc3d_axis0(p, ctx->num_sms, op->d_scratch, c0, c1, op->d_tc_ops, s);
+        e = pc::launch_tc3d_axis0(p, ctx->num_sms, op->d_scratch, op->d_tc_order, c0, c1, op->d_tc_ops,
+                                  op->tc_k1cap, s);
         cudaEventRecord(ev[3], s);
         if (e != cudaSuccess) break;
         cudaEventRecord(ev[4], s);
@@ -504,7 +541,9 @@ pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t
     DeviceGuard dg(ctx->device);
     if (!dg.ok) return fail(ctx, PC_ERR_CUDA, "cannot select the context's device");
     const int32_t npairs = (nrhs + 1) / 2;
-    pc_status st = ensure_done_capacity(op, npairs);
+    // the split 3D path keeps one flag per output-plane group of phase 3
+    const bool split3d = op->d == 3 && op->prec == PC_BF16X3;
+    pc_status st = ensure_done_capacity(op, split3d ? npairs * pc::kPhase3Groups : npairs);
     if (st != PC_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (++op->epoch == 0) op->epoch = 1;
@@ -538,7 +577,7 @@ pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t
         if (e == cudaSuccess) e = cudaEventCreate(&op->ev_end);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "creating events");
     }
-    if (op->d == 3 && op->prec == PC_BF16X3) return apply_split3d(op, p, s);
+    if (split3d) return apply_split3d(op, p, s);
     cudaError_t e = pc::launch_zero(p, op->N, op->prec, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the zero kernel");
     const int ctas = int(std::min<int64_t>(op->ctas, p.total_items));

@@ -165,11 +165,13 @@ __device__ __forceinline__ void phase2_3d(const ApplyParams &p, const Item3 &it,
 }
 
 // ordered overlap-add: wait (bounded) until every overlapping tile of a lower
-// colour has published its contribution for this pair
-__device__ __forceinline__ void wait_deps_3d(const ApplyParams &p, const Item3 &it) {
+// colour has published its contribution for this pair.  A tile's flags for
+// the pair are `ng` consecutive words (one per output-plane group) starting
+// at done[tile * done_ld + pair * ng].
+__device__ __forceinline__ void wait_deps_3d(const ApplyParams &p, const Item3 &it, int ng) {
     const int d0 = p.dep_start[it.ti], nd = p.dep_start[it.ti + 1] - d0;
-    for (int d = threadIdx.x; d < nd; d += blockDim.x) {
-        const uint32_t *f = p.done + int64_t(p.dep[d0 + d]) * p.done_ld + it.pair;
+    for (int d = threadIdx.x; d < nd * ng; d += blockDim.x) {
+        const uint32_t *f = p.done + int64_t(p.dep[d0 + d / ng]) * p.done_ld + int64_t(it.pair) * ng + d % ng;
         long long spins = 0;
         while (ld_acquire_u32(f) != p.epoch) {
             if (++spins > kSpinLimit3) {
@@ -183,10 +185,11 @@ __device__ __forceinline__ void wait_deps_3d(const ApplyParams &p, const Item3 &
     __syncthreads();
 }
 
-// phase 3: inverse 2D FFT of each needed output plane and the overlap-add of
-// its L1 x L2 box into y; then publish this item's flag
+// phase 3: inverse 2D FFT of the output planes o0 in [ob, oe) (of the L0
+// needed) and the overlap-add of their L1 x L2 boxes into y; then publish
+// `flag`
 __device__ __forceinline__ void phase3_3d(const ApplyParams &p, const Item3 &it, const float2 *G, float2 *S,
-                                          const Lines3 &L) {
+                                          const Lines3 &L, int ob, int oe, uint32_t *flag) {
     using C = float2;
     constexpr int P = Lines3::P, R1 = Lines3::R1, R2 = Lines3::R2, LINES = Lines3::LINES, PP = Lines3::PP;
     const Tile &tile = it.tile;
@@ -198,7 +201,8 @@ __device__ __forceinline__ void phase3_3d(const ApplyParams &p, const Item3 &it,
     float *y1 = has1 ? y0 + p.ldy : y0;
     const int n2box = p.n[2];
     const int64_t plane_box = int64_t(p.n[1]) * n2box;
-    for (int o0 = 0; o0 < L0; ++o0) {
+    (void)L0;
+    for (int o0 = ob; o0 < oe; ++o0) {
         const int gy0 = tile.out_lo[0] + o0;
         if (gy0 < 0 || gy0 >= p.n[0]) continue;   // uniform across the CTA
         // inverse along k1 for each k2: rows o1 of S
@@ -241,7 +245,7 @@ __device__ __forceinline__ void phase3_3d(const ApplyParams &p, const Item3 &it,
     }
     if (threadIdx.x == 0) {
         __threadfence();
-        st_release_u32(p.done + int64_t(it.ti) * p.done_ld + it.pair, p.epoch);
+        st_release_u32(flag, p.epoch);
     }
 }
 
@@ -261,8 +265,9 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_kernel(const ApplyParams 
         const Item3 it = decode_item3(p, item);
         phase1_3d(p, it, G, S, L);
         phase2_3d(p, it, G, S, L);
-        wait_deps_3d(p, it);
-        phase3_3d(p, it, G, S, L);
+        wait_deps_3d(p, it, 1);
+        const int L0 = it.tile.in_ext[0] + it.tile.kext[0] - 1;
+        phase3_3d(p, it, G, S, L, 0, L0, p.done + int64_t(it.ti) * p.done_ld + it.pair);
     }
 }
 
@@ -279,23 +284,32 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase1_kernel(const Apply
     }
 }
 
-// Phase 3 claims the chunk's items in increasing order (claim counter reset
-// to 0 before the launch) so that the overlap-add order is the fused kernel's.
+// Phase 3 of the split form works on (item, output-plane group) pieces,
+// kPhase3Groups per item, claimed in increasing order (claim counter reset to
+// 0 before the launch).  A piece waits for every group of each overlapping
+// lower-colour tile, so each voxel still sums its contributions in colour
+// order (the groups of one tile write disjoint planes); the pieces shorten
+// the chain of waits through the colours by the group count.
 __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase3_kernel(const ApplyParams p, const float2 *scratch,
                                                                      int64_t c0, int64_t c1) {
     extern __shared__ __align__(16) unsigned char smem3[];
     float2 *S = reinterpret_cast<float2 *>(smem3);
-    __shared__ int64_t s_item;
+    __shared__ int64_t s_piece;
+    constexpr int NG = kPhase3Groups;
     const Lines3 L(static_cast<const float2 *>(p.tw));
     for (;;) {
         if (threadIdx.x == 0)
-            s_item = c0 + int64_t(atomicAdd(reinterpret_cast<unsigned long long *>(p.ctrl), 1ull));
+            s_piece = c0 * NG + int64_t(atomicAdd(reinterpret_cast<unsigned long long *>(p.ctrl), 1ull));
         __syncthreads();
-        const int64_t item = s_item;
-        if (item >= c1) break;
+        const int64_t piece = s_piece;
+        if (piece >= c1 * NG) break;
+        const int64_t item = piece / NG;
+        const int g = int(piece % NG);
         const Item3 it = decode_item3(p, item);
-        wait_deps_3d(p, it);
-        phase3_3d(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L);
+        wait_deps_3d(p, it, NG);
+        const int L0 = it.tile.in_ext[0] + it.tile.kext[0] - 1;
+        phase3_3d(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L, (L0 * g) / NG, (L0 * (g + 1)) / NG,
+                  p.done + int64_t(it.ti) * p.done_ld + int64_t(it.pair) * NG + g);
     }
 }
 

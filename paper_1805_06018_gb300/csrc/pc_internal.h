@@ -176,6 +176,9 @@ struct pc_operator {
     void *d_scratch = nullptr;   // 3D: per-CTA spectrum volumes (FP32) or per-item volumes of a chunk (BF16x3)
     int64_t scratch_items = 0;   // BF16x3 3D: items d_scratch holds
     void *d_tc_ops = nullptr;    // BF16x3 3D: DFT operand tiles for the tensor cores
+    int tc_k1cap = 0;            // BF16x3 3D: K columns of the GEMM-1 operands
+    int32_t *d_tc_order = nullptr;   // BF16x3 3D: per-chunk item order of the tensor stage
+    int32_t tc_order_npairs = 0;     // ... built for this many pairs
     std::vector<cudaEvent_t> stage_ev;   // BF16x3 3D: [chunk][stage][begin, end] of the last apply
     int stage_chunks = 0;
     uint32_t epoch = 0;
@@ -212,17 +215,26 @@ size_t fft3d_scratch_bytes(int ctas);
 cudaError_t build_spectra_3d(const double *d_psi, int nspec, int W, int P, void *d_spec, const double2 *d_tw64,
                              cudaStream_t s);
 // split 3D path: phase 1 and phase 3 over items [c0, c1), scratch volume of
-// item i at scratch + (i - c0) * fft3d_scratch_bytes(1)
+// item i at scratch + (i - c0) * fft3d_scratch_bytes(1).  Phase 3 keeps
+// kPhase3Groups ordering flags per (tile, pair): done_ld >= npairs * groups.
+constexpr int kPhase3Groups = 4;
 cudaError_t launch_fft3d_phase1(const ApplyParams &p, int ctas, void *scratch, int64_t c0, int64_t c1,
                                 cudaStream_t s);
 cudaError_t launch_fft3d_phase3(const ApplyParams &p, int ctas, const void *scratch, int64_t c0, int64_t c1,
                                 cudaStream_t s);
-// tensor-core first-axis transform (pc_tc3d.cu), one CTA per SM
+// tensor-core first-axis transform (pc_tc3d.cu), one CTA per SM.  Tiles of
+// a BF16x3 operator are at most kTc3dMaxTile wide along the first axis, so
+// GEMM 1 needs K <= kTc3dMaxK1 = 2 kTc3dMaxTile.
 constexpr int64_t kTc3dChunkItems = 4096;
-cudaError_t tc3d_build_operands(void **d_ops);
+constexpr int kTc3dMaxTile = 48;
+constexpr int kTc3dMaxK1 = 2 * kTc3dMaxTile;
+int tc3d_k1cap(int tile);   // GEMM-1 K columns for tiles of extent <= tile
+cudaError_t tc3d_build_operands(int k1cap, void **d_ops);
 cudaError_t tc3d_configure();
-cudaError_t launch_tc3d_axis0(const ApplyParams &p, int ctas, void *scratch, int64_t c0, int64_t c1,
-                              const void *ops, cudaStream_t s);
+// order: the items of every chunk [c0, c1) in tile-then-pair order (absolute
+// item indices, entries c0 ... c1 - 1)
+cudaError_t launch_tc3d_axis0(const ApplyParams &p, int ctas, void *scratch, const int32_t *order, int64_t c0,
+                              int64_t c1, const void *ops, int k1cap, cudaStream_t s);
 pc_status plain_apply(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
                       cudaStream_t s, std::string &err);
 void plain_free(pc_operator *op);

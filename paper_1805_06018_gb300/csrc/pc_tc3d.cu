@@ -18,9 +18,12 @@
 // is taken as a_lo b_hi + a_hi b_lo + a_hi b_hi with FP32 accumulation in
 // tensor memory (the a_lo b_lo term, ~2^-16 relative, is dropped).
 //
-// F1 and F2 (hi and lo, 128 KB) are copied into shared memory once per CTA by
-// the bulk-copy (TMA) engine; the data tile is split and written by the
-// threads; D1 and D2 live in 128 columns of tensor memory.
+// F1 (K limited to k1cap = 16 ceil(2 T / 16) columns, T <= 48 the tile
+// extent) and F2 are copied into shared memory once per CTA by the bulk-copy
+// (TMA) engine; the data tiles are split and written by the threads; D1 and D2
+// live in two 128-column blocks of tensor memory.  Two units are in flight:
+// GEMM 2 of unit u and GEMM 1 of unit u+1 run back to back on the tensor
+// pipe while the threads finish unit u and stage unit u+2.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -38,22 +41,26 @@ constexpr int kP = 64;
 constexpr int kPlane = kP * kP;                     // (k2, k1) lines per item
 constexpr int kBlock = 128;                         // lines per unit = MMA M
 constexpr int kUnitsPerItem = kPlane / kBlock;      // 32
-constexpr int kK = 2 * kP;                          // (index, re|im) = MMA K and N
+constexpr int kK = 2 * kP;                          // (index, re|im): K of GEMM 2, N of both
 constexpr int kTile = kBlock * kK * 2;              // one BF16 128 x 128 operand tile: 32 KB
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
+constexpr int kQuads = kThreads / kBlock;          // threads per line in staging, warps per lane quarter
 constexpr uint32_t kLBO = 128u;                     // core matrices adjacent along K
-constexpr uint32_t kSBO = uint32_t(kK * 2 / 16) * 128u;   // 8-row groups: 2048 B
-constexpr int kSmem = 6 * kTile + 64;
+constexpr uint32_t kSBO2 = uint32_t(kK * 2 / 16) * 128u;   // 8-row groups of a K = 128 tile: 2048 B
 constexpr long long kSpin = 1ll << 24;
 constexpr uint32_t kIdesc = tc::idesc_bf16(kBlock, kK);
 
-static_assert(kSmem <= 227 * 1024, "shared memory");
+// bytes of one BF16 128 x k operand tile (hi or lo)
+__host__ __device__ constexpr int tile_bytes(int k) { return kBlock * k * 2; }
+// shared layout: [F1 hi|lo (k1cap) | F2 hi|lo | A2 hi|lo | A1 hi|lo (k1cap) | 3 mbarriers, TMEM slot]
+__host__ __device__ constexpr int smem_bytes(int k1cap) { return 4 * tile_bytes(k1cap) + 4 * kTile + 64; }
+
+static_assert(smem_bytes(kTc3dMaxK1) <= 227 * 1024, "shared memory");
 static_assert(tc::kmajor_offset(kBlock - 1, kK - 1, kK, 2) == kTile - 2, "tile layout");
 
-// shared layout: [F1 hi | F1 lo | F2 hi | F2 lo | A hi | A lo | mbarriers, TMEM slot]
-
 // 8 consecutive K values of one row -> hi and lo 16-byte core-matrix rows
-__device__ __forceinline__ void split8_store(uint8_t *hi_tile, uint32_t off, const float *v) {
+// (the lo tile follows the hi tile at `lo_off` bytes)
+__device__ __forceinline__ void split8_store(uint8_t *hi_tile, int lo_off, uint32_t off, const float *v) {
     uint32_t h[4], l[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -64,16 +71,18 @@ __device__ __forceinline__ void split8_store(uint8_t *hi_tile, uint32_t off, con
         l[i] = *reinterpret_cast<const uint32_t *>(&lb);
     }
     *reinterpret_cast<uint4 *>(hi_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4 *>(hi_tile + kTile + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    *reinterpret_cast<uint4 *>(hi_tile + lo_off + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// D (tensor memory) = A * B^T over `steps` K steps of 16, three split products each
-__device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const uint8_t *a_tile, const uint8_t *b_tile, int steps) {
-    const uint32_t a = smem_u32(a_tile), b = smem_u32(b_tile);
+// D (tensor memory) = A * B^T over `steps` K steps of 16, three split products
+// each; A and B tiles have K_total = sbo / 16 columns (lo tile at lo_off)
+__device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const uint8_t *a_tile, const uint8_t *b_tile, int lo_off,
+                                           uint32_t sbo, int steps) {
+    const uint32_t a = smem_u32(a_tile), b = smem_u32(b_tile), lo = uint32_t(lo_off);
     for (int s = 0; s < steps; ++s) {
         const uint32_t o = 256u * uint32_t(s);
-        const uint64_t ah = tc::smem_desc(a + o, kLBO, kSBO), al = tc::smem_desc(a + kTile + o, kLBO, kSBO);
-        const uint64_t bh = tc::smem_desc(b + o, kLBO, kSBO), bl = tc::smem_desc(b + kTile + o, kLBO, kSBO);
+        const uint64_t ah = tc::smem_desc(a + o, kLBO, sbo), al = tc::smem_desc(a + lo + o, kLBO, sbo);
+        const uint64_t bh = tc::smem_desc(b + o, kLBO, sbo), bl = tc::smem_desc(b + lo + o, kLBO, sbo);
         tc::mma<false>(d_tmem, al, bh, kIdesc, s > 0 ? 1u : 0u);
         tc::mma<false>(d_tmem, ah, bl, kIdesc, 1u);
         tc::mma<false>(d_tmem, ah, bh, kIdesc, 1u);
@@ -86,12 +95,13 @@ struct Unit {
     float2 *G;   // the item's scratch volume [plane][k2][k1]
 };
 
-__device__ __forceinline__ Unit unit_of(const ApplyParams &p, float2 *scratch, int64_t c0, int64_t nitems,
-                                        int64_t u) {
-    // block index major, so that the items of one tile (all pairs) read the
-    // same 64 KB spectrum block close together in time
+// Units of a chunk: u -> block index blk = u / nitems, then the chunk's items
+// in the host-built order order[c0 + r] (sorted by tile, then pair), so that
+// consecutive units share the tile and block and with them the spectrum block.
+__device__ __forceinline__ Unit unit_of(const ApplyParams &p, float2 *scratch, const int32_t *order, int64_t c0,
+                                        int64_t nitems, int64_t u) {
     const int blk = int(u / nitems);
-    const int64_t item = c0 + (u - int64_t(blk) * nitems);
+    const int64_t item = order[c0 + (u - int64_t(blk) * nitems)];
     int c = 0;
     while (int64_t(p.color_start[c + 1]) * p.npairs <= item) ++c;
     const int64_t cbase = int64_t(p.color_start[c]) * p.npairs;
@@ -107,25 +117,28 @@ __device__ __forceinline__ Unit unit_of(const ApplyParams &p, float2 *scratch, i
     return x;
 }
 
-// The GEMM-1 input of a unit: thread (m = tid % 128, h = tid / 128) holds
-// groups g = h + 2 e of 4 planes (8 K values) of line line0 + m.  All loads
-// are issued before any is used.
-__device__ __forceinline__ void stage_load(const Unit &x, int tid, float2 (&z)[32]) {
+// GEMM-1 input of a unit: thread (m = tid % 128, h = tid / 128) holds groups
+// g = h + 4 e (e < 3, g < k1cap / 8) of 4 planes (8 K values) of line
+// line0 + m.  All loads are issued before any is used.
+constexpr int kGroups = kTc3dMaxK1 / 8 / kQuads;   // groups per thread
+static_assert(kGroups * kQuads * 8 == kTc3dMaxK1, "staging groups");
+__device__ __forceinline__ void stage_load(const Unit &x, int tid, float2 (&z)[4 * kGroups]) {
     const int m = tid & (kBlock - 1), h = tid >> 7;
 #pragma unroll
-    for (int e = 0; e < 8; ++e)
+    for (int e = 0; e < kGroups; ++e)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int i0 = 4 * (h + 2 * e) + q;
+            const int i0 = 4 * (h + kQuads * e) + q;
             z[4 * e + q] = i0 < x.n0 ? __ldcg(x.G + int64_t(i0) * kPlane + x.line0 + m) : make_float2(0.f, 0.f);
         }
 }
 
-__device__ __forceinline__ void stage_store(const Unit &x, int tid, const float2 (&z)[32], uint8_t *sA) {
+__device__ __forceinline__ void stage_store(const Unit &x, int tid, const float2 (&z)[4 * kGroups], uint8_t *sA1,
+                                            int k1cap) {
     const int m = tid & (kBlock - 1), h = tid >> 7;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const int g = h + 2 * e;
+    for (int e = 0; e < kGroups; ++e) {
+        const int g = h + kQuads * e;
         if (g < 2 * x.steps1) {
             float v[8];
 #pragma unroll
@@ -133,100 +146,112 @@ __device__ __forceinline__ void stage_store(const Unit &x, int tid, const float2
                 v[2 * q] = z[4 * e + q].x;
                 v[2 * q + 1] = z[4 * e + q].y;
             }
-            split8_store(sA, tc::kmajor_offset(m, 8 * g, kK, 2), v);
+            split8_store(sA1, tile_bytes(k1cap), tc::kmajor_offset(m, 8 * g, k1cap, 2), v);
         }
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
-    tc3d_axis0_kernel(const ApplyParams p, float2 *scratch, int64_t c0, int64_t c1, const uint8_t *ops) {
+// spectrum of the thread's line, k0 = 16 part ... 16 part + 15 (Hermitian
+// mirror for k2 > P/2)
+__device__ __forceinline__ void spectrum_load(const ApplyParams &p, const Unit &x, int erow, int part,
+                                              float2 (&f)[16]) {
+    const int line = x.line0 + erow, k2 = line / kP, k1 = line % kP;
+    const bool mirror = k2 > kP / 2;
+    const float2 *sp = static_cast<const float2 *>(p.spec) + int64_t(x.spec) * p.spec_stride +
+                       (mirror ? (int64_t(kP - k2) * kP + ((kP - k1) & (kP - 1))) * kP : (int64_t(k2) * kP + k1) * kP);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int k0 = 16 * part + j;
+        f[j] = __ldg(sp + (mirror ? ((kP - k0) & (kP - 1)) : k0));
+        if (mirror) f[j].y = -f[j].y;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) tc3d_axis0_kernel(const ApplyParams p, float2 *scratch,
+                                                                 const int32_t *order, int64_t c0, int64_t c1,
+                                                                 const uint8_t *ops, int k1cap) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    uint8_t *sF1 = sm, *sF2 = sm + 2 * kTile, *sA = sm + 4 * kTile;
-    uint64_t *bar_ld = reinterpret_cast<uint64_t *>(sm + 6 * kTile);
-    uint64_t *bar_mma = bar_ld + 1;
-    uint32_t *slot = reinterpret_cast<uint32_t *>(bar_ld + 2);
+    const int t1 = tile_bytes(k1cap);
+    uint8_t *sF1 = sm, *sF2 = sm + 2 * t1, *sA2 = sF2 + 2 * kTile, *sA1 = sA2 + 2 * kTile;
+    uint64_t *bar_ld = reinterpret_cast<uint64_t *>(sA1 + 2 * t1);
+    uint64_t *bar_g1 = bar_ld + 1, *bar_g2 = bar_ld + 2;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(bar_ld + 3);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t nitems = c1 - c0;
-    const int64_t nunits = nitems * kUnitsPerItem;
+    // this CTA's contiguous range of units
+    const int64_t u_begin = nitems * kUnitsPerItem * blockIdx.x / gridDim.x;
+    const int64_t nunits = nitems * kUnitsPerItem * (blockIdx.x + 1) / gridDim.x;
+    const int64_t stride = 1;
+    const uint32_t sbo1 = uint32_t(k1cap) * 16u;
+    const int steps2 = kK / 16;
 
     if (tid == 0) {
         mbar_init(bar_ld, 1);
-        mbar_init(bar_mma, 1);
+        mbar_init(bar_g1, 1);
+        mbar_init(bar_g2, 1);
         fence_mbar_init();
     }
     if (warp == 0) {
-        tc::tmem_alloc(slot, 128);
+        tc::tmem_alloc(slot, 256);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *slot;
+    const uint32_t d1 = tmem, d2 = tmem + 128u;
     if (tid == 0) {
-        mbar_arrive_expect_tx(bar_ld, 4 * kTile);
-        for (int i = 0; i < 4; ++i) bulk_g2s(sm + i * kTile, ops + i * kTile, kTile, bar_ld);
+        mbar_arrive_expect_tx(bar_ld, uint32_t(2 * t1 + 2 * kTile));
+        bulk_g2s(sF1, ops, uint32_t(2 * t1), bar_ld);
+        bulk_g2s(sF2, ops + 2 * t1, uint32_t(2 * kTile), bar_ld);
     }
-    bool ok = __syncthreads_and(mbar_wait_bounded(bar_ld, 0, kSpin));
-    bool mma_pending = false;
-    uint32_t phase = 0;
-
     // epilogue roles: warp w reads tensor-memory lanes 32 (w % 4) ... (its 32
-    // lines) and the column half w / 4
-    const int quarter = warp & 3, half = warp >> 2;
+    // lines) and the column quarter w / 4 (frequencies 16 (w / 4) ...)
+    const int quarter = warp & 3, part = warp >> 2;
     const int erow = 32 * quarter + lane;
-    const float2 *spec_all = static_cast<const float2 *>(p.spec);
+    const uint32_t lane_base = uint32_t(32 * quarter) << 16;
 
-    // software pipeline: the next unit's input is loaded while GEMM 2 runs,
-    // the spectrum while GEMM 1 runs
-    float2 z[32];
-    int64_t u = blockIdx.x;
-    Unit cur{};
-    if (ok && u < nunits) {
-        cur = unit_of(p, scratch, c0, nitems, u);
+    float2 z[4 * kGroups];   // GEMM-1 input of the next unit to be staged
+    float2 f[16];            // spectrum of the unit whose epilogue 1 is next
+    int64_t u = u_begin;
+    Unit cur{}, nxt{};
+    if (u < nunits) {
+        cur = unit_of(p, scratch, order, c0, nitems, u);
         stage_load(cur, tid, z);
     }
-    for (; ok && u < nunits; u += gridDim.x) {
-        // ---- A = split(U): rows = lines, K = (i0, re|im)
-        stage_store(cur, tid, z, sA);
+    bool ok = __syncthreads_and(mbar_wait_bounded(bar_ld, 0, kSpin));
+    bool pend1 = false, pend2 = false;
+    uint32_t ph1 = 0, ph2 = 0;
+    if (ok && u < nunits) {
+        stage_store(cur, tid, z, sA1, k1cap);
         fence_proxy_async_smem();
         tc::fence_before_sync();
         __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
-            issue_gemm(tmem, sA, sF1, cur.steps1);
-            tc::mma_commit(bar_mma);
+            issue_gemm(d1, sA1, sF1, t1, sbo1, cur.steps1);
+            tc::mma_commit(bar_g1);
         }
-        mma_pending = true;
-        // spectrum of this thread's line, k0 = 32 half ... 32 half + 31
-        // (Hermitian mirror for k2 > P/2)
-        float2 f[32];
-        {
-            const int line = cur.line0 + erow, k2 = line / kP, k1 = line % kP;
-            const bool mirror = k2 > kP / 2;
-            const float2 *sp = spec_all + int64_t(cur.spec) * p.spec_stride +
-                               (mirror ? (int64_t(kP - k2) * kP + ((kP - k1) & (kP - 1))) * kP
-                                       : (int64_t(k2) * kP + k1) * kP);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int k0 = 32 * half + j;
-                f[j] = __ldg(sp + (mirror ? ((kP - k0) & (kP - 1)) : k0));
-                if (mirror) f[j].y = -f[j].y;
-            }
+        pend1 = true;
+        if (u + stride < nunits) {
+            nxt = unit_of(p, scratch, order, c0, nitems, u + stride);
+            stage_load(nxt, tid, z);
         }
-        ok = __syncthreads_and(mbar_wait_bounded(bar_mma, phase, kSpin));
+        spectrum_load(p, cur, erow, part, f);
+    }
+    for (; ok && u < nunits; u += stride) {
+        // ---- epilogue 1 of `cur`: V^ = D1 * phi^, split into A2 (K = (k0, re|im))
+        ok = __syncthreads_and(mbar_wait_bounded(bar_g1, ph1, kSpin));
         if (!ok) break;
-        mma_pending = false;
-        phase ^= 1u;
+        pend1 = false;
+        ph1 ^= 1u;
         tc::fence_after_sync();
-
-        // ---- V^ = D1 * phi^, split into A (K = (k0, re|im))
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
+        {
             float v[32];
-            tc::tmem_ld32(tmem + (uint32_t(32 * quarter) << 16) + uint32_t(64 * half + 32 * cc), v);
+            tc::tmem_ld32(d1 + lane_base + uint32_t(32 * part), v);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const float2 w = f[16 * cc + j];
+                const float2 w = f[j];
                 const float re = v[2 * j] * w.x - v[2 * j + 1] * w.y;
                 const float im = v[2 * j] * w.y + v[2 * j + 1] * w.x;
                 v[2 * j] = re;
@@ -234,55 +259,73 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
 #pragma unroll
             for (int r = 0; r < 4; ++r)
-                split8_store(sA, tc::kmajor_offset(erow, 64 * half + 32 * cc + 8 * r, kK, 2), v + 8 * r);
+                split8_store(sA2, kTile, tc::kmajor_offset(erow, 32 * part + 8 * r, kK, 2), v + 8 * r);
         }
         fence_proxy_async_smem();
         tc::fence_before_sync();
         __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
-            issue_gemm(tmem, sA, sF2, kK / 16);
-            tc::mma_commit(bar_mma);
+            issue_gemm(d2, sA2, sF2, kTile, kSBO2, steps2);
+            tc::mma_commit(bar_g2);
         }
-        mma_pending = true;
-        Unit nxt = cur;
-        if (u + gridDim.x < nunits) {
-            nxt = unit_of(p, scratch, c0, nitems, u + gridDim.x);
-            stage_load(nxt, tid, z);
-        }
-        ok = __syncthreads_and(mbar_wait_bounded(bar_mma, phase, kSpin));
-        if (!ok) break;
-        mma_pending = false;
-        phase ^= 1u;
-        tc::fence_after_sync();
+        pend2 = true;
 
-        // ---- output planes o0 < L0 back into G (in place: this unit's lines only)
+        // ---- GEMM 1 of the next unit (its input tile and D1 are free), then
+        // the loads of the unit after it and of the next unit's spectrum
+        const bool has_next = u + stride < nunits;
+        if (has_next) {
+            stage_store(nxt, tid, z, sA1, k1cap);
+            fence_proxy_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                issue_gemm(d1, sA1, sF1, t1, sbo1, nxt.steps1);
+                tc::mma_commit(bar_g1);
+            }
+            pend1 = true;
+        }
+        Unit nn = nxt;
+        if (u + 2 * stride < nunits) {
+            nn = unit_of(p, scratch, order, c0, nitems, u + 2 * stride);
+            stage_load(nn, tid, z);
+        }
+        // the spectrum registers stay valid while the tile and block repeat
+        if (has_next && (nxt.spec != cur.spec || nxt.line0 != cur.line0)) spectrum_load(p, nxt, erow, part, f);
+
+        // ---- epilogue 2 of `cur`: output planes o0 < L0 back into G (in
+        // place: this unit's lines only)
+        ok = __syncthreads_and(mbar_wait_bounded(bar_g2, ph2, kSpin));
+        if (!ok) break;
+        pend2 = false;
+        ph2 ^= 1u;
+        tc::fence_after_sync();
         {
             float2 *g = cur.G + cur.line0 + erow;
+            float v[32];
+            tc::tmem_ld32(d2 + lane_base + uint32_t(32 * part), v);
 #pragma unroll
-            for (int cc = 0; cc < 2; ++cc) {
-                float v[32];
-                tc::tmem_ld32(tmem + (uint32_t(32 * quarter) << 16) + uint32_t(64 * half + 32 * cc), v);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int o0 = 32 * half + 16 * cc + j;
-                    if (o0 < cur.L0) __stcg(g + int64_t(o0) * kPlane, make_float2(v[2 * j], v[2 * j + 1]));
-                }
+            for (int j = 0; j < 16; ++j) {
+                const int o0 = 16 * part + j;
+                if (o0 < cur.L0) __stcg(g + int64_t(o0) * kPlane, make_float2(v[2 * j], v[2 * j + 1]));
             }
         }
         tc::fence_before_sync();
         __syncthreads();
         cur = nxt;
+        nxt = nn;
     }
     if (!ok) {
         if (tid == 0) atomicExch(p.ctrl + 2, 1);
-        // give an MMA still in flight a bounded chance to finish before the
+        // give MMAs still in flight a bounded chance to finish before the
         // tensor memory is released
-        if (mma_pending) (void)__syncthreads_and(mbar_wait_bounded(bar_mma, phase, kSpin));
+        if (pend1) (void)__syncthreads_and(mbar_wait_bounded(bar_g1, ph1, kSpin));
+        if (pend2) (void)__syncthreads_and(mbar_wait_bounded(bar_g2, ph2, kSpin));
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+    if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
 uint16_t bf16_rn(float f) {
@@ -300,31 +343,38 @@ float bf16_to_float(uint16_t h) {
 
 }  // namespace
 
-// F1 hi, F1 lo, F2 hi, F2 lo in the shared-memory operand layout (128 KB)
-cudaError_t tc3d_build_operands(void **d_ops) {
-    std::vector<uint8_t> h(size_t(4) * kTile, 0);
+int tc3d_k1cap(int tile) { return 16 * ((2 * tile + 15) / 16); }
+
+// F1 hi, F1 lo (K = k1cap), F2 hi, F2 lo in the shared-memory operand layout
+cudaError_t tc3d_build_operands(int k1cap, void **d_ops) {
+    if (k1cap < 16 || k1cap > kTc3dMaxK1 || k1cap % 16) return cudaErrorInvalidValue;
+    const int t1 = tile_bytes(k1cap);
+    std::vector<uint8_t> h(size_t(2 * t1 + 2 * kTile), 0);
     const long double two_pi = 6.283185307179586476925286766559005768L;
-    auto put = [&](int mat, int n, int k, double v) {
+    auto put = [&](size_t base, int tb, int ktot, int n, int k, double v) {
         const uint16_t hi = bf16_rn(float(v));
         const uint16_t lo = bf16_rn(float(v - double(bf16_to_float(hi))));
-        const uint32_t off = tc::kmajor_offset(n, k, kK, 2);
-        std::memcpy(&h[size_t(2 * mat) * kTile + off], &hi, 2);
-        std::memcpy(&h[size_t(2 * mat + 1) * kTile + off], &lo, 2);
+        const uint32_t off = tc::kmajor_offset(n, k, ktot, 2);
+        std::memcpy(&h[base + off], &hi, 2);
+        std::memcpy(&h[base + size_t(tb) + off], &lo, 2);
     };
     for (int a = 0; a < kP; ++a)
         for (int b = 0; b < kP; ++b) {
             const int e = (a * b) % kP;
             const double cs = double(cosl(two_pi * e / kP)), sn = double(sinl(two_pi * e / kP));
             // F1: rows (k0 = a, re|im), columns (i0 = b, re|im): W^(i0 k0)
-            put(0, 2 * a, 2 * b, cs);
-            put(0, 2 * a, 2 * b + 1, sn);
-            put(0, 2 * a + 1, 2 * b, -sn);
-            put(0, 2 * a + 1, 2 * b + 1, cs);
+            if (2 * b + 1 < k1cap) {
+                put(0, t1, k1cap, 2 * a, 2 * b, cs);
+                put(0, t1, k1cap, 2 * a, 2 * b + 1, sn);
+                put(0, t1, k1cap, 2 * a + 1, 2 * b, -sn);
+                put(0, t1, k1cap, 2 * a + 1, 2 * b + 1, cs);
+            }
             // F2: rows (o0 = a, re|im), columns (k0 = b, re|im): W^(-o0 k0)
-            put(1, 2 * a, 2 * b, cs);
-            put(1, 2 * a, 2 * b + 1, -sn);
-            put(1, 2 * a + 1, 2 * b, sn);
-            put(1, 2 * a + 1, 2 * b + 1, cs);
+            const size_t f2 = size_t(2 * t1);
+            put(f2, kTile, kK, 2 * a, 2 * b, cs);
+            put(f2, kTile, kK, 2 * a, 2 * b + 1, -sn);
+            put(f2, kTile, kK, 2 * a + 1, 2 * b, sn);
+            put(f2, kTile, kK, 2 * a + 1, 2 * b + 1, cs);
         }
     cudaError_t e = cudaMalloc(d_ops, h.size());
     if (e != cudaSuccess) return e;
@@ -332,15 +382,17 @@ cudaError_t tc3d_build_operands(void **d_ops) {
 }
 
 cudaError_t tc3d_configure() {
-    return cudaFuncSetAttribute(tc3d_axis0_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    return cudaFuncSetAttribute(tc3d_axis0_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem_bytes(kTc3dMaxK1));
 }
 
-cudaError_t launch_tc3d_axis0(const ApplyParams &p, int ctas, void *scratch, int64_t c0, int64_t c1,
-                              const void *ops, cudaStream_t s) {
+cudaError_t launch_tc3d_axis0(const ApplyParams &p, int ctas, void *scratch, const int32_t *order, int64_t c0,
+                              int64_t c1, const void *ops, int k1cap, cudaStream_t s) {
+    if (k1cap < 16 || k1cap > kTc3dMaxK1 || k1cap % 16) return cudaErrorInvalidValue;
     const int64_t units = (c1 - c0) * kUnitsPerItem;
     const int grid = int(std::min<int64_t>(ctas, units));
-    tc3d_axis0_kernel<<<grid, kThreads, kSmem, s>>>(p, static_cast<float2 *>(scratch), c0, c1,
-                                                    static_cast<const uint8_t *>(ops));
+    tc3d_axis0_kernel<<<grid, kThreads, smem_bytes(k1cap), s>>>(p, static_cast<float2 *>(scratch), order, c0, c1,
+                                                                static_cast<const uint8_t *>(ops), k1cap);
     return cudaGetLastError();
 }
 
