@@ -309,6 +309,8 @@ def main():
     ap.add_argument("--serve", action="store_true", help="serving benchmark instead of the batched apply")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--nrhs", type=int, default=0,
+                    help="override the workload's batch (smaller cases for profiler captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -333,7 +335,7 @@ def main():
         dist.barrier()
 
     cfg_name, precision = WORKLOAD_OPERATOR[args.workload]
-    wl = configs.get(cfg_name)
+    wl = configs.get(cfg_name, **({"nrhs": args.nrhs} if args.nrhs > 0 else {}))
     desc, kname, ksrcs = WORKLOADS[args.workload]
     pts = pcg.pc_sample_points(wl.shape, wl.cells)
     phi = workloads.impulse_windows(wl.shape, pts, wl.kernel)

@@ -160,6 +160,28 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
     uint32_t phase = 0;
     int cur_seg = -1;
     const int *s_cstart = s_cstart_buf;
+    // the last finished item's flag, published (by thread 0) once its
+    // reductions have landed
+    bool pend_flag_any = false;   // uniform: some item is awaiting publication
+    __shared__ uint32_t *pend_flag, *pend_seg_done;
+    __shared__ uint32_t pend_epoch;
+    __shared__ int64_t pend_total;
+    __shared__ int pend_slot;
+    if (threadIdx.x == 0) pend_flag = nullptr;
+    auto publish_pending = [&]() {
+        if (!pend_flag) return;
+        __threadfence();
+        st_release_u32(pend_flag, pend_epoch);
+        if (pend_seg_done) {
+            // the request's last item raises its completion flag in host memory
+            const uint32_t before = atomicAdd(pend_seg_done, 1u);
+            if (int64_t(before) + 1 == pend_total && pend_slot >= 0 && lp.host_flags) {
+                __threadfence_system();
+                st_release_sys_u32(lp.host_flags + pend_slot, 1u);
+            }
+        }
+        pend_flag = nullptr;
+    };
 
     if (threadIdx.x == 0) {
         mbar_init(mbar, 1);
@@ -176,16 +198,19 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
         __syncthreads();
         const int64_t gitem = s_next;
         if (gitem >= total) break;
-        // the request (segment) this item belongs to
-        if (threadIdx.x == 0) {
-            int sx = 0;
-            if (lp.desc)
+        // the request (segment) this item belongs to (a single-apply launch has one)
+        int segidx = 0;
+        if (lp.desc) {
+            if (threadIdx.x == 0) {
+                int sx = 0;
                 while (sx + 1 < nseg && lp.desc->seg[sx + 1].item_begin <= gitem) ++sx;
-            s_segidx = sx;
+                s_segidx = sx;
+            }
+            __syncthreads();
+            segidx = s_segidx;
         }
-        __syncthreads();
-        if (s_segidx != cur_seg) {
-            cur_seg = s_segidx;
+        if (segidx != cur_seg) {
+            cur_seg = segidx;
             if (lp.desc) {
                 const uint32_t *src = reinterpret_cast<const uint32_t *>(lp.desc->seg + cur_seg);
                 for (int q = threadIdx.x; q < int(sizeof(Segment) / 4); q += blockDim.x)
@@ -269,7 +294,15 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
 #pragma unroll
             for (int j = 0; j < R1; ++j) S[i * P + ((t + R2 * j) ^ swz(i))] = a[j];
         }
+        // the previous item's bulk reductions have landed: it can report done
+        if constexpr (sizeof(T) == 4) {
+            if (t == 0 && pend_flag_any) {
+                bulk_wait_all();
+                fence_proxy_async_global();
+            }
+        }
         __syncthreads();
+        if (threadIdx.x == 0) publish_pending();
 
         if (s_next - s_seg.item_begin < p.total_items) prefetch_item<T>(p, s_cstart, s_next - s_seg.item_begin);
 
@@ -305,10 +338,10 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
                 if (row < L1) S[row * P + (col ^ swz(row))] = a[j];
             }
         }
-        __syncthreads();
 
         // ---------------- ordered overlap-add: wait for lower colours
-        // one thread per dependency flag, all polled concurrently
+        // one thread per dependency flag, all polled concurrently; the barrier
+        // after the polls also ends phase B
         {
             const int d0 = p.dep_start[ti], nd = p.dep_start[ti + 1] - d0;
             for (int d = threadIdx.x; d < nd; d += blockDim.x) {
@@ -344,26 +377,29 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
                           y0 + int64_t(oy) * p.n[1], y1 + int64_t(oy) * p.n[1], has1, o1, L2, p.n[1]);
         }
         if constexpr (sizeof(T) == 4) {
-            // the line's bulk reductions are complete before the tile reports done
-            if (t == 0) {
-                bulk_wait_all();
-                fence_proxy_async_global();
-            }
+            // the staging rows are read: the next spectrum may overwrite them.
+            // Completion of the reductions is awaited after the next item's
+            // phase A (or at exit), and only then is this item reported done.
+            if (t == 0) bulk_wait_read();
         }
         __syncthreads();
+        pend_flag_any = true;
         if (threadIdx.x == 0) {
-            __threadfence();
-            st_release_u32(p.done + int64_t(ti) * p.done_ld + pair, p.epoch);
-            if (lp.seg_done) {
-                // the request's last item raises its completion flag in host memory
-                const uint32_t before = atomicAdd(lp.seg_done + cur_seg, 1u);
-                if (int64_t(before) + 1 == p.total_items && s_seg.slot >= 0 && lp.host_flags) {
-                    __threadfence_system();
-                    st_release_sys_u32(lp.host_flags + s_seg.slot, 1u);
-                }
-            }
+            pend_flag = p.done + int64_t(ti) * p.done_ld + pair;
+            pend_epoch = p.epoch;
+            pend_seg_done = lp.seg_done ? lp.seg_done + cur_seg : nullptr;
+            pend_total = p.total_items;
+            pend_slot = s_seg.slot;
         }
     }
+    if constexpr (sizeof(T) == 4) {
+        if (t == 0 && pend_flag_any) {
+            bulk_wait_all();
+            fence_proxy_async_global();
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) publish_pending();
 }
 
 template <typename T>
