@@ -43,19 +43,24 @@ WORKLOAD = "fp32_512"
 # description, kernel name and the sources whose hash keys the profiled DRAM traffic
 WORKLOADS = {
     "fp32_512": ("512x512 regular 16x16 grid (r=256), anisotropic Gaussian R=24, 128^2 patch FFTs, 64 RHS",
-                 "fft2d_kernel<float,128>", ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh"]),
+                 "fft2d_kernel<float,128>", ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_overlap.cuh"]),
     "fp32_128c": ("128^3 regular 8x8x8 grid (r=512), axis-aligned Gaussian R=12, 64^3 patch FFTs, 32 RHS",
                   "fft3d_kernel", ["pc_fft3d.cu", "pc_fftcore.cuh", "pc_ptx.cuh"]),
     "bf16x3_128c": ("128^3 regular 8x8x8 grid (r=512), axis-aligned Gaussian R=12, 64^3 patches: plane FFTs in "
                     "FP32, first-axis DFTs as split-BF16 tensor-core GEMMs, 32 RHS",
                     "tc3d_axis0_kernel", ["pc_tc3d.cu", "pc_tc.cuh", "pc_ptx.cuh"]),
+    "fp32_512_adjoint": ("adjoint apply (Eq. adjoint_random_z) of the 512x512 regular 16x16 grid (r=256) "
+                         "operator, anisotropic Gaussian R=24, 128^2 patch FFTs, 64 RHS",
+                         "fft2d_kernel<float,128,true>", ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh",
+                                                          "pc_overlap.cuh"]),
     "adaptive_1024": ("1024x1024 adaptive quadtree (r=1579), heavy-tailed R=64 (2x2 kernel sub-windows), "
                       "128^2 patch FFTs, 32 RHS", "fft2d_kernel<float,128>",
-                      ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh"]),
+                      ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_overlap.cuh"]),
 }
 # workload name -> (operator configuration, precision)
-WORKLOAD_OPERATOR = {"fp32_512": ("fp32_512", "fp32"), "fp32_128c": ("fp32_128c", "fp32"),
-                     "bf16x3_128c": ("fp32_128c", "bf16x3"), "adaptive_1024": ("adaptive_1024", "fp32")}
+WORKLOAD_OPERATOR = {"fp32_512": ("fp32_512", "fp32"), "fp32_512_adjoint": ("fp32_512", "fp32"),
+                     "fp32_128c": ("fp32_128c", "fp32"), "bf16x3_128c": ("fp32_128c", "bf16x3"),
+                     "adaptive_1024": ("adaptive_1024", "fp32")}
 
 
 def kernel_sources_hash(names):
@@ -151,18 +156,19 @@ def dist_env():
     return rank, world, local
 
 
-def cpu_oracle_rate(wl, x, seconds, seed=0):
+def cpu_oracle_rate(wl, x, seconds, seed=0, adjoint=False):
     """Time the oracle on random output pixels until `seconds` have passed;
     returns (RHS/s-equivalent, pixels, threads, elapsed)."""
     from oracle import PCOracle
     orc = PCOracle.from_workload(wl)
+    fn = orc.apply_adjoint if adjoint else orc.apply
     rng = np.random.default_rng(seed)
     done = 0
     t0 = time.perf_counter()
     chunk = 512
     while time.perf_counter() - t0 < seconds:
         pts = rng.choice(wl.n, chunk, replace=False)
-        orc.apply(x, points=pts)
+        fn(x, points=pts)
         done += chunk
         chunk = min(chunk * 2, 16384)
     el = time.perf_counter() - t0
@@ -180,13 +186,14 @@ def run_reference(args, rank, world):
     x = workloads.rhs(wl.rhs_seed, wl.nrhs, wl.shape)
     from oracle import PCOracle
     orc = PCOracle.from_workload(wl)
+    fn = orc.apply_adjoint if args.workload.endswith("_adjoint") else orc.apply
     rng = np.random.default_rng(1)
     per_step = 2048
     times = []
     for i in range(args.warmup + args.steps):
         pts = rng.choice(wl.n, per_step, replace=False)
         t0 = time.perf_counter()
-        orc.apply(x, points=pts)
+        fn(x, points=pts)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
@@ -351,8 +358,10 @@ def main():
     sp = stream.cuda_stream
     N = wl.n
 
+    apply_fn = op.pc_apply_adjoint_batched if args.workload.endswith("_adjoint") else op.pc_apply_batched
+
     def step():
-        op.pc_apply_batched(wl.nrhs, x.data_ptr(), N, y.data_ptr(), N, sp)
+        apply_fn(wl.nrhs, x.data_ptr(), N, y.data_ptr(), N, sp)
 
     for _ in range(args.warmup):
         step()
@@ -407,7 +416,8 @@ def main():
 
     # ---- plain per-vector path on the same operator
     plain = None
-    if not args.no_plain and wl.ndim == 2:
+    adjoint = args.workload.endswith("_adjoint")
+    if not args.no_plain and wl.ndim == 2 and not adjoint:
         yp = torch.empty_like(x)
         op.pc_apply_plain(wl.nrhs, x.data_ptr(), N, yp.data_ptr(), N, sp)
         torch.cuda.synchronize()
@@ -505,7 +515,7 @@ def main():
         line["roofline_tensor"] = roof_tensor
         line["dtype"] = "f32+bf16x3"
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
-        rate, pix, cores, el = cpu_oracle_rate(wl, x_host, args.cpu_seconds)
+        rate, pix, cores, el = cpu_oracle_rate(wl, x_host, args.cpu_seconds, adjoint=adjoint)
         line["cpu_baseline"] = {"value": rate, "unit": "RHS/s", "cores": cores, "kind": "oracle",
                                 "sample": "%d random output pixels x %d RHS in %.1f s" % (pix, wl.nrhs, el)}
     if rank == 0:

@@ -222,6 +222,18 @@ pc_status pc_apply(pc_operator *op, const void *x, void *y, pc_stream stream);
 pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx,
                            void *y, int64_t ldy, pc_stream stream);
 
+/* Adjoint apply: Y[b] = A~* X[b] for b < nrhs, where
+ *   A~* x = sum_k w_k . (flip(phi_k^E) * x)          (Eq. adjoint_random_z;
+ * real data, so the conjugates drop): the correlation of x with each
+ * extended impulse response, weighted by w_k, summed over k.  This is the
+ * operator the paper's a-posteriori error estimator applies to random
+ * probes (Section 2.6).  Same arguments, layouts, stream semantics and
+ * determinism as pc_apply_batched (y overwritten; each y element sums its
+ * contributions in a fixed order).  2D operators (PC_FP32, PC_FP64); 3D
+ * operators return PC_ERR_UNSUPPORTED. */
+pc_status pc_apply_adjoint_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx,
+                                   void *y, int64_t ldy, pc_stream stream);
+
 /* Plain path for comparison: the same operator applied one vector at a time
  * through a gather kernel, a library FFT (cuFFT) of each padded patch, a
  * spectral product kernel, an inverse library FFT and an output-stationary

@@ -21,6 +21,7 @@ def _load():
     if _lib is None:
         _lib = ctypes.CDLL(build())
         _lib.pc_oracle_apply.restype = ctypes.c_int
+        _lib.pc_oracle_apply_adjoint.restype = ctypes.c_int
     return _lib
 
 
@@ -29,7 +30,8 @@ def _p(a):
 
 
 class PCOracle:
-    """A~ = sum_k phi_k^E * (w_k . f) on a box (Eq. conv_op_approx_main), FP64."""
+    """A~ = sum_k phi_k^E * (w_k . f) on a box (Eq. conv_op_approx_main) and its
+    adjoint A~* = sum_k w_k . (flip(phi_k^E) * f) (Eq. adjoint_random_z), FP64."""
 
     def __init__(self, shape: Sequence[int], cells, phi: np.ndarray, R: int, extend: bool = True,
                  weights=None):
@@ -53,12 +55,7 @@ class PCOracle:
         v = list(v)
         return [fill] * (3 - len(v)) + v
 
-    def apply(self, f: np.ndarray, points: Optional[np.ndarray] = None, nthreads: int = 0) -> np.ndarray:
-        """f: [B][*shape] (any float dtype; promoted to FP64).  Returns [B][*shape],
-        or [B][len(points)] when points (flat C-order indices) is given."""
-        lib = _load()
-        f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(-1, int(np.prod(self.shape))))
-        B = f.shape[0]
+    def _args(self):
         shape3 = np.array(self._pad3(self.shape, 1), dtype=np.int64)
         lo = np.array([self._pad3(self.grid.bbox_lo[k], 0) for k in range(self.grid.r)], dtype=np.int64)
         hi = np.array([self._pad3(self.grid.bbox_hi[k], 0) for k in range(self.grid.r)], dtype=np.int64)
@@ -67,6 +64,12 @@ class PCOracle:
         wcat = np.ascontiguousarray(np.concatenate([w.ravel() for w in self.W]).astype(np.float64))
         win = np.array(self._pad3([2 * self.R + 1] * self.d, 1), dtype=np.int64)
         phiE = np.ascontiguousarray(self.phiE, dtype=np.float64)
+        return shape3, lo, hi, off, wcat, win, phiE
+
+    def _run(self, fn, f, points, nthreads):
+        f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(-1, int(np.prod(self.shape))))
+        B = f.shape[0]
+        shape3, lo, hi, off, wcat, win, phiE = self._args()
         if points is None:
             ny = f.shape[1]
             yl = None
@@ -74,12 +77,21 @@ class PCOracle:
             yl = np.ascontiguousarray(np.asarray(points, dtype=np.int64).ravel())
             ny = yl.size
         out = np.zeros((B, ny))
-        rc = lib.pc_oracle_apply(_p(shape3), ctypes.c_int32(self.grid.r), _p(lo), _p(hi), _p(off), _p(wcat),
-                                 _p(win), _p(phiE), ctypes.c_int32(B), _p(f), ctypes.c_int64(ny),
-                                 _p(yl) if yl is not None else ctypes.c_void_p(0), _p(out),
-                                 ctypes.c_int32(nthreads))
+        rc = fn(_p(shape3), ctypes.c_int32(self.grid.r), _p(lo), _p(hi), _p(off), _p(wcat), _p(win), _p(phiE),
+                ctypes.c_int32(B), _p(f), ctypes.c_int64(ny), _p(yl) if yl is not None else ctypes.c_void_p(0),
+                _p(out), ctypes.c_int32(nthreads))
         if rc != 0:
             raise MemoryError("oracle apply failed to allocate")
         if points is None:
             return out.reshape((B,) + self.shape)
         return out
+
+    def apply(self, f: np.ndarray, points: Optional[np.ndarray] = None, nthreads: int = 0) -> np.ndarray:
+        """f: [B][*shape] (any float dtype; promoted to FP64).  Returns [B][*shape],
+        or [B][len(points)] when points (flat C-order indices) is given."""
+        return self._run(_load().pc_oracle_apply, f, points, nthreads)
+
+    def apply_adjoint(self, f: np.ndarray, points: Optional[np.ndarray] = None, nthreads: int = 0) -> np.ndarray:
+        """A~* f (Eq. adjoint_random_z, real data: w_k times the correlation of
+        f with phi_k^E); same shapes as apply."""
+        return self._run(_load().pc_oracle_apply_adjoint, f, points, nthreads)

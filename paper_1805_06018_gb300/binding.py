@@ -97,6 +97,7 @@ _PROTOS = {
     "pc_apply_plain": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
     "pc_operator_check": (ctypes.c_int, [_VP]),
     "pc_operator_kernel_time": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "pc_apply_adjoint_batched": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
     "pc_operator_launches": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     "pc_operator_stage_time": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
     "pc_operator_destroy": (ctypes.c_int, [_VP]),
@@ -262,6 +263,10 @@ class Operator:
         _check(lib().pc_apply_batched_noalloc(self.handle, ctypes.c_int32(nrhs), _VP(x_ptr), ctypes.c_int64(ldx),
                                               _VP(y_ptr), ctypes.c_int64(ldy), _VP(stream_ptr)), self.ctx.handle)
 
+    def pc_apply_adjoint_batched(self, nrhs: int, x_ptr: int, ldx: int, y_ptr: int, ldy: int, stream_ptr: int):
+        _check(lib().pc_apply_adjoint_batched(self.handle, ctypes.c_int32(nrhs), _VP(x_ptr), ctypes.c_int64(ldx),
+                                              _VP(y_ptr), ctypes.c_int64(ldy), _VP(stream_ptr)), self.ctx.handle)
+
     def pc_apply_plain(self, nrhs: int, x_ptr: int, ldx: int, y_ptr: int, ldy: int, stream_ptr: int):
         _check(lib().pc_apply_plain(self.handle, ctypes.c_int32(nrhs), _VP(x_ptr), ctypes.c_int64(ldx),
                                     _VP(y_ptr), ctypes.c_int64(ldy), _VP(stream_ptr)), self.ctx.handle)
@@ -305,6 +310,12 @@ class Operator:
         """y = A~ x for x of shape [B, *box] (or [*box])."""
         B, y = self._args(x, out)
         self.pc_apply_batched(B, x.data_ptr(), self.N, y.data_ptr(), self.N, _stream_ptr(stream))
+        return y
+
+    def apply_adjoint(self, x, out=None, stream=None):
+        """y = A~* x (Eq. adjoint_random_z) for x of shape [B, *box] (or [*box])."""
+        B, y = self._args(x, out)
+        self.pc_apply_adjoint_batched(B, x.data_ptr(), self.N, y.data_ptr(), self.N, _stream_ptr(stream))
         return y
 
     def apply_plain(self, x, out=None, stream=None):

@@ -525,10 +525,11 @@ static pc_status apply_split3d(pc_operator *op, const pc::ApplyParams &p, cudaSt
     return PC_OK;
 }
 
-pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
-                           pc_stream stream) {
+static pc_status apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
+                               pc_stream stream, bool adjoint) {
     if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
     pc_context *ctx = op->ctx;
+    if (adjoint && op->d != 2) return fail(ctx, PC_ERR_UNSUPPORTED, "the adjoint apply covers 2D operators");
     if (nrhs < 0) return fail(ctx, PC_ERR_ARG, "nrhs < 0");
     if (nrhs == 0) return PC_OK;
     if (!x || !y) return fail(ctx, PC_ERR_ARG, "null x or y");
@@ -582,13 +583,24 @@ pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the zero kernel");
     const int ctas = int(std::min<int64_t>(op->ctas, p.total_items));
     cudaEventRecord(op->ev_begin, s);
-    e = op->d == 3 ? pc::launch_fft3d(p, ctas, op->d_scratch, s) : pc::launch_fft2d(p, op->P, op->prec, ctas, s);
+    e = op->d == 3 ? pc::launch_fft3d(p, ctas, op->d_scratch, s)
+                   : pc::launch_fft2d(p, op->P, op->prec, ctas, s, adjoint);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the patch kernel");
     cudaEventRecord(op->ev_end, s);
     op->timed = true;
     op->last_stream = s;
     op->launches_last = 2;
     return PC_OK;
+}
+
+pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
+                           pc_stream stream) {
+    return apply_batched(op, nrhs, x, ldx, y, ldy, stream, false);
+}
+
+pc_status pc_apply_adjoint_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
+                                   pc_stream stream) {
+    return apply_batched(op, nrhs, x, ldx, y, ldy, stream, true);
 }
 
 pc_status pc_apply(pc_operator *op, const void *x, void *y, pc_stream stream) {

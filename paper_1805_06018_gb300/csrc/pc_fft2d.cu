@@ -22,6 +22,14 @@
 // which makes y bitwise reproducible.  Items are taken from an atomic counter
 // in colour-major order, so a tile only ever waits on items that were taken
 // earlier by running CTAs: the wait always ends.
+//
+// The adjoint y = sum_k w_k . (flip(phi_k^E) * x) (Eq. adjoint_random_z, real
+// data) is the same kernel with ADJ = true: phase A gathers x (unweighted)
+// over the tile's output box, phase B multiplies by the conjugate spectrum
+// (a correlation, free of wrap-around for the same P >= n + 2R), and phase
+// C keeps the n1 x n2 input box, weights it by w_k and adds it there.  Tiles
+// of one colour also have disjoint input boxes, so the adjoint sums in
+// colour order as well.
 #include "pc_fftcore.cuh"
 #include "pc_internal.h"
 #include "pc_overlap.cuh"
@@ -128,7 +136,7 @@ __device__ __forceinline__ void add_row(const C *a, int t, unsigned lmask, float
     }
 }
 
-template <typename T, int P>
+template <typename T, int P, bool ADJ>
 __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const LaunchParams lp) {
     using C = typename Cx<T>::type;
     using L = Smem2d<T, P>;
@@ -259,40 +267,79 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
         // ---------------- phase A: stage w, x0, x1 rows (cp.async), weight, row FFTs
         // rows of one warp sit 2P reals apart (same banks): shift each row's staging
         // by (row & 3) * 8 reals when the three arrays leave room
-        const int shmul = 3 * n2 + 24 <= 2 * P ? 8 : 0;
-        for (int i = line; i < n1; i += LINES) {
-            T *row = Sf + i * 2 * P + (i & 3) * shmul;
-            const int64_t xr = int64_t(i0 + i) * p.n[1] + j0;
-            const T *wr = wt + int64_t(i) * tile.w_ld[0];
+        if constexpr (!ADJ) {
+            const int shmul = 3 * n2 + 24 <= 2 * P ? 8 : 0;
+            for (int i = line; i < n1; i += LINES) {
+                T *row = Sf + i * 2 * P + (i & 3) * shmul;
+                const int64_t xr = int64_t(i0 + i) * p.n[1] + j0;
+                const T *wr = wt + int64_t(i) * tile.w_ld[0];
 #pragma unroll
-            for (int j = 0; j < R1; ++j) {
-                const int col = t + R2 * j;
-                if (col < n2) {
-                    cp_async<sizeof(T)>(row + col, wr + col);
-                    cp_async<sizeof(T)>(row + n2 + col, x0 + xr + col);
-                    if (has1) cp_async<sizeof(T)>(row + 2 * n2 + col, x1 + xr + col);
+                for (int j = 0; j < R1; ++j) {
+                    const int col = t + R2 * j;
+                    if (col < n2) {
+                        cp_async<sizeof(T)>(row + col, wr + col);
+                        cp_async<sizeof(T)>(row + n2 + col, x0 + xr + col);
+                        if (has1) cp_async<sizeof(T)>(row + 2 * n2 + col, x1 + xr + col);
+                    }
                 }
             }
-        }
-        cp_async_wait_all();
-        __syncwarp(lmask);
-        for (int i = line; i < n1; i += LINES) {
-            const T *row = Sf + i * 2 * P + (i & 3) * shmul;
-            C a[R1];
+            cp_async_wait_all();
+            __syncwarp(lmask);
+            for (int i = line; i < n1; i += LINES) {
+                const T *row = Sf + i * 2 * P + (i & 3) * shmul;
+                C a[R1];
 #pragma unroll
-            for (int j = 0; j < R1; ++j) {
-                const int col = t + R2 * j;
-                if (col < n2) {
-                    const T wv = row[col];
-                    a[j] = C{wv * row[n2 + col], has1 ? wv * row[2 * n2 + col] : T(0)};
-                } else {
-                    a[j] = zero;
+                for (int j = 0; j < R1; ++j) {
+                    const int col = t + R2 * j;
+                    if (col < n2) {
+                        const T wv = row[col];
+                        a[j] = C{wv * row[n2 + col], has1 ? wv * row[2 * n2 + col] : T(0)};
+                    } else {
+                        a[j] = zero;
+                    }
+                }
+                RowScratch<P, C> scr{S, i};
+                fft_line<P, false>(a, tw, t, scr, lmask);
+#pragma unroll
+                for (int j = 0; j < R1; ++j) S[i * P + ((t + R2 * j) ^ swz(i))] = a[j];
+            }
+        } else {
+            // adjoint: x over the output box (L1 x L2 at (o0, o1)), zero outside
+            // Omega, staged as [x0 | x1] per row
+            for (int i = line; i < L1; i += LINES) {
+                const int gr = o0 + i;
+                if (gr < 0 || gr >= p.n[0]) continue;
+                T *row = Sf + i * 2 * P;
+                const int64_t xr = int64_t(gr) * p.n[1] + o1;
+#pragma unroll
+                for (int j = 0; j < R1; ++j) {
+                    const int col = t + R2 * j;
+                    const int gc = o1 + col;
+                    if (col < L2 && gc >= 0 && gc < p.n[1]) {
+                        cp_async<sizeof(T)>(row + col, x0 + xr + col);
+                        if (has1) cp_async<sizeof(T)>(row + L2 + col, x1 + xr + col);
+                    }
                 }
             }
-            RowScratch<P, C> scr{S, i};
-            fft_line<P, false>(a, tw, t, scr, lmask);
+            cp_async_wait_all();
+            __syncwarp(lmask);
+            for (int i = line; i < L1; i += LINES) {
+                const int gr = o0 + i;
+                const bool rin = gr >= 0 && gr < p.n[0];
+                const T *row = Sf + i * 2 * P;
+                C a[R1];
 #pragma unroll
-            for (int j = 0; j < R1; ++j) S[i * P + ((t + R2 * j) ^ swz(i))] = a[j];
+                for (int j = 0; j < R1; ++j) {
+                    const int col = t + R2 * j;
+                    const int gc = o1 + col;
+                    a[j] = rin && col < L2 && gc >= 0 && gc < p.n[1] ? C{row[col], has1 ? row[L2 + col] : T(0)}
+                                                                    : zero;
+                }
+                RowScratch<P, C> scr{S, i};
+                fft_line<P, false>(a, tw, t, scr, lmask);
+#pragma unroll
+                for (int j = 0; j < R1; ++j) S[i * P + ((t + R2 * j) ^ swz(i))] = a[j];
+            }
         }
         // the previous item's bulk reductions have landed: it can report done
         if constexpr (sizeof(T) == 4) {
@@ -314,28 +361,34 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
         phase ^= 1u;
         for (int col = line; col < P; col += LINES) {
             C a[R1];
+            // rows in: n1 (forward) or L1 (adjoint); rows kept: the other
+            const int rows_in = ADJ ? L1 : n1, rows_out = ADJ ? n1 : L1;
 #pragma unroll
             for (int j = 0; j < R1; ++j) {
                 const int row = t + R2 * j;
-                a[j] = row < n1 ? S[row * P + (col ^ swz(row))] : zero;
+                a[j] = row < rows_in ? S[row * P + (col ^ swz(row))] : zero;
             }
             ColScratch<P, C> scr{S, col};
             fft_line<P, false>(a, tw, t, scr, lmask);
-            // Hermitian half spectrum stored as [k2 <= P/2][k1]
+            // Hermitian half spectrum stored as [k2 <= P/2][k1]; the adjoint
+            // multiplies by the conjugate
             if (col <= P / 2) {
                 const C *sc = SP + col * L::SPLD;
 #pragma unroll
-                for (int j = 0; j < R1; ++j) a[j] = cmul(a[j], sc[t + R2 * j]);
+                for (int j = 0; j < R1; ++j) a[j] = ADJ ? cmulc(a[j], sc[t + R2 * j]) : cmul(a[j], sc[t + R2 * j]);
             } else {
                 const C *sc = SP + (P - col) * L::SPLD;
 #pragma unroll
-                for (int j = 0; j < R1; ++j) a[j] = cmulc(a[j], sc[(P - (t + R2 * j)) & (P - 1)]);
+                for (int j = 0; j < R1; ++j) {
+                    const C v = sc[(P - (t + R2 * j)) & (P - 1)];
+                    a[j] = ADJ ? cmul(a[j], v) : cmulc(a[j], v);
+                }
             }
             fft_line<P, true>(a, tw, t, scr, lmask);
 #pragma unroll
             for (int j = 0; j < R1; ++j) {
                 const int row = t + R2 * j;
-                if (row < L1) S[row * P + (col ^ swz(row))] = a[j];
+                if (row < rows_out) S[row * P + (col ^ swz(row))] = a[j];
             }
         }
 
@@ -365,16 +418,36 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
         T *y0 = y + int64_t(b0) * p.ldy;
         T *y1 = has1 ? y0 + p.ldy : y0;
         if (sizeof(T) == 4 && t == 0) fence_proxy_async_global();
-        for (int n = line; n < L1; n += LINES) {
-            const int oy = o0 + n;
-            if (oy < 0 || oy >= p.n[0]) continue;
-            C a[R1];
+        if constexpr (!ADJ) {
+            for (int n = line; n < L1; n += LINES) {
+                const int oy = o0 + n;
+                if (oy < 0 || oy >= p.n[0]) continue;
+                C a[R1];
 #pragma unroll
-            for (int j = 0; j < R1; ++j) a[j] = S[n * P + ((t + R2 * j) ^ swz(n))];
-            RowScratch<P, C> scr{S, n};
-            fft_line<P, true>(a, tw, t, scr, lmask);
-            add_row<T, P>(a, t, lmask, reinterpret_cast<float *>(SP) + line * L::STAGE,
-                          y0 + int64_t(oy) * p.n[1], y1 + int64_t(oy) * p.n[1], has1, o1, L2, p.n[1]);
+                for (int j = 0; j < R1; ++j) a[j] = S[n * P + ((t + R2 * j) ^ swz(n))];
+                RowScratch<P, C> scr{S, n};
+                fft_line<P, true>(a, tw, t, scr, lmask);
+                add_row<T, P>(a, t, lmask, reinterpret_cast<float *>(SP) + line * L::STAGE,
+                              y0 + int64_t(oy) * p.n[1], y1 + int64_t(oy) * p.n[1], has1, o1, L2, p.n[1]);
+            }
+        } else {
+            // adjoint: the n1 x n2 input box, weighted by w_k, added at (i0, j0)
+            for (int n = line; n < n1; n += LINES) {
+                const T *wr = wt + int64_t(n) * tile.w_ld[0];
+                T wv[R1];
+#pragma unroll
+                for (int j = 0; j < R1; ++j) wv[j] = t + R2 * j < n2 ? __ldg(wr + t + R2 * j) : T(0);
+                C a[R1];
+#pragma unroll
+                for (int j = 0; j < R1; ++j) a[j] = S[n * P + ((t + R2 * j) ^ swz(n))];
+                RowScratch<P, C> scr{S, n};
+                fft_line<P, true>(a, tw, t, scr, lmask);
+#pragma unroll
+                for (int j = 0; j < R1; ++j) a[j] = C{a[j].x * wv[j], a[j].y * wv[j]};
+                const int oy = i0 + n;
+                add_row<T, P>(a, t, lmask, reinterpret_cast<float *>(SP) + line * L::STAGE,
+                              y0 + int64_t(oy) * p.n[1], y1 + int64_t(oy) * p.n[1], has1, j0, n2, p.n[1]);
+            }
         }
         if constexpr (sizeof(T) == 4) {
             // the staging rows are read: the next spectrum may overwrite them.
@@ -427,10 +500,13 @@ cudaError_t launch_zero(const ApplyParams &p, int64_t N, pc_precision prec, cuda
 template <typename T, int P>
 static cudaError_t configure_one(int *ctas_per_sm, size_t *smem) {
     const size_t bytes = Smem2d<T, P>::bytes;
-    cudaError_t e = cudaFuncSetAttribute(fft2d_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    cudaError_t e =
+        cudaFuncSetAttribute(fft2d_kernel<T, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fft2d_kernel<T, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
     if (e != cudaSuccess) return e;
     int n = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fft2d_kernel<T, P>, KCfg<T, P>::threads, bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fft2d_kernel<T, P, false>, KCfg<T, P>::threads, bytes);
     if (e != cudaSuccess) return e;
     if (ctas_per_sm) *ctas_per_sm = n;
     if (smem) *smem = bytes;
@@ -447,7 +523,17 @@ cudaError_t fft2d_configure(int P, pc_precision prec, int *ctas_per_sm, size_t *
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_fft2d(const ApplyParams &p, int P, pc_precision prec, int ctas, cudaStream_t s) {
+template <bool ADJ>
+static void launch_one(const LaunchParams &lp, int P, pc_precision prec, int ctas, size_t smem, cudaStream_t s) {
+    if (prec == PC_FP64)
+        fft2d_kernel<double, 64, ADJ><<<ctas, KCfg<double, 64>::threads, smem, s>>>(lp);
+    else if (P == 64)
+        fft2d_kernel<float, 64, ADJ><<<ctas, KCfg<float, 64>::threads, smem, s>>>(lp);
+    else
+        fft2d_kernel<float, 128, ADJ><<<ctas, KCfg<float, 128>::threads, smem, s>>>(lp);
+}
+
+cudaError_t launch_fft2d(const ApplyParams &p, int P, pc_precision prec, int ctas, cudaStream_t s, bool adjoint) {
     size_t smem = 0;
     cudaError_t e = fft2d_configure(P, prec, nullptr, &smem);
     if (e != cudaSuccess) return e;
@@ -458,12 +544,10 @@ cudaError_t launch_fft2d(const ApplyParams &p, int P, pc_precision prec, int cta
     lp.one.slot = -1;
     lp.counter = reinterpret_cast<unsigned long long *>(p.ctrl);
     lp.status = p.ctrl + 2;
-    if (prec == PC_FP64)
-        fft2d_kernel<double, 64><<<ctas, KCfg<double, 64>::threads, smem, s>>>(lp);
-    else if (P == 64)
-        fft2d_kernel<float, 64><<<ctas, KCfg<float, 64>::threads, smem, s>>>(lp);
+    if (adjoint)
+        launch_one<true>(lp, P, prec, ctas, smem, s);
     else
-        fft2d_kernel<float, 128><<<ctas, KCfg<float, 128>::threads, smem, s>>>(lp);
+        launch_one<false>(lp, P, prec, ctas, smem, s);
     return cudaGetLastError();
 }
 
@@ -499,7 +583,7 @@ cudaError_t launch_round(const LaunchDesc *d_desc, unsigned long long *counter, 
     lp.status = status;
     lp.seg_done = seg_done;
     lp.host_flags = host_flags;
-    fft2d_kernel<float, 128><<<ctas, KCfg<float, 128>::threads, smem, s>>>(lp);
+    fft2d_kernel<float, 128, false><<<ctas, KCfg<float, 128>::threads, smem, s>>>(lp);
     return cudaGetLastError();
 }
 

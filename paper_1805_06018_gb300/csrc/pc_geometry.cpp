@@ -296,19 +296,24 @@ void build_schedule(const Geometry &g, int R, int T, const WindowSplit &wsp, con
                 }
     }
     const int nt = int(tiles.size());
-    // output boxes, clipped to Omega
-    std::vector<std::array<int64_t, 6>> ob(nt);
+    // output boxes, clipped to Omega, and input boxes: the forward apply adds
+    // into the output box, the adjoint into the input box, so two tiles
+    // conflict when either box pair overlaps
+    std::vector<std::array<int64_t, 6>> ob(nt), ib(nt);
     for (int i = 0; i < nt; ++i)
         for (int a = 0; a < 3; ++a) {
             ob[i][a] = std::max<int64_t>(0, tiles[i].out_lo[a]);
             ob[i][3 + a] = std::min<int64_t>(g.shape[a] - 1,
                                              int64_t(tiles[i].out_lo[a]) + tiles[i].in_ext[a] + tiles[i].kext[a] - 2);
+            ib[i][a] = tiles[i].in_lo[a];
+            ib[i][3 + a] = int64_t(tiles[i].in_lo[a]) + tiles[i].in_ext[a] - 1;
         }
-    auto overlap = [&](int i, int j) {
+    auto boxes_meet = [](const std::array<int64_t, 6> &u, const std::array<int64_t, 6> &v) {
         for (int a = 0; a < 3; ++a)
-            if (ob[i][3 + a] < ob[j][a] || ob[j][3 + a] < ob[i][a]) return false;
+            if (u[3 + a] < v[a] || v[3 + a] < u[a]) return false;
         return true;
     };
+    auto overlap = [&](int i, int j) { return boxes_meet(ob[i], ob[j]) || boxes_meet(ib[i], ib[j]); };
     std::vector<std::vector<int32_t>> nbr(nt);
     for (int i = 0; i < nt; ++i)
         for (int j = i + 1; j < nt; ++j)

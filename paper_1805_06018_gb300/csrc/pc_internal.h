@@ -83,8 +83,10 @@ struct Schedule {
 
 // Split each bbox(U_k) into input tiles of extent <= T, colour the tiles so
 // that tiles of one colour have disjoint output boxes (tile (+) [-R, R]^d,
-// clipped to Omega), and list for every tile the overlapping tiles of lower
-// colour.  Output pixels then receive their contributions in colour order.
+// clipped to Omega) and disjoint input boxes, and list for every tile the
+// overlapping tiles of lower colour.  Output pixels of the forward apply (and
+// of the adjoint, which adds into the input boxes) then receive their
+// contributions in colour order.
 void build_schedule(const Geometry &g, int R, int T, const WindowSplit &ws, const std::vector<int64_t> &w_off,
                     Schedule &s);
 
@@ -199,7 +201,9 @@ struct pc_operator {
 namespace pc {
 // kernels (pc_fft2d.cu, pc_spectra.cu, pc_plain.cu)
 cudaError_t launch_zero(const ApplyParams &p, int64_t N, pc_precision prec, cudaStream_t s);
-cudaError_t launch_fft2d(const ApplyParams &p, int P, pc_precision prec, int ctas, cudaStream_t s);
+// adjoint = false: y = A~ x; true: y = A~* x (Eq. adjoint_random_z)
+cudaError_t launch_fft2d(const ApplyParams &p, int P, pc_precision prec, int ctas, cudaStream_t s,
+                         bool adjoint = false);
 // multi-request launch (FP32, P = 128): y zero-fill + claim reset, then the fused kernel
 // (fft2d_configure(128, PC_FP32, ...) must have been called; capturable)
 cudaError_t launch_round(const LaunchDesc *d_desc, unsigned long long *counter, int32_t *status, uint32_t *seg_done,
