@@ -234,6 +234,23 @@ pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t
 pc_status pc_apply_adjoint_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx,
                                    void *y, int64_t ldy, pc_stream stream);
 
+/* Randomized a-posteriori error estimator (Section 2.6,
+ * Eq. randomized_estimator_ec): for every leaf cell C of the operator's grid
+ * (the cells passed to pc_build_spectra, in that order, as closed boxes),
+ *   eta[C] = (1/sqrt(q)) || (A~* Z)[C, .] - Y[C, .] ||_F
+ * where Z holds q probe vectors and Y = A* Z is supplied by the caller (the
+ * paper's matrix-free access to A*).  With Z ~ N(0,1)^{N x q} this estimates
+ * e_C = ||(A~ - A)[Omega, C]|| (Eq. relative_error).
+ *   z, y   device, [q][N] with strides ldz, ldy >= N, operator precision.
+ *   eta    host array of num_cells doubles, written before the call returns
+ *          (the call synchronises `stream`).
+ * The library applies A~* to z (as pc_apply_adjoint_batched, into scratch
+ * that it allocates and keeps) and reduces each cell in FP64 in a fixed
+ * order, so eta is bitwise reproducible.  2D operators; 3D operators return
+ * PC_ERR_UNSUPPORTED. */
+pc_status pc_estimate_cell_errors(pc_operator *op, int32_t q, const void *z, int64_t ldz, const void *y,
+                                  int64_t ldy, double *eta, pc_stream stream);
+
 /* Plain path for comparison: the same operator applied one vector at a time
  * through a gather kernel, a library FFT (cuFFT) of each padded patch, a
  * spectral product kernel, an inverse library FFT and an output-stationary

@@ -98,6 +98,8 @@ _PROTOS = {
     "pc_operator_check": (ctypes.c_int, [_VP]),
     "pc_operator_kernel_time": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
     "pc_apply_adjoint_batched": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
+    "pc_estimate_cell_errors": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64,
+                                                ctypes.POINTER(ctypes.c_double), _VP]),
     "pc_operator_launches": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     "pc_operator_stage_time": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
     "pc_operator_destroy": (ctypes.c_int, [_VP]),
@@ -317,6 +319,22 @@ class Operator:
         B, y = self._args(x, out)
         self.pc_apply_adjoint_batched(B, x.data_ptr(), self.N, y.data_ptr(), self.N, _stream_ptr(stream))
         return y
+
+    def estimate_cell_errors(self, z, y, num_cells: int, stream=None) -> np.ndarray:
+        """eta_C for every leaf cell (Section 2.6): z, y = A* z are contiguous
+        CUDA tensors [q, *box] of the operator's precision."""
+        for t, name in ((z, "z"), (y, "y")):
+            if not (t.is_cuda and t.is_contiguous()):
+                raise ValueError("%s must be a contiguous CUDA tensor" % name)
+        q = z.numel() // self.N
+        if y.numel() != q * self.N:
+            raise ValueError("z and y must hold the same number of vectors")
+        eta = np.zeros(num_cells)
+        _check(lib().pc_estimate_cell_errors(self.handle, ctypes.c_int32(q), _VP(z.data_ptr()), ctypes.c_int64(self.N),
+                                             _VP(y.data_ptr()), ctypes.c_int64(self.N),
+                                             eta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             _VP(_stream_ptr(stream))), self.ctx.handle)
+        return eta
 
     def apply_plain(self, x, out=None, stream=None):
         B, y = self._args(x, out)

@@ -85,6 +85,9 @@ void free_operator(pc_operator *op) {
     cudaFree(op->d_scratch);
     cudaFree(op->d_tc_ops);
     cudaFree(op->d_tc_order);
+    cudaFree(op->d_cells);
+    cudaFree(op->d_cell_sums);
+    cudaFree(op->d_est);
     for (cudaEvent_t ev : op->stage_ev) cudaEventDestroy(ev);
     if (op->ev_begin) cudaEventDestroy(op->ev_begin);
     if (op->ev_end) cudaEventDestroy(op->ev_end);
@@ -321,6 +324,27 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     std::vector<int32_t> depv = sch.dep;
     if (depv.empty()) depv.push_back(0);
     if ((e = upload(&op->d_dep, depv.data(), depv.size(), acct)) != cudaSuccess) return bail(e, "dependencies");
+    {
+        // leaf cells for the error estimator, on the canonical box (2D as (1, n0, n1))
+        std::vector<int32_t> cells6;
+        const int nc = int(g.cell_lo.size());
+        for (int c = 0; c < nc; ++c) {
+            if (g.d == 2) {
+                const int32_t v[6] = {0, int32_t(g.cell_lo[c][0]), int32_t(g.cell_lo[c][1]),
+                                      0, int32_t(g.cell_hi[c][0]), int32_t(g.cell_hi[c][1])};
+                cells6.insert(cells6.end(), v, v + 6);
+            } else {
+                const int32_t v[6] = {int32_t(g.cell_lo[c][0]), int32_t(g.cell_lo[c][1]), int32_t(g.cell_lo[c][2]),
+                                      int32_t(g.cell_hi[c][0]), int32_t(g.cell_hi[c][1]), int32_t(g.cell_hi[c][2])};
+                cells6.insert(cells6.end(), v, v + 6);
+            }
+        }
+        op->n_cells = nc;
+        if ((e = upload(&op->d_cells, cells6.data(), cells6.size(), acct)) != cudaSuccess) return bail(e, "cells");
+        if ((e = cudaMalloc(&op->d_cell_sums, sizeof(double) * std::max(nc, 1))) != cudaSuccess)
+            return bail(e, "cell sums");
+        acct += sizeof(double) * std::max(nc, 1);
+    }
     if ((e = cudaMalloc(&op->d_ctrl, 64)) != cudaSuccess) return bail(e, "control block");
     acct += 64;
     if ((e = cudaMemset(op->d_ctrl, 0, 64)) != cudaSuccess) return bail(e, "control block");
@@ -482,6 +506,9 @@ static pc_status apply_split3d(pc_operator *op, const pc::ApplyParams &p, cudaSt
         if (op->d_tc_order && (e = cudaDeviceSynchronize()) != cudaSuccess)
             return cuda_fail(ctx, e, "synchronising before replacing the unit order");
         cudaFree(op->d_tc_order);
+    cudaFree(op->d_cells);
+    cudaFree(op->d_cell_sums);
+    cudaFree(op->d_est);
         op->d_tc_order = nullptr;
         op->tc_order_npairs = 0;
         if ((e = cudaMalloc(&op->d_tc_order, order.size() * sizeof(int32_t))) != cudaSuccess)
@@ -601,6 +628,48 @@ pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t
 pc_status pc_apply_adjoint_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
                                    pc_stream stream) {
     return apply_batched(op, nrhs, x, ldx, y, ldy, stream, true);
+}
+
+pc_status pc_estimate_cell_errors(pc_operator *op, int32_t q, const void *z, int64_t ldz, const void *y, int64_t ldy,
+                                  double *eta, pc_stream stream) {
+    if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
+    pc_context *ctx = op->ctx;
+    if (q < 1) return fail(ctx, PC_ERR_ARG, "q must be >= 1");
+    if (!z || !y || !eta) return fail(ctx, PC_ERR_ARG, "null z, y or eta");
+    if (op->d != 2) return fail(ctx, PC_ERR_UNSUPPORTED, "the error estimator covers 2D operators");
+    if (ldy < op->N) return fail(ctx, PC_ERR_ARG, "ldy must be >= N");
+    if (reinterpret_cast<uintptr_t>(y) % op->elem) return fail(ctx, PC_ERR_ARG, "y must be aligned to the element size");
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return fail(ctx, PC_ERR_CUDA, "cannot select the context's device");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (op->est_cap < q) {
+        if (op->d_est && (e = cudaDeviceSynchronize()) != cudaSuccess)
+            return cuda_fail(ctx, e, "synchronising before growing the estimator scratch");
+        cudaFree(op->d_est);
+        op->d_est = nullptr;
+        op->est_cap = 0;
+        if ((e = cudaMalloc(&op->d_est, size_t(q) * size_t(op->N) * op->elem)) != cudaSuccess)
+            return cuda_fail(ctx, e, "allocating the estimator scratch");
+        op->est_cap = q;
+    }
+    // Y~ = A~* Z, then the per-cell sums of squares of Y~ - Y
+    pc_status st = apply_batched(op, q, z, ldz, op->d_est, op->N, stream, true);
+    if (st != PC_OK) return st;
+    // extents of the canonical box's two fastest axes (2D grids as (1, n0, n1))
+    const int64_t n1 = op->d == 2 ? op->shape[0] : op->shape[1];
+    const int64_t n2 = op->d == 2 ? op->shape[1] : op->shape[2];
+    if ((e = pc::launch_cell_sqdiff(op->prec, op->d_est, op->N, y, ldy, q, op->d_cells, op->n_cells, n1, n2,
+                                    op->d_cell_sums, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "launching the cell reduction");
+    std::vector<double> sums(size_t(op->n_cells));
+    if ((e = cudaMemcpyAsync(sums.data(), op->d_cell_sums, sizeof(double) * sums.size(), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "reading the cell sums");
+    for (int c = 0; c < op->n_cells; ++c) eta[c] = std::sqrt(sums[size_t(c)] / double(q));
+    op->launches_last += 1;
+    return PC_OK;
 }
 
 pc_status pc_apply(pc_operator *op, const void *x, void *y, pc_stream stream) {

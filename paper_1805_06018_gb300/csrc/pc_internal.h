@@ -180,6 +180,13 @@ struct pc_operator {
     void *d_tc_ops = nullptr;    // BF16x3 3D: DFT operand tiles for the tensor cores
     int tc_k1cap = 0;            // BF16x3 3D: K columns of the GEMM-1 operands
     int32_t *d_tc_order = nullptr;   // BF16x3 3D: per-chunk item order of the tensor stage
+    // error estimator (Section 2.6): leaf cells [n][6] on the canonical box
+    // (2D grids as (1, n0, n1)), per-cell sums, adjoint scratch
+    int32_t *d_cells = nullptr;
+    int32_t n_cells = 0;
+    double *d_cell_sums = nullptr;
+    void *d_est = nullptr;
+    int64_t est_cap = 0;             // right-hand sides d_est holds
     int32_t tc_order_npairs = 0;     // ... built for this many pairs
     std::vector<cudaEvent_t> stage_ev;   // BF16x3 3D: [chunk][stage][begin, end] of the last apply
     int stage_chunks = 0;
@@ -242,4 +249,8 @@ cudaError_t launch_tc3d_axis0(const ApplyParams &p, int ctas, void *scratch, con
 pc_status plain_apply(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
                       cudaStream_t s, std::string &err);
 void plain_free(pc_operator *op);
+// error estimator (pc_estimate.cu): out[c] = sum over cell c and q columns of (yt - y)^2, FP64
+cudaError_t launch_cell_sqdiff(pc_precision prec, const void *yt, int64_t ldyt, const void *y, int64_t ldy, int32_t q,
+                               const int32_t *cells, int32_t ncells, int64_t n1, int64_t n2, double *out,
+                               cudaStream_t s);
 }  // namespace pc
