@@ -216,10 +216,11 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def serve_operators(pcg, ctx):
+def serve_operators(pcg, ctx, with_3d=True):
     """The served operator mix: 2D 256^2 (9x9 grid), 512^2 (the benchmark
     operator), 1024^2 (adaptive quadtree, heavy-tailed, R = 64) and 2048^2
-    (65x65 grid), all FP32 with 128^2 patch FFTs."""
+    (65x65 grid), FP32 with 128^2 patch FFTs; and 3D 64^3 ... 160^3 in FP32
+    and BF16x3."""
     import workloads
     from workloads import configs
     wls = []
@@ -238,6 +239,19 @@ def serve_operators(pcg, ctx):
         pts = pcg.pc_sample_points(shape, cells)
         ops.append((name, pcg.Operator(ctx, shape, cells, R, workloads.impulse_windows(shape, pts, kern),
                                        precision="fp32", fft_size=128)))
+    if with_3d:
+        # 3D: 64^3 (5^3 grid), 96^3 (7^3), 128^3 (8^3, the 3D workload), 160^3
+        # (10^3); axis-aligned Gaussian, sigma in [1.5, 5], R = 12, 64^3 patches;
+        # each in FP32 and in the BF16x3 (tensor-core) mode
+        for L, n in ((64, 5), (96, 7), (128, 8), (160, 10)):
+            shape = (L, L, L)
+            s3 = [workloads.SmoothField(shape, 1.5, 5.0, 4000 + 1 + i) for i in range(3)]
+            kern = workloads.GaussianAxis3D(s3[0], s3[1], s3[2], 12)
+            cells = workloads.regular_grid(shape, (n, n, n))
+            pts = pcg.pc_sample_points(shape, cells)
+            phi = workloads.impulse_windows(shape, pts, kern)
+            for prec in ("fp32", "bf16x3"):
+                ops.append(("gaussian3d_%d_%s" % (L, prec), pcg.Operator(ctx, shape, cells, 12, phi, precision=prec)))
     return ops
 
 
@@ -251,7 +265,11 @@ def run_serve(args):
     libbuild.build()
     ctx = pcg.Context(0)
     ops = serve_operators(pcg, ctx)
-    pools = [torch.from_numpy(workloads.rhs(7000 + i, 64, op.shape)).cuda() for i, (_, op) in enumerate(ops)]
+    by_shape = {}
+    for i, (_, op) in enumerate(ops):
+        if op.shape not in by_shape:
+            by_shape[op.shape] = torch.from_numpy(workloads.rhs(7000 + i, 64, op.shape)).cuda()
+    pools = [by_shape[op.shape] for _, op in ops]
     rng = np.random.default_rng(17)
 
     def make_requests(n):
@@ -288,11 +306,14 @@ def run_serve(args):
         loads.append({"load": f, "requests": st["completed"], "rhs_per_s": st["rhs_per_s"],
                       "p50_ms": 1e3 * st["p50_latency_s"], "p99_ms": 1e3 * st["p99_latency_s"],
                       "launches": st["launches"], "peak_budget_bytes": st["peak_bytes"]})
-    # the plain per-vector path on the saturated request set, one request after another
+    # the plain per-vector path on the saturated request set, one request after
+    # another (2D requests: the plain path is 2D only)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     rhs = 0
     for o, k in sat_reqs:
+        if len(ops[o][1].shape) != 2:
+            continue
         y = torch.empty_like(pools[o][:k])
         ops[o][1].apply_plain(pools[o][:k], y)
         rhs += k
@@ -306,7 +327,8 @@ def run_serve(args):
             "loads": loads, "plain_gpu_rhs_per_s": plain,
             "config": {"operators": [n for n, _ in ops], "rhs_per_request": "U[1,64]", "budget_bytes": 120 << 30,
                        "arrivals": "Poisson at 50/80/95% of the saturated rate",
-                       "not_served": "3D operators (no 3D patch kernel yet); compensated-BF16 mode (not built)"}}
+                       "modes": "2D FP32; 3D FP32 and BF16x3 (tensor-core first axis)",
+                       "plain_gpu": "2D requests of the saturated set only"}}
     print(json.dumps(line), flush=True)
 
 

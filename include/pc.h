@@ -105,7 +105,8 @@ typedef struct {
     int32_t num_colors;      /* overlap-add order classes */
     int32_t precision;       /* pc_precision */
     int64_t spectra_bytes;   /* device bytes of the stored spectra */
-    int64_t device_bytes;    /* all device bytes owned by the operator */
+    int64_t device_bytes;    /* all device bytes owned by the operator, including the
+                                buffers its applies have grown so far */
     double build_seconds;
 } pc_operator_info;
 
@@ -234,6 +235,17 @@ pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t
 pc_status pc_apply_adjoint_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx,
                                    void *y, int64_t ldy, pc_stream stream);
 
+/* Matrix entries in O(1) each (Section 3.1, Eq. conv_matrix_entries):
+ *   out[i] = A~[rows[i], cols[i]] = sum_{k : x in U_k} w_k[x] phi_k^E[y - x],
+ * y = rows[i], x = cols[i] flat C-order indices into Omega.  Only the sample
+ * points of a leaf cell containing x carry weight at x, so each entry visits
+ * a handful of terms.  rows, cols: device int64 [n]; out: device double [n];
+ * stream-ordered.  phi_k^E is kept in FP64, w_k in the operator's precision.
+ * An index outside [0, N) yields NaN for that entry (no memory access).
+ * These are the entries an H-matrix or CUR builder asks for (Section 3.4). */
+pc_status pc_entries(pc_operator *op, int64_t n, const int64_t *rows, const int64_t *cols, double *out,
+                     pc_stream stream);
+
 /* Randomized a-posteriori error estimator (Section 2.6,
  * Eq. randomized_estimator_ec): for every leaf cell C of the operator's grid
  * (the cells passed to pc_build_spectra, in that order, as closed boxes),
@@ -301,7 +313,11 @@ pc_status pc_apply_batched_noalloc(pc_operator *op, int32_t nrhs, const void *x,
  * from a CUDA graph captured at creation.  Launch slots run on separate
  * streams, so a new launch starts while earlier ones finish.  Each request
  * is computed exactly as pc_apply_batched would compute it alone.
- * Supported operators: 2D, PC_FP32, fft_size 128.
+ * Supported operators: 2D PC_FP32 with fft_size 128 (batched together as
+ * above) and 3D PC_FP32 / PC_BF16X3.  A 3D request runs alone on a launch
+ * slot through the operator's own apply, one request per 3D operator at a
+ * time; 3D requests of different operators, and 2D launches, overlap on the
+ * other slots.
  * --------------------------------------------------------------------- */
 
 /* Create a server on ctx's device: a scheduler thread, `streams` launch
@@ -311,7 +327,11 @@ pc_status pc_serve_create(pc_context *ctx, const pc_serve_config *cfg, pc_server
 
 /* Queue Y = A~ X for nrhs vectors: x and y are device arrays [nrhs][N] of
  * float (contiguous), owned by the caller and kept alive until pc_serve_poll
- * returns PC_OK for the ticket.  Returns at once with *ticket.  Errors:
+ * returns PC_OK for the ticket.  Returns at once with *ticket.  While an
+ * operator has requests queued or running, the caller must not apply or
+ * destroy it through other calls (the server's scheduler thread owns it;
+ * for a 3D operator it grows the operator's ordering flags and scratch
+ * before the launch, which may synchronise the device).  Errors:
  * PC_ERR_UNSUPPORTED for operators the server cannot launch, PC_ERR_BUDGET
  * if the operator and request alone exceed the budget, PC_ERR_ARG for bad
  * arguments.  flags: reserved, pass 0. */

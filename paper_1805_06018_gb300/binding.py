@@ -100,6 +100,7 @@ _PROTOS = {
     "pc_apply_adjoint_batched": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
     "pc_estimate_cell_errors": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64,
                                                 ctypes.POINTER(ctypes.c_double), _VP]),
+    "pc_entries": (ctypes.c_int, [_VP, ctypes.c_int64, _VP, _VP, _VP, _VP]),
     "pc_operator_launches": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     "pc_operator_stage_time": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
     "pc_operator_destroy": (ctypes.c_int, [_VP]),
@@ -319,6 +320,18 @@ class Operator:
         B, y = self._args(x, out)
         self.pc_apply_adjoint_batched(B, x.data_ptr(), self.N, y.data_ptr(), self.N, _stream_ptr(stream))
         return y
+
+    def entries(self, rows, cols, stream=None):
+        """A~[rows[i], cols[i]] (flat indices; int64 CUDA tensors) as an FP64 CUDA tensor."""
+        import torch
+        rows = rows.to(device="cuda", dtype=torch.int64).contiguous()
+        cols = cols.to(device="cuda", dtype=torch.int64).contiguous()
+        if rows.numel() != cols.numel():
+            raise ValueError("rows and cols must have the same length")
+        out = torch.empty(rows.numel(), dtype=torch.float64, device="cuda")
+        _check(lib().pc_entries(self.handle, ctypes.c_int64(rows.numel()), _VP(rows.data_ptr()), _VP(cols.data_ptr()),
+                                _VP(out.data_ptr()), _VP(_stream_ptr(stream))), self.ctx.handle)
+        return out
 
     def estimate_cell_errors(self, z, y, num_cells: int, stream=None) -> np.ndarray:
         """eta_C for every leaf cell (Section 2.6): z, y = A* z are contiguous

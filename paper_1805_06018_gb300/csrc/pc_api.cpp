@@ -84,10 +84,11 @@ void free_operator(pc_operator *op) {
     cudaFree(op->d_tw);
     cudaFree(op->d_scratch);
     cudaFree(op->d_tc_ops);
-    cudaFree(op->d_tc_order);
+    for (auto &kv : op->tc_orders) cudaFree(kv.second);
     cudaFree(op->d_cells);
     cudaFree(op->d_cell_sums);
     cudaFree(op->d_est);
+    cudaFree(op->d_entry_mem);
     for (cudaEvent_t ev : op->stage_ev) cudaEventDestroy(ev);
     if (op->ev_begin) cudaEventDestroy(op->ev_begin);
     if (op->ev_end) cudaEventDestroy(op->ev_end);
@@ -345,6 +346,53 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
             return bail(e, "cell sums");
         acct += sizeof(double) * std::max(nc, 1);
     }
+    {
+        // O(1) matrix entries (Section 3.1): pixel -> one containing leaf cell,
+        // cell -> its sample points, per-patch bbox and weight offsets, phi_k^E
+        const int64_t N = g.shape[0] * g.shape[1] * g.shape[2];
+        std::vector<int32_t> cell_of(size_t(N), 0), cstart(1, 0), cpts, bblo, bbext;
+        for (size_t c = 0; c < g.cell_lo.size(); ++c) {
+            for (int64_t a = g.cell_lo[c][0]; a <= g.cell_hi[c][0]; ++a)
+                for (int64_t b = g.cell_lo[c][1]; b <= g.cell_hi[c][1]; ++b)
+                    for (int64_t q = g.cell_lo[c][2]; q <= g.cell_hi[c][2]; ++q)
+                        cell_of[size_t((a * g.shape[1] + b) * g.shape[2] + q)] = int32_t(c);
+            for (int32_t k : g.points_of[c]) cpts.push_back(k);
+            cstart.push_back(int32_t(cpts.size()));
+        }
+        for (int k = 0; k < r; ++k)
+            for (int a = 0; a < 3; ++a) {
+                bblo.push_back(a < g.d ? int32_t(g.bb_lo[k][a]) : 0);
+                bbext.push_back(a < g.d ? int32_t(g.bb_hi[k][a] - g.bb_lo[k][a] + 1) : 1);
+            }
+        if (cpts.empty()) cpts.push_back(0);
+        auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+        const size_t o_cell = 0, o_cs = o_cell + al(cell_of.size() * 4), o_cp = o_cs + al(cstart.size() * 4),
+                     o_lo = o_cp + al(cpts.size() * 4), o_ext = o_lo + al(bblo.size() * 4),
+                     o_wo = o_ext + al(bbext.size() * 4), o_phi = o_wo + al(woff.size() * 8),
+                     total = o_phi + al(phiE.size() * 8);
+        if ((e = cudaMalloc(&op->d_entry_mem, total)) != cudaSuccess) return bail(e, "entry tables");
+        acct += total;
+        char *base = static_cast<char *>(op->d_entry_mem);
+        const std::pair<size_t, std::pair<const void *, size_t>> parts[] = {
+            {o_cell, {cell_of.data(), cell_of.size() * 4}}, {o_cs, {cstart.data(), cstart.size() * 4}},
+            {o_cp, {cpts.data(), cpts.size() * 4}},         {o_lo, {bblo.data(), bblo.size() * 4}},
+            {o_ext, {bbext.data(), bbext.size() * 4}},     {o_wo, {woff.data(), woff.size() * 8}},
+            {o_phi, {phiE.data(), phiE.size() * 8}}};
+        for (const auto &pt : parts)
+            if (e == cudaSuccess) e = cudaMemcpy(base + pt.first, pt.second.first, pt.second.second, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return bail(e, "entry tables");
+        pc::EntryData &ed = op->entry;
+        ed.d = g.d;
+        ed.R = radius;
+        for (int a = 0; a < 3; ++a) ed.n[a] = int32_t(g.shape[a]);
+        ed.cell_of = reinterpret_cast<const int32_t *>(base + o_cell);
+        ed.cpts_start = reinterpret_cast<const int32_t *>(base + o_cs);
+        ed.cpts = reinterpret_cast<const int32_t *>(base + o_cp);
+        ed.bb_lo = reinterpret_cast<const int32_t *>(base + o_lo);
+        ed.bb_ext = reinterpret_cast<const int32_t *>(base + o_ext);
+        ed.w_off = reinterpret_cast<const int64_t *>(base + o_wo);
+        ed.phiE = reinterpret_cast<const double *>(base + o_phi);
+    }
     if ((e = cudaMalloc(&op->d_ctrl, 64)) != cudaSuccess) return bail(e, "control block");
     acct += 64;
     if ((e = cudaMemset(op->d_ctrl, 0, 64)) != cudaSuccess) return bail(e, "control block");
@@ -450,6 +498,7 @@ static pc_status ensure_done_capacity(pc_operator *op, int32_t npairs) {
     if (e != cudaSuccess) return cuda_fail(op->ctx, e, "synchronising before growing flags");
     cudaFree(op->d_done);
     op->d_done = nullptr;
+    op->device_bytes -= sizeof(uint32_t) * size_t(op->n_tiles) * size_t(op->done_cap);
     const int32_t cap = std::max<int32_t>(npairs, 32);
     const size_t bytes = sizeof(uint32_t) * size_t(op->n_tiles) * cap;
     e = cudaMalloc(&op->d_done, bytes);
@@ -457,6 +506,7 @@ static pc_status ensure_done_capacity(pc_operator *op, int32_t npairs) {
         op->done_cap = 0;
         return cuda_fail(op->ctx, e, "allocating ordering flags");
     }
+    op->device_bytes += bytes;
     e = cudaMemset(op->d_done, 0, bytes);
     if (e != cudaSuccess) return cuda_fail(op->ctx, e, "clearing ordering flags");
     op->done_cap = cap;
@@ -467,27 +517,43 @@ static pc_status ensure_done_capacity(pc_operator *op, int32_t npairs) {
 // 3D, BF16x3: the items run in chunks of at most kTc3dChunkItems through
 // three kernels (phase 1 -> tensor-core first-axis transform -> phase 3),
 // each item with its own scratch volume; stream-ordered like the fused path.
+// BF16x3 3D: per-item scratch volumes for a chunk of min(total, kTc3dChunkItems) items
+static pc_status ensure_split3d_scratch(pc_operator *op, int64_t total) {
+    const int64_t chunk = std::min<int64_t>(total, pc::kTc3dChunkItems);
+    if (op->scratch_items >= chunk) return PC_OK;
+    cudaError_t e = cudaSuccess;
+    if (op->d_scratch && (e = cudaDeviceSynchronize()) != cudaSuccess)
+        return cuda_fail(op->ctx, e, "synchronising before growing the scratch volumes");
+    cudaFree(op->d_scratch);
+    op->d_scratch = nullptr;
+    op->device_bytes -= size_t(op->scratch_items) * pc::fft3d_scratch_bytes(1);
+    op->scratch_items = 0;
+    if ((e = cudaMalloc(&op->d_scratch, size_t(chunk) * pc::fft3d_scratch_bytes(1))) != cudaSuccess)
+        return cuda_fail(op->ctx, e, "allocating the 3D scratch volumes");
+    op->scratch_items = chunk;
+    op->device_bytes += size_t(chunk) * pc::fft3d_scratch_bytes(1);
+    return PC_OK;
+}
+
 static pc_status apply_split3d(pc_operator *op, const pc::ApplyParams &p, cudaStream_t s) {
     pc_context *ctx = op->ctx;
     const int64_t total = p.total_items;
     const int64_t chunk = std::min<int64_t>(total, pc::kTc3dChunkItems);
     cudaError_t e = cudaSuccess;
-    if (op->scratch_items < chunk) {
-        if (op->d_scratch && (e = cudaDeviceSynchronize()) != cudaSuccess)
-            return cuda_fail(ctx, e, "synchronising before growing the scratch volumes");
-        cudaFree(op->d_scratch);
-        op->d_scratch = nullptr;
-        op->scratch_items = 0;
-        if ((e = cudaMalloc(&op->d_scratch, size_t(chunk) * pc::fft3d_scratch_bytes(1))) != cudaSuccess)
-            return cuda_fail(ctx, e, "allocating the 3D scratch volumes");
-        op->scratch_items = chunk;
-    }
+    pc_status st0 = ensure_split3d_scratch(op, total);
+    if (st0 != PC_OK) return st0;
     const int nchunks = int((total + chunk - 1) / chunk);
-    if (op->tc_order_npairs != p.npairs) {
+    int32_t *order = nullptr;
+    auto oit = op->tc_orders.find(p.npairs);
+    if (oit != op->tc_orders.end()) {
+        order = oit->second;
+    } else {
         // items of each chunk sorted by (tile, pair): the tensor stage then
-        // visits the pairs of one tile and line block back to back
+        // visits the pairs of one tile and line block back to back.  One
+        // table per batch shape, kept until the operator is destroyed, so
+        // applies in flight never see their table replaced.
         const int32_t np = p.npairs;
-        std::vector<int32_t> order(static_cast<size_t>(total));
+        std::vector<int32_t> ord(static_cast<size_t>(total));
         std::vector<std::pair<int64_t, int32_t>> key;
         for (int c = 0; c < nchunks; ++c) {
             const int64_t c0 = int64_t(c) * chunk, c1 = std::min<int64_t>(total, c0 + chunk);
@@ -501,22 +567,15 @@ static pc_status apply_split3d(pc_operator *op, const pc::ApplyParams &p, cudaSt
                 key.emplace_back(ti * np + pair, int32_t(item));
             }
             std::sort(key.begin(), key.end());
-            for (size_t i = 0; i < key.size(); ++i) order[size_t(c0) + i] = key[i].second;
+            for (size_t i = 0; i < key.size(); ++i) ord[size_t(c0) + i] = key[i].second;
         }
-        if (op->d_tc_order && (e = cudaDeviceSynchronize()) != cudaSuccess)
-            return cuda_fail(ctx, e, "synchronising before replacing the unit order");
-        cudaFree(op->d_tc_order);
-    cudaFree(op->d_cells);
-    cudaFree(op->d_cell_sums);
-    cudaFree(op->d_est);
-        op->d_tc_order = nullptr;
-        op->tc_order_npairs = 0;
-        if ((e = cudaMalloc(&op->d_tc_order, order.size() * sizeof(int32_t))) != cudaSuccess)
+        if ((e = cudaMalloc(&order, ord.size() * sizeof(int32_t))) != cudaSuccess)
             return cuda_fail(ctx, e, "allocating the unit order");
-        if ((e = cudaMemcpy(op->d_tc_order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) !=
-            cudaSuccess)
+        if ((e = cudaMemcpy(order, ord.data(), ord.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess) {
+            cudaFree(order);
             return cuda_fail(ctx, e, "uploading the unit order");
-        op->tc_order_npairs = np;
+        }
+        op->tc_orders[np] = order;
     }
     while (op->stage_ev.size() < size_t(nchunks) * 6) {
         cudaEvent_t ev = nullptr;
@@ -535,8 +594,7 @@ static pc_status apply_split3d(pc_operator *op, const pc::ApplyParams &p, cudaSt
         cudaEventRecord(ev[1], s);
         if (e != cudaSuccess) break;
         cudaEventRecord(ev[2], s);
-        e = pc::launch_tc3d_axis0(p, ctx->num_sms, op->d_scratch, op->d_tc_order, c0, c1, op->d_tc_ops,
-                                  op->tc_k1cap, s);
+        e = pc::launch_tc3d_axis0(p, ctx->num_sms, op->d_scratch, order, c0, c1, op->d_tc_ops, op->tc_k1cap, s);
         cudaEventRecord(ev[3], s);
         if (e != cudaSuccess) break;
         cudaEventRecord(ev[4], s);
@@ -550,6 +608,20 @@ static pc_status apply_split3d(pc_operator *op, const pc::ApplyParams &p, cudaSt
     op->last_stream = s;
     op->launches_last = 1 + 3 * int64_t(nchunks);
     return PC_OK;
+}
+
+// Grow what an apply of nrhs vectors allocates on demand (ordering flags,
+// BF16x3 scratch), so that a later apply of at most nrhs vectors allocates
+// nothing.  May synchronise the device when something grows.
+static pc_status prepare_batch_impl(pc_operator *op, int32_t nrhs) {
+    if (!op || nrhs < 1) return fail(op ? op->ctx : nullptr, PC_ERR_ARG, "bad operator or nrhs");
+    DeviceGuard dg(op->ctx->device);
+    if (!dg.ok) return fail(op->ctx, PC_ERR_CUDA, "cannot select the context's device");
+    const int32_t npairs = (nrhs + 1) / 2;
+    const bool split3d = op->d == 3 && op->prec == PC_BF16X3;
+    pc_status st = ensure_done_capacity(op, split3d ? npairs * pc::kPhase3Groups : npairs);
+    if (st == PC_OK && split3d) st = ensure_split3d_scratch(op, int64_t(op->n_tiles) * npairs);
+    return st;
 }
 
 static pc_status apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
@@ -647,6 +719,7 @@ pc_status pc_estimate_cell_errors(pc_operator *op, int32_t q, const void *z, int
         if (op->d_est && (e = cudaDeviceSynchronize()) != cudaSuccess)
             return cuda_fail(ctx, e, "synchronising before growing the estimator scratch");
         cudaFree(op->d_est);
+    cudaFree(op->d_entry_mem);
         op->d_est = nullptr;
         op->est_cap = 0;
         if ((e = cudaMalloc(&op->d_est, size_t(q) * size_t(op->N) * op->elem)) != cudaSuccess)
@@ -669,6 +742,20 @@ pc_status pc_estimate_cell_errors(pc_operator *op, int32_t q, const void *z, int
         return cuda_fail(ctx, e, "reading the cell sums");
     for (int c = 0; c < op->n_cells; ++c) eta[c] = std::sqrt(sums[size_t(c)] / double(q));
     op->launches_last += 1;
+    return PC_OK;
+}
+
+pc_status pc_entries(pc_operator *op, int64_t n, const int64_t *rows, const int64_t *cols, double *out,
+                     pc_stream stream) {
+    if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
+    if (n < 0) return fail(op->ctx, PC_ERR_ARG, "n < 0");
+    if (n == 0) return PC_OK;
+    if (!rows || !cols || !out) return fail(op->ctx, PC_ERR_ARG, "null rows, cols or out");
+    DeviceGuard dg(op->ctx->device);
+    if (!dg.ok) return fail(op->ctx, PC_ERR_CUDA, "cannot select the context's device");
+    const cudaError_t e = pc::launch_entries(op->prec, n, rows, cols, out, op->entry, op->d_w,
+                                             static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(op->ctx, e, "launching the entries kernel");
     return PC_OK;
 }
 
@@ -753,3 +840,7 @@ pc_status pc_operator_destroy(pc_operator *op) {
 }
 
 }  // extern "C"
+
+namespace pc {
+pc_status prepare_batch(pc_operator *op, int32_t nrhs) { return prepare_batch_impl(op, nrhs); }
+}  // namespace pc

@@ -7,6 +7,7 @@
 #include <array>
 #include <cstdint>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "pc.h"
@@ -141,6 +142,21 @@ struct LaunchParams {
     uint32_t *host_flags;           // mapped host memory: host_flags[slot] = 1 once a segment is complete
 };
 
+// Device data of the O(1) matrix entries (pc_entries.cu): box (2D: n[2] = 1),
+// per pixel one leaf cell containing it, per cell its sample points (CSR),
+// per patch bbox(U_k) origin/extents and weight offset, phi_k^E in FP64.
+struct EntryData {
+    int32_t d, R;
+    int32_t n[3];
+    const int32_t *cell_of;       // [N]
+    const int32_t *cpts_start;    // [ncells + 1]
+    const int32_t *cpts;          // sample points of each cell
+    const int32_t *bb_lo;         // [r][3]
+    const int32_t *bb_ext;        // [r][3] (axes beyond d: 1)
+    const int64_t *w_off;         // [r]
+    const double *phiE;           // [r][(2R+1)^d]
+};
+
 }  // namespace pc
 
 struct pc_context {
@@ -179,7 +195,8 @@ struct pc_operator {
     int64_t scratch_items = 0;   // BF16x3 3D: items d_scratch holds
     void *d_tc_ops = nullptr;    // BF16x3 3D: DFT operand tiles for the tensor cores
     int tc_k1cap = 0;            // BF16x3 3D: K columns of the GEMM-1 operands
-    int32_t *d_tc_order = nullptr;   // BF16x3 3D: per-chunk item order of the tensor stage
+    // BF16x3 3D: per batch shape (pairs), the per-chunk item order of the tensor stage
+    std::unordered_map<int32_t, int32_t *> tc_orders;
     // error estimator (Section 2.6): leaf cells [n][6] on the canonical box
     // (2D grids as (1, n0, n1)), per-cell sums, adjoint scratch
     int32_t *d_cells = nullptr;
@@ -187,7 +204,9 @@ struct pc_operator {
     double *d_cell_sums = nullptr;
     void *d_est = nullptr;
     int64_t est_cap = 0;             // right-hand sides d_est holds
-    int32_t tc_order_npairs = 0;     // ... built for this many pairs
+    // O(1) matrix entries (Section 3.1): device tables, one allocation
+    void *d_entry_mem = nullptr;
+    pc::EntryData entry{};
     std::vector<cudaEvent_t> stage_ev;   // BF16x3 3D: [chunk][stage][begin, end] of the last apply
     int stage_chunks = 0;
     uint32_t epoch = 0;
@@ -249,6 +268,11 @@ cudaError_t launch_tc3d_axis0(const ApplyParams &p, int ctas, void *scratch, con
 pc_status plain_apply(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
                       cudaStream_t s, std::string &err);
 void plain_free(pc_operator *op);
+// matrix entries (pc_entries.cu): out[i] = A~[rows[i], cols[i]] (flat indices), FP64
+cudaError_t launch_entries(pc_precision prec, int64_t n, const int64_t *rows, const int64_t *cols, double *out,
+                           const EntryData &e, const void *w, cudaStream_t s);
+// grow the on-demand device buffers of an apply of nrhs vectors (pc_api.cpp)
+pc_status prepare_batch(pc_operator *op, int32_t nrhs);
 // error estimator (pc_estimate.cu): out[c] = sum over cell c and q columns of (yt - y)^2, FP64
 cudaError_t launch_cell_sqdiff(pc_precision prec, const void *yt, int64_t ldyt, const void *y, int64_t ldy, int32_t q,
                                const int32_t *cells, int32_t ncells, int64_t n1, int64_t n2, double *out,

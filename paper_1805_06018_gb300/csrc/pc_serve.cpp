@@ -12,6 +12,15 @@
 // streams, so the next launch is already running while the previous one
 // drains: requests that arrive while others run are admitted as soon as a
 // slot and memory free up.
+//
+// 3D operators (FP32, or BF16x3 with the tensor-core first axis) do not fit
+// the multi-request 2D kernel: a 3D request at the head of the queue takes a
+// free slot on its own and runs the operator's own apply on that slot's
+// stream.  A 3D operator has at most one request in flight (its ordering
+// flags and scratch volumes are per operator); different operators run
+// concurrently on different slots.  The buffers such an apply grows on demand
+// are grown by the scheduler thread just before the launch (the only thread
+// that touches a served operator), which may synchronise the device once.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -44,6 +53,7 @@ struct Request {
     int status = PC_OK;
     int hslot = -1;     // host completion flag index
     int launch_requests = 0;
+    bool solo = false;  // 3D: runs alone through the operator's own apply
     std::string error;
 };
 
@@ -59,6 +69,7 @@ struct LaunchSlot {
     int32_t *d_status = nullptr;
     cudaEvent_t done = nullptr;
     bool busy = false;
+    bool solo = false;                  // running one 3D request
     std::vector<Request *> reqs;
 };
 
@@ -81,6 +92,7 @@ struct pc_server {
     std::vector<int> free_hslots;
     int64_t budget_used = 0, budget_peak = 0;
     std::unordered_map<pc_operator *, int> op_inflight;
+    std::unordered_map<pc_operator *, int64_t> op_bytes;   // operator bytes counted while it has work in flight
     int inflight = 0;
     std::vector<double> latencies;
     int64_t rhs_done = 0, launches = 0;
@@ -103,7 +115,8 @@ void release_budget(pc_server *s, Request *r) {
     s->budget_used -= r->scratch_bytes;
     auto it = s->op_inflight.find(r->op);
     if (it != s->op_inflight.end() && --it->second == 0) {
-        s->budget_used -= int64_t(r->op->device_bytes);
+        s->budget_used -= s->op_bytes[r->op];
+        s->op_bytes.erase(r->op);
         s->op_inflight.erase(it);
     }
     --s->inflight;
@@ -121,7 +134,9 @@ void reap(pc_server *s) {
         if (!sl.busy) continue;
         const double t = s->now();
         for (Request *r : sl.reqs) {
-            if (r->state != 1) continue;
+            // early completion through the mapped flag (batched 2D requests
+            // only: a 3D request has no flag slot and completes with its launch)
+            if (r->state != 1 || r->hslot < 0) continue;
             if (reinterpret_cast<volatile uint32_t *>(s->h_flags)[r->hslot] != 0u) {
                 r->state = 2;
                 r->finish_s = t;
@@ -133,10 +148,12 @@ void reap(pc_server *s) {
         }
         const cudaError_t q = cudaEventQuery(sl.done);
         if (q == cudaErrorNotReady) continue;
-        // the launch has ended: anything not flagged failed
+        // the launch has ended: anything not flagged failed.  A 3D request
+        // reports through its operator's timeout flag.
         int32_t status = 0;
+        int32_t *d_status = sl.solo ? sl.reqs.front()->op->d_ctrl + 2 : sl.d_status;
         if (q == cudaSuccess &&
-            cudaMemcpyAsync(&status, sl.d_status, sizeof(status), cudaMemcpyDeviceToHost, sl.stream) == cudaSuccess)
+            cudaMemcpyAsync(&status, d_status, sizeof(status), cudaMemcpyDeviceToHost, sl.stream) == cudaSuccess)
             cudaStreamSynchronize(sl.stream);
         for (Request *r : sl.reqs) {
             if (r->state != 1) continue;
@@ -161,19 +178,69 @@ void reap(pc_server *s) {
             }
             release_budget(s, r);
         }
-        if (status) cudaMemsetAsync(sl.d_status, 0, sizeof(int32_t), sl.stream);
+        if (status) cudaMemsetAsync(d_status, 0, sizeof(int32_t), sl.stream);
         sl.reqs.clear();
         sl.busy = false;
+        sl.solo = false;
     }
+}
+
+// A 3D request at the head of the queue, alone on slot sl.  Returns false if
+// it has to wait (FIFO: nothing behind it overtakes).
+bool launch_solo(pc_server *s, LaunchSlot &sl) {
+    Request *r = s->queue.front();
+    if (s->op_inflight.count(r->op)) return false;              // one request per 3D operator
+    if (s->inflight >= s->cfg.max_inflight) return false;
+    // Grow the operator's ordering flags and scratch for this request here,
+    // on the scheduler thread, the only thread that touches a served
+    // operator.  Growing synchronises the device first, so no launch still
+    // uses the buffers it frees.
+    const pc_status pst = pc::prepare_batch(r->op, r->nrhs);
+    if (pst != PC_OK) {
+        s->queue.pop_front();
+        r->state = 3;
+        r->status = int(pst);
+        r->error = r->op->ctx->last_error;
+        return true;
+    }
+    if (s->budget_used + admission_bytes(s, r) > s->cfg.hbm_budget_bytes) return false;
+    s->budget_used += admission_bytes(s, r);
+    s->op_bytes[r->op] = int64_t(r->op->device_bytes);
+    s->op_inflight[r->op]++;
+    ++s->inflight;
+    s->budget_peak = std::max(s->budget_peak, s->budget_used);
+    s->queue.pop_front();
+    r->state = 1;
+    r->launch_s = s->now();
+    r->launch_requests = 1;
+    pc_status st = pc_apply_batched(r->op, r->nrhs, r->x, r->op->N, r->y, r->op->N, sl.stream);
+    cudaError_t e = st == PC_OK ? cudaEventRecord(sl.done, sl.stream) : cudaSuccess;
+    if (st != PC_OK || e != cudaSuccess) {
+        r->state = 3;
+        r->status = st != PC_OK ? int(st) : int(PC_ERR_CUDA);
+        r->error = st != PC_OK ? r->op->ctx->last_error : std::string(cudaGetErrorString(e));
+        release_budget(s, r);
+        return true;
+    }
+    sl.reqs.assign(1, r);
+    sl.busy = true;
+    sl.solo = true;
+    ++s->launches;
+    return true;
 }
 
 void try_launch(pc_server *s) {
     for (auto &sl : s->slots) {
         if (sl.busy || s->queue.empty()) continue;
+        if (s->queue.front()->solo) {
+            if (!launch_solo(s, sl)) return;
+            continue;
+        }
         std::vector<Request *> take;
         int64_t words = 0, extra = 0;
         std::unordered_map<pc_operator *, int> seen;
         for (Request *r : s->queue) {
+            if (r->solo) break;   // the 3D request takes a slot of its own next
             if (int(take.size()) >= s->cfg.max_requests_per_launch) break;
             if (s->inflight + int(take.size()) >= s->cfg.max_inflight) break;
             if (s->free_hslots.size() <= take.size()) break;
@@ -229,7 +296,10 @@ void try_launch(pc_server *s) {
             items += p.total_items;
             woff += r->flag_words;
             // admit
-            if (!s->op_inflight.count(op)) s->budget_used += int64_t(op->device_bytes);
+            if (!s->op_inflight.count(op)) {
+                s->budget_used += int64_t(op->device_bytes);
+                s->op_bytes[op] = int64_t(op->device_bytes);
+            }
             s->op_inflight[op]++;
             s->budget_used += r->scratch_bytes;
             ++s->inflight;
@@ -368,8 +438,9 @@ pc_status pc_serve_submit(pc_server *s, pc_operator *op, int32_t nrhs, const voi
     if (!s || !ticket) return PC_ERR_ARG;
     if (!op || nrhs < 1 || !x || !y || flags != 0) return srv_fail(s, PC_ERR_ARG, "bad request arguments");
     if (op->ctx->device != s->ctx->device) return srv_fail(s, PC_ERR_ARG, "operator lives on another device");
-    if (op->d != 2 || op->prec != PC_FP32 || op->P != 128)
-        return srv_fail(s, PC_ERR_UNSUPPORTED, "served operators are 2D, FP32, fft_size 128");
+    const bool solo = op->d == 3;
+    if (!solo && (op->d != 2 || op->prec != PC_FP32 || op->P != 128))
+        return srv_fail(s, PC_ERR_UNSUPPORTED, "served 2D operators are FP32 with fft_size 128");
     if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) % 4)
         return srv_fail(s, PC_ERR_ARG, "x and y must be 4-byte aligned");
     auto *r = new Request;
@@ -377,8 +448,11 @@ pc_status pc_serve_submit(pc_server *s, pc_operator *op, int32_t nrhs, const voi
     r->nrhs = nrhs;
     r->x = x;
     r->y = y;
-    r->flag_words = int64_t(op->n_tiles) * ((nrhs + 1) / 2);
-    r->scratch_bytes = r->flag_words * 4;
+    r->solo = solo;
+    // 2D: the request's ordering flags live in the launch slot's arena; 3D:
+    // in the operator, whose scratch has already been counted in its size
+    r->flag_words = solo ? 0 : int64_t(op->n_tiles) * ((nrhs + 1) / 2);
+    r->scratch_bytes = solo ? 0 : r->flag_words * 4;
     if (r->flag_words > kFlagArenaWords) {
         delete r;
         return srv_fail(s, PC_ERR_BUDGET, "request needs more ordering flags than a launch slot holds; split it");

@@ -113,3 +113,38 @@ def test_autotune_picks_a_valid_shape():
     x = workloads.rhs(3, 2, wl.shape)
     y = op.apply(torch.from_numpy(x).cuda()).cpu().numpy()
     assert np.all(rel_l2(y, orc.apply(x)) <= 1e-5)
+
+
+def test_3d_requests_in_the_mix(ops):
+    """3D operators (FP32 fused and BF16x3 tensor-core) served beside 2D ones:
+    each 3D request runs alone on a slot, one per operator at a time, and
+    every result equals the request applied alone, bit for bit."""
+    import paper_1805_06018_gb300 as pcg
+    shape = (40, 36, 30)
+    cells = workloads.regular_grid(shape, (3, 3, 3))
+    kern = workloads.GaussianAxis3D(lambda x: 1.2 + 0.3 * np.sin(x[..., 0] / 7.0), lambda x: 1.6 + 0 * x[..., 0],
+                                    lambda x: 1.0 + 0.2 * np.cos(x[..., 2] / 5.0), 5)
+    op32 = make_pair(shape, cells, kern, "fp32")[0]
+    op16 = make_pair(shape, cells, kern, "bf16x3")[0]
+    # runs of 2D requests between the 3D ones: a FIFO queue (no overtaking)
+    # merges the 2D requests of a run into one launch
+    mix = [ops[0], ops[1], ops[2], op32, op16, ops[1], ops[0], op32, op16, op32]
+    srv = pcg.Server(context(), budget_bytes=32 << 30, streams=3, max_requests_per_launch=8)
+    rng = np.random.default_rng(1)
+    prepared = []
+    for q, op in enumerate(mix * 2):
+        nrhs = int(rng.integers(1, 7))
+        x = torch.from_numpy(workloads.rhs(600 + q, nrhs, op.shape)).cuda()
+        prepared.append((op, x, torch.full_like(x, float("nan"))))
+    torch.cuda.synchronize()
+    jobs = [(op, x, y, srv.submit(op, x, y)) for op, x, y in prepared]
+    done = _wait(srv, [j[3] for j in jobs], timeout=120.0)
+    for op, x, y, t in jobs:
+        alone = op.apply(x)
+        torch.cuda.synchronize()
+        assert torch.equal(y, alone)
+        assert done[t]["status"] == 0
+    st = srv.stats()
+    assert st["completed"] == len(jobs)
+    assert st["launches"] < len(jobs)                 # the 2D requests still share launches
+    srv.close()
