@@ -356,8 +356,8 @@ class Operator:
 
     def close(self):
         if getattr(self, "handle", None):
-            lib().pc_operator_destroy(self.handle)
-            self.handle = None
+            h, self.handle = self.handle, None
+            _check(lib().pc_operator_destroy(h), self.ctx.handle)
 
     def __del__(self):
         try:

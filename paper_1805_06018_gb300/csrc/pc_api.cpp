@@ -70,29 +70,36 @@ std::vector<double> twiddles64(int P) {
     return tw;
 }
 
-void free_operator(pc_operator *op) {
-    if (!op) return;
+// Frees everything the operator owns; returns the first failing step (or
+// nullptr) so that teardown errors are reported instead of left pending.
+const char *free_operator(pc_operator *op) {
+    if (!op) return nullptr;
+    const char *bad = nullptr;
+    auto chk = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && !bad) bad = what;
+    };
     pc::plain_free(op);
-    cudaFree(op->d_spec);
-    cudaFree(op->d_w);
-    cudaFree(op->d_tiles);
-    cudaFree(op->d_color_start);
-    cudaFree(op->d_dep_start);
-    cudaFree(op->d_dep);
-    cudaFree(op->d_done);
-    cudaFree(op->d_ctrl);
-    cudaFree(op->d_tw);
-    cudaFree(op->d_scratch);
-    cudaFree(op->d_tc_ops);
-    for (auto &kv : op->tc_orders) cudaFree(kv.second);
-    cudaFree(op->d_cells);
-    cudaFree(op->d_cell_sums);
-    cudaFree(op->d_est);
-    cudaFree(op->d_entry_mem);
-    for (cudaEvent_t ev : op->stage_ev) cudaEventDestroy(ev);
-    if (op->ev_begin) cudaEventDestroy(op->ev_begin);
-    if (op->ev_end) cudaEventDestroy(op->ev_end);
+    chk(cudaFree(op->d_spec), "spectra");
+    chk(cudaFree(op->d_w), "weights");
+    chk(cudaFree(op->d_tiles), "tiles");
+    chk(cudaFree(op->d_color_start), "colours");
+    chk(cudaFree(op->d_dep_start), "dependency starts");
+    chk(cudaFree(op->d_dep), "dependencies");
+    chk(cudaFree(op->d_done), "ordering flags");
+    chk(cudaFree(op->d_ctrl), "control block");
+    chk(cudaFree(op->d_tw), "twiddles");
+    chk(cudaFree(op->d_scratch), "scratch volumes");
+    chk(cudaFree(op->d_tc_ops), "tensor-core operands");
+    for (auto &kv : op->tc_orders) chk(cudaFree(kv.second), "unit orders");
+    chk(cudaFree(op->d_cells), "cells");
+    chk(cudaFree(op->d_cell_sums), "cell sums");
+    chk(cudaFree(op->d_est), "estimator scratch");
+    chk(cudaFree(op->d_entry_mem), "entry tables");
+    for (cudaEvent_t ev : op->stage_ev) chk(cudaEventDestroy(ev), "stage events");
+    if (op->ev_begin) chk(cudaEventDestroy(op->ev_begin), "events");
+    if (op->ev_end) chk(cudaEventDestroy(op->ev_end), "events");
     delete op;
+    return bad;
 }
 
 }  // namespace
@@ -719,7 +726,6 @@ pc_status pc_estimate_cell_errors(pc_operator *op, int32_t q, const void *z, int
         if (op->d_est && (e = cudaDeviceSynchronize()) != cudaSuccess)
             return cuda_fail(ctx, e, "synchronising before growing the estimator scratch");
         cudaFree(op->d_est);
-    cudaFree(op->d_entry_mem);
         op->d_est = nullptr;
         op->est_cap = 0;
         if ((e = cudaMalloc(&op->d_est, size_t(q) * size_t(op->N) * op->elem)) != cudaSuccess)
@@ -833,9 +839,12 @@ pc_status pc_operator_launches(const pc_operator *op, int64_t *kernels_last_appl
 
 pc_status pc_operator_destroy(pc_operator *op) {
     if (!op) return PC_OK;
-    DeviceGuard dg(op->ctx->device);
-    cudaDeviceSynchronize();
-    free_operator(op);
+    pc_context *ctx = op->ctx;
+    DeviceGuard dg(ctx->device);
+    const cudaError_t se = cudaDeviceSynchronize();
+    const char *bad = free_operator(op);
+    if (se != cudaSuccess) return cuda_fail(ctx, se, "synchronising before the operator was freed");
+    if (bad) return fail(ctx, PC_ERR_CUDA, std::string("freeing the operator: ") + bad);
     return PC_OK;
 }
 

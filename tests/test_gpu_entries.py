@@ -67,3 +67,22 @@ def test_sampled_entries_of_the_512_operator_and_bad_indices():
         assert abs(got[i] - col) <= 1e-6 * max(1e-3, abs(col)), (i, got[i], col)
     bad = op.entries(torch.tensor([0, -1, wl.n]), torch.tensor([wl.n + 5, 0, 3])).cpu().numpy()
     assert np.all(np.isnan(bad))
+
+
+def test_entries_after_estimator_and_clean_teardown():
+    """Every entry point on one operator, in turn: the estimator's scratch must
+    not disturb the entry tables, and destroying the operator must free
+    everything without a CUDA error."""
+    shape = (13, 11)
+    cells = workloads.regular_grid(shape, (3, 3))
+    op, orc = make_pair(shape, cells, _kernel(2, 3), "fp64")
+    N = int(np.prod(shape))
+    ref = dense_pc(orc)
+    z = torch.from_numpy(workloads.rhs(86, 3, shape).astype(np.float64)).cuda()
+    for q in (1, 3):    # the second call grows the estimator scratch
+        op.estimate_cell_errors(z[:q], z[:q], len(cells))
+        got = _all_entries(op, N)
+        assert np.max(np.abs(got - ref)) <= 1e-13 * np.abs(ref).max()
+    op.close()
+    torch.cuda.synchronize()
+    torch.zeros(4, device="cuda").sum().item()

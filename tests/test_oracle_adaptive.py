@@ -1,0 +1,97 @@
+"""Oracle adaptive construction (Algorithm 1) against what the method fixes.
+
+* a translation-invariant operator is reproduced exactly (Section 2), so the
+  estimator is zero at the first pass and nothing is refined;
+* anisotropic refinement (Section 2.7): when the impulse responses change
+  only along one axis, every split is along that axis;
+* the loop stops once eta_Omega <= tau, and refining drives the true error
+  (dense matrices, tiny box) down with the estimate;
+* a planted mistake (splitting in the direction of least change) breaks the
+  anisotropy pin.
+"""
+import numpy as np
+
+import workloads
+from oracle import adaptive, Grid
+from oracle.adaptive import construct, split_direction
+from oracle.dense import dense_pc
+from oracle.apply import PCOracle
+
+
+def _impulse(shape, kern):
+    return lambda pts: workloads.impulse_windows(shape, pts, kern)
+
+
+def _probes(shape, A, q=6, seed=3):
+    Z = np.random.default_rng(seed).standard_normal((q, int(np.prod(shape))))
+    return Z, Z @ A
+
+
+def test_translation_invariant_needs_no_refinement():
+    shape = (30, 26)
+    kern = workloads.Skewed([0.5, -0.2], lambda x: 1.3 + 0 * x[..., 0], 4)
+    A = workloads.dense_operator(shape, kern)
+    Z, Y = _probes(shape, A)
+    cells, hist = construct(shape, _impulse(shape, kern), 4, Z, Y, tau=1e-8)
+    assert len(hist) == 1 and hist[0][1] < 1e-10
+    assert len(cells) == 4
+
+
+def test_refinement_follows_the_axis_of_change():
+    shape = (48, 40)
+    L = 48.0
+    kern = workloads.GaussianIso(lambda x: 0.7 + 3.0 * x[..., 0] / L, 6)   # varies along axis 0 only
+    A = workloads.dense_operator(shape, kern)
+    Z, Y = _probes(shape, A)
+    cells, hist = construct(shape, _impulse(shape, kern), 6, Z, Y, tau=1e-3, max_passes=8)
+    assert len(hist) == 8
+    # the four first cells were split along axis 0 only: every leaf still
+    # spans one of the two axis-1 halves of the first split
+    m1 = (shape[1] - 1) // 2
+    spans = {(int(c[0][1]), int(c[1][1])) for c in cells}
+    assert spans == {(0, m1), (m1, shape[1] - 1)}
+
+
+def test_loop_stops_at_tau_and_the_true_error_drops():
+    shape = (40, 36)
+    L = 40.0
+    kern = workloads.GaussianAniso2D(lambda x: 1.0 + 1.5 * x[..., 0] / L, lambda x: 1.2 + 0.8 * x[..., 1] / L,
+                                     lambda x: 0.3 + 0 * x[..., 0], 5)
+    A = workloads.dense_operator(shape, kern)
+    Z, Y = _probes(shape, A, q=8)
+    tau = 0.02
+    cells, hist = construct(shape, _impulse(shape, kern), 5, Z, Y, tau=tau, max_passes=60, batch=2)
+    assert hist[-1][1] <= tau < hist[0][1]
+    g = Grid(shape, cells)
+    orc = PCOracle(shape, cells, workloads.impulse_windows(shape, g.points, kern), 5)
+    true_final = np.linalg.norm(dense_pc(orc) - A) / np.linalg.norm(A)
+    g0 = Grid(shape, adaptive.initial_cells(shape))
+    orc0 = PCOracle(shape, g0.cells, workloads.impulse_windows(shape, g0.points, kern), 5)
+    true_first = np.linalg.norm(dense_pc(orc0) - A) / np.linalg.norm(A)
+    assert true_final < 0.5 * true_first
+    # the estimate tracks the true relative Frobenius error within a small factor
+    assert 0.2 < hist[-1][1] / true_final < 5.0
+
+
+def test_planted_direction_mistake_is_caught(monkeypatch):
+    """The anisotropy pin fails when the split direction is chosen wrongly
+    (here: the direction of least change)."""
+    shape = (48, 40)
+    kern = workloads.GaussianIso(lambda x: 0.7 + 3.0 * x[..., 0] / 48.0, 6)
+    g = Grid(shape, adaptive.initial_cells(shape))
+    orc = PCOracle(shape, g.cells, workloads.impulse_windows(shape, g.points, kern), 6)
+    assert all(split_direction(g, orc.phiE, 6, c) == 0 for c in range(4))
+    real = adaptive.split_direction
+
+    def least_change(grid, phiE, R, c):
+        best = real(grid, phiE, R, c)
+        lo, hi = grid.cells[c]
+        others = [i for i in range(grid.d) if i != best and hi[i] - lo[i] > 2]
+        return others[0] if others else best
+
+    monkeypatch.setattr(adaptive, "split_direction", least_change)
+    A = workloads.dense_operator(shape, kern)
+    Z, Y = _probes(shape, A)
+    cells, _ = construct(shape, _impulse(shape, kern), 6, Z, Y, tau=1e-3, max_passes=8)
+    m1 = (shape[1] - 1) // 2
+    assert {(int(c[0][1]), int(c[1][1])) for c in cells} != {(0, m1), (m1, shape[1] - 1)}
