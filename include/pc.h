@@ -246,6 +246,61 @@ pc_status pc_apply_adjoint_batched(pc_operator *op, int32_t nrhs, const void *x,
 pc_status pc_entries(pc_operator *op, int64_t n, const int64_t *rows, const int64_t *cols, double *out,
                      pc_stream stream);
 
+/* ---------------------------------------------------------------------
+ * Block apply (Section 3.3).  For closed boxes T (targets) and S (sources)
+ * inside Omega, and x_S extended by zero outside S:
+ *   forward  y_T = A~[T, S] x_S
+ *                = sum_{k : U_k meets S} (phi_k^E * (w_k . x_S))[T],
+ *   adjoint  y_T = (A~*)[T, S] x_S
+ *                = sum_{k : U_k meets T} w_k[T] . (flip(phi_k^E) * x_S)[T].
+ * Each term is the paper's translated small convolution: a plan keeps the
+ * operator's input tiles of bbox(U_k) that meet S (T for the adjoint) and
+ * whose output box (tile (+) kernel sub-window) meets T (S), clips each to
+ * S (T) and re-expresses it in the block's own coordinates.  The patch
+ * spectra of the operator are reused as they are (the sub-window of
+ * phi_k^E a tile convolves with does not depend on the tile's extent), so
+ * a plan stores no spectra.  Work: one FFT convolution of the operator's
+ * patch size per kept tile and pair of right-hand sides, i.e.
+ * O(r_S P^d log P) per vector (r_T for the adjoint).  A plan fixes
+ * (operator, T, S, direction); applying it repeatedly, as a Krylov or
+ * randomized-SVD low-rank builder does (Section 3.4), needs no host work
+ * beyond the launches.
+ * --------------------------------------------------------------------- */
+typedef struct pc_block_plan pc_block_plan;
+
+/* t_lo, t_hi, s_lo, s_hi: host arrays of d int64 values (C axis order),
+ * closed boxes with 0 <= lo <= hi < shape per axis, else PC_ERR_ARG.
+ * adjoint: 0 (A~[T,S]) or 1 ((A~*)[T,S]).  2D operators (PC_FP32, PC_FP64);
+ * 3D operators return PC_ERR_UNSUPPORTED.  The plan allocates its device
+ * tables (kept tiles, colour offsets, dependency lists, ordering flags,
+ * control block); the call synchronises the device.  The operator must
+ * outlive the plan.  *plan is NULL on failure. */
+pc_status pc_block_plan_create(pc_operator *op, const int64_t *t_lo, const int64_t *t_hi, const int64_t *s_lo,
+                               const int64_t *s_hi, int32_t adjoint, pc_block_plan **plan);
+
+/* Y[b] = block X[b] for b < nrhs.  X[b] = x + b*ldx holds |S| values in C
+ * order over S, Y[b] = y + b*ldy holds |T| values in C order over T (device,
+ * operator precision, ldx >= |S|, ldy >= |T|, x and y disjoint).  y is
+ * overwritten; every y element sums its contributions in a fixed order, so
+ * the result is bitwise reproducible, and with S = T = Omega it is bitwise
+ * that of pc_apply_batched (pc_apply_adjoint_batched).  Stream-ordered; the
+ * first call with a larger batch grows the plan's ordering flags (and
+ * synchronises the device).  Calls on one plan must be serialised (one
+ * stream); different plans and the operator's own applies may overlap.
+ * nrhs = 0 is a no-op. */
+pc_status pc_block_apply(pc_block_plan *plan, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
+                         pc_stream stream);
+
+/* terms: distinct k with a kept tile (at most r_S, r_T for the adjoint);
+ * tiles: kept tiles.  Either pointer may be NULL. */
+pc_status pc_block_plan_info(const pc_block_plan *plan, int32_t *terms, int32_t *tiles);
+
+/* As pc_operator_check, for the plan's launches: synchronises the plan's
+ * last stream; PC_ERR_TIMEOUT if a bounded wait gave up (flag cleared). */
+pc_status pc_block_plan_check(pc_block_plan *plan);
+
+pc_status pc_block_plan_destroy(pc_block_plan *plan);
+
 /* Randomized a-posteriori error estimator (Section 2.6,
  * Eq. randomized_estimator_ec): for every leaf cell C of the operator's grid
  * (the cells passed to pc_build_spectra, in that order, as closed boxes),

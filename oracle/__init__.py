@@ -20,10 +20,14 @@ What it computes, step by step, in the paper's order and notation:
 4. Apply (Eq. conv_op_approx_main with the convolution of Eq.
    convolution_definition) by direct summation, plain C with OpenMP over
    output points only: for each y, for k ascending, for x in bbox(U_k) with
-   |y - x|_2 <= R: acc += (w_k[x] f[x]) phi_k^E[y - x].  -> :mod:`oracle.apply`
+   y - x in the window [-R, R]^d: acc += (w_k[x] f[x]) phi_k^E[y - x] (the
+   impulse responses vanish outside |z|_2 <= R).  -> :mod:`oracle.apply`
 5. Tiny boxes: dense A~ from the entry formula (Eq. conv_matrix_entries),
    W_k (Eq. Wj_def), F_k (Eq. translation_failure_operator), F (Eq.
    defn_of_F) and the sets mu_k^E (Eq. skew_cylinder_set).  -> :mod:`oracle.dense`
+6. Blocks A~[T, S] and (A~*)[T, S] applied to vectors (Section 3.3): the
+   restricted definition, and the translated small convolution per term.
+   -> :mod:`oracle.block`
 
 Readings where the paper is silent (each one is listed with its reason in the
 design notes): n-point regular grids include the box corners, midpoints round

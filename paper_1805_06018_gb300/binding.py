@@ -101,6 +101,11 @@ _PROTOS = {
     "pc_estimate_cell_errors": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64,
                                                 ctypes.POINTER(ctypes.c_double), _VP]),
     "pc_entries": (ctypes.c_int, [_VP, ctypes.c_int64, _VP, _VP, _VP, _VP]),
+    "pc_block_plan_create": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(_VP)]),
+    "pc_block_apply": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
+    "pc_block_plan_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "pc_block_plan_check": (ctypes.c_int, [_VP]),
+    "pc_block_plan_destroy": (ctypes.c_int, [_VP]),
     "pc_operator_launches": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     "pc_operator_stage_time": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
     "pc_operator_destroy": (ctypes.c_int, [_VP]),
@@ -358,6 +363,63 @@ class Operator:
         if getattr(self, "handle", None):
             h, self.handle = self.handle, None
             _check(lib().pc_operator_destroy(h), self.ctx.handle)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BlockPlan:
+    """Block apply (Section 3.3): y_T = A~[T, S] x_S, or (A~*)[T, S] x_S with
+    adjoint=True, for closed boxes T = [t_lo, t_hi], S = [s_lo, s_hi]
+    (pc_block_plan_create / pc_block_apply).  The operator must outlive the
+    plan."""
+
+    def __init__(self, op: Operator, t_lo, t_hi, s_lo, s_hi, adjoint: bool = False):
+        self.op = op
+        box = [np.ascontiguousarray(b, dtype=np.int64) for b in (t_lo, t_hi, s_lo, s_hi)]
+        self.t_shape = tuple(int(b - a + 1) for a, b in zip(box[0], box[1]))
+        self.s_shape = tuple(int(b - a + 1) for a, b in zip(box[2], box[3]))
+        self.adjoint = bool(adjoint)
+        h = _VP()
+        _check(lib().pc_block_plan_create(op.handle, *[_ptr(b) for b in box], ctypes.c_int32(int(adjoint)),
+                                          ctypes.byref(h)), op.ctx.handle)
+        self.handle = h
+
+    def info(self):
+        """(terms, tiles): distinct k and tiles the block touches."""
+        terms, tiles = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().pc_block_plan_info(self.handle, ctypes.byref(terms), ctypes.byref(tiles)))
+        return terms.value, tiles.value
+
+    def pc_block_apply(self, nrhs: int, x_ptr: int, ldx: int, y_ptr: int, ldy: int, stream_ptr: int):
+        _check(lib().pc_block_apply(self.handle, ctypes.c_int32(nrhs), _VP(x_ptr), ctypes.c_int64(ldx),
+                                    _VP(y_ptr), ctypes.c_int64(ldy), _VP(stream_ptr)), self.op.ctx.handle)
+
+    def apply(self, x, out=None, stream=None):
+        """x: contiguous CUDA tensor [B, *S] (or [*S]); returns [B, *T] (or [*T])."""
+        import torch
+        nS, nT = int(np.prod(self.s_shape)), int(np.prod(self.t_shape))
+        want = torch.float64 if self.op.precision == "fp64" else torch.float32
+        if not (x.is_cuda and x.is_contiguous()) or x.dtype != want:
+            raise ValueError("x must be a contiguous CUDA tensor of %s" % want)
+        B = x.numel() // nS
+        if B * nS != x.numel():
+            raise ValueError("x does not hold whole vectors on S")
+        shape = (B,) + self.t_shape if x.dim() > len(self.s_shape) else self.t_shape
+        y = torch.empty(shape, dtype=want, device=x.device) if out is None else out
+        self.pc_block_apply(B, x.data_ptr(), nS, y.data_ptr(), nT, _stream_ptr(stream))
+        return y
+
+    def check(self):
+        _check(lib().pc_block_plan_check(self.handle), self.op.ctx.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            h, self.handle = self.handle, None
+            _check(lib().pc_block_plan_destroy(h), self.op.ctx.handle)
 
     def __del__(self):
         try:

@@ -102,6 +102,84 @@ const char *free_operator(pc_operator *op) {
     return bad;
 }
 
+// Schedule of a block apply (Section 3.3), from the operator's schedule.
+// A tile convolves its input box (inside bbox(U_k)) with one sub-window of
+// phi_k^E; restricting x to a box C only clips that input box, and shifting
+// the input box by delta shifts the tile's output box by delta with the same
+// sub-window (the translation of Section 3.3), so the tile keeps its
+// spectrum.  Forward: C = S and the output box must meet T; adjoint (which
+// gathers x over the output box and adds into the input box): C = T and the
+// output box must meet S.  Kept tiles are re-expressed in block coordinates:
+// input boxes relative to C, output boxes relative to the other box.  A
+// subset of a proper colouring is proper, and a clipped tile overlaps only
+// tiles its original overlapped, so the colour order and the dependency
+// lists restricted to kept tiles still order every sum.
+struct BlockSchedule {
+    std::vector<pc::Tile> tiles;
+    std::vector<int32_t> color_start{0}, dep_start{0}, dep;
+    int terms = 0;
+};
+
+void build_block_schedule(const pc_operator *op, const int64_t *t_lo, const int64_t *t_hi, const int64_t *s_lo,
+                          const int64_t *s_hi, bool adjoint, BlockSchedule &b) {
+    const int64_t *clo = adjoint ? t_lo : s_lo, *chi = adjoint ? t_hi : s_hi;
+    const int64_t *olo = adjoint ? s_lo : t_lo, *ohi = adjoint ? s_hi : t_hi;
+    std::vector<int32_t> remap(op->tiles_h.size(), -1);
+    std::vector<char> used(size_t(op->r), 0);
+    for (int c = 0; c < op->n_colors; ++c) {
+        for (int ti = op->color_start_h[size_t(c)]; ti < op->color_start_h[size_t(c) + 1]; ++ti) {
+            const pc::Tile &t = op->tiles_h[size_t(ti)];
+            int64_t delta[2], ext[2];
+            bool keep = true;
+            for (int a = 0; a < 2 && keep; ++a) {
+                const int64_t lo = std::max<int64_t>(t.in_lo[a], clo[a]);
+                const int64_t hi = std::min<int64_t>(int64_t(t.in_lo[a]) + t.in_ext[a] - 1, chi[a]);
+                delta[a] = lo - t.in_lo[a];
+                ext[a] = hi - lo + 1;
+                const int64_t o_lo = t.out_lo[a] + delta[a];
+                const int64_t o_hi = o_lo + ext[a] + t.kext[a] - 2;
+                keep = ext[a] > 0 && o_hi >= olo[a] && o_lo <= ohi[a];
+            }
+            if (!keep) continue;
+            pc::Tile u = t;
+            for (int a = 0; a < 2; ++a) {
+                u.in_lo[a] = int32_t(t.in_lo[a] + delta[a] - clo[a]);
+                u.in_ext[a] = int32_t(ext[a]);
+                u.out_lo[a] = int32_t(t.out_lo[a] + delta[a] - olo[a]);
+            }
+            u.w_base = t.w_base + delta[0] * t.w_ld[0] + delta[1] * t.w_ld[1];
+            remap[size_t(ti)] = int32_t(b.tiles.size());
+            b.tiles.push_back(u);
+            for (int q = op->dep_start_h[size_t(ti)]; q < op->dep_start_h[size_t(ti) + 1]; ++q) {
+                const int32_t m = remap[size_t(op->dep_h[size_t(q)])];
+                if (m >= 0) b.dep.push_back(m);
+            }
+            b.dep_start.push_back(int32_t(b.dep.size()));
+            if (!used[size_t(t.patch)]) {
+                used[size_t(t.patch)] = 1;
+                ++b.terms;
+            }
+        }
+        if (int32_t(b.tiles.size()) > b.color_start.back()) b.color_start.push_back(int32_t(b.tiles.size()));
+    }
+}
+
+const char *free_block_plan(pc_block_plan *bp) {
+    if (!bp) return nullptr;
+    const char *bad = nullptr;
+    auto chk = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && !bad) bad = what;
+    };
+    chk(cudaFree(bp->d_tiles), "tiles");
+    chk(cudaFree(bp->d_color_start), "colours");
+    chk(cudaFree(bp->d_dep_start), "dependency starts");
+    chk(cudaFree(bp->d_dep), "dependencies");
+    chk(cudaFree(bp->d_done), "ordering flags");
+    chk(cudaFree(bp->d_ctrl), "control block");
+    delete bp;
+    return bad;
+}
+
 }  // namespace
 
 extern "C" {
@@ -309,6 +387,8 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     op->ctas = ctx->num_sms * ctas_per_sm;
     op->color_start_h = sch.color_start;
     op->tiles_h = sch.tiles;
+    op->dep_start_h = sch.dep_start;
+    op->dep_h = sch.dep;
     size_t acct = 0;
     auto bail = [&](cudaError_t ee, const char *what) {
         pc_status s2 = cuda_fail(ctx, ee, what);
@@ -664,6 +744,8 @@ static pc_status apply_batched(pc_operator *op, int32_t nrhs, const void *x, int
     p.n[0] = int32_t(op->shape[0]);
     p.n[1] = int32_t(op->shape[1]);
     p.n[2] = int32_t(op->shape[2]);
+    p.nx[0] = p.n[0];
+    p.nx[1] = p.n[1];
     p.R = op->R;
     p.tiles = op->d_tiles;
     p.color_start = op->d_color_start;
@@ -785,6 +867,168 @@ pc_status pc_apply_plain(pc_operator *op, int32_t nrhs, const void *x, int64_t l
     pc_status st = pc::plain_apply(op, nrhs, x, ldx, y, ldy, static_cast<cudaStream_t>(stream), err);
     if (st != PC_OK) return fail(ctx, st, err);
     op->last_stream = static_cast<cudaStream_t>(stream);
+    return PC_OK;
+}
+
+pc_status pc_block_plan_create(pc_operator *op, const int64_t *t_lo, const int64_t *t_hi, const int64_t *s_lo,
+                               const int64_t *s_hi, int32_t adjoint, pc_block_plan **plan) {
+    if (!plan) return fail(op ? op->ctx : nullptr, PC_ERR_ARG, "plan is null");
+    *plan = nullptr;
+    if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
+    pc_context *ctx = op->ctx;
+    if (!t_lo || !t_hi || !s_lo || !s_hi) return fail(ctx, PC_ERR_ARG, "null box bound");
+    if (adjoint != 0 && adjoint != 1) return fail(ctx, PC_ERR_ARG, "adjoint must be 0 or 1");
+    if (op->d != 2) return fail(ctx, PC_ERR_UNSUPPORTED, "block applies cover 2D operators");
+    for (int a = 0; a < 2; ++a) {
+        if (t_lo[a] < 0 || t_lo[a] > t_hi[a] || t_hi[a] >= op->shape[size_t(a)])
+            return fail(ctx, PC_ERR_ARG, "target box T must satisfy 0 <= lo <= hi < shape");
+        if (s_lo[a] < 0 || s_lo[a] > s_hi[a] || s_hi[a] >= op->shape[size_t(a)])
+            return fail(ctx, PC_ERR_ARG, "source box S must satisfy 0 <= lo <= hi < shape");
+    }
+    BlockSchedule b;
+    build_block_schedule(op, t_lo, t_hi, s_lo, s_hi, adjoint == 1, b);
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return fail(ctx, PC_ERR_CUDA, "cannot select the context's device");
+    auto *bp = new (std::nothrow) pc_block_plan;
+    if (!bp) return fail(ctx, PC_ERR_NOMEM, "out of host memory");
+    bp->op = op;
+    bp->adjoint = adjoint == 1;
+    for (int a = 0; a < 2; ++a) {
+        bp->t_ext[a] = t_hi[a] - t_lo[a] + 1;
+        bp->s_ext[a] = s_hi[a] - s_lo[a] + 1;
+    }
+    bp->nT = bp->t_ext[0] * bp->t_ext[1];
+    bp->nS = bp->s_ext[0] * bp->s_ext[1];
+    bp->n_tiles = int(b.tiles.size());
+    bp->n_colors = int(b.color_start.size()) - 1;
+    bp->terms = b.terms;
+    size_t acct = 0;
+    auto bail = [&](cudaError_t ee, const char *what) {
+        pc_status s2 = cuda_fail(ctx, ee, what);
+        free_block_plan(bp);
+        return s2;
+    };
+    cudaError_t e;
+    if (bp->n_tiles > 0) {
+        if ((e = upload(&bp->d_tiles, b.tiles.data(), b.tiles.size(), acct)) != cudaSuccess) return bail(e, "tiles");
+        if ((e = upload(&bp->d_color_start, b.color_start.data(), b.color_start.size(), acct)) != cudaSuccess)
+            return bail(e, "colours");
+        if ((e = upload(&bp->d_dep_start, b.dep_start.data(), b.dep_start.size(), acct)) != cudaSuccess)
+            return bail(e, "dependencies");
+        if (b.dep.empty()) b.dep.push_back(0);
+        if ((e = upload(&bp->d_dep, b.dep.data(), b.dep.size(), acct)) != cudaSuccess)
+            return bail(e, "dependencies");
+    }
+    if ((e = cudaMalloc(&bp->d_ctrl, 64)) != cudaSuccess) return bail(e, "control block");
+    if ((e = cudaMemset(bp->d_ctrl, 0, 64)) != cudaSuccess) return bail(e, "control block");
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "synchronising after the plan's uploads");
+    *plan = bp;
+    return PC_OK;
+}
+
+pc_status pc_block_apply(pc_block_plan *bp, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
+                         pc_stream stream) {
+    if (!bp) return fail(nullptr, PC_ERR_ARG, "plan is null");
+    pc_operator *op = bp->op;
+    pc_context *ctx = op->ctx;
+    if (nrhs < 0) return fail(ctx, PC_ERR_ARG, "nrhs < 0");
+    if (nrhs == 0) return PC_OK;
+    if (!x || !y) return fail(ctx, PC_ERR_ARG, "null x or y");
+    if (ldx < bp->nS || ldy < bp->nT) return fail(ctx, PC_ERR_ARG, "need ldx >= |S| and ldy >= |T|");
+    const uintptr_t xa = reinterpret_cast<uintptr_t>(x), ya = reinterpret_cast<uintptr_t>(y);
+    if (xa % op->elem || ya % op->elem) return fail(ctx, PC_ERR_ARG, "x and y must be aligned to the element size");
+    const uintptr_t xe = xa + uintptr_t((int64_t(nrhs - 1) * ldx + bp->nS) * int64_t(op->elem));
+    const uintptr_t ye = ya + uintptr_t((int64_t(nrhs - 1) * ldy + bp->nT) * int64_t(op->elem));
+    if (xa < ye && ya < xe) return fail(ctx, PC_ERR_ARG, "x and y overlap");
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return fail(ctx, PC_ERR_CUDA, "cannot select the context's device");
+    const int32_t npairs = (nrhs + 1) / 2;
+    cudaError_t e = cudaSuccess;
+    if (bp->n_tiles > 0 && npairs > bp->done_cap) {
+        if (bp->launched && (e = cudaDeviceSynchronize()) != cudaSuccess)
+            return cuda_fail(ctx, e, "synchronising before growing the plan's flags");
+        cudaFree(bp->d_done);
+        bp->d_done = nullptr;
+        bp->done_cap = 0;
+        const int32_t cap = std::max<int32_t>(npairs, 32);
+        const size_t bytes = sizeof(uint32_t) * size_t(bp->n_tiles) * size_t(cap);
+        if ((e = cudaMalloc(&bp->d_done, bytes)) != cudaSuccess) return cuda_fail(ctx, e, "allocating plan flags");
+        if ((e = cudaMemset(bp->d_done, 0, bytes)) != cudaSuccess) return cuda_fail(ctx, e, "clearing plan flags");
+        bp->done_cap = cap;
+        bp->epoch = 0;
+    }
+    if (++bp->epoch == 0) bp->epoch = 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    pc::ApplyParams p{};
+    p.x = x;
+    p.y = y;
+    p.ldx = ldx;
+    p.ldy = ldy;
+    p.nrhs = nrhs;
+    p.npairs = npairs;
+    p.n[0] = int32_t(bp->t_ext[0]);
+    p.n[1] = int32_t(bp->t_ext[1]);
+    p.n[2] = 1;
+    p.R = op->R;
+    p.nx[0] = int32_t(bp->s_ext[0]);
+    p.nx[1] = int32_t(bp->s_ext[1]);
+    p.tiles = bp->d_tiles;
+    p.color_start = bp->d_color_start;
+    p.n_colors = bp->n_colors;
+    p.dep_start = bp->d_dep_start;
+    p.dep = bp->d_dep;
+    p.done = bp->d_done;
+    p.done_ld = bp->done_cap;
+    p.epoch = bp->epoch;
+    p.ctrl = bp->d_ctrl;
+    p.spec = op->d_spec;
+    p.spec_stride = op->spec_stride;
+    p.w = op->d_w;
+    p.tw = op->d_tw;
+    p.total_items = int64_t(bp->n_tiles) * npairs;
+    if ((e = pc::launch_zero(p, bp->nT, op->prec, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "launching the zero kernel");
+    if (p.total_items > 0) {
+        const int ctas = int(std::min<int64_t>(op->ctas, p.total_items));
+        if ((e = pc::launch_fft2d(p, op->P, op->prec, ctas, s, bp->adjoint)) != cudaSuccess)
+            return cuda_fail(ctx, e, "launching the patch kernel");
+    }
+    bp->last_stream = s;
+    bp->launched = true;
+    return PC_OK;
+}
+
+pc_status pc_block_plan_info(const pc_block_plan *bp, int32_t *terms, int32_t *tiles) {
+    if (!bp) return fail(nullptr, PC_ERR_ARG, "plan is null");
+    if (terms) *terms = bp->terms;
+    if (tiles) *tiles = bp->n_tiles;
+    return PC_OK;
+}
+
+pc_status pc_block_plan_check(pc_block_plan *bp) {
+    if (!bp) return fail(nullptr, PC_ERR_ARG, "plan is null");
+    pc_context *ctx = bp->op->ctx;
+    DeviceGuard dg(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(bp->last_stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "asynchronous CUDA error");
+    int32_t ctrl[4] = {0, 0, 0, 0};
+    if ((e = cudaMemcpy(ctrl, bp->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(ctx, e, "reading the status word");
+    if (ctrl[2]) {
+        cudaMemset(bp->d_ctrl + 2, 0, sizeof(int32_t));
+        return fail(ctx, PC_ERR_TIMEOUT, "a bounded wait in the patch kernel timed out");
+    }
+    return PC_OK;
+}
+
+pc_status pc_block_plan_destroy(pc_block_plan *bp) {
+    if (!bp) return PC_OK;
+    pc_context *ctx = bp->op->ctx;
+    DeviceGuard dg(ctx->device);
+    const cudaError_t se = cudaDeviceSynchronize();
+    const char *bad = free_block_plan(bp);
+    if (se != cudaSuccess) return cuda_fail(ctx, se, "synchronising before freeing the plan");
+    if (bad) return fail(ctx, PC_ERR_CUDA, std::string("freeing the plan: ") + bad);
     return PC_OK;
 }
 

@@ -83,31 +83,44 @@ __device__ __forceinline__ void prefetch_l2(const void *ptr) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
 }
 
-// Pull the rows that `item` will gather (weights and both right-hand sides)
-// into L2, one 128-byte line per thread-iteration.
-template <typename T>
+// Pull the rows that `item` will gather into L2, one 128-byte line per
+// thread-iteration: the weights and both right-hand sides over the input box
+// (forward), or the right-hand sides over the output box clipped to the box x
+// lives on (adjoint).
+template <typename T, bool ADJ>
 __device__ __forceinline__ void prefetch_item(const ApplyParams &p, const int *cs, int64_t item) {
     if (item >= p.total_items) return;
     int ti, pair;
     decode_item(p, cs, item, ti, pair);
     const Tile tile = p.tiles[ti];
-    const int n1 = tile.in_ext[0], n2 = tile.in_ext[1];
     constexpr int per_line = 128 / int(sizeof(T));
-    const int lines_per_row = (n2 + per_line - 1) / per_line + 1;   // +1: rows need not start on a line
     const int b0 = 2 * pair;
-    const int narr = b0 + 1 < p.nrhs ? 3 : 2;
-    const int total = narr * n1 * lines_per_row;
+    const int nx_arr = b0 + 1 < p.nrhs ? 2 : 1;
+    int r0, nr, c0, nc, narr;
+    if constexpr (!ADJ) {
+        r0 = tile.in_lo[0], nr = tile.in_ext[0], c0 = tile.in_lo[1], nc = tile.in_ext[1];
+        narr = nx_arr + 1;   // weights first
+    } else {
+        r0 = max(tile.out_lo[0], 0);
+        nr = min(tile.out_lo[0] + tile.in_ext[0] + tile.kext[0] - 1, p.nx[0]) - r0;
+        c0 = max(tile.out_lo[1], 0);
+        nc = min(tile.out_lo[1] + tile.in_ext[1] + tile.kext[1] - 1, p.nx[1]) - c0;
+        narr = nx_arr;
+        if (nr <= 0 || nc <= 0) return;
+    }
+    const int lines_per_row = (nc + per_line - 1) / per_line + 1;   // +1: rows need not start on a line
+    const int total = narr * nr * lines_per_row;
     for (int q = threadIdx.x; q < total; q += blockDim.x) {
-        const int arr = q / (n1 * lines_per_row);
-        const int rem = q - arr * n1 * lines_per_row;
+        const int arr = q / (nr * lines_per_row);
+        const int rem = q - arr * nr * lines_per_row;
         const int i = rem / lines_per_row, l = rem % lines_per_row;
-        const int col = min(l * per_line, n2 - 1);
+        const int col = min(l * per_line, nc - 1);
         const T *base;
-        if (arr == 0)
+        if (!ADJ && arr == 0)
             base = static_cast<const T *>(p.w) + tile.w_base + int64_t(i) * tile.w_ld[0];
         else
-            base = static_cast<const T *>(p.x) + int64_t(b0 + arr - 1) * p.ldx +
-                   int64_t(tile.in_lo[0] + i) * p.n[1] + tile.in_lo[1];
+            base = static_cast<const T *>(p.x) + int64_t(b0 + arr - (ADJ ? 0 : 1)) * p.ldx +
+                   int64_t(r0 + i) * p.nx[1] + c0;
         prefetch_l2(base + col);
     }
 }
@@ -271,7 +284,7 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
             const int shmul = 3 * n2 + 24 <= 2 * P ? 8 : 0;
             for (int i = line; i < n1; i += LINES) {
                 T *row = Sf + i * 2 * P + (i & 3) * shmul;
-                const int64_t xr = int64_t(i0 + i) * p.n[1] + j0;
+                const int64_t xr = int64_t(i0 + i) * p.nx[1] + j0;
                 const T *wr = wt + int64_t(i) * tile.w_ld[0];
 #pragma unroll
                 for (int j = 0; j < R1; ++j) {
@@ -305,17 +318,17 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
             }
         } else {
             // adjoint: x over the output box (L1 x L2 at (o0, o1)), zero outside
-            // Omega, staged as [x0 | x1] per row
+            // the box x lives on, staged as [x0 | x1] per row
             for (int i = line; i < L1; i += LINES) {
                 const int gr = o0 + i;
-                if (gr < 0 || gr >= p.n[0]) continue;
+                if (gr < 0 || gr >= p.nx[0]) continue;
                 T *row = Sf + i * 2 * P;
-                const int64_t xr = int64_t(gr) * p.n[1] + o1;
+                const int64_t xr = int64_t(gr) * p.nx[1] + o1;
 #pragma unroll
                 for (int j = 0; j < R1; ++j) {
                     const int col = t + R2 * j;
                     const int gc = o1 + col;
-                    if (col < L2 && gc >= 0 && gc < p.n[1]) {
+                    if (col < L2 && gc >= 0 && gc < p.nx[1]) {
                         cp_async<sizeof(T)>(row + col, x0 + xr + col);
                         if (has1) cp_async<sizeof(T)>(row + L2 + col, x1 + xr + col);
                     }
@@ -325,14 +338,14 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
             __syncwarp(lmask);
             for (int i = line; i < L1; i += LINES) {
                 const int gr = o0 + i;
-                const bool rin = gr >= 0 && gr < p.n[0];
+                const bool rin = gr >= 0 && gr < p.nx[0];
                 const T *row = Sf + i * 2 * P;
                 C a[R1];
 #pragma unroll
                 for (int j = 0; j < R1; ++j) {
                     const int col = t + R2 * j;
                     const int gc = o1 + col;
-                    a[j] = rin && col < L2 && gc >= 0 && gc < p.n[1] ? C{row[col], has1 ? row[L2 + col] : T(0)}
+                    a[j] = rin && col < L2 && gc >= 0 && gc < p.nx[1] ? C{row[col], has1 ? row[L2 + col] : T(0)}
                                                                     : zero;
                 }
                 RowScratch<P, C> scr{S, i};
@@ -351,7 +364,7 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
         __syncthreads();
         if (threadIdx.x == 0) publish_pending();
 
-        if (s_next - s_seg.item_begin < p.total_items) prefetch_item<T>(p, s_cstart, s_next - s_seg.item_begin);
+        if (s_next - s_seg.item_begin < p.total_items) prefetch_item<T, ADJ>(p, s_cstart, s_next - s_seg.item_begin);
 
         // ---------------- phase B: column FFT, spectral product, inverse column FFT
         if (!mbar_wait_bounded(mbar, phase, kMbarLimit)) {

@@ -97,8 +97,10 @@ struct ApplyParams {
     void *y;
     int64_t ldx, ldy;
     int32_t nrhs, npairs;
-    int32_t n[3];               // box extents (2D: n[2] = 1)
+    int32_t n[3];               // extents of the box y lives on (2D: n[2] = 1)
     int32_t R;
+    int32_t nx[2];              // 2D: extents of the box x lives on (n[0], n[1] for a whole-box apply;
+                                // the source box S of a block apply)
     const Tile *tiles;
     const int32_t *color_start;
     int32_t n_colors;
@@ -217,11 +219,33 @@ struct pc_operator {
     int64_t launches_last = 0;
     size_t device_bytes = 0;
     double build_seconds = 0;
-    // host copies used by the plain path
+    // host copies of the schedule (plain path, block plans)
     std::vector<int32_t> color_start_h;
     std::vector<pc::Tile> tiles_h;
+    std::vector<int32_t> dep_start_h, dep_h;
     // plain-path scratch (lazily allocated)
     void *plain = nullptr;
+};
+
+// Block apply (Section 3.3): the operator's tiles that contribute to
+// A~[T, S] (or (A~*)[T, S]), clipped and re-expressed in block coordinates,
+// with their own ordering flags and control block.
+struct pc_block_plan {
+    pc_operator *op = nullptr;
+    bool adjoint = false;
+    int64_t t_ext[2] = {0, 0}, s_ext[2] = {0, 0};
+    int64_t nT = 0, nS = 0;
+    int n_tiles = 0, n_colors = 0, terms = 0;
+    pc::Tile *d_tiles = nullptr;
+    int32_t *d_color_start = nullptr;
+    int32_t *d_dep_start = nullptr;
+    int32_t *d_dep = nullptr;
+    uint32_t *d_done = nullptr;
+    int32_t done_cap = 0;
+    int32_t *d_ctrl = nullptr;
+    uint32_t epoch = 0;
+    cudaStream_t last_stream = nullptr;
+    bool launched = false;
 };
 
 namespace pc {

@@ -1,0 +1,162 @@
+"""Block apply (Section 3.3) through the C ABI against the FP64 oracle.
+
+Relative l2 per right-hand side: 1e-10 (FP64 operators), 1e-5 (FP32), as for
+the whole-box apply.  With S = T = Omega a plan keeps every tile unchanged,
+so its result must be bitwise the whole-box apply's."""
+import numpy as np
+import pytest
+
+import workloads
+from workloads import configs
+from oracle import block as ob
+
+from gpu_common import context, make_pair, rel_l2
+from test_oracle_geometry import ADAPTIVE_CELLS, ADAPTIVE_SHAPE
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    context()
+
+
+def _kernel(shape, R):
+    L = float(max(shape))
+    return workloads.Skewed([0.6, -0.3], lambda x: 1.0 + 0.4 * np.sin(2 * np.pi * x[..., 0] / L), R)
+
+
+def _dev(a, prec):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda",
+                                                        dtype=torch.float64 if prec == "fp64" else torch.float32)
+
+
+def _run_block(op, t_lo, t_hi, s_lo, s_hi, x, adjoint):
+    from paper_1805_06018_gb300 import BlockPlan
+    plan = BlockPlan(op, t_lo, t_hi, s_lo, s_hi, adjoint)
+    y = plan.apply(_dev(x, op.precision))
+    torch.cuda.synchronize()
+    plan.check()
+    return plan, y.cpu().numpy().astype(np.float64)
+
+
+def _check(got, ref, prec):
+    ref = ref.reshape(len(ref), -1)
+    got = got.reshape(len(ref), -1)
+    nz = np.linalg.norm(ref, axis=1) > 0
+    if np.any(nz):
+        assert np.max(rel_l2(got[nz], ref[nz])) <= TOL[prec]
+    assert np.all(np.abs(got[~nz]) <= TOL[prec] * (np.abs(got).max() + 1e-300))
+
+
+BOXES = [   # (t_lo, t_hi, s_lo, s_hi) on a 40 x 36 box
+    ((0, 0), (39, 35), (0, 0), (39, 35)),          # the whole box
+    ((5, 7), (20, 30), (10, 2), (33, 14)),         # overlapping, ragged
+    ((0, 0), (9, 9), (12, 0), (20, 6)),            # beside, within reach
+    ((30, 30), (39, 35), (0, 0), (5, 5)),          # beyond the kernel's reach: zero
+    ((17, 17), (17, 17), (17, 17), (17, 17)),      # one pixel
+    ((0, 3), (39, 3), (2, 0), (2, 35)),            # one column x one row
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_blocks_regular_grid(prec, adjoint):
+    shape = (40, 36)
+    cells = workloads.regular_grid(shape, (4, 3))
+    op, orc = make_pair(shape, cells, _kernel(shape, 5), prec)
+    rng = np.random.default_rng(60)
+    for t_lo, t_hi, s_lo, s_hi in BOXES:
+        sS = tuple(b - a + 1 for a, b in zip(s_lo, s_hi))
+        x = rng.standard_normal((3,) + sS).astype(np.float32).astype(np.float64)
+        plan, got = _run_block(op, t_lo, t_hi, s_lo, s_hi, x, adjoint)
+        ref = ob.apply_block_translated(orc, t_lo, t_hi, s_lo, s_hi, x, adjoint)
+        _check(got, ref, prec)
+        terms, tiles = plan.info()
+        assert terms <= len(ob.block_terms(orc, t_lo, t_hi, s_lo, s_hi, adjoint))
+        if t_lo == s_lo and t_hi == s_hi:
+            assert terms == len(ob.block_terms(orc, t_lo, t_hi, s_lo, s_hi, adjoint))
+        if not np.any(ref):
+            assert tiles == 0
+        plan.close()
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_blocks_adaptive_grid_fp64(adjoint):
+    shape, cells = ADAPTIVE_SHAPE, np.array(ADAPTIVE_CELLS)
+    op, orc = make_pair(shape, cells, _kernel(shape, 4), "fp64")
+    rng = np.random.default_rng(61)
+    for _ in range(6):
+        lo = [sorted(rng.integers(0, m, 2)) for m in shape]
+        lo2 = [sorted(rng.integers(0, m, 2)) for m in shape]
+        t_lo, t_hi = [a for a, _ in lo], [b for _, b in lo]
+        s_lo, s_hi = [a for a, _ in lo2], [b for _, b in lo2]
+        sS = tuple(int(b - a + 1) for a, b in zip(s_lo, s_hi))
+        x = rng.standard_normal((2,) + sS)
+        _, got = _run_block(op, t_lo, t_hi, s_lo, s_hi, x, adjoint)
+        _check(got, ob.apply_block(orc, t_lo, t_hi, s_lo, s_hi, x, adjoint), "fp64")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_whole_box_block_is_bitwise_the_apply(prec, adjoint):
+    from paper_1805_06018_gb300 import BlockPlan
+    shape = (40, 36)
+    op, _ = make_pair(shape, workloads.regular_grid(shape, (4, 3)), _kernel(shape, 5), prec)
+    x = _dev(workloads.rhs(62, 5, shape), prec)
+    plan = BlockPlan(op, (0, 0), (39, 35), (0, 0), (39, 35), adjoint)
+    yb = plan.apply(x)
+    ya = op.apply_adjoint(x) if adjoint else op.apply(x)
+    torch.cuda.synchronize()
+    assert torch.equal(yb, ya)
+    assert torch.equal(plan.apply(x), yb)      # and reproducible
+    plan.close()
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_blocks_of_the_512_operator(adjoint):
+    """The 512^2 benchmark operator (R = 24, FFT size 128): a near-field block
+    (adjacent 64 x 64 boxes), an overlapping block and a far-field block, 5
+    right-hand sides (odd: one pair is half used)."""
+    wl = configs.fp32_512()
+    op, orc = make_pair(wl.shape, wl.cells, wl.kernel, "fp32")
+    cases = [((128, 128), (191, 191), (192, 128), (255, 191)),
+             ((300, 40), (363, 103), (320, 60), (383, 123)),
+             ((0, 0), (63, 63), (400, 400), (463, 463))]
+    for t_lo, t_hi, s_lo, s_hi in cases:
+        x = workloads.rhs(63, 5, (64, 64)).astype(np.float64)
+        _, got = _run_block(op, t_lo, t_hi, s_lo, s_hi, x, adjoint)
+        _check(got, ob.apply_block_translated(orc, t_lo, t_hi, s_lo, s_hi, x, adjoint), "fp32")
+
+
+def test_bad_arguments():
+    import paper_1805_06018_gb300 as pcg
+    from paper_1805_06018_gb300 import BlockPlan
+    from paper_1805_06018_gb300.binding import PC_ERR_ARG, PC_ERR_UNSUPPORTED
+    shape = (40, 36)
+    op, _ = make_pair(shape, workloads.regular_grid(shape, (4, 3)), _kernel(shape, 5), "fp32")
+    for box in [((0, 0), (40, 35), (0, 0), (3, 3)), ((5, 5), (4, 9), (0, 0), (3, 3)),
+                ((0, 0), (3, 3), (-1, 0), (3, 3))]:
+        with pytest.raises(pcg.PCError) as ei:
+            BlockPlan(op, *box)
+        assert ei.value.status == PC_ERR_ARG
+    plan = BlockPlan(op, (0, 0), (9, 9), (0, 0), (9, 9))
+    x = torch.zeros(100, device="cuda")
+    y = torch.zeros(100, device="cuda")
+    with pytest.raises(pcg.PCError) as ei:
+        plan.pc_block_apply(1, x.data_ptr(), 99, y.data_ptr(), 100, 0)
+    assert ei.value.status == PC_ERR_ARG
+    plan.pc_block_apply(0, x.data_ptr(), 100, y.data_ptr(), 100, 0)   # no-op
+    plan.close()
+    shape3 = (12, 10, 8)
+    kern3 = workloads.GaussianAxis3D(lambda x: 1.2 + 0 * x[..., 0], lambda x: 1.0 + 0 * x[..., 0],
+                                     lambda x: 1.0 + 0 * x[..., 0], 3)
+    op3, _ = make_pair(shape3, workloads.regular_grid(shape3, (2, 2, 2)), kern3, "fp32")
+    with pytest.raises(pcg.PCError) as ei:
+        BlockPlan(op3, (0, 0, 0), (3, 3, 3), (0, 0, 0), (3, 3, 3))
+    assert ei.value.status == PC_ERR_UNSUPPORTED
