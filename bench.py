@@ -57,15 +57,45 @@ WORKLOADS = {
                            "A~* of 64 probes, then per-cell FP64 norms of A~*Z - A*Z over the 225 leaf cells",
                            "fft2d_kernel<float,128,true>", ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh",
                                                             "pc_overlap.cuh"]),
+    "fp32_512_block": ("block apply A~[T,S] (Section 3.3) of the 512x512 regular 16x16 grid operator: "
+                       "T = [128,255]^2, S = [256,383]x[128,255] (adjacent 128^2 boxes, an H-matrix near-field "
+                       "block), 64 RHS", "fft2d_kernel<float,128>",
+                       ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_overlap.cuh"]),
     "adaptive_1024": ("1024x1024 adaptive quadtree (r=1579), heavy-tailed R=64 (2x2 kernel sub-windows), "
                       "128^2 patch FFTs, 32 RHS", "fft2d_kernel<float,128>",
                       ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_overlap.cuh"]),
 }
 # workload name -> (operator configuration, precision)
 WORKLOAD_OPERATOR = {"fp32_512": ("fp32_512", "fp32"), "fp32_512_adjoint": ("fp32_512", "fp32"),
-                     "fp32_512_estimator": ("fp32_512", "fp32"),
+                     "fp32_512_estimator": ("fp32_512", "fp32"), "fp32_512_block": ("fp32_512", "fp32"),
                      "fp32_128c": ("fp32_128c", "fp32"), "bf16x3_128c": ("fp32_128c", "bf16x3"),
                      "adaptive_1024": ("adaptive_1024", "fp32")}
+
+
+# closed boxes (lo, hi) of the block workload: targets T, sources S
+BLOCK_T = ((128, 128), (255, 255))
+BLOCK_S = ((256, 128), (383, 255))
+
+
+def block_algorithmic_flops(lo, hi, R, nrhs):
+    """Nominal FLOPs of a block apply: over the terms k whose bbox(U_k) meets
+    S and whose reach bbox(U_k) (+) [-R, R]^2 meets T, 5 L log2 L + 3 L with
+    L = prod_a (|S cap bbox(U_k)|_a + 2R), the linear-convolution extent of
+    the translated term (Section 3.3)."""
+    (slo, shi), (tlo, thi) = BLOCK_S, BLOCK_T
+    flops = 0.0
+    terms = 0
+    for a, b in zip(lo, hi):
+        ca = [max(int(a[i]), slo[i]) for i in range(2)]
+        cb = [min(int(b[i]), shi[i]) for i in range(2)]
+        if any(cb[i] < ca[i] for i in range(2)):
+            continue
+        if any(cb[i] + R < tlo[i] or ca[i] - R > thi[i] for i in range(2)):
+            continue
+        L = float(np.prod([cb[i] - ca[i] + 1 + 2 * R for i in range(2)]))
+        flops += 5.0 * L * math.log2(L) + 3.0 * L
+        terms += 1
+    return flops * nrhs, terms
 
 
 def kernel_sources_hash(names):
@@ -180,6 +210,35 @@ def cpu_oracle_rate(wl, x, seconds, seed=0, adjoint=False):
     return wl.nrhs * (done / wl.n) / el, done, os.cpu_count(), el
 
 
+def run_reference_block(args, wl):
+    """Reference arm of the block workload: the oracle's translated block
+    apply, one right-hand side per step (a bounded sample of the 64)."""
+    import workloads
+    from oracle import PCOracle
+    from oracle.block import apply_block_translated
+    (tlo, thi), (slo, shi) = BLOCK_T, BLOCK_S
+    sS = tuple(b - a + 1 for a, b in zip(slo, shi))
+    x = workloads.rhs(wl.rhs_seed, wl.nrhs, sS)
+    orc = PCOracle.from_workload(wl)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        apply_block_translated(orc, tlo, thi, slo, shi, x[i % wl.nrhs:i % wl.nrhs + 1])
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][0],
+                                            "global_batch": wl.nrhs, "parallelism": "cpu"},
+            "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": 1, "kind": "oracle",
+                             "sample": "1 of the %d RHS per step through the translated block apply" % wl.nrhs},
+            "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -188,6 +247,8 @@ def run_reference(args, rank, world):
     from oracle import build as obuild
     obuild.build()
     wl = configs.get(WORKLOAD_OPERATOR[args.workload][0])
+    if args.workload.endswith("_block"):
+        return run_reference_block(args, wl)
     x = workloads.rhs(wl.rhs_seed, wl.nrhs, wl.shape)
     from oracle import PCOracle
     orc = PCOracle.from_workload(wl)
@@ -214,6 +275,140 @@ def run_reference(args, rank, world):
                              "sample": sample},
             "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def block_oracle_rate(wl, xS, seconds):
+    """The oracle's translated block apply (Section 3.3) on whole right-hand
+    sides until `seconds` have passed; returns (RHS/s, RHS done, elapsed)."""
+    from oracle import PCOracle
+    from oracle.block import apply_block_translated
+    orc = PCOracle.from_workload(wl)
+    (tlo, thi), (slo, shi) = BLOCK_T, BLOCK_S
+    done = 0
+    t0 = time.perf_counter()
+    while done < len(xS) and (done == 0 or time.perf_counter() - t0 < seconds):
+        apply_block_translated(orc, tlo, thi, slo, shi, xS[done:done + 1])
+        done += 1
+    el = time.perf_counter() - t0
+    return done / el, done, el
+
+
+def run_block(args, rank, world):
+    """One step = pc_block_apply of the workload's 64 right-hand sides on
+    S, giving them on T; the plan is made once, before the timed region."""
+    import torch
+    import workloads
+    from workloads import configs
+    import paper_1805_06018_gb300 as pcg
+    from paper_1805_06018_gb300 import build as libbuild
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(rank % max(1, torch.cuda.device_count()))
+    libbuild.build()
+    wl = configs.get("fp32_512", **({"nrhs": args.nrhs} if args.nrhs > 0 else {}))
+    desc, kname, _ = WORKLOADS[args.workload]
+    pts = pcg.pc_sample_points(wl.shape, wl.cells)
+    phi = workloads.impulse_windows(wl.shape, pts, wl.kernel)
+    ctx = pcg.Context(torch.cuda.current_device())
+    op = pcg.Operator(ctx, wl.shape, wl.cells, wl.radius, phi, precision="fp32")
+    (tlo, thi), (slo, shi) = BLOCK_T, BLOCK_S
+    plan = pcg.BlockPlan(op, tlo, thi, slo, shi)
+    terms, tiles = plan.info()
+    sS = tuple(b - a + 1 for a, b in zip(slo, shi))
+    sT = tuple(b - a + 1 for a, b in zip(tlo, thi))
+    nS, nT = int(np.prod(sS)), int(np.prod(sT))
+    x_host = workloads.rhs(wl.rhs_seed, wl.nrhs, sS)
+    x = torch.from_numpy(x_host).cuda()
+    y = torch.empty((wl.nrhs,) + sT, dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def step():
+        plan.pc_block_apply(wl.nrhs, x.data_ptr(), nS, y.data_ptr(), nT, sp)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.check()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev0[i].record(stream)
+            step()
+            ev1[i].record(stream)
+        torch.cuda.synchronize()
+    plan.check()
+    step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
+    tot_ms = float(step_ms.sum())
+    if world > 1:
+        dist.barrier()
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * args.steps * wl.nrhs / (tot_ms / 1e3)
+
+    xh = torch.from_numpy(x_host).pin_memory()
+    yh = torch.empty(y.shape, dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 50))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        x.copy_(xh, non_blocking=True)
+        step()
+        yh.copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * e2e_steps * wl.nrhs / e2e_s
+
+    lo, hi = pcg.pc_neighbourhood_boxes(wl.shape, wl.cells)
+    flops, nominal_terms = block_algorithmic_flops(lo, hi, wl.radius, wl.nrhs)
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    step_mean = float(step_ms.mean())
+    achieved = flops / (step_mean / 1e3) / 1e12
+    line = {"metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "global_batch": wl.nrhs * world, "per_gpu_batch": wl.nrhs,
+                       "grid": list(wl.shape), "radius": wl.radius, "T": [list(tlo), list(thi)],
+                       "S": [list(slo), list(shi)], "terms": terms, "tiles": tiles,
+                       "parallelism": "replicas%d" % world, "l2": "flushed between steps (256 MB write)"},
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                           "per": "block apply of %d RHS" % wl.nrhs},
+            "e2e": {"value": e2e_value, "unit": "RHS/s", "h2d_bytes_per_step": int(x_host.nbytes),
+                    "d2h_bytes_per_step": int(yh.numel() * 4)},
+            "gpu_launches": 2 * args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak, "traffic": None, "kernel": kname,
+                         "kernel_ms": step_mean, "timed": "zero fill + patch kernel (events around the call)",
+                         "algorithmic_flop_per_launch": flops, "nominal_terms": nominal_terms,
+                         "peak_basis": "FP32 FMA pipe: SMs x 128 lanes x 2 x %.0f MHz" % sm_max},
+            "clocks": clk.summary()}
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        rate, done, el = block_oracle_rate(wl, x_host, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "RHS/s", "cores": 1, "kind": "oracle",
+                                "sample": "%d of the %d RHS through the translated block apply in %.1f s"
+                                          % (done, wl.nrhs, el)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    op.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def serve_operators(pcg, ctx, with_3d=True):
@@ -352,6 +547,8 @@ def main():
         return run_reference(args, rank, world)
     if args.serve:
         return run_serve(args)
+    if args.workload.endswith("_block"):
+        return run_block(args, rank, world)
 
     import torch
     import torch.distributed as dist
@@ -420,6 +617,7 @@ def main():
     if world > 1:
         dist.barrier()
     op.check()
+    launches_per_step = int(op.launches())
     step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
     tot_ms = float(step_ms.sum())
     if world > 1:
@@ -435,12 +633,18 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    is_adj = args.workload.endswith("_adjoint")
+    if not estimator:
+        # pc_apply_host: pinned host buffers in and out, copies pipelined with the kernels
+        op.pc_apply_host(wl.nrhs, xh.data_ptr(), N, yh.data_ptr(), N, is_adj, 0, sp)
+        torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        x.copy_(xh, non_blocking=True)
-        step()   # the estimator returns its per-cell result on the host itself
-        if not estimator:
-            yh.copy_(y, non_blocking=True)
+        if estimator:
+            x.copy_(xh, non_blocking=True)
+            step()   # the estimator returns its per-cell result on the host itself
+        else:
+            op.pc_apply_host(wl.nrhs, xh.data_ptr(), N, yh.data_ptr(), N, is_adj, 0, sp)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     if world > 1:
@@ -538,8 +742,10 @@ def main():
                            "per": "apply of %d RHS" % wl.nrhs},
             "plain_gpu": plain,
             "e2e": {"value": e2e_value, "unit": "RHS/s", "h2d_bytes_per_step": int(x_host.nbytes),
-                    "d2h_bytes_per_step": 8 * len(wl.cells) if estimator else int(x_host.nbytes)},
-            "gpu_launches": int(op.launches()) * args.steps,
+                    "d2h_bytes_per_step": 8 * len(wl.cells) if estimator else int(x_host.nbytes),
+                    "call": "pc_estimate_cell_errors after a host-to-device copy of Z" if estimator else
+                    "pc_apply_host (pinned host x, y; chunked copies overlapped with the kernels)"},
+            "gpu_launches": launches_per_step * args.steps,
             "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": kname, "kernel_ms": kern_ms,

@@ -235,6 +235,28 @@ pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t
 pc_status pc_apply_adjoint_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx,
                                    void *y, int64_t ldy, pc_stream stream);
 
+/* Y[b] = A~ X[b] (adjoint = 0) or A~* X[b] (adjoint = 1) for b < nrhs with
+ * x and y in HOST memory (X[b] at x + b*ldx, Y[b] at y + b*ldy elements,
+ * ldx, ldy >= N, disjoint).  The batch runs in chunks of `chunk`
+ * right-hand sides (0: about a quarter of the batch for 2D operators, the
+ * whole batch for 3D ones, whose kernels gain little from smaller batches;
+ * rounded up to an even
+ * count so that the right-hand-side pairs, and so every rounding, are those
+ * of one device apply of the whole batch: the result is bitwise that of
+ * pc_apply_batched / pc_apply_adjoint_batched).  Chunk i is copied in on an
+ * internal copy stream, applied on `stream`, and copied out on a second
+ * copy stream, through two device staging slots that the operator allocates
+ * on first use (4 * chunk * N elements) and keeps; so the copies of one
+ * chunk overlap the kernels of its neighbours.  Stream-ordered: the copies
+ * start after the work already queued on `stream`, and work queued on
+ * `stream` after the call starts once y is complete; the call itself
+ * returns once everything is queued.  x and y must stay valid until then,
+ * and should be page-locked (cudaHostAlloc or cudaHostRegister) for the
+ * copies to run asynchronously.  Calls on one operator must be serialised
+ * (one stream).  The adjoint covers 2D operators. */
+pc_status pc_apply_host(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
+                        int32_t adjoint, int32_t chunk, pc_stream stream);
+
 /* Matrix entries in O(1) each (Section 3.1, Eq. conv_matrix_entries):
  *   out[i] = A~[rows[i], cols[i]] = sum_{k : x in U_k} w_k[x] phi_k^E[y - x],
  * y = rows[i], x = cols[i] flat C-order indices into Omega.  Only the sample

@@ -101,6 +101,8 @@ _PROTOS = {
     "pc_estimate_cell_errors": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64,
                                                 ctypes.POINTER(ctypes.c_double), _VP]),
     "pc_entries": (ctypes.c_int, [_VP, ctypes.c_int64, _VP, _VP, _VP, _VP]),
+    "pc_apply_host": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, ctypes.c_int32,
+                                     ctypes.c_int32, _VP]),
     "pc_block_plan_create": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(_VP)]),
     "pc_block_apply": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
     "pc_block_plan_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
@@ -324,6 +326,29 @@ class Operator:
         """y = A~* x (Eq. adjoint_random_z) for x of shape [B, *box] (or [*box])."""
         B, y = self._args(x, out)
         self.pc_apply_adjoint_batched(B, x.data_ptr(), self.N, y.data_ptr(), self.N, _stream_ptr(stream))
+        return y
+
+    def pc_apply_host(self, nrhs: int, x_ptr: int, ldx: int, y_ptr: int, ldy: int, adjoint: bool, chunk: int,
+                      stream_ptr: int):
+        _check(lib().pc_apply_host(self.handle, ctypes.c_int32(nrhs), _VP(x_ptr), ctypes.c_int64(ldx), _VP(y_ptr),
+                                   ctypes.c_int64(ldy), ctypes.c_int32(int(adjoint)), ctypes.c_int32(chunk),
+                                   _VP(stream_ptr)), self.ctx.handle)
+
+    def apply_host(self, x, out=None, adjoint: bool = False, chunk: int = 0, stream=None):
+        """A~ x (or A~* x) for a CPU tensor x [B, *box] (pinned for overlap);
+        returns a CPU tensor.  Waits for the result unless `out` is given
+        (then the caller synchronises `stream`)."""
+        import torch
+        want = torch.float64 if self.precision == "fp64" else torch.float32
+        if x.is_cuda or not x.is_contiguous() or x.dtype != want:
+            raise ValueError("x must be a contiguous CPU tensor of %s" % want)
+        B = x.numel() // self.N
+        if B * self.N != x.numel():
+            raise ValueError("x does not hold whole vectors of the operator's box")
+        y = torch.empty(x.shape, dtype=want, pin_memory=x.is_pinned()) if out is None else out
+        self.pc_apply_host(B, x.data_ptr(), self.N, y.data_ptr(), self.N, adjoint, chunk, _stream_ptr(stream))
+        if out is None:
+            (torch.cuda.current_stream() if stream is None else stream).synchronize()
         return y
 
     def entries(self, rows, cols, stream=None):

@@ -95,6 +95,11 @@ const char *free_operator(pc_operator *op) {
     chk(cudaFree(op->d_cell_sums), "cell sums");
     chk(cudaFree(op->d_est), "estimator scratch");
     chk(cudaFree(op->d_entry_mem), "entry tables");
+    chk(cudaFree(op->d_host_stage), "host-apply staging");
+    for (cudaEvent_t ev : op->host_ev)
+        if (ev) chk(cudaEventDestroy(ev), "host-apply events");
+    if (op->s_h2d) chk(cudaStreamDestroy(op->s_h2d), "copy streams");
+    if (op->s_d2h) chk(cudaStreamDestroy(op->s_d2h), "copy streams");
     for (cudaEvent_t ev : op->stage_ev) chk(cudaEventDestroy(ev), "stage events");
     if (op->ev_begin) chk(cudaEventDestroy(op->ev_begin), "events");
     if (op->ev_end) chk(cudaEventDestroy(op->ev_end), "events");
@@ -789,6 +794,103 @@ pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t
 pc_status pc_apply_adjoint_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
                                    pc_stream stream) {
     return apply_batched(op, nrhs, x, ldx, y, ldy, stream, true);
+}
+
+pc_status pc_apply_host(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
+                        int32_t adjoint, int32_t chunk, pc_stream stream) {
+    if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
+    pc_context *ctx = op->ctx;
+    if (adjoint != 0 && adjoint != 1) return fail(ctx, PC_ERR_ARG, "adjoint must be 0 or 1");
+    if (adjoint && op->d != 2) return fail(ctx, PC_ERR_UNSUPPORTED, "the adjoint apply covers 2D operators");
+    if (nrhs < 0 || chunk < 0) return fail(ctx, PC_ERR_ARG, "nrhs and chunk must be >= 0");
+    if (nrhs == 0) return PC_OK;
+    if (!x || !y) return fail(ctx, PC_ERR_ARG, "null x or y");
+    if (ldx < op->N || ldy < op->N) return fail(ctx, PC_ERR_ARG, "ldx and ldy must be >= N");
+    const int64_t el = int64_t(op->elem);
+    const uintptr_t xa = reinterpret_cast<uintptr_t>(x), ya = reinterpret_cast<uintptr_t>(y);
+    const uintptr_t xe = xa + uintptr_t((int64_t(nrhs - 1) * ldx + op->N) * el);
+    const uintptr_t ye = ya + uintptr_t((int64_t(nrhs - 1) * ldy + op->N) * el);
+    if (xa < ye && ya < xe) return fail(ctx, PC_ERR_ARG, "x and y overlap");
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return fail(ctx, PC_ERR_CUDA, "cannot select the context's device");
+    // chunks of an even number of right-hand sides keep the pairs (and so the
+    // rounding) of one apply of the whole batch.  Default: quarters for 2D;
+    // one chunk for 3D, whose patch kernels take nearly as long for a quarter
+    // of a batch as for all of it
+    int32_t c = chunk > 0 ? chunk : op->d == 3 ? nrhs : (nrhs + 3) / 4;
+    if (c >= nrhs) {
+        c = nrhs;
+    } else if (c & 1) {
+        ++c;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!op->s_h2d) {
+        if ((e = cudaStreamCreateWithFlags(&op->s_h2d, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&op->s_d2h, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(ctx, e, "creating copy streams");
+        for (cudaEvent_t &ev : op->host_ev)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(ctx, e, "creating pipeline events");
+    }
+    const size_t vec = size_t(op->N) * op->elem;
+    if (c > op->host_cap) {
+        if (op->d_host_stage && (e = cudaDeviceSynchronize()) != cudaSuccess)
+            return cuda_fail(ctx, e, "synchronising before growing the staging buffers");
+        cudaFree(op->d_host_stage);
+        op->d_host_stage = nullptr;
+        op->device_bytes -= 4 * vec * size_t(op->host_cap);
+        op->host_cap = 0;
+        if ((e = cudaMalloc(&op->d_host_stage, 4 * vec * size_t(c))) != cudaSuccess)
+            return cuda_fail(ctx, e, "allocating the staging buffers");
+        op->host_cap = c;
+        op->device_bytes += 4 * vec * size_t(c);
+    }
+    pc_status st = prepare_batch_impl(op, c);
+    if (st != PC_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t *ev = op->host_ev;
+    char *base = static_cast<char *>(op->d_host_stage);
+    const size_t slot = vec * size_t(op->host_cap);
+    // slot j: x at base + 2j * slot, y at base + (2j + 1) * slot
+    cudaEventRecord(ev[6], s);
+    cudaStreamWaitEvent(op->s_h2d, ev[6], 0);
+    cudaStreamWaitEvent(op->s_d2h, ev[6], 0);
+    const int32_t nch = (nrhs + c - 1) / c;
+    int64_t launches = 0;
+    for (int32_t i = 0; i < nch; ++i) {
+        const int j = i & 1;
+        const int64_t b0 = int64_t(i) * c;
+        const int32_t cnt = int32_t(std::min<int64_t>(c, nrhs - b0));
+        char *xs = base + 2 * j * slot, *ys = base + (2 * j + 1) * slot;
+        // copy in once chunk i - 2 has been computed from this slot
+        if (i >= 2) cudaStreamWaitEvent(op->s_h2d, ev[2 + j], 0);
+        const char *xsrc = static_cast<const char *>(x) + b0 * ldx * el;
+        e = ldx == op->N ? cudaMemcpyAsync(xs, xsrc, vec * size_t(cnt), cudaMemcpyHostToDevice, op->s_h2d)
+                         : cudaMemcpy2DAsync(xs, vec, xsrc, size_t(ldx * el), vec, size_t(cnt),
+                                             cudaMemcpyHostToDevice, op->s_h2d);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copying a chunk in");
+        cudaEventRecord(ev[j], op->s_h2d);
+        // compute once it is in and chunk i - 2's result has left this slot
+        cudaStreamWaitEvent(s, ev[j], 0);
+        if (i >= 2) cudaStreamWaitEvent(s, ev[4 + j], 0);
+        st = apply_batched(op, cnt, xs, op->N, ys, op->N, stream, adjoint == 1);
+        if (st != PC_OK) return st;
+        launches += op->launches_last;
+        cudaEventRecord(ev[2 + j], s);
+        // copy out
+        cudaStreamWaitEvent(op->s_d2h, ev[2 + j], 0);
+        char *ydst = static_cast<char *>(y) + b0 * ldy * el;
+        e = ldy == op->N ? cudaMemcpyAsync(ydst, ys, vec * size_t(cnt), cudaMemcpyDeviceToHost, op->s_d2h)
+                         : cudaMemcpy2DAsync(ydst, size_t(ldy * el), ys, vec, vec, size_t(cnt),
+                                             cudaMemcpyDeviceToHost, op->s_d2h);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copying a chunk out");
+        cudaEventRecord(ev[4 + j], op->s_d2h);
+    }
+    // the caller's stream continues once the last copy out (the copy stream is in order) is done
+    if ((e = cudaStreamWaitEvent(s, ev[4 + ((nch - 1) & 1)], 0)) != cudaSuccess)
+        return cuda_fail(ctx, e, "ordering the caller's stream after the copies");
+    op->launches_last = launches;
+    return PC_OK;
 }
 
 pc_status pc_estimate_cell_errors(pc_operator *op, int32_t q, const void *z, int64_t ldz, const void *y, int64_t ldy,

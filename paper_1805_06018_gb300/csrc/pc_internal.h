@@ -209,6 +209,12 @@ struct pc_operator {
     // O(1) matrix entries (Section 3.1): device tables, one allocation
     void *d_entry_mem = nullptr;
     pc::EntryData entry{};
+    // host-buffer applies: two device staging slots, each holding x and y of
+    // host_cap right-hand sides, two copy streams and the pipeline's events
+    void *d_host_stage = nullptr;
+    int32_t host_cap = 0;
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t host_ev[7] = {};         // [0, 1] copied in, [2, 3] computed, [4, 5] copied out, [6] call start
     std::vector<cudaEvent_t> stage_ev;   // BF16x3 3D: [chunk][stage][begin, end] of the last apply
     int stage_chunks = 0;
     uint32_t epoch = 0;
