@@ -237,23 +237,36 @@ pc_status pc_apply_adjoint_batched(pc_operator *op, int32_t nrhs, const void *x,
 
 /* Y[b] = A~ X[b] (adjoint = 0) or A~* X[b] (adjoint = 1) for b < nrhs with
  * x and y in HOST memory (X[b] at x + b*ldx, Y[b] at y + b*ldy elements,
- * ldx, ldy >= N, disjoint).  The batch runs in chunks of `chunk`
- * right-hand sides (0: about a quarter of the batch for 2D operators, the
- * whole batch for 3D ones, whose kernels gain little from smaller batches;
- * rounded up to an even
- * count so that the right-hand-side pairs, and so every rounding, are those
- * of one device apply of the whole batch: the result is bitwise that of
- * pc_apply_batched / pc_apply_adjoint_batched).  Chunk i is copied in on an
- * internal copy stream, applied on `stream`, and copied out on a second
- * copy stream, through two device staging slots that the operator allocates
- * on first use (4 * chunk * N elements) and keeps; so the copies of one
- * chunk overlap the kernels of its neighbours.  Stream-ordered: the copies
- * start after the work already queued on `stream`, and work queued on
- * `stream` after the call starts once y is complete; the call itself
- * returns once everything is queued.  x and y must stay valid until then,
- * and should be page-locked (cudaHostAlloc or cudaHostRegister) for the
- * copies to run asynchronously.  Calls on one operator must be serialised
- * (one stream).  The adjoint covers 2D operators. */
+ * ldx, ldy >= N, disjoint).  The batch moves in chunks of `chunk`
+ * right-hand sides, rounded up to an even count so that the right-hand-side
+ * pairs, and so every rounding, are those of one device apply of the whole
+ * batch: the result is bitwise that of pc_apply_batched /
+ * pc_apply_adjoint_batched.
+ *   - 2D operators (chunk 0: about a quarter of the batch, at most 64
+ *     chunks): the whole batch is staged on the device (2 * nrhs * N
+ *     elements, kept by the operator) and computed by ONE persistent launch
+ *     of the patch kernel.  Chunk i is copied in on an internal copy stream;
+ *     when the calling thread sees that copy complete it sets the chunk's
+ *     ready word in mapped host memory, which the kernel's CTAs wait for
+ *     (bounded) before they take the chunk's work.  The kernel raises a
+ *     completion flag in mapped host memory once the chunk's last result has
+ *     landed, and the calling thread then copies the chunk out on a second
+ *     copy stream.  The call therefore BLOCKS until the kernel has
+ *     finished (at most 60 s after the work queued earlier on `stream`,
+ *     else PC_ERR_TIMEOUT); the copies out of the last chunks may still be
+ *     in flight when it returns.
+ *   - 3D operators (chunk 0: the whole batch, as their patch kernels gain
+ *     little from smaller batches): chunk i is copied in, applied on
+ *     `stream` and copied out
+ *     through two device staging slots (4 * chunk * N elements), so that the
+ *     copies of one chunk overlap the kernels of its neighbours; the call
+ *     returns once everything is queued.
+ * Stream-ordered: the copies start after the work already queued on
+ * `stream`, and work queued on `stream` after the call starts once y is
+ * complete.  x and y must stay valid until then and should be page-locked
+ * (cudaHostAlloc or cudaHostRegister) for the copies to run asynchronously.
+ * Calls on one operator must be serialised (one stream).  The adjoint
+ * covers 2D operators. */
 pc_status pc_apply_host(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
                         int32_t adjoint, int32_t chunk, pc_stream stream);
 

@@ -96,6 +96,12 @@ const char *free_operator(pc_operator *op) {
     chk(cudaFree(op->d_est), "estimator scratch");
     chk(cudaFree(op->d_entry_mem), "entry tables");
     chk(cudaFree(op->d_host_stage), "host-apply staging");
+    if (op->h_host_desc) chk(cudaFreeHost(op->h_host_desc), "host-apply descriptor");
+    chk(cudaFree(op->d_host_desc), "host-apply descriptor");
+    chk(cudaFree(op->d_host_seg_done), "host-apply counters");
+    if (op->h_host_ready) chk(cudaFreeHost(op->h_host_ready), "host-apply ready words");
+    for (cudaEvent_t ev : op->host_in_ev) chk(cudaEventDestroy(ev), "host-apply events");
+    if (op->h_host_flags) chk(cudaFreeHost(op->h_host_flags), "host-apply flags");
     for (cudaEvent_t ev : op->host_ev)
         if (ev) chk(cudaEventDestroy(ev), "host-apply events");
     if (op->s_h2d) chk(cudaStreamDestroy(op->s_h2d), "copy streams");
@@ -796,6 +802,253 @@ pc_status pc_apply_adjoint_batched(pc_operator *op, int32_t nrhs, const void *x,
     return apply_batched(op, nrhs, x, ldx, y, ldy, stream, true);
 }
 
+}  // extern "C"
+
+namespace {
+
+pc_status ensure_host_resources(pc_operator *op, size_t stage_bytes) {
+    pc_context *ctx = op->ctx;
+    cudaError_t e = cudaSuccess;
+    if (!op->s_h2d) {
+        if ((e = cudaStreamCreateWithFlags(&op->s_h2d, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&op->s_d2h, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(ctx, e, "creating copy streams");
+        for (cudaEvent_t &ev : op->host_ev)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(ctx, e, "creating pipeline events");
+    }
+    if (stage_bytes > op->host_stage_bytes) {
+        if (op->d_host_stage && (e = cudaDeviceSynchronize()) != cudaSuccess)
+            return cuda_fail(ctx, e, "synchronising before growing the staging buffers");
+        cudaFree(op->d_host_stage);
+        op->d_host_stage = nullptr;
+        op->device_bytes -= op->host_stage_bytes;
+        op->host_stage_bytes = 0;
+        if ((e = cudaMalloc(&op->d_host_stage, stage_bytes)) != cudaSuccess)
+            return cuda_fail(ctx, e, "allocating the staging buffers");
+        op->host_stage_bytes = stage_bytes;
+        op->device_bytes += stage_bytes;
+    }
+    return PC_OK;
+}
+
+cudaError_t copy_rows(void *dst, size_t dld, const void *src, size_t sld, size_t width, size_t rows,
+                      cudaMemcpyKind kind, cudaStream_t s) {
+    if (dld == width && sld == width) return cudaMemcpyAsync(dst, src, width * rows, kind, s);
+    return cudaMemcpy2DAsync(dst, dld, src, sld, width, rows, kind, s);
+}
+
+// 2D host apply as one persistent launch over segments of c right-hand sides
+// (c even, so each segment keeps the pairs of the whole batch).  The whole
+// batch is staged on the device.  Chunk i is copied in on s_h2d; when this
+// thread sees the copy's event complete it sets the segment's ready word (in
+// mapped host memory), which a CTA reaching the segment's items waits for
+// (bounded).  The kernel raises each segment's completion flag in mapped
+// host memory when its last item has landed; this thread then copies the
+// segment out on s_d2h.
+pc_status apply_host_segmented(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
+                               bool adjoint, int32_t c, cudaStream_t s) {
+    pc_context *ctx = op->ctx;
+    const int32_t nch = (nrhs + c - 1) / c;
+    const size_t vec = size_t(op->N) * op->elem;
+    const int64_t el = int64_t(op->elem);
+    cudaError_t e = cudaSuccess;
+    if (!op->h_host_desc) {
+        const size_t w = sizeof(uint32_t) * pc::kMaxSegments;
+        if ((e = cudaHostAlloc(reinterpret_cast<void **>(&op->h_host_desc), sizeof(pc::LaunchDesc), 0)) != cudaSuccess ||
+            (e = cudaMalloc(&op->d_host_desc, sizeof(pc::LaunchDesc))) != cudaSuccess ||
+            (e = cudaMalloc(&op->d_host_seg_done, w)) != cudaSuccess ||
+            (e = cudaHostAlloc(reinterpret_cast<void **>(&op->h_host_ready), w, cudaHostAllocMapped)) != cudaSuccess ||
+            (e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&op->d_host_ready), op->h_host_ready, 0)) !=
+                cudaSuccess ||
+            (e = cudaHostAlloc(reinterpret_cast<void **>(&op->h_host_flags), w, cudaHostAllocMapped)) != cudaSuccess ||
+            (e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&op->d_host_flags), op->h_host_flags, 0)) !=
+                cudaSuccess)
+            return cuda_fail(ctx, e, "allocating the segmented launch's descriptor and flags");
+        std::memset(op->h_host_ready, 0, w);
+        op->device_bytes += sizeof(pc::LaunchDesc) + w;
+        op->host_in_ev.assign(size_t(pc::kMaxSegments), nullptr);
+        for (cudaEvent_t &ev : op->host_in_ev)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(ctx, e, "creating copy events");
+    }
+    pc_status st = ensure_host_resources(op, 2 * vec * size_t(nrhs));
+    if (st != PC_OK) return st;
+    if ((st = ensure_done_capacity(op, (nrhs + 1) / 2)) != PC_OK) return st;
+    size_t smem = 0;
+    if ((e = pc::fft2d_configure(op->P, op->prec, nullptr, &smem)) != cudaSuccess)
+        return cuda_fail(ctx, e, "configuring the patch kernel");
+    if (++op->epoch == 0) op->epoch = 1;
+    const uint32_t ep = op->epoch;
+    char *xs = static_cast<char *>(op->d_host_stage), *ys = xs + vec * size_t(nrhs);
+    pc::LaunchDesc &d = *op->h_host_desc;
+    std::memset(&d, 0, sizeof(pc::LaunchDesc));
+    volatile uint32_t *hf = op->h_host_flags;
+    int64_t items = 0;
+    for (int32_t i = 0; i < nch; ++i) {
+        const int64_t b0 = int64_t(i) * c;
+        const int32_t cnt = int32_t(std::min<int64_t>(c, nrhs - b0));
+        const int32_t np = (cnt + 1) / 2;
+        pc::Segment &sg = d.seg[i];
+        pc::ApplyParams &p = sg.p;
+        p.x = xs + size_t(b0) * vec;
+        p.y = ys + size_t(b0) * vec;
+        p.ldx = p.ldy = op->N;
+        p.nrhs = cnt;
+        p.npairs = np;
+        p.n[0] = int32_t(op->shape[0]);
+        p.n[1] = int32_t(op->shape[1]);
+        p.n[2] = int32_t(op->shape[2]);
+        p.nx[0] = p.n[0];
+        p.nx[1] = p.n[1];
+        p.R = op->R;
+        p.tiles = op->d_tiles;
+        p.color_start = op->d_color_start;
+        p.n_colors = op->n_colors;
+        p.dep_start = op->d_dep_start;
+        p.dep = op->d_dep;
+        p.done = op->d_done + int64_t(op->n_tiles) * (b0 / 2);   // disjoint per segment
+        p.done_ld = np;
+        p.epoch = ep;
+        p.ctrl = op->d_ctrl;
+        p.spec = op->d_spec;
+        p.spec_stride = op->spec_stride;
+        p.w = op->d_w;
+        p.tw = op->d_tw;
+        p.total_items = int64_t(op->n_tiles) * np;
+        sg.item_begin = items;
+        sg.ready = op->d_host_ready + i;
+        sg.ready_val = ep;
+        sg.slot = i;
+        items += p.total_items;
+        hf[i] = 0u;
+    }
+    d.nseg = nch;
+    d.total_items = items;
+    cudaEvent_t *ev = op->host_ev;
+    // copies start after the work already queued on the caller's stream
+    cudaEventRecord(ev[6], s);
+    cudaStreamWaitEvent(op->s_h2d, ev[6], 0);
+    cudaStreamWaitEvent(op->s_d2h, ev[6], 0);
+    for (int32_t i = 0; i < nch; ++i) {
+        const int64_t b0 = int64_t(i) * c;
+        const size_t cnt = size_t(std::min<int64_t>(c, nrhs - b0));
+        if ((e = copy_rows(xs + size_t(b0) * vec, vec, static_cast<const char *>(x) + b0 * ldx * el,
+                           size_t(ldx * el), vec, cnt, cudaMemcpyHostToDevice, op->s_h2d)) != cudaSuccess)
+            return cuda_fail(ctx, e, "copying a chunk in");
+        if ((e = cudaEventRecord(op->host_in_ev[size_t(i)], op->s_h2d)) != cudaSuccess)
+            return cuda_fail(ctx, e, "recording a copy event");
+    }
+    if ((e = cudaMemcpyAsync(op->d_host_desc, op->h_host_desc, sizeof(pc::LaunchDesc), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+        return cuda_fail(ctx, e, "uploading the launch descriptor");
+    if (!op->ev_begin) {
+        if ((e = cudaEventCreate(&op->ev_begin)) == cudaSuccess) e = cudaEventCreate(&op->ev_end);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "creating events");
+    }
+    const int ctas = int(std::min<int64_t>(op->ctas, items));
+    cudaEventRecord(op->ev_begin, s);
+    if ((e = pc::launch_round(op->d_host_desc, reinterpret_cast<unsigned long long *>(op->d_ctrl), op->d_ctrl + 2,
+                              op->d_host_seg_done, op->d_host_flags, ctas, smem, s, op->P, op->prec, adjoint)) !=
+        cudaSuccess)
+        return cuda_fail(ctx, e, "launching the segmented patch kernel");
+    cudaEventRecord(op->ev_end, s);
+    op->timed = true;
+    op->last_stream = s;
+    op->launches_last = 2;
+    // mark each segment ready once its copy in has completed, and copy each
+    // segment out once the kernel has finished it
+    if ((e = cudaEventSynchronize(ev[6])) != cudaSuccess) return cuda_fail(ctx, e, "waiting for earlier work");
+    volatile uint32_t *hr = op->h_host_ready;
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::seconds(60);
+    int32_t next_in = 0, next_out = 0;
+    for (uint64_t polls = 0; next_out < nch; ++polls) {
+        while (next_in < nch) {
+            const cudaError_t q = cudaEventQuery(op->host_in_ev[size_t(next_in)]);
+            if (q == cudaErrorNotReady) break;
+            if (q != cudaSuccess) return cuda_fail(ctx, q, "copying a chunk in");
+            hr[next_in] = ep;   // the kernel reads it with a system-scope acquire
+            ++next_in;
+        }
+        bool progressed = false;
+        while (next_out < next_in && hf[next_out] != 0u) {
+            const int64_t b0 = int64_t(next_out) * c;
+            const size_t cnt = size_t(std::min<int64_t>(c, nrhs - b0));
+            if ((e = copy_rows(static_cast<char *>(y) + b0 * ldy * el, size_t(ldy * el), ys + size_t(b0) * vec, vec,
+                               vec, cnt, cudaMemcpyDeviceToHost, op->s_d2h)) != cudaSuccess)
+                return cuda_fail(ctx, e, "copying a chunk out");
+            ++next_out;
+            progressed = true;
+        }
+        if (progressed || (polls & 1023) != 1023) continue;
+        const cudaError_t q = cudaStreamQuery(s);
+        if (q != cudaSuccess && q != cudaErrorNotReady) return cuda_fail(ctx, q, "the segmented patch kernel");
+        if (q == cudaSuccess && next_out < nch && next_in == nch && hf[next_out] == 0u)
+            return fail(ctx, PC_ERR_CUDA, "the patch kernel ended without finishing a segment");
+        if (std::chrono::steady_clock::now() > deadline)
+            return fail(ctx, PC_ERR_TIMEOUT, "the host apply did not finish within 60 s");
+    }
+    cudaEventRecord(ev[4], op->s_d2h);
+    if ((e = cudaStreamWaitEvent(s, ev[4], 0)) != cudaSuccess)
+        return cuda_fail(ctx, e, "ordering the caller's stream after the copies");
+    return PC_OK;
+}
+
+// Chunked pipeline: chunk i copied in on s_h2d, applied on s, copied out on
+// s_d2h, through two device staging slots.
+pc_status apply_host_chunked(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
+                             bool adjoint, int32_t c, cudaStream_t s) {
+    pc_context *ctx = op->ctx;
+    const size_t vec = size_t(op->N) * op->elem;
+    const int64_t el = int64_t(op->elem);
+    pc_status st = ensure_host_resources(op, 4 * vec * size_t(c));
+    if (st != PC_OK) return st;
+    if ((st = prepare_batch_impl(op, c)) != PC_OK) return st;
+    cudaEvent_t *ev = op->host_ev;
+    char *base = static_cast<char *>(op->d_host_stage);
+    const size_t slot = vec * size_t(c);
+    // slot j: x at base + 2j * slot, y at base + (2j + 1) * slot
+    cudaEventRecord(ev[6], s);
+    cudaStreamWaitEvent(op->s_h2d, ev[6], 0);
+    cudaStreamWaitEvent(op->s_d2h, ev[6], 0);
+    const int32_t nch = (nrhs + c - 1) / c;
+    int64_t launches = 0;
+    cudaError_t e = cudaSuccess;
+    for (int32_t i = 0; i < nch; ++i) {
+        const int j = i & 1;
+        const int64_t b0 = int64_t(i) * c;
+        const int32_t cnt = int32_t(std::min<int64_t>(c, nrhs - b0));
+        char *xs = base + 2 * j * slot, *ys = base + (2 * j + 1) * slot;
+        // copy in once chunk i - 2 has been computed from this slot
+        if (i >= 2) cudaStreamWaitEvent(op->s_h2d, ev[2 + j], 0);
+        if ((e = copy_rows(xs, vec, static_cast<const char *>(x) + b0 * ldx * el, size_t(ldx * el), vec, size_t(cnt),
+                           cudaMemcpyHostToDevice, op->s_h2d)) != cudaSuccess)
+            return cuda_fail(ctx, e, "copying a chunk in");
+        cudaEventRecord(ev[j], op->s_h2d);
+        // compute once it is in and chunk i - 2's result has left this slot
+        cudaStreamWaitEvent(s, ev[j], 0);
+        if (i >= 2) cudaStreamWaitEvent(s, ev[4 + j], 0);
+        st = apply_batched(op, cnt, xs, op->N, ys, op->N, s, adjoint);
+        if (st != PC_OK) return st;
+        launches += op->launches_last;
+        cudaEventRecord(ev[2 + j], s);
+        cudaStreamWaitEvent(op->s_d2h, ev[2 + j], 0);
+        if ((e = copy_rows(static_cast<char *>(y) + b0 * ldy * el, size_t(ldy * el), ys, vec, vec, size_t(cnt),
+                           cudaMemcpyDeviceToHost, op->s_d2h)) != cudaSuccess)
+            return cuda_fail(ctx, e, "copying a chunk out");
+        cudaEventRecord(ev[4 + j], op->s_d2h);
+    }
+    // the caller's stream continues once the last copy out (the copy stream is in order) is done
+    if ((e = cudaStreamWaitEvent(s, ev[4 + ((nch - 1) & 1)], 0)) != cudaSuccess)
+        return cuda_fail(ctx, e, "ordering the caller's stream after the copies");
+    op->launches_last = launches;
+    return PC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 pc_status pc_apply_host(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
                         int32_t adjoint, int32_t chunk, pc_stream stream) {
     if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
@@ -813,84 +1066,24 @@ pc_status pc_apply_host(pc_operator *op, int32_t nrhs, const void *x, int64_t ld
     if (xa < ye && ya < xe) return fail(ctx, PC_ERR_ARG, "x and y overlap");
     DeviceGuard dg(ctx->device);
     if (!dg.ok) return fail(ctx, PC_ERR_CUDA, "cannot select the context's device");
-    // chunks of an even number of right-hand sides keep the pairs (and so the
-    // rounding) of one apply of the whole batch.  Default: quarters for 2D;
-    // one chunk for 3D, whose patch kernels take nearly as long for a quarter
-    // of a batch as for all of it
-    int32_t c = chunk > 0 ? chunk : op->d == 3 ? nrhs : (nrhs + 3) / 4;
-    if (c >= nrhs) {
-        c = nrhs;
-    } else if (c & 1) {
-        ++c;
-    }
-    cudaError_t e = cudaSuccess;
-    if (!op->s_h2d) {
-        if ((e = cudaStreamCreateWithFlags(&op->s_h2d, cudaStreamNonBlocking)) != cudaSuccess ||
-            (e = cudaStreamCreateWithFlags(&op->s_d2h, cudaStreamNonBlocking)) != cudaSuccess)
-            return cuda_fail(ctx, e, "creating copy streams");
-        for (cudaEvent_t &ev : op->host_ev)
-            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
-                return cuda_fail(ctx, e, "creating pipeline events");
-    }
-    const size_t vec = size_t(op->N) * op->elem;
-    if (c > op->host_cap) {
-        if (op->d_host_stage && (e = cudaDeviceSynchronize()) != cudaSuccess)
-            return cuda_fail(ctx, e, "synchronising before growing the staging buffers");
-        cudaFree(op->d_host_stage);
-        op->d_host_stage = nullptr;
-        op->device_bytes -= 4 * vec * size_t(op->host_cap);
-        op->host_cap = 0;
-        if ((e = cudaMalloc(&op->d_host_stage, 4 * vec * size_t(c))) != cudaSuccess)
-            return cuda_fail(ctx, e, "allocating the staging buffers");
-        op->host_cap = c;
-        op->device_bytes += 4 * vec * size_t(c);
-    }
-    pc_status st = prepare_batch_impl(op, c);
-    if (st != PC_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaEvent_t *ev = op->host_ev;
-    char *base = static_cast<char *>(op->d_host_stage);
-    const size_t slot = vec * size_t(op->host_cap);
-    // slot j: x at base + 2j * slot, y at base + (2j + 1) * slot
-    cudaEventRecord(ev[6], s);
-    cudaStreamWaitEvent(op->s_h2d, ev[6], 0);
-    cudaStreamWaitEvent(op->s_d2h, ev[6], 0);
-    const int32_t nch = (nrhs + c - 1) / c;
-    int64_t launches = 0;
-    for (int32_t i = 0; i < nch; ++i) {
-        const int j = i & 1;
-        const int64_t b0 = int64_t(i) * c;
-        const int32_t cnt = int32_t(std::min<int64_t>(c, nrhs - b0));
-        char *xs = base + 2 * j * slot, *ys = base + (2 * j + 1) * slot;
-        // copy in once chunk i - 2 has been computed from this slot
-        if (i >= 2) cudaStreamWaitEvent(op->s_h2d, ev[2 + j], 0);
-        const char *xsrc = static_cast<const char *>(x) + b0 * ldx * el;
-        e = ldx == op->N ? cudaMemcpyAsync(xs, xsrc, vec * size_t(cnt), cudaMemcpyHostToDevice, op->s_h2d)
-                         : cudaMemcpy2DAsync(xs, vec, xsrc, size_t(ldx * el), vec, size_t(cnt),
-                                             cudaMemcpyHostToDevice, op->s_h2d);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "copying a chunk in");
-        cudaEventRecord(ev[j], op->s_h2d);
-        // compute once it is in and chunk i - 2's result has left this slot
-        cudaStreamWaitEvent(s, ev[j], 0);
-        if (i >= 2) cudaStreamWaitEvent(s, ev[4 + j], 0);
-        st = apply_batched(op, cnt, xs, op->N, ys, op->N, stream, adjoint == 1);
-        if (st != PC_OK) return st;
-        launches += op->launches_last;
-        cudaEventRecord(ev[2 + j], s);
-        // copy out
-        cudaStreamWaitEvent(op->s_d2h, ev[2 + j], 0);
-        char *ydst = static_cast<char *>(y) + b0 * ldy * el;
-        e = ldy == op->N ? cudaMemcpyAsync(ydst, ys, vec * size_t(cnt), cudaMemcpyDeviceToHost, op->s_d2h)
-                         : cudaMemcpy2DAsync(ydst, size_t(ldy * el), ys, vec, vec, size_t(cnt),
-                                             cudaMemcpyDeviceToHost, op->s_d2h);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "copying a chunk out");
-        cudaEventRecord(ev[4 + j], op->s_d2h);
+    pc_status st = ensure_host_resources(op, 0);
+    if (st != PC_OK) return st;
+    // chunks of an even number of right-hand sides keep the pairs (and so the
+    // rounding) of one apply of the whole batch
+    auto even = [&](int32_t v) { return v >= nrhs ? nrhs : v + (v & 1); };
+    if (op->d == 2) {
+        // one segmented launch: chunks of about a quarter of the batch (a
+        // segment's colour chain is its critical path, so smaller chunks run
+        // longer), at most kMaxSegments of them
+        int32_t c = even(std::max<int32_t>(chunk > 0 ? chunk : (nrhs + 3) / 4,
+                                           (nrhs + pc::kMaxSegments - 1) / pc::kMaxSegments));
+        return apply_host_segmented(op, nrhs, x, ldx, y, ldy, adjoint == 1, c, s);
     }
-    // the caller's stream continues once the last copy out (the copy stream is in order) is done
-    if ((e = cudaStreamWaitEvent(s, ev[4 + ((nch - 1) & 1)], 0)) != cudaSuccess)
-        return cuda_fail(ctx, e, "ordering the caller's stream after the copies");
-    op->launches_last = launches;
-    return PC_OK;
+    // 3D: the chunked pipeline, by default in one chunk (the 3D patch kernels
+    // take nearly as long for a quarter of a batch as for all of it)
+    const int32_t c = even(chunk > 0 ? chunk : nrhs);
+    return apply_host_chunked(op, nrhs, x, ldx, y, ldy, adjoint == 1, c, s);
 }
 
 pc_status pc_estimate_cell_errors(pc_operator *op, int32_t q, const void *z, int64_t ldz, const void *y, int64_t ldy,

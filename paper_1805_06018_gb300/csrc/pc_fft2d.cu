@@ -240,6 +240,17 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
                 s_seg = lp.one;
             }
             __syncthreads();
+            // a segment whose input is still being copied in: wait (bounded) for its ready word
+            if (threadIdx.x == 0 && s_seg.ready) {
+                long long spins = 0;
+                while (ld_acquire_sys_u32(s_seg.ready) != s_seg.ready_val) {
+                    if (++spins > kSpinLimit) {
+                        atomicExch(lp.status, 1);   // timeout flag; result of this apply is invalid
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+            }
             const int nc = s_seg.p.n_colors;
             s_cstart = nc <= kMaxColorsCached ? s_cstart_buf : s_seg.p.color_start;
             for (int c = threadIdx.x; c <= nc && c <= kMaxColorsCached; c += blockDim.x)
@@ -564,8 +575,9 @@ cudaError_t launch_fft2d(const ApplyParams &p, int P, pc_precision prec, int cta
     return cudaGetLastError();
 }
 
-// Multi-request launch: every segment's y zeroed, its ordering flags and
+// Multi-segment launch: every segment's y zeroed, its ordering flags and
 // finished-item counter cleared, the claim counter reset.
+template <typename T>
 __global__ void round_prepare(const LaunchDesc *d, unsigned long long *counter, uint32_t *seg_done) {
     const int nseg = d->nseg;
     if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0ull;
@@ -575,11 +587,11 @@ __global__ void round_prepare(const LaunchDesc *d, unsigned long long *counter, 
     for (int sx = 0; sx < nseg; ++sx) {
         const ApplyParams &p = d->seg[sx].p;
         const int64_t N = int64_t(p.n[0]) * p.n[1] * p.n[2];
-        float *y = static_cast<float *>(p.y);
+        T *y = static_cast<T *>(p.y);
         const int64_t tot = int64_t(p.nrhs) * N;
         for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < tot; q += stride) {
             const int64_t b = q / N, e = q - b * N;
-            y[b * p.ldy + e] = 0.0f;
+            y[b * p.ldy + e] = T(0);
         }
         const int64_t nf = int64_t(p.color_start[p.n_colors]) * p.done_ld;
         for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < nf; q += stride) p.done[q] = 0u;
@@ -587,8 +599,12 @@ __global__ void round_prepare(const LaunchDesc *d, unsigned long long *counter, 
 }
 
 cudaError_t launch_round(const LaunchDesc *d_desc, unsigned long long *counter, int32_t *status, uint32_t *seg_done,
-                         uint32_t *host_flags, int ctas, size_t smem, cudaStream_t s) {
-    round_prepare<<<1024, 256, 0, s>>>(d_desc, counter, seg_done);
+                         uint32_t *host_flags, int ctas, size_t smem, cudaStream_t s, int P, pc_precision prec,
+                         bool adjoint) {
+    if (prec == PC_FP64)
+        round_prepare<double><<<1024, 256, 0, s>>>(d_desc, counter, seg_done);
+    else
+        round_prepare<float><<<1024, 256, 0, s>>>(d_desc, counter, seg_done);
     LaunchParams lp{};
     lp.desc = d_desc;
     lp.one.slot = -1;
@@ -596,7 +612,10 @@ cudaError_t launch_round(const LaunchDesc *d_desc, unsigned long long *counter, 
     lp.status = status;
     lp.seg_done = seg_done;
     lp.host_flags = host_flags;
-    fft2d_kernel<float, 128, false><<<ctas, KCfg<float, 128>::threads, smem, s>>>(lp);
+    if (adjoint)
+        launch_one<true>(lp, P, prec, ctas, smem, s);
+    else
+        launch_one<false>(lp, P, prec, ctas, smem, s);
     return cudaGetLastError();
 }
 

@@ -121,8 +121,9 @@ struct ApplyParams {
 struct Segment {
     ApplyParams p;          // operator data, the request's x/y/nrhs, its ordering flags; p.total_items = its items
     int64_t item_begin;     // first launch-wide item index of the segment
+    const uint32_t *ready;  // nullptr, or a word that equals ready_val once the segment's x is in place
+    uint32_t ready_val;
     int32_t slot;           // completion slot in the host flag array, or -1
-    int32_t pad_;
 };
 
 constexpr int kMaxSegments = 64;
@@ -209,12 +210,22 @@ struct pc_operator {
     // O(1) matrix entries (Section 3.1): device tables, one allocation
     void *d_entry_mem = nullptr;
     pc::EntryData entry{};
-    // host-buffer applies: two device staging slots, each holding x and y of
-    // host_cap right-hand sides, two copy streams and the pipeline's events
+    // host-buffer applies: device staging (the whole batch's x and y for a
+    // segmented launch, two chunk slots for the chunked pipeline), two copy
+    // streams and the pipeline's events
     void *d_host_stage = nullptr;
-    int32_t host_cap = 0;
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     cudaEvent_t host_ev[7] = {};         // [0, 1] copied in, [2, 3] computed, [4, 5] copied out, [6] call start
+    size_t host_stage_bytes = 0;
+    // 2D host applies as one segmented launch: descriptor (pinned host and
+    // device copies), per-segment finished-item counters, and in mapped host
+    // memory per-segment ready words (host-written) and completion flags
+    // (kernel-written); one event per segment's copy in
+    pc::LaunchDesc *h_host_desc = nullptr, *d_host_desc = nullptr;
+    uint32_t *d_host_seg_done = nullptr;
+    uint32_t *h_host_ready = nullptr, *d_host_ready = nullptr;
+    uint32_t *h_host_flags = nullptr, *d_host_flags = nullptr;
+    std::vector<cudaEvent_t> host_in_ev;
     std::vector<cudaEvent_t> stage_ev;   // BF16x3 3D: [chunk][stage][begin, end] of the last apply
     int stage_chunks = 0;
     uint32_t epoch = 0;
@@ -262,8 +273,12 @@ cudaError_t launch_fft2d(const ApplyParams &p, int P, pc_precision prec, int cta
                          bool adjoint = false);
 // multi-request launch (FP32, P = 128): y zero-fill + claim reset, then the fused kernel
 // (fft2d_configure(128, PC_FP32, ...) must have been called; capturable)
+// Multi-segment persistent launch of the 2D patch kernel (every segment's y
+// zeroed and its flags cleared first): P = 128 FP32 for served requests;
+// any 2D configuration (P, precision, direction) for chunked host applies.
 cudaError_t launch_round(const LaunchDesc *d_desc, unsigned long long *counter, int32_t *status, uint32_t *seg_done,
-                         uint32_t *host_flags, int ctas, size_t smem, cudaStream_t s);
+                         uint32_t *host_flags, int ctas, size_t smem, cudaStream_t s, int P = 128,
+                         pc_precision prec = PC_FP32, bool adjoint = false);
 cudaError_t fft2d_configure(int P, pc_precision prec, int *ctas_per_sm, size_t *smem);
 // d_psi: [nspec][W][W] FP64 windows placed at [0, W)^2; spectra [nspec][P/2+1][P]
 cudaError_t build_spectra_2d(const double *d_psi, int nspec, int W, int P, pc_precision prec, void *d_spec,
