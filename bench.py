@@ -392,7 +392,7 @@ def run_block(args, rank, world):
                     "d2h_bytes_per_step": int(yh.numel() * 4)},
             "gpu_launches": 2 * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp32_peak, "traffic": None, "kernel": kname,
+                         "frac": achieved / fp32_peak, "traffic": profiled_traffic(args.workload), "kernel": kname,
                          "kernel_ms": step_mean, "timed": "zero fill + patch kernel (events around the call)",
                          "algorithmic_flop_per_launch": flops, "nominal_terms": nominal_terms,
                          "peak_basis": "FP32 FMA pipe: SMs x 128 lanes x 2 x %.0f MHz" % sm_max},

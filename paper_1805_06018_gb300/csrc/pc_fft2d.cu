@@ -45,6 +45,13 @@ constexpr int kThreads2d = 512;
 template <typename T, int P> struct KCfg {
     static constexpr int threads = kThreads2d;
 };
+// acquire load at system scope (a ready word the host writes in mapped memory)
+__device__ __forceinline__ uint32_t ld_acquire_sys_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 constexpr long long kSpinLimit = 1ll << 24;   // x >= 64 ns per spin: about a second at least
 constexpr long long kMbarLimit = 1ll << 24;   // try_wait rounds for the spectrum copy
 
