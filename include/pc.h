@@ -230,8 +230,8 @@ pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t
  * operator the paper's a-posteriori error estimator applies to random
  * probes (Section 2.6).  Same arguments, layouts, stream semantics and
  * determinism as pc_apply_batched (y overwritten; each y element sums its
- * contributions in a fixed order).  2D operators (PC_FP32, PC_FP64); 3D
- * operators return PC_ERR_UNSUPPORTED. */
+ * contributions in a fixed order).  PC_FP32 and PC_FP64 operators, 2D and
+ * 3D; PC_BF16X3 operators return PC_ERR_UNSUPPORTED. */
 pc_status pc_apply_adjoint_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx,
                                    void *y, int64_t ldy, pc_stream stream);
 
@@ -266,7 +266,7 @@ pc_status pc_apply_adjoint_batched(pc_operator *op, int32_t nrhs, const void *x,
  * complete.  x and y must stay valid until then and should be page-locked
  * (cudaHostAlloc or cudaHostRegister) for the copies to run asynchronously.
  * Calls on one operator must be serialised (one stream).  The adjoint
- * covers 2D operators. */
+ * covers PC_FP32 and PC_FP64 operators. */
 pc_status pc_apply_host(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
                         int32_t adjoint, int32_t chunk, pc_stream stream);
 
@@ -348,7 +348,8 @@ pc_status pc_block_plan_destroy(pc_block_plan *plan);
  *          (the call synchronises `stream`).
  * The library applies A~* to z (as pc_apply_adjoint_batched, into scratch
  * that it allocates and keeps) and reduces each cell in FP64 in a fixed
- * order, so eta is bitwise reproducible.  2D operators; 3D operators return
+ * order, so eta is bitwise reproducible.  PC_FP32 and PC_FP64 operators,
+ * 2D and 3D (cells as closed boxes); PC_BF16X3 operators return
  * PC_ERR_UNSUPPORTED. */
 pc_status pc_estimate_cell_errors(pc_operator *op, int32_t q, const void *z, int64_t ldz, const void *y,
                                   int64_t ldy, double *eta, pc_stream stream);

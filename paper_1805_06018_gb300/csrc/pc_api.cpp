@@ -726,7 +726,8 @@ static pc_status apply_batched(pc_operator *op, int32_t nrhs, const void *x, int
                                pc_stream stream, bool adjoint) {
     if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
     pc_context *ctx = op->ctx;
-    if (adjoint && op->d != 2) return fail(ctx, PC_ERR_UNSUPPORTED, "the adjoint apply covers 2D operators");
+    if (adjoint && op->prec == PC_BF16X3)
+        return fail(ctx, PC_ERR_UNSUPPORTED, "the adjoint apply covers FP32 and FP64 operators");
     if (nrhs < 0) return fail(ctx, PC_ERR_ARG, "nrhs < 0");
     if (nrhs == 0) return PC_OK;
     if (!x || !y) return fail(ctx, PC_ERR_ARG, "null x or y");
@@ -782,7 +783,7 @@ static pc_status apply_batched(pc_operator *op, int32_t nrhs, const void *x, int
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the zero kernel");
     const int ctas = int(std::min<int64_t>(op->ctas, p.total_items));
     cudaEventRecord(op->ev_begin, s);
-    e = op->d == 3 ? pc::launch_fft3d(p, ctas, op->d_scratch, s)
+    e = op->d == 3 ? pc::launch_fft3d(p, ctas, op->d_scratch, s, adjoint)
                    : pc::launch_fft2d(p, op->P, op->prec, ctas, s, adjoint);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the patch kernel");
     cudaEventRecord(op->ev_end, s);
@@ -1054,7 +1055,8 @@ pc_status pc_apply_host(pc_operator *op, int32_t nrhs, const void *x, int64_t ld
     if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
     pc_context *ctx = op->ctx;
     if (adjoint != 0 && adjoint != 1) return fail(ctx, PC_ERR_ARG, "adjoint must be 0 or 1");
-    if (adjoint && op->d != 2) return fail(ctx, PC_ERR_UNSUPPORTED, "the adjoint apply covers 2D operators");
+    if (adjoint && op->prec == PC_BF16X3)
+        return fail(ctx, PC_ERR_UNSUPPORTED, "the adjoint apply covers FP32 and FP64 operators");
     if (nrhs < 0 || chunk < 0) return fail(ctx, PC_ERR_ARG, "nrhs and chunk must be >= 0");
     if (nrhs == 0) return PC_OK;
     if (!x || !y) return fail(ctx, PC_ERR_ARG, "null x or y");
@@ -1092,7 +1094,8 @@ pc_status pc_estimate_cell_errors(pc_operator *op, int32_t q, const void *z, int
     pc_context *ctx = op->ctx;
     if (q < 1) return fail(ctx, PC_ERR_ARG, "q must be >= 1");
     if (!z || !y || !eta) return fail(ctx, PC_ERR_ARG, "null z, y or eta");
-    if (op->d != 2) return fail(ctx, PC_ERR_UNSUPPORTED, "the error estimator covers 2D operators");
+    if (op->prec == PC_BF16X3)
+        return fail(ctx, PC_ERR_UNSUPPORTED, "the error estimator covers FP32 and FP64 operators");
     if (ldy < op->N) return fail(ctx, PC_ERR_ARG, "ldy must be >= N");
     if (reinterpret_cast<uintptr_t>(y) % op->elem) return fail(ctx, PC_ERR_ARG, "y must be aligned to the element size");
     DeviceGuard dg(ctx->device);

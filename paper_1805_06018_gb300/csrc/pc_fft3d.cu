@@ -20,6 +20,8 @@
 // tensor-core first-axis transform of pc_tc3d.cu, then phase 3).  Scratch
 // traffic is about 6.7 MB per item; the line FFTs (about 20,000 of length 64
 // per item) dominate the time.
+#include <algorithm>
+
 #include "pc_fftcore.cuh"
 #include "pc_internal.h"
 #include "pc_ptx.cuh"
@@ -68,7 +70,11 @@ struct Lines3 {
     }
 };
 
-// phase 1: 2D FFT of each of the n0 non-zero input planes -> G[i0][k2][k1]
+// phase 1: 2D FFT of each of the n0 non-zero input planes -> G[i0][k2][k1].
+// Adjoint: of the L0 planes of the output box, x unweighted and zero outside
+// Omega (rows and columns L1 x L2 at out_lo); planes outside Omega are
+// skipped here and read as zero by phase 2.
+template <bool ADJ>
 __device__ __forceinline__ void phase1_3d(const ApplyParams &p, const Item3 &it, float2 *G, float2 *S,
                                           const Lines3 &L) {
     using C = float2;
@@ -76,23 +82,38 @@ __device__ __forceinline__ void phase1_3d(const ApplyParams &p, const Item3 &it,
     const C zero{0.0f, 0.0f};
     const Tile &tile = it.tile;
     const int n0 = tile.in_ext[0], n1 = tile.in_ext[1], n2 = tile.in_ext[2];
+    // planes, rows and columns of the gathered box
+    const int m0 = ADJ ? n0 + tile.kext[0] - 1 : n0;
+    const int m1 = ADJ ? n1 + tile.kext[1] - 1 : n1;
+    const int m2 = ADJ ? n2 + tile.kext[2] - 1 : n2;
+    const int g0 = ADJ ? tile.out_lo[0] : tile.in_lo[0];
+    const int g1 = ADJ ? tile.out_lo[1] : tile.in_lo[1];
+    const int g2 = ADJ ? tile.out_lo[2] : tile.in_lo[2];
     const int b0 = 2 * it.pair;
     const bool has1 = b0 + 1 < p.nrhs;
     const float *x0 = static_cast<const float *>(p.x) + int64_t(b0) * p.ldx;
     const float *x1 = has1 ? x0 + p.ldx : x0;
     const float *wt = static_cast<const float *>(p.w) + tile.w_base;
     const int64_t plane_box = int64_t(p.n[1]) * p.n[2];
-    for (int i0 = 0; i0 < n0; ++i0) {
+    for (int i0 = 0; i0 < m0; ++i0) {
+        if (ADJ && (g0 + i0 < 0 || g0 + i0 >= p.n[0])) continue;   // uniform across the CTA
         const float *wp = wt + int64_t(i0) * tile.w_ld[0];
-        const int64_t xp = int64_t(tile.in_lo[0] + i0) * plane_box;
-        for (int r = L.line; r < n1; r += LINES) {
+        const int64_t xp = int64_t(g0 + i0) * plane_box;
+        for (int r = L.line; r < m1; r += LINES) {
             C a[R1];
-            const int64_t xr = xp + int64_t(tile.in_lo[1] + r) * p.n[2] + tile.in_lo[2];
+            const int gr = g1 + r;
+            const bool rin = !ADJ || (gr >= 0 && gr < p.n[1]);
+            const int64_t xr = xp + int64_t(gr) * p.n[2] + g2;
             const float *wr = wp + int64_t(r) * tile.w_ld[1];
 #pragma unroll
             for (int j = 0; j < R1; ++j) {
                 const int col = L.t + R2 * j;
-                if (col < n2) {
+                if constexpr (ADJ) {
+                    const int gc = g2 + col;
+                    a[j] = rin && col < m2 && gc >= 0 && gc < p.n[2]
+                               ? C{__ldg(x0 + xr + col), has1 ? __ldg(x1 + xr + col) : 0.0f}
+                               : zero;
+                } else if (col < n2) {
                     const float wv = __ldg(wr + col);
                     a[j] = C{wv * __ldg(x0 + xr + col), has1 ? wv * __ldg(x1 + xr + col) : 0.0f};
                 } else {
@@ -110,7 +131,7 @@ __device__ __forceinline__ void phase1_3d(const ApplyParams &p, const Item3 &it,
 #pragma unroll
             for (int j = 0; j < R1; ++j) {
                 const int row = L.t + R2 * j;
-                a[j] = row < n1 ? S[row * P + (k2 ^ swz(row))] : zero;
+                a[j] = row < m1 ? S[row * P + (k2 ^ swz(row))] : zero;
             }
             ColScratch<P, C> scr{S, k2};
             fft_line<P, false>(a, L.tw, L.t, scr, L.lmask);
@@ -126,12 +147,17 @@ __device__ __forceinline__ void phase1_3d(const ApplyParams &p, const Item3 &it,
 // the n0 non-zero planes, product with the stored spectrum, inverse FFT,
 // keeping the L0 needed output planes.  Stored spectrum: Hermitian half in
 // k2, layout [k2 <= P/2][k1][k0].
+// Adjoint: the L0 output-box planes in (those outside Omega read as zero),
+// the conjugate spectrum, the n0 input-box planes kept.
+template <bool ADJ>
 __device__ __forceinline__ void phase2_3d(const ApplyParams &p, const Item3 &it, float2 *G, float2 *S,
                                           const Lines3 &L) {
     using C = float2;
     constexpr int P = Lines3::P, R1 = Lines3::R1, R2 = Lines3::R2, LINES = Lines3::LINES, PP = Lines3::PP;
     const C zero{0.0f, 0.0f};
     const int n0 = it.tile.in_ext[0], L0 = n0 + it.tile.kext[0] - 1;
+    const int rows_in = ADJ ? L0 : n0, rows_out = ADJ ? n0 : L0;
+    const int g0 = it.tile.out_lo[0];
     const C *sp = static_cast<const C *>(p.spec) + int64_t(it.tile.spec) * p.spec_stride;
     for (int l = L.line; l < PP; l += LINES) {
         const int k2 = l / P, k1 = l % P;
@@ -140,25 +166,33 @@ __device__ __forceinline__ void phase2_3d(const ApplyParams &p, const Item3 &it,
 #pragma unroll
         for (int j = 0; j < R1; ++j) {
             const int i0 = L.t + R2 * j;
-            a[j] = i0 < n0 ? __ldcg(g + int64_t(i0) * PP) : zero;
+            const bool in = i0 < rows_in && (!ADJ || (g0 + i0 >= 0 && g0 + i0 < p.n[0]));
+            a[j] = in ? __ldcg(g + int64_t(i0) * PP) : zero;
         }
         // S is idle in this phase: row `line` is the line's transpose scratch
         RowScratch<P, C> scr{S, L.line};
         fft_line<P, false>(a, L.tw, L.t, scr, L.lmask);
+        // the adjoint multiplies by the conjugate spectrum
         if (k2 <= P / 2) {
             const C *sc = sp + (int64_t(k2) * P + k1) * P;
 #pragma unroll
-            for (int j = 0; j < R1; ++j) a[j] = cmul(a[j], __ldg(sc + L.t + R2 * j));
+            for (int j = 0; j < R1; ++j) {
+                const C v = __ldg(sc + L.t + R2 * j);
+                a[j] = ADJ ? cmulc(a[j], v) : cmul(a[j], v);
+            }
         } else {
             const C *sc = sp + (int64_t(P - k2) * P + ((P - k1) & (P - 1))) * P;
 #pragma unroll
-            for (int j = 0; j < R1; ++j) a[j] = cmulc(a[j], __ldg(sc + ((P - (L.t + R2 * j)) & (P - 1))));
+            for (int j = 0; j < R1; ++j) {
+                const C v = __ldg(sc + ((P - (L.t + R2 * j)) & (P - 1)));
+                a[j] = ADJ ? cmul(a[j], v) : cmulc(a[j], v);
+            }
         }
         fft_line<P, true>(a, L.tw, L.t, scr, L.lmask);
 #pragma unroll
         for (int j = 0; j < R1; ++j) {
             const int o0 = L.t + R2 * j;
-            if (o0 < L0) __stcg(g + int64_t(o0) * PP, a[j]);
+            if (o0 < rows_out) __stcg(g + int64_t(o0) * PP, a[j]);
         }
     }
     __syncthreads();
@@ -187,23 +221,30 @@ __device__ __forceinline__ void wait_deps_3d(const ApplyParams &p, const Item3 &
 
 // phase 3: inverse 2D FFT of the output planes o0 in [ob, oe) (of the L0
 // needed) and the overlap-add of their L1 x L2 boxes into y; then publish
-// `flag`
+// `flag`.  Adjoint: the planes are the n0 of the input box, each n1 x n2,
+// weighted by w_k and added at the tile's origin.
+template <bool ADJ>
 __device__ __forceinline__ void phase3_3d(const ApplyParams &p, const Item3 &it, const float2 *G, float2 *S,
                                           const Lines3 &L, int ob, int oe, uint32_t *flag) {
     using C = float2;
     constexpr int P = Lines3::P, R1 = Lines3::R1, R2 = Lines3::R2, LINES = Lines3::LINES, PP = Lines3::PP;
     const Tile &tile = it.tile;
     const int n0 = tile.in_ext[0], n1 = tile.in_ext[1], n2 = tile.in_ext[2];
-    const int L0 = n0 + tile.kext[0] - 1, L1 = n1 + tile.kext[1] - 1, L2 = n2 + tile.kext[2] - 1;
+    // kept box (rows, columns) and its origin in y
+    const int m1 = ADJ ? n1 : n1 + tile.kext[1] - 1, m2 = ADJ ? n2 : n2 + tile.kext[2] - 1;
+    const int h0 = ADJ ? tile.in_lo[0] : tile.out_lo[0];
+    const int h1 = ADJ ? tile.in_lo[1] : tile.out_lo[1];
+    const int h2 = ADJ ? tile.in_lo[2] : tile.out_lo[2];
     const int b0 = 2 * it.pair;
     const bool has1 = b0 + 1 < p.nrhs;
     float *y0 = static_cast<float *>(p.y) + int64_t(b0) * p.ldy;
     float *y1 = has1 ? y0 + p.ldy : y0;
+    const float *wt = static_cast<const float *>(p.w) + tile.w_base;
     const int n2box = p.n[2];
     const int64_t plane_box = int64_t(p.n[1]) * n2box;
-    (void)L0;
+    (void)n0;
     for (int o0 = ob; o0 < oe; ++o0) {
-        const int gy0 = tile.out_lo[0] + o0;
+        const int gy0 = h0 + o0;
         if (gy0 < 0 || gy0 >= p.n[0]) continue;   // uniform across the CTA
         // inverse along k1 for each k2: rows o1 of S
         const C *gp = G + int64_t(o0) * PP;
@@ -216,26 +257,35 @@ __device__ __forceinline__ void phase3_3d(const ApplyParams &p, const Item3 &it,
 #pragma unroll
             for (int j = 0; j < R1; ++j) {
                 const int o1 = L.t + R2 * j;
-                if (o1 < L1) S[o1 * P + (k2 ^ swz(o1))] = a[j];
+                if (o1 < m1) S[o1 * P + (k2 ^ swz(o1))] = a[j];
             }
         }
         __syncthreads();
-        for (int o1 = L.line; o1 < L1; o1 += LINES) {
-            const int gy1 = tile.out_lo[1] + o1;
+        for (int o1 = L.line; o1 < m1; o1 += LINES) {
+            const int gy1 = h1 + o1;
             if (gy1 < 0 || gy1 >= p.n[1]) continue;
             C a[R1];
 #pragma unroll
             for (int j = 0; j < R1; ++j) a[j] = S[o1 * P + ((L.t + R2 * j) ^ swz(o1))];
             RowScratch<P, C> scr{S, o1};
             fft_line<P, true>(a, L.tw, L.t, scr, L.lmask);
+            if constexpr (ADJ) {
+                const float *wr = wt + int64_t(o0) * tile.w_ld[0] + int64_t(o1) * tile.w_ld[1];
+#pragma unroll
+                for (int j = 0; j < R1; ++j) {
+                    const int o2 = L.t + R2 * j;
+                    const float wv = o2 < n2 ? __ldg(wr + o2) : 0.0f;
+                    a[j] = C{a[j].x * wv, a[j].y * wv};
+                }
+            }
             const int64_t yr = int64_t(gy0) * plane_box + int64_t(gy1) * n2box;
             // a warp's atomics land in 32-byte sectors of four output rows;
             // staging the row for vector or bulk reductions measured slower
 #pragma unroll
             for (int j = 0; j < R1; ++j) {
                 const int o2 = L.t + R2 * j;
-                const int gy2 = tile.out_lo[2] + o2;
-                if (o2 < L2 && gy2 >= 0 && gy2 < n2box) {
+                const int gy2 = h2 + o2;
+                if (o2 < m2 && gy2 >= 0 && gy2 < n2box) {
                     atomicAdd(y0 + yr + gy2, a[j].x);
                     if (has1) atomicAdd(y1 + yr + gy2, a[j].y);
                 }
@@ -251,6 +301,7 @@ __device__ __forceinline__ void phase3_3d(const ApplyParams &p, const Item3 &it,
 
 // The fused FP32 kernel: persistent CTAs claim items in increasing order and
 // run the three phases through their own scratch volume.
+template <bool ADJ>
 __global__ void __launch_bounds__(kThreads3d, 3) fft3d_kernel(const ApplyParams p, float2 *scratch) {
     extern __shared__ __align__(16) unsigned char smem3[];
     float2 *S = reinterpret_cast<float2 *>(smem3);
@@ -263,11 +314,12 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_kernel(const ApplyParams 
         const int64_t item = s_item;
         if (item >= p.total_items) break;
         const Item3 it = decode_item3(p, item);
-        phase1_3d(p, it, G, S, L);
-        phase2_3d(p, it, G, S, L);
+        phase1_3d<ADJ>(p, it, G, S, L);
+        phase2_3d<ADJ>(p, it, G, S, L);
         wait_deps_3d(p, it, 1);
-        const int L0 = it.tile.in_ext[0] + it.tile.kext[0] - 1;
-        phase3_3d(p, it, G, S, L, 0, L0, p.done + int64_t(it.ti) * p.done_ld + it.pair);
+        // planes kept: the L0 of the output box, or the n0 of the input box (adjoint)
+        const int m0 = ADJ ? it.tile.in_ext[0] : it.tile.in_ext[0] + it.tile.kext[0] - 1;
+        phase3_3d<ADJ>(p, it, G, S, L, 0, m0, p.done + int64_t(it.ti) * p.done_ld + it.pair);
     }
 }
 
@@ -280,7 +332,7 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase1_kernel(const Apply
     const Lines3 L(static_cast<const float2 *>(p.tw));
     for (int64_t item = c0 + blockIdx.x; item < c1; item += gridDim.x) {
         const Item3 it = decode_item3(p, item);
-        phase1_3d(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L);
+        phase1_3d<false>(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L);
     }
 }
 
@@ -308,23 +360,32 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase3_kernel(const Apply
         const Item3 it = decode_item3(p, item);
         wait_deps_3d(p, it, NG);
         const int L0 = it.tile.in_ext[0] + it.tile.kext[0] - 1;
-        phase3_3d(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L, (L0 * g) / NG, (L0 * (g + 1)) / NG,
+        phase3_3d<false>(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L, (L0 * g) / NG, (L0 * (g + 1)) / NG,
                   p.done + int64_t(it.ti) * p.done_ld + int64_t(it.pair) * NG + g);
     }
 }
 
 cudaError_t fft3d_configure(int *ctas_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(fft3d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
+    cudaError_t e = cudaFuncSetAttribute(fft3d_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fft3d_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fft3d_phase3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
-    int n = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fft3d_kernel, kThreads3d, kSmem3);
-    if (ctas_per_sm) *ctas_per_sm = n;
+    int n = 0, na = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fft3d_kernel<false>, kThreads3d, kSmem3);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&na, fft3d_kernel<true>, kThreads3d, kSmem3);
+    // one CTA count serves both directions (the per-CTA scratch volumes are sized by it)
+    if (ctas_per_sm) *ctas_per_sm = std::min(n, na);
     return e;
 }
 
-cudaError_t launch_fft3d(const ApplyParams &p, int ctas, void *scratch, cudaStream_t s) {
-    fft3d_kernel<<<ctas, kThreads3d, kSmem3, s>>>(p, static_cast<float2 *>(scratch));
+cudaError_t launch_fft3d(const ApplyParams &p, int ctas, void *scratch, cudaStream_t s, bool adjoint) {
+    if (adjoint)
+        fft3d_kernel<true><<<ctas, kThreads3d, kSmem3, s>>>(p, static_cast<float2 *>(scratch));
+    else
+        fft3d_kernel<false><<<ctas, kThreads3d, kSmem3, s>>>(p, static_cast<float2 *>(scratch));
     return cudaGetLastError();
 }
 

@@ -285,7 +285,7 @@ cudaError_t build_spectra_2d(const double *d_psi, int nspec, int W, int P, pc_pr
                              const double2 *d_tw64, cudaStream_t s);
 // 3D patch path (pc_fft3d.cu), FP32, P = 64
 cudaError_t fft3d_configure(int *ctas_per_sm);
-cudaError_t launch_fft3d(const ApplyParams &p, int ctas, void *scratch, cudaStream_t s);
+cudaError_t launch_fft3d(const ApplyParams &p, int ctas, void *scratch, cudaStream_t s, bool adjoint = false);
 size_t fft3d_scratch_bytes(int ctas);
 cudaError_t build_spectra_3d(const double *d_psi, int nspec, int W, int P, void *d_spec, const double2 *d_tw64,
                              cudaStream_t s);

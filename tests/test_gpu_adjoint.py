@@ -112,14 +112,56 @@ def test_adjoint_workload_512_sampled():
     assert np.all(rel_l2(y[[5, 38]], full) <= TOL["fp32"])
 
 
-def test_adjoint_3d_unsupported():
+def _skew3(shape, R):
+    L = float(max(shape))
+    return workloads.Skewed([0.7, -0.4, 0.3], lambda x: 1.1 + 0.4 * np.sin(2 * np.pi * x[..., 0] / L), R)
+
+
+def test_adjoint_3d_fp32_ragged():
+    """3D (P = 64): ragged tiles, output boxes cut by the boundary, an
+    asymmetric kernel (an unflipped correlation would fail), an odd batch;
+    bitwise reproducible."""
+    shape = (37, 29, 33)
+    op, orc = make_pair(shape, workloads.regular_grid(shape, (3, 3, 4)), _skew3(shape, 5), "fp32")
+    x = workloads.rhs(76, 3, shape)
+    y = run_adjoint(op, x)
+    assert np.all(rel_l2(y, orc.apply_adjoint(x)) <= TOL["fp32"])
+    assert np.array_equal(y, run_adjoint(op, x))
+
+
+def test_adjoint_3d_identity():
+    """<A~ x, y> = <x, A~* y> for 3D operators, both sides on the GPU (FP32)."""
+    shape = (30, 26, 22)
+    op, _ = make_pair(shape, workloads.regular_grid(shape, (3, 3, 3)), _skew3(shape, 4), "fp32")
+    x, y = workloads.rhs(77, 2, shape), workloads.rhs(78, 2, shape)
+    ax, aty = run_forward(op, x).astype(np.float64), run_adjoint(op, y).astype(np.float64)
+    lhs = np.sum((ax * y).reshape(2, -1), axis=1)
+    rhs = np.sum((x * aty).reshape(2, -1), axis=1)
+    scale = np.linalg.norm(ax.reshape(2, -1), axis=1) * np.linalg.norm(y.reshape(2, -1), axis=1)
+    assert np.all(np.abs(lhs - rhs) <= 1e-5 * scale), (lhs, rhs)
+
+
+def test_adjoint_3d_workload_128_sampled():
+    """The 128^3 operator at its benchmark batch of 32: 256 seeded voxels of
+    every right-hand side against the oracle."""
+    wl = configs.fp32_128c()
+    op, orc = make_pair(wl.shape, wl.cells, wl.kernel, "fp32")
+    x = workloads.rhs(wl.rhs_seed, 32, wl.shape)
+    y = run_adjoint(op, x).reshape(32, -1)
+    pts = np.random.default_rng(79).choice(wl.n, 256, replace=False)
+    ref = orc.apply_adjoint(x, points=pts)
+    err = np.linalg.norm(y[:, pts] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert np.all(err <= TOL["fp32"]), err
+
+
+def test_adjoint_bf16x3_unsupported():
     import paper_1805_06018_gb300 as pcg
     from paper_1805_06018_gb300.binding import PC_ERR_UNSUPPORTED
     shape = (24, 20, 18)
     cells = workloads.regular_grid(shape, (2, 2, 2))
     kern = workloads.GaussianAxis3D(lambda x: 1.5 + 0 * x[..., 0], lambda x: 1.2 + 0 * x[..., 0],
                                     lambda x: 1.0 + 0 * x[..., 0], 4)
-    op, _ = make_pair(shape, cells, kern, "fp32")
+    op, _ = make_pair(shape, cells, kern, "bf16x3")
     with pytest.raises(pcg.PCError) as ei:
         run_adjoint(op, workloads.rhs(76, 1, shape))
     assert ei.value.status == PC_ERR_UNSUPPORTED

@@ -96,14 +96,30 @@ def test_workload_512_cells():
     _assert_within_adjoint_bound(op, orc, Z, Y, eta)
 
 
-def test_estimator_3d_unsupported():
+def test_estimator_3d_fp32():
+    """3D cells (closed boxes, facet voxels in every cell holding them): the
+    per-cell bound against the oracle on true A* Z."""
+    shape = (14, 12, 10)
+    cells = workloads.regular_grid(shape, (3, 3, 2))
+    kern = workloads.Skewed([0.7, -0.4, 0.3], lambda x: 1.1 + 0.4 * np.sin(x[..., 0] / 5.0), 3)
+    op, orc = make_pair(shape, cells, kern, "fp32")
+    A = workloads.dense_operator(shape, kern)
+    Z = workloads.rhs(85, 6, shape).reshape(6, -1).astype(np.float64)
+    Y = (Z @ A).astype(np.float32).astype(np.float64)
+    eta = op.estimate_cell_errors(_dev(Z, "fp32"), _dev(Y, "fp32"), len(cells))
+    op.check()
+    ref = _assert_within_adjoint_bound(op, orc, Z, Y, eta)
+    assert np.all(ref > 0)
+
+
+def test_estimator_bf16x3_unsupported():
     import paper_1805_06018_gb300 as pcg
     from paper_1805_06018_gb300.binding import PC_ERR_UNSUPPORTED
     shape = (24, 20, 18)
     cells = workloads.regular_grid(shape, (2, 2, 2))
     kern = workloads.GaussianAxis3D(lambda x: 1.5 + 0 * x[..., 0], lambda x: 1.2 + 0 * x[..., 0],
                                     lambda x: 1.0 + 0 * x[..., 0], 4)
-    op, _ = make_pair(shape, cells, kern, "fp32")
+    op, _ = make_pair(shape, cells, kern, "bf16x3")
     z = _dev(workloads.rhs(84, 1, shape), "fp32")
     with pytest.raises(pcg.PCError) as ei:
         op.estimate_cell_errors(z, z, len(cells))
