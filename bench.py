@@ -45,10 +45,13 @@ WORKLOADS = {
     "fp32_512": ("512x512 regular 16x16 grid (r=256), anisotropic Gaussian R=24, 128^2 patch FFTs, 64 RHS",
                  "fft2d_kernel<float,128>", ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_overlap.cuh"]),
     "fp32_128c": ("128^3 regular 8x8x8 grid (r=512), axis-aligned Gaussian R=12, 64^3 patch FFTs, 32 RHS",
-                  "fft3d_kernel", ["pc_fft3d.cu", "pc_fftcore.cuh", "pc_ptx.cuh"]),
+                  "fft3d_kernel<false>", ["pc_fft3d.cu", "pc_fftcore.cuh", "pc_ptx.cuh"]),
     "bf16x3_128c": ("128^3 regular 8x8x8 grid (r=512), axis-aligned Gaussian R=12, 64^3 patches: plane FFTs in "
                     "FP32, first-axis DFTs as split-BF16 tensor-core GEMMs, 32 RHS",
                     "tc3d_axis0_kernel", ["pc_tc3d.cu", "pc_tc.cuh", "pc_ptx.cuh"]),
+    "fp32_128c_adjoint": ("adjoint apply (Eq. adjoint_random_z) of the 128^3 regular 8x8x8 grid (r=512) operator, "
+                          "axis-aligned Gaussian R=12, 64^3 patch FFTs, 32 RHS", "fft3d_kernel<true>",
+                          ["pc_fft3d.cu", "pc_fftcore.cuh", "pc_ptx.cuh"]),
     "fp32_512_adjoint": ("adjoint apply (Eq. adjoint_random_z) of the 512x512 regular 16x16 grid (r=256) "
                          "operator, anisotropic Gaussian R=24, 128^2 patch FFTs, 64 RHS",
                          "fft2d_kernel<float,128,true>", ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh",
@@ -69,6 +72,7 @@ WORKLOADS = {
 WORKLOAD_OPERATOR = {"fp32_512": ("fp32_512", "fp32"), "fp32_512_adjoint": ("fp32_512", "fp32"),
                      "fp32_512_estimator": ("fp32_512", "fp32"), "fp32_512_block": ("fp32_512", "fp32"),
                      "fp32_128c": ("fp32_128c", "fp32"), "bf16x3_128c": ("fp32_128c", "bf16x3"),
+                     "fp32_128c_adjoint": ("fp32_128c", "fp32"),
                      "adaptive_1024": ("adaptive_1024", "fp32")}
 
 
