@@ -282,6 +282,37 @@ pc_status pc_entries(pc_operator *op, int64_t n, const int64_t *rows, const int6
                      pc_stream stream);
 
 /* ---------------------------------------------------------------------
+ * Incremental estimator for the adaptive construction (Algorithm 1,
+ * Section 2.8).  Y~ = A~* Z = sum_k w_k . c_k with the unweighted
+ * correlations c_k = flip(phi_k^E) * Z on bbox(U_k) (Eq. adjoint_random_z).
+ * c_k depends only on phi_k^E and bbox(U_k), so between the operators of
+ * successive refinement passes it is recomputed only for sample points that
+ * are new or whose extension changed (a new neighbour); the rest are kept.
+ * --------------------------------------------------------------------- */
+typedef struct pc_estimator pc_estimator;
+
+/* q probes Z and Y = A* Z (device, [q][N] with strides ldz, ldy >= N, in
+ * `prec`, PC_FP32 or PC_FP64) on the 2D box `box`; both stay owned by the
+ * caller and must outlive the estimator.  Allocates Y~ scratch (q * N). */
+pc_status pc_estimator_create(pc_context *ctx, const pc_box *box, pc_precision prec, int32_t q, const void *z,
+                              int64_t ldz, const void *y, int64_t ldy, pc_estimator **est);
+
+/* eta[C] = (1/sqrt(q)) ||Y~[C, .] - Y[C, .]|| for every leaf cell C of op
+ * (Eq. randomized_estimator_ec), as pc_estimate_cell_errors, with Y~ formed
+ * from the kept and the recomputed correlations: a sample point's block is
+ * kept when its coordinates, bbox(U_k), patch tiling and phi_k^E (compared
+ * by a 64-bit hash of its FP64 values) are unchanged.  *recomputed (if not
+ * NULL) receives the number of points recomputed.  op must be a 2D operator
+ * on the estimator's box in its precision; it is read only during the call.
+ * Each output sums its terms in a fixed order (bitwise reproducible); the
+ * result agrees with pc_estimate_cell_errors up to rounding (the two sum
+ * the terms in different orders).  Synchronises `stream`. */
+pc_status pc_estimator_update(pc_estimator *est, pc_operator *op, double *eta, int32_t *recomputed,
+                              pc_stream stream);
+
+pc_status pc_estimator_destroy(pc_estimator *est);
+
+/* ---------------------------------------------------------------------
  * Block apply (Section 3.3).  For closed boxes T (targets) and S (sources)
  * inside Omega, and x_S extended by zero outside S:
  *   forward  y_T = A~[T, S] x_S

@@ -21,8 +21,13 @@ the largest are a tie, won by the lowest i.  The split is at
 floor((c_min + c_max) / 2).  batch > 1 splits up to that many leaves per
 pass (largest eta_C first); batch = 1 is Algorithm 1 as printed.
 
-Each pass rebuilds the operator; the incremental update of A~* Z (only the
-convolutions of new or re-extended points) is not implemented.
+Each pass rebuilds the operator (geometry, weights and spectra in libpc).
+Y~ = A~* Z is updated incrementally, as Algorithm 1 does (`incremental`,
+the default): the correlations flip(phi_k^E) * Z of sample points whose
+phi_k^E and bbox(U_k) are unchanged are kept from the previous pass, and
+only new points and points with a new neighbour are recomputed
+(pc_estimator_update).  With incremental=False every pass recomputes all of
+them (pc_estimate_cell_errors).
 """
 from __future__ import annotations
 
@@ -31,7 +36,7 @@ from typing import Callable, List, Tuple
 
 import numpy as np
 
-from .binding import Operator, pc_extend_impulse, pc_sample_points
+from .binding import Estimator, Operator, pc_extend_impulse, pc_sample_points
 
 
 def _first_cells(shape) -> List[Tuple[List[int], List[int]]]:
@@ -75,10 +80,15 @@ def _direction(shape, lo, hi, point_index, phiE, R) -> int:
 
 
 def construct(ctx, shape, impulse: Callable[[np.ndarray], np.ndarray], R: int, Z, Y, tau: float,
-              precision: str = "fp32", max_passes: int = 100, batch: int = 1, **tune):
-    """Algorithm 1.  Returns (operator, cells [n][2][d], history [(r, eta_Omega)])."""
+              precision: str = "fp32", max_passes: int = 100, batch: int = 1, incremental: bool = True,
+              stats: dict = None, **tune):
+    """Algorithm 1.  Returns (operator, cells [n][2][d], history [(r, eta_Omega)]).
+    If `stats` is a dict it receives "recomputed": the number of sample
+    points whose correlations each pass computed."""
     shape = tuple(int(n) for n in shape)
     q = Z.shape[0]
+    est = Estimator(ctx, shape, Z, Y, precision) if incremental else None
+    recomputed = []
     ynorm = float(np.linalg.norm(Y.reshape(q, -1).double().cpu().numpy())) / np.sqrt(q)
     cells = _first_cells(shape)
     known = {}
@@ -95,7 +105,11 @@ def construct(ctx, shape, impulse: Callable[[np.ndarray], np.ndarray], R: int, Z
         if op is not None:
             op.close()
         op = Operator(ctx, shape, arr, R, phi, precision=precision, **tune)
-        eta_c = op.estimate_cell_errors(Z, Y, len(cells))
+        if est is not None:
+            eta_c, nrec = est.update(op, len(cells))
+        else:
+            eta_c, nrec = op.estimate_cell_errors(Z, Y, len(cells)), len(pts)
+        recomputed.append(nrec)
         eta_o = float(np.sqrt(np.sum(eta_c ** 2))) / ynorm
         history.append((len(pts), eta_o))
         if eta_o <= tau:
@@ -116,4 +130,8 @@ def construct(ctx, shape, impulse: Callable[[np.ndarray], np.ndarray], R: int, Z
             m = (lo[i] + hi[i]) // 2
             cells.append((lo, [m if a == i else hi[a] for a in range(len(shape))]))
             cells.append(([m if a == i else lo[a] for a in range(len(shape))], hi))
+    if est is not None:
+        est.close()
+    if stats is not None:
+        stats["recomputed"] = recomputed
     return op, np.array(cells), history

@@ -103,6 +103,11 @@ _PROTOS = {
     "pc_entries": (ctypes.c_int, [_VP, ctypes.c_int64, _VP, _VP, _VP, _VP]),
     "pc_apply_host": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, ctypes.c_int32,
                                      ctypes.c_int32, _VP]),
+    "pc_estimator_create": (ctypes.c_int, [_VP, ctypes.POINTER(pc_box), ctypes.c_int, ctypes.c_int32, _VP,
+                                           ctypes.c_int64, _VP, ctypes.c_int64, ctypes.POINTER(_VP)]),
+    "pc_estimator_update": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
+                                           _VP]),
+    "pc_estimator_destroy": (ctypes.c_int, [_VP]),
     "pc_block_plan_create": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(_VP)]),
     "pc_block_apply": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
     "pc_block_plan_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
@@ -388,6 +393,45 @@ class Operator:
         if getattr(self, "handle", None):
             h, self.handle = self.handle, None
             _check(lib().pc_operator_destroy(h), self.ctx.handle)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Estimator:
+    """Incremental randomized estimator (Algorithm 1): Z and Y = A* Z are
+    CUDA tensors [q, *box] kept alive by this object; update(op) returns the
+    per-cell estimates of op and the number of sample points whose
+    correlations were recomputed."""
+
+    def __init__(self, ctx: Context, shape, z, y, precision: str = "fp32"):
+        self.ctx = ctx
+        self.z, self.y = z.contiguous(), y.contiguous()
+        N = int(np.prod(shape))
+        q = self.z.numel() // N
+        b = _box(shape)
+        h = _VP()
+        _check(lib().pc_estimator_create(ctx.handle, ctypes.byref(b), PRECISIONS[precision], ctypes.c_int32(q),
+                                         _VP(self.z.data_ptr()), ctypes.c_int64(N), _VP(self.y.data_ptr()),
+                                         ctypes.c_int64(N), ctypes.byref(h)), ctx.handle)
+        self.handle = h
+        self.recomputed_total = 0
+
+    def update(self, op: "Operator", num_cells: int, stream=None):
+        eta = np.zeros(num_cells, dtype=np.float64)
+        rec = ctypes.c_int32()
+        _check(lib().pc_estimator_update(self.handle, op.handle, eta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         ctypes.byref(rec), _VP(_stream_ptr(stream))), self.ctx.handle)
+        self.recomputed_total += rec.value
+        return eta, rec.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            h, self.handle = self.handle, None
+            _check(lib().pc_estimator_destroy(h), self.ctx.handle)
 
     def __del__(self):
         try:

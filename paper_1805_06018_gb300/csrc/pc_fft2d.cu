@@ -462,7 +462,8 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
                               y0 + int64_t(oy) * p.n[1], y1 + int64_t(oy) * p.n[1], has1, o1, L2, p.n[1]);
             }
         } else {
-            // adjoint: the n1 x n2 input box, weighted by w_k, added at (i0, j0)
+            // adjoint: the n1 x n2 input box, weighted by w_k, added at (i0, j0);
+            // in store mode (incremental estimator) stored unweighted to the tile's block
             for (int n = line; n < n1; n += LINES) {
                 const T *wr = wt + int64_t(n) * tile.w_ld[0];
                 T wv[R1];
@@ -473,6 +474,19 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
                 for (int j = 0; j < R1; ++j) a[j] = S[n * P + ((t + R2 * j) ^ swz(n))];
                 RowScratch<P, C> scr{S, n};
                 fft_line<P, true>(a, tw, t, scr, lmask);
+                if (p.store) {
+                    const StoreDesc sd = p.store[ti];
+                    T *st0 = static_cast<T *>(p.store_base) + sd.off + int64_t(b0) * sd.ld_rhs + int64_t(n) * sd.ld_row;
+#pragma unroll
+                    for (int j = 0; j < R1; ++j) {
+                        const int col = t + R2 * j;
+                        if (col < n2) {
+                            st0[col] = a[j].x;
+                            if (has1) st0[sd.ld_rhs + col] = a[j].y;
+                        }
+                    }
+                    continue;
+                }
 #pragma unroll
                 for (int j = 0; j < R1; ++j) a[j] = C{a[j].x * wv[j], a[j].y * wv[j]};
                 const int oy = i0 + n;

@@ -7,6 +7,7 @@
 #include <array>
 #include <cstdint>
 #include <string>
+#include <map>
 #include <unordered_map>
 #include <vector>
 
@@ -91,6 +92,16 @@ struct Schedule {
 void build_schedule(const Geometry &g, int R, int T, const WindowSplit &ws, const std::vector<int64_t> &w_off,
                     Schedule &s);
 
+// Where the 2D adjoint kernel's store mode writes a tile's unweighted
+// correlation block: element (b, row, col) of the tile's input box goes to
+// store_base[off + b * ld_rhs + row * ld_row + col].
+struct StoreDesc {
+    int64_t off;
+    int64_t ld_rhs;
+    int32_t ld_row;
+    int32_t pad_;
+};
+
 // Kernel parameter block shared by the 2D and 3D fused kernels.
 struct ApplyParams {
     const void *x;
@@ -115,6 +126,10 @@ struct ApplyParams {
     const void *w;              // weights (compute precision)
     const void *tw;             // W_P^k, k < P, compute precision complex
     int64_t total_items;
+    // 2D adjoint only: when set, each tile's correlation flip(phi) * x over its
+    // input box is stored unweighted (incremental estimator), not added to y
+    const StoreDesc *store;
+    void *store_base;
 };
 
 // One request on one operator inside a launch.
@@ -240,8 +255,37 @@ struct pc_operator {
     std::vector<int32_t> color_start_h;
     std::vector<pc::Tile> tiles_h;
     std::vector<int32_t> dep_start_h, dep_h;
+    // per sample point: coordinates, bbox(U_k) origin and extents (axes beyond d: 0 and 1),
+    // and a 64-bit FNV-1a hash of phi_k^E's FP64 bytes (incremental estimator)
+    std::vector<int32_t> pts_h, bb_lo_h, bb_ext_h;
+    std::vector<uint64_t> phiE_hash;
     // plain-path scratch (lazily allocated)
     void *plain = nullptr;
+};
+
+// Incremental randomized estimator (Algorithm 1): the probes Z and Y = A* Z
+// (caller-owned, device), Y~ scratch, and per sample point (keyed by its
+// coordinates) the unweighted correlations flip(phi_k^E) * Z on bbox(U_k),
+// kept in an arena as [nsub^2][q][e0][e1] blocks between operators.
+struct pc_estimator {
+    struct Entry {
+        int32_t bb_lo[2], bb_ext[2];
+        uint64_t hash;           // of phi_k^E
+        int32_t P, T, nsub;      // the tiling that produced the block
+        int64_t off, len;        // elements in the arena
+    };
+    pc_context *ctx = nullptr;
+    pc_precision prec = PC_FP32;
+    size_t elem = 4;
+    int64_t shape[2] = {0, 0};
+    int64_t N = 0;
+    int32_t q = 0;
+    const void *z = nullptr, *y = nullptr;
+    int64_t ldz = 0, ldy = 0;
+    void *d_yt = nullptr;        // [q][N]
+    void *arena = nullptr;
+    std::map<std::pair<int32_t, int32_t>, Entry> cache;
+    int64_t recomputed_total = 0;
 };
 
 // Block apply (Section 3.3): the operator's tiles that contribute to
@@ -319,6 +363,13 @@ cudaError_t launch_entries(pc_precision prec, int64_t n, const int64_t *rows, co
 // grow the on-demand device buffers of an apply of nrhs vectors (pc_api.cpp)
 pc_status prepare_batch(pc_operator *op, int32_t nrhs);
 // error estimator (pc_estimate.cu): out[c] = sum over cell c and q columns of (yt - y)^2, FP64
+// incremental estimator (pc_incremental.cu): copy kept correlation blocks
+// (copies[i] = {src, dst, len} in elements) and form
+// yt[b][x] = sum_{k in points of cell_of[x]} w_k[x] * sum_s c_{k,s}[b][x - lo_k]
+cudaError_t launch_block_copies(pc_precision prec, const int64_t *copies, int32_t n, const void *src, void *dst,
+                                cudaStream_t s);
+cudaError_t launch_corr_combine(pc_precision prec, const EntryData &e, const void *w, const void *c,
+                                const int64_t *blk_off, int32_t nsub2, int32_t q, void *yt, int64_t N, cudaStream_t s);
 cudaError_t launch_cell_sqdiff(pc_precision prec, const void *yt, int64_t ldyt, const void *y, int64_t ldy, int32_t q,
                                const int32_t *cells, int32_t ncells, int64_t n1, int64_t n2, double *out,
                                cudaStream_t s);

@@ -95,3 +95,49 @@ def test_planted_direction_mistake_is_caught(monkeypatch):
     cells, _ = construct(shape, _impulse(shape, kern), 6, Z, Y, tau=1e-3, max_passes=8)
     m1 = (shape[1] - 1) // 2
     assert {(int(c[0][1]), int(c[1][1])) for c in cells} != {(0, m1), (m1, shape[1] - 1)}
+
+
+def test_update_reuses_exactly_the_unaffected_correlations():
+    """Section 2.8: after a refinement only the correlations of sample points
+    that are new or have a new neighbour change.  Pinned on the oracle: every
+    other point keeps bbox(U_k) and phi_k^E exactly, so its correlation
+    flip(phi_k^E) * z on bbox(U_k) is reusable; and an update that reuses them
+    and recomputes only the others reproduces A~* Z of the refined operator."""
+    from oracle.adaptive import initial_cells, subdivide
+    shape = (40, 36)
+    kern = workloads.Skewed([0.6, -0.3], lambda x: 1.0 + 0.4 * np.sin(x[..., 0] / 6.0), 4)
+    impulse = _impulse(shape, kern)
+    cells_a = subdivide(subdivide(initial_cells(shape), 0, 0), 2, 1)
+    cells_b = subdivide(cells_a, 3, 1)
+    ga, gb = Grid(shape, cells_a), Grid(shape, cells_b)
+    oa = PCOracle(shape, cells_a, impulse(ga.points), 4)
+    ob = PCOracle(shape, cells_b, impulse(gb.points), 4)
+    ia = {tuple(p): k for k, p in enumerate(ga.points)}
+    z = np.random.default_rng(5).standard_normal((2,) + shape)
+
+    def corr(orc, k):
+        # flip(phi_k^E) * z restricted to bbox(U_k), unweighted
+        w = [np.zeros_like(W) for W in orc.W]
+        lo, hi = orc.grid.bbox_lo[k], orc.grid.bbox_hi[k]
+        w[k] = np.ones(orc.grid.bbox_shape(k))
+        one = PCOracle(shape, orc.grid.cells, orc.phi, orc.R, weights=w)
+        one.phiE = orc.phiE
+        return one.apply_adjoint(z)[(slice(None),) + tuple(slice(a, b + 1) for a, b in zip(lo, hi))]
+
+    affected = 0
+    yt = np.zeros((2,) + shape)
+    for k, p in enumerate(gb.points):
+        ka = ia.get(tuple(p))
+        new_nbr = ka is None or set(map(tuple, gb.points[gb.nbrs[k]])) != set(map(tuple, ga.points[ga.nbrs[ka]]))
+        if not new_nbr:
+            assert np.array_equal(ob.phiE[k], oa.phiE[ka])
+            assert np.array_equal(gb.bbox_lo[k], ga.bbox_lo[ka]) and np.array_equal(gb.bbox_hi[k], ga.bbox_hi[ka])
+            c = corr(oa, ka)
+        else:
+            affected += 1
+            c = corr(ob, k)
+        lo, hi = gb.bbox_lo[k], gb.bbox_hi[k]
+        yt[(slice(None),) + tuple(slice(a, b + 1) for a, b in zip(lo, hi))] += ob.W[k] * c
+    assert 0 < affected < gb.r
+    ref = ob.apply_adjoint(z)
+    assert np.max(np.abs(yt - ref)) <= 1e-12 * np.abs(ref).max()
