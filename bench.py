@@ -64,6 +64,10 @@ WORKLOADS = {
                        "T = [128,255]^2, S = [256,383]x[128,255] (adjacent 128^2 boxes, an H-matrix near-field "
                        "block), 64 RHS", "fft2d_kernel<float,128>",
                        ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_overlap.cuh"]),
+    "fp32_512_blocks": ("the 100 near-field blocks A~[T_i,S_j] (Section 3.3) of the 512x512 regular 16x16 grid "
+                        "operator for a 4x4 partition into 128^2 boxes (every pair of boxes that touch, itself "
+                        "included), 64 RHS per block, one plan in two launches", "fft2d_kernel<float,128>",
+                        ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_overlap.cuh"]),
     "adaptive_1024": ("1024x1024 adaptive quadtree (r=1579), heavy-tailed R=64 (2x2 kernel sub-windows), "
                       "128^2 patch FFTs, 32 RHS", "fft2d_kernel<float,128>",
                       ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_overlap.cuh"]),
@@ -71,6 +75,7 @@ WORKLOADS = {
 # workload name -> (operator configuration, precision)
 WORKLOAD_OPERATOR = {"fp32_512": ("fp32_512", "fp32"), "fp32_512_adjoint": ("fp32_512", "fp32"),
                      "fp32_512_estimator": ("fp32_512", "fp32"), "fp32_512_block": ("fp32_512", "fp32"),
+                     "fp32_512_blocks": ("fp32_512", "fp32"),
                      "fp32_128c": ("fp32_128c", "fp32"), "bf16x3_128c": ("fp32_128c", "bf16x3"),
                      "fp32_128c_adjoint": ("fp32_128c", "fp32"),
                      "adaptive_1024": ("adaptive_1024", "fp32")}
@@ -81,12 +86,26 @@ BLOCK_T = ((128, 128), (255, 255))
 BLOCK_S = ((256, 128), (383, 255))
 
 
-def block_algorithmic_flops(lo, hi, R, nrhs):
+def near_field_blocks(n=512, box=128):
+    """(T, S) pairs of a partition of [0, n)^2 into box x box squares: every
+    ordered pair of squares that touch (itself included)."""
+    m = n // box
+    out = []
+    for i0 in range(m):
+        for i1 in range(m):
+            for j0 in range(max(0, i0 - 1), min(m, i0 + 2)):
+                for j1 in range(max(0, i1 - 1), min(m, i1 + 2)):
+                    out.append((((i0 * box, i1 * box), (i0 * box + box - 1, i1 * box + box - 1)),
+                                ((j0 * box, j1 * box), (j0 * box + box - 1, j1 * box + box - 1))))
+    return out
+
+
+def block_algorithmic_flops(lo, hi, R, nrhs, block=None):
     """Nominal FLOPs of a block apply: over the terms k whose bbox(U_k) meets
     S and whose reach bbox(U_k) (+) [-R, R]^2 meets T, 5 L log2 L + 3 L with
     L = prod_a (|S cap bbox(U_k)|_a + 2R), the linear-convolution extent of
     the translated term (Section 3.3)."""
-    (slo, shi), (tlo, thi) = BLOCK_S, BLOCK_T
+    (tlo, thi), (slo, shi) = block if block is not None else (BLOCK_T, BLOCK_S)
     flops = 0.0
     terms = 0
     for a, b in zip(lo, hi):
@@ -251,7 +270,7 @@ def run_reference(args, rank, world):
     from oracle import build as obuild
     obuild.build()
     wl = configs.get(WORKLOAD_OPERATOR[args.workload][0])
-    if args.workload.endswith("_block"):
+    if args.workload.endswith("_block") or args.workload.endswith("_blocks"):
         return run_reference_block(args, wl)
     x = workloads.rhs(wl.rhs_seed, wl.nrhs, wl.shape)
     from oracle import PCOracle
@@ -415,6 +434,163 @@ def run_block(args, rank, world):
         dist.destroy_process_group()
 
 
+def run_blocks(args, rank, world):
+    """One step = pc_block_apply_many of the 100 near-field blocks, 64 RHS
+    each; value counts block right-hand sides per second.  The same blocks
+    as 100 single-block plans, one after another, are timed beside it."""
+    import torch
+    import workloads
+    from workloads import configs
+    import paper_1805_06018_gb300 as pcg
+    from paper_1805_06018_gb300 import build as libbuild
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(rank % max(1, torch.cuda.device_count()))
+    libbuild.build()
+    wl = configs.get("fp32_512", **({"nrhs": args.nrhs} if args.nrhs > 0 else {}))
+    desc, kname, _ = WORKLOADS[args.workload]
+    pts = pcg.pc_sample_points(wl.shape, wl.cells)
+    phi = workloads.impulse_windows(wl.shape, pts, wl.kernel)
+    ctx = pcg.Context(torch.cuda.current_device())
+    op = pcg.Operator(ctx, wl.shape, wl.cells, wl.radius, phi, precision="fp32")
+    blocks = near_field_blocks()
+    nb = len(blocks)
+    plan = pcg.BlockPlan(op, [b[0][0] for b in blocks], [b[0][1] for b in blocks], [b[1][0] for b in blocks],
+                         [b[1][1] for b in blocks])
+    terms, tiles = plan.info()
+    nS = [int(np.prod(sh)) for sh in plan.s_shapes]
+    nT = [int(np.prod(sh)) for sh in plan.t_shapes]
+    xh = [workloads.rhs(wl.rhs_seed + i, wl.nrhs, sh) for i, sh in enumerate(plan.s_shapes)]
+    xs = [torch.from_numpy(a).cuda() for a in xh]
+    ys = [torch.empty((wl.nrhs,) + sh, dtype=torch.float32, device="cuda") for sh in plan.t_shapes]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    xp, yp = [x.data_ptr() for x in xs], [y.data_ptr() for y in ys]
+
+    def step():
+        plan.pc_block_apply_many(wl.nrhs, xp, nS, yp, nT, sp)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.check()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev0[i].record(stream)
+            step()
+            ev1[i].record(stream)
+        torch.cuda.synchronize()
+    plan.check()
+    step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
+    tot_ms = float(step_ms.sum())
+    if world > 1:
+        dist.barrier()
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * args.steps * wl.nrhs * nb / (tot_ms / 1e3)
+    # the same blocks as separate single-block plans
+    singles = [pcg.BlockPlan(op, *b[0], *b[1]) for b in blocks]
+    for pl, x, y, a, c in zip(singles, xp, yp, nS, nT):
+        pl.pc_block_apply(wl.nrhs, x, a, y, c, sp)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sep = []
+    for _ in range(max(3, min(args.steps // 10, 10))):
+        flush.fill_(1.0)
+        s0.record(stream)
+        for pl, x, y, a, c in zip(singles, xp, yp, nS, nT):
+            pl.pc_block_apply(wl.nrhs, x, a, y, c, sp)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        sep.append(s0.elapsed_time(s1))
+    for pl in singles:
+        pl.close()
+    # end to end with host buffers (pinned), copies in the timed region
+    xph = [torch.from_numpy(a).pin_memory() for a in xh]
+    yph = [torch.empty(y.shape, dtype=torch.float32).pin_memory() for y in ys]
+    e2e_steps = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for x, h in zip(xs, xph):
+            x.copy_(h, non_blocking=True)
+        step()
+        for y, h in zip(ys, yph):
+            h.copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_value = world * e2e_steps * wl.nrhs * nb / (time.perf_counter() - t0)
+    lo, hi = pcg.pc_neighbourhood_boxes(wl.shape, wl.cells)
+    flops = 0.0
+    nominal = 0
+    for b in blocks:
+        f, t_ = block_algorithmic_flops(lo, hi, wl.radius, wl.nrhs, block=b)
+        flops += f
+        nominal += t_
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    step_mean = float(step_ms.mean())
+    achieved = flops / (step_mean / 1e3) / 1e12
+    rounds = (nb + 63) // 64
+    line = {"metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "blocks": nb, "counted": "block right-hand sides (blocks x RHS)",
+                       "global_batch": wl.nrhs * world, "per_gpu_batch": wl.nrhs, "grid": list(wl.shape),
+                       "radius": wl.radius, "terms": terms, "tiles": tiles, "parallelism": "replicas%d" % world,
+                       "l2": "inputs (400 MB) larger than L2, and flushed between steps (256 MB write)"},
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                           "per": "%d blocks x %d RHS" % (nb, wl.nrhs)},
+            "separate_single_block_plans": {"value": nb * wl.nrhs / (np.mean(sep) / 1e3), "unit": "RHS/s",
+                                            "ms": float(np.mean(sep)), "kernels": 2 * nb},
+            "e2e": {"value": e2e_value, "unit": "RHS/s",
+                    "h2d_bytes_per_step": int(sum(a.nbytes for a in xh)),
+                    "d2h_bytes_per_step": int(sum(y.numel() * 4 for y in ys))},
+            "gpu_launches": 2 * rounds * args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak, "traffic": profiled_traffic(args.workload), "kernel": kname,
+                         "kernel_ms": step_mean,
+                         "timed": "%d rounds of zero fill + patch kernel (events around the call)" % rounds,
+                         "algorithmic_flop_per_launch": flops / rounds, "nominal_terms": nominal,
+                         "peak_basis": "FP32 FMA pipe: SMs x 128 lanes x 2 x %.0f MHz" % sm_max},
+            "clocks": clk.summary()}
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        from oracle import PCOracle
+        from oracle.block import apply_block_translated
+        orc = PCOracle.from_workload(wl)
+        done = 0
+        t0 = time.perf_counter()
+        while done == 0 or time.perf_counter() - t0 < args.cpu_seconds:
+            (tlo, thi), (slo, shi) = blocks[done % nb]
+            apply_block_translated(orc, tlo, thi, slo, shi, xh[done % nb][:1])
+            done += 1
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": done / el, "unit": "RHS/s", "cores": 1, "kind": "oracle",
+                                "sample": "%d block right-hand sides through the translated block apply in %.1f s"
+                                          % (done, el)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    op.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def serve_operators(pcg, ctx, with_3d=True):
     """The served operator mix: 2D 256^2 (9x9 grid), 512^2 (the benchmark
     operator), 1024^2 (adaptive quadtree, heavy-tailed, R = 64) and 2048^2
@@ -553,6 +729,8 @@ def main():
         return run_serve(args)
     if args.workload.endswith("_block"):
         return run_block(args, rank, world)
+    if args.workload.endswith("_blocks"):
+        return run_blocks(args, rank, world)
 
     import torch
     import torch.distributed as dist

@@ -353,12 +353,29 @@ pc_status pc_block_plan_create(pc_operator *op, const int64_t *t_lo, const int64
  * first call with a larger batch grows the plan's ordering flags (and
  * synchronises the device).  Calls on one plan must be serialised (one
  * stream); different plans and the operator's own applies may overlap.
- * nrhs = 0 is a no-op. */
+ * nrhs = 0 is a no-op.  PC_ERR_ARG for a plan of several blocks. */
 pc_status pc_block_apply(pc_block_plan *plan, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
                          pc_stream stream);
 
-/* terms: distinct k with a kept tile (at most r_S, r_T for the adjoint);
- * tiles: kept tiles.  Either pointer may be NULL. */
+/* Several blocks of one operator and one direction in one plan: box bounds
+ * as [nblocks][d] host arrays (block i at t_lo + i*d, ...).  Applying it runs
+ * every block in one persistent launch (rounds of at most 64 blocks), each
+ * block with its own tiles, colour order and ordering flags, so each block's
+ * result is bitwise that of a single-block plan of that block; a low-rank
+ * builder's many small blocks then fill the GPU together. */
+pc_status pc_block_plan_create_many(pc_operator *op, int32_t nblocks, const int64_t *t_lo, const int64_t *t_hi,
+                                    const int64_t *s_lo, const int64_t *s_hi, int32_t adjoint, pc_block_plan **plan);
+
+/* Y_i[b] = block_i X_i[b] for every block i of the plan and b < nrhs: x, y,
+ * ldx, ldy are host arrays with one entry per block (device pointers and
+ * strides as in pc_block_apply).  The blocks' y arrays must not overlap one
+ * another.  Same stream semantics as pc_block_apply. */
+pc_status pc_block_apply_many(pc_block_plan *plan, int32_t nrhs, const void *const *x, const int64_t *ldx,
+                              void *const *y, const int64_t *ldy, pc_stream stream);
+
+/* terms: sum over the blocks of the distinct k with a kept tile (at most
+ * r_S, r_T for the adjoint, per block); tiles: kept tiles.  Either pointer
+ * may be NULL. */
 pc_status pc_block_plan_info(const pc_block_plan *plan, int32_t *terms, int32_t *tiles);
 
 /* As pc_operator_check, for the plan's launches: synchronises the plan's

@@ -110,6 +110,10 @@ _PROTOS = {
     "pc_estimator_destroy": (ctypes.c_int, [_VP]),
     "pc_block_plan_create": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(_VP)]),
     "pc_block_apply": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
+    "pc_block_plan_create_many": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, ctypes.c_int32,
+                                                 ctypes.POINTER(_VP)]),
+    "pc_block_apply_many": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_int64), _VP]),
     "pc_block_plan_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "pc_block_plan_check": (ctypes.c_int, [_VP]),
     "pc_block_plan_destroy": (ctypes.c_int, [_VP]),
@@ -443,22 +447,29 @@ class Estimator:
 class BlockPlan:
     """Block apply (Section 3.3): y_T = A~[T, S] x_S, or (A~*)[T, S] x_S with
     adjoint=True, for closed boxes T = [t_lo, t_hi], S = [s_lo, s_hi]
-    (pc_block_plan_create / pc_block_apply).  The operator must outlive the
-    plan."""
+    (pc_block_plan_create / pc_block_apply).  Bounds given as [nblocks][2]
+    arrays make a plan of several blocks that apply_many runs in one launch
+    (pc_block_plan_create_many / pc_block_apply_many).  The operator must
+    outlive the plan."""
 
     def __init__(self, op: Operator, t_lo, t_hi, s_lo, s_hi, adjoint: bool = False):
         self.op = op
-        box = [np.ascontiguousarray(b, dtype=np.int64) for b in (t_lo, t_hi, s_lo, s_hi)]
-        self.t_shape = tuple(int(b - a + 1) for a, b in zip(box[0], box[1]))
-        self.s_shape = tuple(int(b - a + 1) for a, b in zip(box[2], box[3]))
+        d = len(op.shape)
+        box = [np.ascontiguousarray(np.asarray(b, dtype=np.int64).reshape(-1, d)) for b in (t_lo, t_hi, s_lo, s_hi)]
+        self.nblocks = len(box[0])
+        if any(len(b) != self.nblocks for b in box):
+            raise ValueError("t_lo, t_hi, s_lo, s_hi must hold the same number of blocks")
+        self.t_shapes = [tuple(int(v) for v in h - l + 1) for l, h in zip(box[0], box[1])]
+        self.s_shapes = [tuple(int(v) for v in h - l + 1) for l, h in zip(box[2], box[3])]
+        self.t_shape, self.s_shape = self.t_shapes[0], self.s_shapes[0]
         self.adjoint = bool(adjoint)
         h = _VP()
-        _check(lib().pc_block_plan_create(op.handle, *[_ptr(b) for b in box], ctypes.c_int32(int(adjoint)),
-                                          ctypes.byref(h)), op.ctx.handle)
+        _check(lib().pc_block_plan_create_many(op.handle, ctypes.c_int32(self.nblocks), *[_ptr(b) for b in box],
+                                               ctypes.c_int32(int(adjoint)), ctypes.byref(h)), op.ctx.handle)
         self.handle = h
 
     def info(self):
-        """(terms, tiles): distinct k and tiles the block touches."""
+        """(terms, tiles): distinct k and tiles the blocks touch (summed over blocks)."""
         terms, tiles = ctypes.c_int32(), ctypes.c_int32()
         _check(lib().pc_block_plan_info(self.handle, ctypes.byref(terms), ctypes.byref(tiles)))
         return terms.value, tiles.value
@@ -467,11 +478,24 @@ class BlockPlan:
         _check(lib().pc_block_apply(self.handle, ctypes.c_int32(nrhs), _VP(x_ptr), ctypes.c_int64(ldx),
                                     _VP(y_ptr), ctypes.c_int64(ldy), _VP(stream_ptr)), self.op.ctx.handle)
 
+    def pc_block_apply_many(self, nrhs: int, x_ptrs, ldx, y_ptrs, ldy, stream_ptr: int):
+        n = self.nblocks
+        xs = (_VP * n)(*[_VP(v) for v in x_ptrs])
+        ys = (_VP * n)(*[_VP(v) for v in y_ptrs])
+        lx = (ctypes.c_int64 * n)(*ldx)
+        ly = (ctypes.c_int64 * n)(*ldy)
+        _check(lib().pc_block_apply_many(self.handle, ctypes.c_int32(nrhs), xs, lx, ys, ly, _VP(stream_ptr)),
+               self.op.ctx.handle)
+
+    def _dtype(self):
+        import torch
+        return torch.float64 if self.op.precision == "fp64" else torch.float32
+
     def apply(self, x, out=None, stream=None):
-        """x: contiguous CUDA tensor [B, *S] (or [*S]); returns [B, *T] (or [*T])."""
+        """Single-block plans: x is a contiguous CUDA tensor [B, *S] (or [*S]); returns [B, *T] (or [*T])."""
         import torch
         nS, nT = int(np.prod(self.s_shape)), int(np.prod(self.t_shape))
-        want = torch.float64 if self.op.precision == "fp64" else torch.float32
+        want = self._dtype()
         if not (x.is_cuda and x.is_contiguous()) or x.dtype != want:
             raise ValueError("x must be a contiguous CUDA tensor of %s" % want)
         B = x.numel() // nS
@@ -481,6 +505,23 @@ class BlockPlan:
         y = torch.empty(shape, dtype=want, device=x.device) if out is None else out
         self.pc_block_apply(B, x.data_ptr(), nS, y.data_ptr(), nT, _stream_ptr(stream))
         return y
+
+    def apply_many(self, xs, stream=None):
+        """xs: one contiguous CUDA tensor [B, *S_i] per block; returns the [B, *T_i] results."""
+        import torch
+        want = self._dtype()
+        if len(xs) != self.nblocks:
+            raise ValueError("one x per block")
+        B = xs[0].shape[0]
+        ys = []
+        for x, sS, sT in zip(xs, self.s_shapes, self.t_shapes):
+            if not (x.is_cuda and x.is_contiguous()) or x.dtype != want or tuple(x.shape) != (B,) + sS:
+                raise ValueError("each x must be a contiguous CUDA tensor [B, *S_i] of %s" % want)
+            ys.append(torch.empty((B,) + sT, dtype=want, device=x.device))
+        self.pc_block_apply_many(B, [x.data_ptr() for x in xs], [int(np.prod(s)) for s in self.s_shapes],
+                                 [y.data_ptr() for y in ys], [int(np.prod(t)) for t in self.t_shapes],
+                                 _stream_ptr(stream))
+        return ys
 
     def check(self):
         _check(lib().pc_block_plan_check(self.handle), self.op.ctx.handle)

@@ -156,7 +156,9 @@ __device__ __forceinline__ void add_row(const C *a, int t, unsigned lmask, float
     }
 }
 
-template <typename T, int P, bool ADJ>
+// MULTI: launches through a descriptor, which may carry a run table (the
+// claim order across segments); single-apply launches compile without it.
+template <typename T, int P, bool ADJ, bool MULTI>
 __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const LaunchParams lp) {
     using C = typename Cx<T>::type;
     using L = Smem2d<T, P>;
@@ -171,10 +173,13 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw + L::ws + L::sp);
     __shared__ int64_t s_next;
     __shared__ int s_segidx;
+    __shared__ int s_run, s_runcol;
+    __shared__ int64_t s_runbase;
     __shared__ __align__(16) Segment s_seg;          // the current item's request
     __shared__ int s_cstart_buf[kMaxColorsCached + 1];
 
     const int nseg = lp.desc ? lp.desc->nseg : 1;
+    const int nrun = MULTI && lp.desc ? lp.desc->nrun : 0;
     const int64_t total = lp.desc ? lp.desc->total_items : lp.one.p.total_items;
     const int t = threadIdx.x % R2;
     const int line = threadIdx.x / R2;
@@ -221,7 +226,10 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
     // increasing order, and the lowest unfinished item is always one that a
     // CTA is working on, so every dependency wait ends.
     unsigned long long *counter = lp.counter;
-    if (threadIdx.x == 0) s_next = int64_t(atomicAdd(counter, 1ull));
+    if (threadIdx.x == 0) {
+        s_next = int64_t(atomicAdd(counter, 1ull));
+        s_run = 0;
+    }
     for (;;) {
         __syncthreads();
         const int64_t gitem = s_next;
@@ -230,9 +238,19 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
         int segidx = 0;
         if (lp.desc) {
             if (threadIdx.x == 0) {
-                int sx = 0;
-                while (sx + 1 < nseg && lp.desc->seg[sx + 1].item_begin <= gitem) ++sx;
-                s_segidx = sx;
+                if (MULTI && nrun > 0) {
+                    // run table: resume where this CTA's last search ended (its claims increase)
+                    int b = s_run;
+                    while (b + 1 < nrun && lp.desc->run_begin[b + 1] <= gitem) ++b;
+                    s_run = b;
+                    s_runbase = lp.desc->run_begin[b];
+                    s_segidx = lp.desc->run_segcol[2 * b];
+                    s_runcol = lp.desc->run_segcol[2 * b + 1];
+                } else {
+                    int sx = MULTI && cur_seg > 0 ? cur_seg : 0;
+                    while (sx + 1 < nseg && lp.desc->seg[sx + 1].item_begin <= gitem) ++sx;
+                    s_segidx = sx;
+                }
             }
             __syncthreads();
             segidx = s_segidx;
@@ -271,7 +289,15 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
         const T *w = static_cast<const T *>(p.w);
         const C *spec = static_cast<const C *>(p.spec);
         int ti, pair;
-        decode_item(p, s_cstart, item, ti, pair);
+        if (MULTI && nrun > 0) {
+            // within a run: the colour's items in decode_item's order
+            const int64_t local = gitem - s_runbase;
+            const int c = s_runcol, ntc = s_cstart[c + 1] - s_cstart[c];
+            pair = int(local / ntc);
+            ti = s_cstart[c] + int(local % ntc);
+        } else {
+            decode_item(p, s_cstart, item, ti, pair);
+        }
         const Tile tile = p.tiles[ti];
         if (threadIdx.x == 0) mbar_arrive_expect_tx(mbar, uint32_t(H * P * sizeof(C)));
         __syncthreads();   // everyone has read s_next; the spectrum copy is announced
@@ -382,7 +408,8 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
         __syncthreads();
         if (threadIdx.x == 0) publish_pending();
 
-        if (s_next - s_seg.item_begin < p.total_items) prefetch_item<T, ADJ>(p, s_cstart, s_next - s_seg.item_begin);
+        if ((!MULTI || nrun == 0) && s_next - s_seg.item_begin < p.total_items)
+            prefetch_item<T, ADJ>(p, s_cstart, s_next - s_seg.item_begin);
 
         // ---------------- phase B: column FFT, spectral product, inverse column FFT
         if (!mbar_wait_bounded(mbar, phase, kMbarLimit)) {
@@ -545,13 +572,17 @@ cudaError_t launch_zero(const ApplyParams &p, int64_t N, pc_precision prec, cuda
 template <typename T, int P>
 static cudaError_t configure_one(int *ctas_per_sm, size_t *smem) {
     const size_t bytes = Smem2d<T, P>::bytes;
-    cudaError_t e =
-        cudaFuncSetAttribute(fft2d_kernel<T, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fft2d_kernel<T, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    cudaError_t e = cudaSuccess;
+    const void *fns[4] = {reinterpret_cast<const void *>(fft2d_kernel<T, P, false, false>),
+                          reinterpret_cast<const void *>(fft2d_kernel<T, P, true, false>),
+                          reinterpret_cast<const void *>(fft2d_kernel<T, P, false, true>),
+                          reinterpret_cast<const void *>(fft2d_kernel<T, P, true, true>)};
+    for (const void *f : fns)
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
     if (e != cudaSuccess) return e;
     int n = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fft2d_kernel<T, P, false>, KCfg<T, P>::threads, bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fft2d_kernel<T, P, false, false>, KCfg<T, P>::threads,
+                                                      bytes);
     if (e != cudaSuccess) return e;
     if (ctas_per_sm) *ctas_per_sm = n;
     if (smem) *smem = bytes;
@@ -568,14 +599,14 @@ cudaError_t fft2d_configure(int P, pc_precision prec, int *ctas_per_sm, size_t *
     return cudaErrorInvalidValue;
 }
 
-template <bool ADJ>
+template <bool ADJ, bool MULTI>
 static void launch_one(const LaunchParams &lp, int P, pc_precision prec, int ctas, size_t smem, cudaStream_t s) {
     if (prec == PC_FP64)
-        fft2d_kernel<double, 64, ADJ><<<ctas, KCfg<double, 64>::threads, smem, s>>>(lp);
+        fft2d_kernel<double, 64, ADJ, MULTI><<<ctas, KCfg<double, 64>::threads, smem, s>>>(lp);
     else if (P == 64)
-        fft2d_kernel<float, 64, ADJ><<<ctas, KCfg<float, 64>::threads, smem, s>>>(lp);
+        fft2d_kernel<float, 64, ADJ, MULTI><<<ctas, KCfg<float, 64>::threads, smem, s>>>(lp);
     else
-        fft2d_kernel<float, 128, ADJ><<<ctas, KCfg<float, 128>::threads, smem, s>>>(lp);
+        fft2d_kernel<float, 128, ADJ, MULTI><<<ctas, KCfg<float, 128>::threads, smem, s>>>(lp);
 }
 
 cudaError_t launch_fft2d(const ApplyParams &p, int P, pc_precision prec, int ctas, cudaStream_t s, bool adjoint) {
@@ -590,9 +621,9 @@ cudaError_t launch_fft2d(const ApplyParams &p, int P, pc_precision prec, int cta
     lp.counter = reinterpret_cast<unsigned long long *>(p.ctrl);
     lp.status = p.ctrl + 2;
     if (adjoint)
-        launch_one<true>(lp, P, prec, ctas, smem, s);
+        launch_one<true, false>(lp, P, prec, ctas, smem, s);
     else
-        launch_one<false>(lp, P, prec, ctas, smem, s);
+        launch_one<false, false>(lp, P, prec, ctas, smem, s);
     return cudaGetLastError();
 }
 
@@ -634,9 +665,9 @@ cudaError_t launch_round(const LaunchDesc *d_desc, unsigned long long *counter, 
     lp.seg_done = seg_done;
     lp.host_flags = host_flags;
     if (adjoint)
-        launch_one<true>(lp, P, prec, ctas, smem, s);
+        launch_one<true, true>(lp, P, prec, ctas, smem, s);
     else
-        launch_one<false>(lp, P, prec, ctas, smem, s);
+        launch_one<false, true>(lp, P, prec, ctas, smem, s);
     return cudaGetLastError();
 }
 

@@ -144,10 +144,18 @@ struct Segment {
 constexpr int kMaxSegments = 64;
 
 // Device-resident descriptor of a launch that serves several requests.
+// Items are claimed segment by segment, unless nrun > 0: then the launch's
+// item order is the run table, runs of one (segment, colour) each in
+// colour-major order across the segments (run i covers items
+// [run_begin[i], run_begin[i + 1]) of segment run_segcol[2 i], colour
+// run_segcol[2 i + 1], tile-major within the run as decode_item orders a
+// colour), so that independent segments share every colour step.
 struct LaunchDesc {
     int32_t nseg;
-    int32_t pad_;
+    int32_t nrun;
     int64_t total_items;
+    const int64_t *run_begin;       // [nrun + 1]
+    const int32_t *run_segcol;      // [nrun][2]
     Segment seg[kMaxSegments];
 };
 
@@ -288,23 +296,38 @@ struct pc_estimator {
     int64_t recomputed_total = 0;
 };
 
-// Block apply (Section 3.3): the operator's tiles that contribute to
-// A~[T, S] (or (A~*)[T, S]), clipped and re-expressed in block coordinates,
-// with their own ordering flags and control block.
+// Block apply (Section 3.3): for each block of the plan, the operator's tiles
+// that contribute to A~[T, S] (or (A~*)[T, S]), clipped and re-expressed in
+// block coordinates; all blocks' tables concatenated, each block with its own
+// ordering flags; one multi-segment launch runs up to kMaxSegments blocks.
 struct pc_block_plan {
+    struct Block {
+        int64_t t_ext[2], s_ext[2];
+        int64_t nT, nS;
+        int32_t tile_off, n_tiles, cs_off, n_colors, ds_off, dep_off, terms;
+    };
     pc_operator *op = nullptr;
     bool adjoint = false;
-    int64_t t_ext[2] = {0, 0}, s_ext[2] = {0, 0};
-    int64_t nT = 0, nS = 0;
-    int n_tiles = 0, n_colors = 0, terms = 0;
+    std::vector<Block> blocks;
+    int n_tiles = 0, terms = 0;       // totals over the blocks
     pc::Tile *d_tiles = nullptr;
     int32_t *d_color_start = nullptr;
     int32_t *d_dep_start = nullptr;
     int32_t *d_dep = nullptr;
-    uint32_t *d_done = nullptr;
+    uint32_t *d_done = nullptr;       // block b's flags at tile_off * done_cap
     int32_t done_cap = 0;
     int32_t *d_ctrl = nullptr;
     uint32_t epoch = 0;
+    std::vector<int32_t> cs_h;        // host copy of the colour offsets
+    // multi-block launches: per round of kMaxSegments blocks, a descriptor and
+    // a run table (pinned host staging, then device); run_cap runs per round
+    std::vector<pc::LaunchDesc *> h_desc;
+    pc::LaunchDesc *d_desc = nullptr;
+    std::vector<char *> h_runs;
+    char *d_runs = nullptr;
+    int32_t run_cap = 0;
+    uint32_t *d_seg_done = nullptr;
+    cudaEvent_t desc_ev = nullptr;    // after the last descriptor upload
     cudaStream_t last_stream = nullptr;
     bool launched = false;
 };

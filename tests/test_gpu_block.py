@@ -160,3 +160,74 @@ def test_bad_arguments():
     with pytest.raises(pcg.PCError) as ei:
         BlockPlan(op3, (0, 0, 0), (3, 3, 3), (0, 0, 0), (3, 3, 3))
     assert ei.value.status == PC_ERR_UNSUPPORTED
+
+
+def _random_blocks(shape, n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        t = [sorted(rng.integers(0, m, 2)) for m in shape]
+        s = [sorted(rng.integers(0, m, 2)) for m in shape]
+        out.append(([a for a, _ in t], [b for _, b in t], [a for a, _ in s], [b for _, b in s]))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_many_blocks_in_one_launch_are_bitwise_the_single_blocks(prec, adjoint):
+    from paper_1805_06018_gb300 import BlockPlan
+    shape = (40, 36)
+    op, orc = make_pair(shape, workloads.regular_grid(shape, (4, 3)), _kernel(shape, 5), prec)
+    blocks = [tuple(map(list, b)) for b in BOXES] + _random_blocks(shape, 8, 64)
+    plan = BlockPlan(op, *[[b[i] for b in blocks] for i in range(4)], adjoint)
+    rng = np.random.default_rng(65)
+    xs = [_dev(rng.standard_normal((3,) + tuple(sh)), prec) for sh in plan.s_shapes]
+    ys = plan.apply_many(xs)
+    torch.cuda.synchronize()
+    plan.check()
+    for (t_lo, t_hi, s_lo, s_hi), x, y in zip(blocks, xs, ys):
+        one = BlockPlan(op, t_lo, t_hi, s_lo, s_hi, adjoint)
+        assert torch.equal(one.apply(x), y)
+        one.close()
+    for (t_lo, t_hi, s_lo, s_hi), x, y in list(zip(blocks, xs, ys))[:4]:
+        ref = ob.apply_block_translated(orc, t_lo, t_hi, s_lo, s_hi, x.double().cpu().numpy(), adjoint)
+        _check(y.double().cpu().numpy(), ref, prec)
+    plan.close()
+
+
+def test_more_blocks_than_one_launch_holds():
+    """70 blocks: two launch rounds of one plan."""
+    from paper_1805_06018_gb300 import BlockPlan
+    shape = (40, 36)
+    op, _ = make_pair(shape, workloads.regular_grid(shape, (4, 3)), _kernel(shape, 5), "fp32")
+    blocks = _random_blocks(shape, 70, 66)
+    plan = BlockPlan(op, *[[b[i] for b in blocks] for i in range(4)])
+    rng = np.random.default_rng(67)
+    xs = [_dev(rng.standard_normal((2,) + tuple(sh)), "fp32") for sh in plan.s_shapes]
+    ys = plan.apply_many(xs)
+    ys2 = plan.apply_many(xs)   # descriptors reused across calls
+    torch.cuda.synchronize()
+    plan.check()
+    for i in (0, 33, 63, 64, 69):
+        one = BlockPlan(op, *blocks[i])
+        assert torch.equal(one.apply(xs[i]), ys[i]) and torch.equal(ys[i], ys2[i])
+        one.close()
+    plan.close()
+
+
+def test_many_blocks_reject_overlapping_outputs():
+    import paper_1805_06018_gb300 as pcg
+    from paper_1805_06018_gb300 import BlockPlan
+    from paper_1805_06018_gb300.binding import PC_ERR_ARG
+    shape = (40, 36)
+    op, _ = make_pair(shape, workloads.regular_grid(shape, (4, 3)), _kernel(shape, 5), "fp32")
+    plan = BlockPlan(op, [[0, 0], [10, 10]], [[9, 9], [19, 19]], [[0, 0], [10, 10]], [[9, 9], [19, 19]])
+    x = torch.zeros(2, 100, device="cuda")
+    y = torch.zeros(150, device="cuda")
+    with pytest.raises(pcg.PCError) as ei:
+        plan.pc_block_apply_many(1, [x[0].data_ptr(), x[1].data_ptr()], [100, 100],
+                                 [y.data_ptr(), y[50:].data_ptr()], [100, 100], 0)
+    assert ei.value.status == PC_ERR_ARG
+    with pytest.raises(pcg.PCError):
+        plan.pc_block_apply(1, x.data_ptr(), 100, y.data_ptr(), 100, 0)   # several blocks: apply_many only
+    plan.close()
