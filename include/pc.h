@@ -336,8 +336,11 @@ typedef struct pc_block_plan pc_block_plan;
 
 /* t_lo, t_hi, s_lo, s_hi: host arrays of d int64 values (C axis order),
  * closed boxes with 0 <= lo <= hi < shape per axis, else PC_ERR_ARG.
- * adjoint: 0 (A~[T,S]) or 1 ((A~*)[T,S]).  2D operators (PC_FP32, PC_FP64);
- * 3D operators return PC_ERR_UNSUPPORTED.  The plan allocates its device
+ * adjoint: 0 (A~[T,S]) or 1 ((A~*)[T,S]).  PC_FP32 and PC_FP64 operators,
+ * 2D and 3D; PC_BF16X3 operators return PC_ERR_UNSUPPORTED.  A 3D plan runs
+ * on the operator's per-CTA scratch volumes: its applies must not overlap
+ * the operator's own applies or other 3D plans of the same operator (one
+ * stream serialises them).  The plan allocates its device
  * tables (kept tiles, colour offsets, dependency lists, ordering flags,
  * control block); the call synchronises the device.  The operator must
  * outlive the plan.  *plan is NULL on failure. */
@@ -362,7 +365,8 @@ pc_status pc_block_apply(pc_block_plan *plan, int32_t nrhs, const void *x, int64
  * every block in one persistent launch (rounds of at most 64 blocks), each
  * block with its own tiles, colour order and ordering flags, so each block's
  * result is bitwise that of a single-block plan of that block; a low-rank
- * builder's many small blocks then fill the GPU together. */
+ * builder's many small blocks then fill the GPU together.  (3D plans run
+ * their blocks one launch after another.) */
 pc_status pc_block_plan_create_many(pc_operator *op, int32_t nblocks, const int64_t *t_lo, const int64_t *t_hi,
                                     const int64_t *s_lo, const int64_t *s_hi, int32_t adjoint, pc_block_plan **plan);
 

@@ -133,6 +133,7 @@ struct BlockSchedule {
 
 void build_block_schedule(const pc_operator *op, const int64_t *t_lo, const int64_t *t_hi, const int64_t *s_lo,
                           const int64_t *s_hi, bool adjoint, BlockSchedule &b) {
+    const int d = op->d;
     const int64_t *clo = adjoint ? t_lo : s_lo, *chi = adjoint ? t_hi : s_hi;
     const int64_t *olo = adjoint ? s_lo : t_lo, *ohi = adjoint ? s_hi : t_hi;
     std::vector<int32_t> remap(op->tiles_h.size(), -1);
@@ -140,9 +141,9 @@ void build_block_schedule(const pc_operator *op, const int64_t *t_lo, const int6
     for (int c = 0; c < op->n_colors; ++c) {
         for (int ti = op->color_start_h[size_t(c)]; ti < op->color_start_h[size_t(c) + 1]; ++ti) {
             const pc::Tile &t = op->tiles_h[size_t(ti)];
-            int64_t delta[2], ext[2];
+            int64_t delta[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
             bool keep = true;
-            for (int a = 0; a < 2 && keep; ++a) {
+            for (int a = 0; a < d && keep; ++a) {
                 const int64_t lo = std::max<int64_t>(t.in_lo[a], clo[a]);
                 const int64_t hi = std::min<int64_t>(int64_t(t.in_lo[a]) + t.in_ext[a] - 1, chi[a]);
                 delta[a] = lo - t.in_lo[a];
@@ -153,12 +154,13 @@ void build_block_schedule(const pc_operator *op, const int64_t *t_lo, const int6
             }
             if (!keep) continue;
             pc::Tile u = t;
-            for (int a = 0; a < 2; ++a) {
+            for (int a = 0; a < d; ++a) {
                 u.in_lo[a] = int32_t(t.in_lo[a] + delta[a] - clo[a]);
                 u.in_ext[a] = int32_t(ext[a]);
                 u.out_lo[a] = int32_t(t.out_lo[a] + delta[a] - olo[a]);
             }
-            u.w_base = t.w_base + delta[0] * t.w_ld[0] + delta[1] * t.w_ld[1];
+            // weight strides: 2D {ext1, 1}; 3D {ext1 * ext2, ext2} with unit stride on the last axis
+            u.w_base = t.w_base + delta[0] * t.w_ld[0] + delta[1] * t.w_ld[1] + (d == 3 ? delta[2] : 0);
             remap[size_t(ti)] = int32_t(b.tiles.size());
             b.tiles.push_back(u);
             for (int q = op->dep_start_h[size_t(ti)]; q < op->dep_start_h[size_t(ti) + 1]; ++q) {
@@ -778,6 +780,7 @@ static pc_status apply_batched(pc_operator *op, int32_t nrhs, const void *x, int
     p.n[2] = int32_t(op->shape[2]);
     p.nx[0] = p.n[0];
     p.nx[1] = p.n[1];
+    p.nx[2] = p.n[2];
     p.R = op->R;
     p.tiles = op->d_tiles;
     p.color_start = op->d_color_start;
@@ -922,6 +925,7 @@ pc_status apply_host_segmented(pc_operator *op, int32_t nrhs, const void *x, int
         p.n[2] = int32_t(op->shape[2]);
         p.nx[0] = p.n[0];
         p.nx[1] = p.n[1];
+        p.nx[2] = p.n[2];
         p.R = op->R;
         p.tiles = op->d_tiles;
         p.color_start = op->d_color_start;
@@ -1350,6 +1354,7 @@ pc_status pc_estimator_update(pc_estimator *est, pc_operator *op, double *eta, i
         p.n[2] = 1;
         p.nx[0] = p.n[0];
         p.nx[1] = p.n[1];
+        p.nx[2] = p.n[2];
         p.R = op->R;
         p.tiles = d_tiles;
         p.color_start = d_cs;
@@ -1424,10 +1429,11 @@ pc_status pc_block_plan_create_many(pc_operator *op, int32_t nblocks, const int6
     if (nblocks < 1) return fail(ctx, PC_ERR_ARG, "nblocks must be >= 1");
     if (!t_lo || !t_hi || !s_lo || !s_hi) return fail(ctx, PC_ERR_ARG, "null box bound");
     if (adjoint != 0 && adjoint != 1) return fail(ctx, PC_ERR_ARG, "adjoint must be 0 or 1");
-    if (op->d != 2) return fail(ctx, PC_ERR_UNSUPPORTED, "block applies cover 2D operators");
+    if (op->prec == PC_BF16X3) return fail(ctx, PC_ERR_UNSUPPORTED, "block applies cover FP32 and FP64 operators");
+    const int d = op->d;
     for (int32_t i = 0; i < nblocks; ++i)
-        for (int a = 0; a < 2; ++a) {
-            const int64_t j = int64_t(i) * 2 + a;
+        for (int a = 0; a < d; ++a) {
+            const int64_t j = int64_t(i) * d + a;
             if (t_lo[j] < 0 || t_lo[j] > t_hi[j] || t_hi[j] >= op->shape[size_t(a)])
                 return fail(ctx, PC_ERR_ARG, "target box T must satisfy 0 <= lo <= hi < shape");
             if (s_lo[j] < 0 || s_lo[j] > s_hi[j] || s_hi[j] >= op->shape[size_t(a)])
@@ -1441,14 +1447,14 @@ pc_status pc_block_plan_create_many(pc_operator *op, int32_t nblocks, const int6
     std::vector<int32_t> cs, ds, dep;
     for (int32_t i = 0; i < nblocks; ++i) {
         BlockSchedule b;
-        build_block_schedule(op, t_lo + 2 * i, t_hi + 2 * i, s_lo + 2 * i, s_hi + 2 * i, adjoint == 1, b);
+        build_block_schedule(op, t_lo + d * i, t_hi + d * i, s_lo + d * i, s_hi + d * i, adjoint == 1, b);
         pc_block_plan::Block blk{};
-        for (int a = 0; a < 2; ++a) {
-            blk.t_ext[a] = t_hi[2 * i + a] - t_lo[2 * i + a] + 1;
-            blk.s_ext[a] = s_hi[2 * i + a] - s_lo[2 * i + a] + 1;
+        for (int a = 0; a < 3; ++a) {
+            blk.t_ext[a] = a < d ? t_hi[d * i + a] - t_lo[d * i + a] + 1 : 1;
+            blk.s_ext[a] = a < d ? s_hi[d * i + a] - s_lo[d * i + a] + 1 : 1;
         }
-        blk.nT = blk.t_ext[0] * blk.t_ext[1];
-        blk.nS = blk.s_ext[0] * blk.s_ext[1];
+        blk.nT = blk.t_ext[0] * blk.t_ext[1] * blk.t_ext[2];
+        blk.nS = blk.s_ext[0] * blk.s_ext[1] * blk.s_ext[2];
         blk.tile_off = int32_t(tiles.size());
         blk.n_tiles = int32_t(b.tiles.size());
         blk.cs_off = int32_t(cs.size());
@@ -1486,7 +1492,7 @@ pc_status pc_block_plan_create_many(pc_operator *op, int32_t nblocks, const int6
         return bail(e, "colours and dependencies");
     if ((e = cudaMalloc(&bp->d_ctrl, 64)) != cudaSuccess) return bail(e, "control block");
     if ((e = cudaMemset(bp->d_ctrl, 0, 64)) != cudaSuccess) return bail(e, "control block");
-    if (nblocks > 1) {
+    if (nblocks > 1 && d == 2) {
         const int rounds = (nblocks + pc::kMaxSegments - 1) / pc::kMaxSegments;
         for (int rnd = 0; rnd < rounds; ++rnd) {
             int32_t runs = 0;
@@ -1576,12 +1582,11 @@ pc_status pc_block_apply_many(pc_block_plan *bp, int32_t nrhs, const void *const
         p.ldy = ldy[i];
         p.nrhs = nrhs;
         p.npairs = npairs;
-        p.n[0] = int32_t(b.t_ext[0]);
-        p.n[1] = int32_t(b.t_ext[1]);
-        p.n[2] = 1;
+        for (int a = 0; a < 3; ++a) {
+            p.n[a] = int32_t(b.t_ext[a]);
+            p.nx[a] = int32_t(b.s_ext[a]);
+        }
         p.R = op->R;
-        p.nx[0] = int32_t(b.s_ext[0]);
-        p.nx[1] = int32_t(b.s_ext[1]);
         p.tiles = bp->d_tiles ? bp->d_tiles + b.tile_off : nullptr;
         p.color_start = bp->d_color_start + b.cs_off;
         p.n_colors = b.n_colors;
@@ -1599,16 +1604,21 @@ pc_status pc_block_apply_many(pc_block_plan *bp, int32_t nrhs, const void *const
         return p;
     };
     int64_t launches = 0;
-    if (nb == 1) {
-        const pc::ApplyParams p = params(0);
-        if ((e = pc::launch_zero(p, bp->blocks[0].nT, op->prec, s)) != cudaSuccess)
-            return cuda_fail(ctx, e, "launching the zero kernel");
-        ++launches;
-        if (p.total_items > 0) {
-            const int ctas = int(std::min<int64_t>(op->ctas, p.total_items));
-            if ((e = pc::launch_fft2d(p, op->P, op->prec, ctas, s, bp->adjoint)) != cudaSuccess)
-                return cuda_fail(ctx, e, "launching the patch kernel");
+    if (nb == 1 || op->d == 3) {
+        // one block per launch (3D: the patch kernel runs one block at a time, on
+        // the operator's per-CTA scratch volumes)
+        for (int32_t i = 0; i < nb; ++i) {
+            const pc::ApplyParams p = params(i);
+            if ((e = pc::launch_zero(p, bp->blocks[size_t(i)].nT, op->prec, s)) != cudaSuccess)
+                return cuda_fail(ctx, e, "launching the zero kernel");
             ++launches;
+            if (p.total_items > 0) {
+                const int ctas = int(std::min<int64_t>(op->ctas, p.total_items));
+                e = op->d == 3 ? pc::launch_fft3d(p, ctas, op->d_scratch, s, bp->adjoint)
+                               : pc::launch_fft2d(p, op->P, op->prec, ctas, s, bp->adjoint);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the patch kernel");
+                ++launches;
+            }
         }
     } else {
         size_t smem = 0;

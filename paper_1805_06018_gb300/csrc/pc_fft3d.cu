@@ -94,23 +94,23 @@ __device__ __forceinline__ void phase1_3d(const ApplyParams &p, const Item3 &it,
     const float *x0 = static_cast<const float *>(p.x) + int64_t(b0) * p.ldx;
     const float *x1 = has1 ? x0 + p.ldx : x0;
     const float *wt = static_cast<const float *>(p.w) + tile.w_base;
-    const int64_t plane_box = int64_t(p.n[1]) * p.n[2];
+    const int64_t plane_box = int64_t(p.nx[1]) * p.nx[2];   // x lives on the box nx
     for (int i0 = 0; i0 < m0; ++i0) {
-        if (ADJ && (g0 + i0 < 0 || g0 + i0 >= p.n[0])) continue;   // uniform across the CTA
+        if (ADJ && (g0 + i0 < 0 || g0 + i0 >= p.nx[0])) continue;   // uniform across the CTA
         const float *wp = wt + int64_t(i0) * tile.w_ld[0];
         const int64_t xp = int64_t(g0 + i0) * plane_box;
         for (int r = L.line; r < m1; r += LINES) {
             C a[R1];
             const int gr = g1 + r;
-            const bool rin = !ADJ || (gr >= 0 && gr < p.n[1]);
-            const int64_t xr = xp + int64_t(gr) * p.n[2] + g2;
+            const bool rin = !ADJ || (gr >= 0 && gr < p.nx[1]);
+            const int64_t xr = xp + int64_t(gr) * p.nx[2] + g2;
             const float *wr = wp + int64_t(r) * tile.w_ld[1];
 #pragma unroll
             for (int j = 0; j < R1; ++j) {
                 const int col = L.t + R2 * j;
                 if constexpr (ADJ) {
                     const int gc = g2 + col;
-                    a[j] = rin && col < m2 && gc >= 0 && gc < p.n[2]
+                    a[j] = rin && col < m2 && gc >= 0 && gc < p.nx[2]
                                ? C{__ldg(x0 + xr + col), has1 ? __ldg(x1 + xr + col) : 0.0f}
                                : zero;
                 } else if (col < n2) {
@@ -166,7 +166,7 @@ __device__ __forceinline__ void phase2_3d(const ApplyParams &p, const Item3 &it,
 #pragma unroll
         for (int j = 0; j < R1; ++j) {
             const int i0 = L.t + R2 * j;
-            const bool in = i0 < rows_in && (!ADJ || (g0 + i0 >= 0 && g0 + i0 < p.n[0]));
+            const bool in = i0 < rows_in && (!ADJ || (g0 + i0 >= 0 && g0 + i0 < p.nx[0]));
             a[j] = in ? __ldcg(g + int64_t(i0) * PP) : zero;
         }
         // S is idle in this phase: row `line` is the line's transpose scratch

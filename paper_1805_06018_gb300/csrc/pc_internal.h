@@ -110,8 +110,9 @@ struct ApplyParams {
     int32_t nrhs, npairs;
     int32_t n[3];               // extents of the box y lives on (2D: n[2] = 1)
     int32_t R;
-    int32_t nx[2];              // 2D: extents of the box x lives on (n[0], n[1] for a whole-box apply;
-                                // the source box S of a block apply)
+    int32_t nx[3];              // extents of the box x lives on (n for a whole-box apply; the source box S
+                                // of a block apply); 2D: nx[2] = 1
+    int32_t pad_nx_;
     const Tile *tiles;
     const int32_t *color_start;
     int32_t n_colors;
@@ -302,7 +303,7 @@ struct pc_estimator {
 // ordering flags; one multi-segment launch runs up to kMaxSegments blocks.
 struct pc_block_plan {
     struct Block {
-        int64_t t_ext[2], s_ext[2];
+        int64_t t_ext[3], s_ext[3];   // axes beyond d: 1
         int64_t nT, nS;
         int32_t tile_off, n_tiles, cs_off, n_colors, ds_off, dep_off, terms;
     };

@@ -275,6 +275,7 @@ void try_launch(pc_server *s) {
             p.n[2] = int32_t(op->shape[2]);
             p.nx[0] = p.n[0];
             p.nx[1] = p.n[1];
+            p.nx[2] = p.n[2];
             p.R = op->R;
             p.tiles = op->d_tiles;
             p.color_start = op->d_color_start;

@@ -156,7 +156,7 @@ def test_bad_arguments():
     shape3 = (12, 10, 8)
     kern3 = workloads.GaussianAxis3D(lambda x: 1.2 + 0 * x[..., 0], lambda x: 1.0 + 0 * x[..., 0],
                                      lambda x: 1.0 + 0 * x[..., 0], 3)
-    op3, _ = make_pair(shape3, workloads.regular_grid(shape3, (2, 2, 2)), kern3, "fp32")
+    op3, _ = make_pair(shape3, workloads.regular_grid(shape3, (2, 2, 2)), kern3, "bf16x3")
     with pytest.raises(pcg.PCError) as ei:
         BlockPlan(op3, (0, 0, 0), (3, 3, 3), (0, 0, 0), (3, 3, 3))
     assert ei.value.status == PC_ERR_UNSUPPORTED
@@ -230,4 +230,49 @@ def test_many_blocks_reject_overlapping_outputs():
     assert ei.value.status == PC_ERR_ARG
     with pytest.raises(pcg.PCError):
         plan.pc_block_apply(1, x.data_ptr(), 100, y.data_ptr(), 100, 0)   # several blocks: apply_many only
+    plan.close()
+
+
+def _skew3(shape, R):
+    return workloads.Skewed([0.7, -0.4, 0.3], lambda x: 1.1 + 0.4 * np.sin(x[..., 0] / 5.0), R)
+
+
+BOXES3 = [   # (t_lo, t_hi, s_lo, s_hi) on a 30 x 26 x 22 box
+    ((0, 0, 0), (29, 25, 21), (0, 0, 0), (29, 25, 21)),
+    ((3, 5, 2), (17, 20, 15), (8, 1, 6), (25, 12, 21)),
+    ((0, 0, 0), (8, 8, 8), (10, 0, 2), (16, 6, 9)),
+    ((25, 20, 18), (29, 25, 21), (0, 0, 0), (4, 4, 4)),
+    ((11, 12, 13), (11, 12, 13), (11, 12, 13), (11, 12, 13)),
+]
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_blocks_3d_fp32(adjoint):
+    """3D operators (P = 64): ragged, beside, out-of-reach and one-voxel
+    blocks against the oracle; the whole-box block bitwise the apply; several
+    blocks in one plan (one launch each) bitwise their single plans."""
+    from paper_1805_06018_gb300 import BlockPlan
+    shape = (30, 26, 22)
+    op, orc = make_pair(shape, workloads.regular_grid(shape, (3, 3, 3)), _skew3(shape, 4), "fp32")
+    rng = np.random.default_rng(68)
+    xs = []
+    for t_lo, t_hi, s_lo, s_hi in BOXES3:
+        sS = tuple(b - a + 1 for a, b in zip(s_lo, s_hi))
+        x = rng.standard_normal((3,) + sS).astype(np.float32).astype(np.float64)
+        xs.append(x)
+        _, got = _run_block(op, t_lo, t_hi, s_lo, s_hi, x, adjoint)
+        _check(got, ob.apply_block_translated(orc, t_lo, t_hi, s_lo, s_hi, x, adjoint), "fp32")
+    xw = _dev(workloads.rhs(69, 3, shape), "fp32")
+    whole = BlockPlan(op, *BOXES3[0], adjoint)
+    ref = op.apply_adjoint(xw) if adjoint else op.apply(xw)
+    assert torch.equal(whole.apply(xw), ref)
+    whole.close()
+    plan = BlockPlan(op, *[[b[i] for b in BOXES3] for i in range(4)], adjoint)
+    ys = plan.apply_many([_dev(x, "fp32") for x in xs])
+    torch.cuda.synchronize()
+    plan.check()
+    for b, x, y in zip(BOXES3, xs, ys):
+        one = BlockPlan(op, *b, adjoint)
+        assert torch.equal(one.apply(_dev(x, "fp32")), y)
+        one.close()
     plan.close()
