@@ -639,7 +639,7 @@ def run_serve(args):
     from paper_1805_06018_gb300 import build as libbuild
     libbuild.build()
     ctx = pcg.Context(0)
-    ops = serve_operators(pcg, ctx)
+    ops = serve_operators(pcg, ctx, with_3d=not args.serve_2d)
     by_shape = {}
     for i, (_, op) in enumerate(ops):
         if op.shape not in by_shape:
@@ -702,7 +702,8 @@ def run_serve(args):
             "loads": loads, "plain_gpu_rhs_per_s": plain,
             "config": {"operators": [n for n, _ in ops], "rhs_per_request": "U[1,64]", "budget_bytes": 120 << 30,
                        "arrivals": "Poisson at 50/80/95% of the saturated rate",
-                       "modes": "2D FP32; 3D FP32 and BF16x3 (tensor-core first axis)",
+                       "modes": "2D FP32" if args.serve_2d else "2D FP32; 3D FP32 and BF16x3 (tensor-core first axis)",
+                       "requests_after_warmup": sat["completed"] + sum(lv["requests"] for lv in loads),
                        "plain_gpu": "2D requests of the saturated set only"}}
     print(json.dumps(line), flush=True)
 
@@ -717,6 +718,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--serve", action="store_true", help="serving benchmark instead of the batched apply")
     ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-2d", action="store_true", help="serve the 2D operators of the mix only")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--nrhs", type=int, default=0,
                     help="override the workload's batch (smaller cases for profiler captures)")
