@@ -468,6 +468,10 @@ pc_status pc_apply_batched_noalloc(pc_operator *op, int32_t nrhs, const void *x,
  * flags for up to 2^22 (tile, pair) units) and mapped completion flags. */
 pc_status pc_serve_create(pc_context *ctx, const pc_serve_config *cfg, pc_server **srv);
 
+/* pc_serve_submit flag: queue the adjoint Y = A~* X (Eq. adjoint_random_z)
+ * instead; launches hold requests of one direction. */
+#define PC_SERVE_ADJOINT 1u
+
 /* Queue Y = A~ X for nrhs vectors: x and y are device arrays [nrhs][N] of
  * float (contiguous), owned by the caller and kept alive until pc_serve_poll
  * returns PC_OK for the ticket.  Returns at once with *ticket.  While an
@@ -477,7 +481,8 @@ pc_status pc_serve_create(pc_context *ctx, const pc_serve_config *cfg, pc_server
  * before the launch, which may synchronise the device).  Errors:
  * PC_ERR_UNSUPPORTED for operators the server cannot launch, PC_ERR_BUDGET
  * if the operator and request alone exceed the budget, PC_ERR_ARG for bad
- * arguments.  flags: reserved, pass 0. */
+ * arguments.  flags: 0, or PC_SERVE_ADJOINT for Y = A~* X (not for
+ * PC_BF16X3 operators: PC_ERR_UNSUPPORTED). */
 pc_status pc_serve_submit(pc_server *srv, pc_operator *op, int32_t nrhs, const void *x, void *y, uint32_t flags,
                           uint64_t *ticket);
 

@@ -22,6 +22,7 @@ PC_OK, PC_ERR_ARG, PC_ERR_GRID, PC_ERR_NOMEM, PC_ERR_BUDGET, PC_ERR_CUDA, PC_ERR
 STATUS_NAMES = ["PC_OK", "PC_ERR_ARG", "PC_ERR_GRID", "PC_ERR_NOMEM", "PC_ERR_BUDGET", "PC_ERR_CUDA",
                 "PC_ERR_TIMEOUT", "PC_ERR_NOT_READY", "PC_ERR_UNSUPPORTED"]
 PC_FP64, PC_FP32, PC_BF16X3, PC_TF32X3 = range(4)
+PC_SERVE_ADJOINT = 1
 PRECISIONS = {"fp64": PC_FP64, "fp32": PC_FP32, "bf16x3": PC_BF16X3, "tf32x3": PC_TF32X3}
 
 
@@ -570,13 +571,15 @@ class Server:
         self.handle = h
         self._keep = {}
 
-    def submit(self, op: "Operator", x, y) -> int:
-        """Queue y = A~ x (x, y: contiguous float32 CUDA tensors [nrhs, *box]).
-        The tensors are kept alive until poll() reports the ticket done."""
+    def submit(self, op: "Operator", x, y, adjoint: bool = False) -> int:
+        """Queue y = A~ x, or y = A~* x with adjoint=True (x, y: contiguous
+        float32 CUDA tensors [nrhs, *box]).  The tensors are kept alive until
+        poll() reports the ticket done."""
         nrhs = x.numel() // op.N
         t = ctypes.c_uint64()
         _check(lib().pc_serve_submit(self.handle, op.handle, ctypes.c_int32(nrhs), _VP(x.data_ptr()),
-                                     _VP(y.data_ptr()), ctypes.c_uint32(0), ctypes.byref(t)), self.ctx.handle)
+                                     _VP(y.data_ptr()), ctypes.c_uint32(PC_SERVE_ADJOINT if adjoint else 0),
+                                     ctypes.byref(t)), self.ctx.handle)
         self._keep[t.value] = (x, y)
         return t.value
 

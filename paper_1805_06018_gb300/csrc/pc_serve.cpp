@@ -54,13 +54,14 @@ struct Request {
     int hslot = -1;     // host completion flag index
     int launch_requests = 0;
     bool solo = false;  // 3D: runs alone through the operator's own apply
+    bool adjoint = false;   // Y = A~* X (Eq. adjoint_random_z)
     std::string error;
 };
 
 struct LaunchSlot {
     cudaStream_t stream = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr, graph_adj = nullptr;     // forward and adjoint launches
+    cudaGraphExec_t exec = nullptr, exec_adj = nullptr;
     pc::LaunchDesc *h_desc = nullptr;   // pinned
     pc::LaunchDesc *d_desc = nullptr;
     uint32_t *d_flags = nullptr;
@@ -213,7 +214,8 @@ bool launch_solo(pc_server *s, LaunchSlot &sl) {
     r->state = 1;
     r->launch_s = s->now();
     r->launch_requests = 1;
-    pc_status st = pc_apply_batched(r->op, r->nrhs, r->x, r->op->N, r->y, r->op->N, sl.stream);
+    pc_status st = r->adjoint ? pc_apply_adjoint_batched(r->op, r->nrhs, r->x, r->op->N, r->y, r->op->N, sl.stream)
+                              : pc_apply_batched(r->op, r->nrhs, r->x, r->op->N, r->y, r->op->N, sl.stream);
     cudaError_t e = st == PC_OK ? cudaEventRecord(sl.done, sl.stream) : cudaSuccess;
     if (st != PC_OK || e != cudaSuccess) {
         r->state = 3;
@@ -239,8 +241,10 @@ void try_launch(pc_server *s) {
         std::vector<Request *> take;
         int64_t words = 0, extra = 0;
         std::unordered_map<pc_operator *, int> seen;
+        const bool adj = s->queue.front()->adjoint;
         for (Request *r : s->queue) {
             if (r->solo) break;   // the 3D request takes a slot of its own next
+            if (r->adjoint != adj) break;   // one direction per launch (FIFO: no overtaking)
             if (int(take.size()) >= s->cfg.max_requests_per_launch) break;
             if (s->inflight + int(take.size()) >= s->cfg.max_inflight) break;
             if (s->free_hslots.size() <= take.size()) break;
@@ -315,7 +319,7 @@ void try_launch(pc_server *s) {
         d.total_items = items;
         s->budget_peak = std::max(s->budget_peak, s->budget_used);
         for (size_t q = 0; q < take.size(); ++q) s->queue.pop_front();
-        cudaError_t e = cudaGraphLaunch(sl.exec, sl.stream);
+        cudaError_t e = cudaGraphLaunch(adj ? sl.exec_adj : sl.exec, sl.stream);
         if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
         if (e != cudaSuccess) {
             s->fatal = std::string("graph launch: ") + cudaGetErrorString(e);
@@ -357,6 +361,8 @@ void free_server(pc_server *s) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.exec) cudaGraphExecDestroy(sl.exec);
         if (sl.graph) cudaGraphDestroy(sl.graph);
+        if (sl.exec_adj) cudaGraphExecDestroy(sl.exec_adj);
+        if (sl.graph_adj) cudaGraphDestroy(sl.graph_adj);
         if (sl.h_desc) cudaFreeHost(sl.h_desc);
         cudaFree(sl.d_desc);
         cudaFree(sl.d_flags);
@@ -413,18 +419,24 @@ pc_status pc_serve_create(pc_context *ctx, const pc_serve_config *cfg, pc_server
         if (e == cudaSuccess) e = cudaMalloc(&sl.d_status, sizeof(int32_t));
         if (e == cudaSuccess) e = cudaMemset(sl.d_status, 0, sizeof(int32_t));
         if (e == cudaSuccess) std::memset(sl.h_desc, 0, sizeof(pc::LaunchDesc));
-        // capture: descriptor upload, zero-fill, persistent fused kernel
-        if (e == cudaSuccess) e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            cudaError_t e1 = cudaMemcpyAsync(sl.d_desc, sl.h_desc, sizeof(pc::LaunchDesc), cudaMemcpyHostToDevice,
-                                             sl.stream);
-            cudaError_t e2 = e1 == cudaSuccess ? pc::launch_round(sl.d_desc, sl.d_counter, sl.d_status, sl.d_seg_done,
-                                                                  s->d_hflags, s->ctas, s->smem, sl.stream)
-                                               : e1;
-            e = cudaStreamEndCapture(sl.stream, &sl.graph);
-            if (e == cudaSuccess) e = e2;
+        // capture, forward and adjoint: descriptor upload, zero-fill, persistent fused kernel
+        for (int adj = 0; adj < 2 && e == cudaSuccess; ++adj) {
+            cudaGraph_t &g = adj ? sl.graph_adj : sl.graph;
+            cudaGraphExec_t &x = adj ? sl.exec_adj : sl.exec;
+            e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t e1 = cudaMemcpyAsync(sl.d_desc, sl.h_desc, sizeof(pc::LaunchDesc), cudaMemcpyHostToDevice,
+                                                 sl.stream);
+                cudaError_t e2 = e1 == cudaSuccess
+                                     ? pc::launch_round(sl.d_desc, sl.d_counter, sl.d_status, sl.d_seg_done,
+                                                        s->d_hflags, s->ctas, s->smem, sl.stream, 128, PC_FP32,
+                                                        adj == 1)
+                                     : e1;
+                e = cudaStreamEndCapture(sl.stream, &g);
+                if (e == cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
         }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&sl.exec, sl.graph, 0);
     }
     if (e != cudaSuccess) {
         ctx->last_error = std::string("pc_serve_create: ") + cudaGetErrorString(e);
@@ -439,7 +451,11 @@ pc_status pc_serve_create(pc_context *ctx, const pc_serve_config *cfg, pc_server
 pc_status pc_serve_submit(pc_server *s, pc_operator *op, int32_t nrhs, const void *x, void *y, uint32_t flags,
                           uint64_t *ticket) {
     if (!s || !ticket) return PC_ERR_ARG;
-    if (!op || nrhs < 1 || !x || !y || flags != 0) return srv_fail(s, PC_ERR_ARG, "bad request arguments");
+    if (!op || nrhs < 1 || !x || !y || (flags & ~PC_SERVE_ADJOINT) != 0)
+        return srv_fail(s, PC_ERR_ARG, "bad request arguments");
+    const bool adjoint = (flags & PC_SERVE_ADJOINT) != 0;
+    if (adjoint && op->prec == PC_BF16X3)
+        return srv_fail(s, PC_ERR_UNSUPPORTED, "adjoint requests need an FP32 operator");
     if (op->ctx->device != s->ctx->device) return srv_fail(s, PC_ERR_ARG, "operator lives on another device");
     const bool solo = op->d == 3;
     if (!solo && (op->d != 2 || op->prec != PC_FP32 || op->P != 128))
@@ -452,6 +468,7 @@ pc_status pc_serve_submit(pc_server *s, pc_operator *op, int32_t nrhs, const voi
     r->x = x;
     r->y = y;
     r->solo = solo;
+    r->adjoint = adjoint;
     // 2D: the request's ordering flags live in the launch slot's arena; 3D:
     // in the operator, whose scratch has already been counted in its size
     r->flag_words = solo ? 0 : int64_t(op->n_tiles) * ((nrhs + 1) / 2);

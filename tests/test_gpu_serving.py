@@ -148,3 +148,40 @@ def test_3d_requests_in_the_mix(ops):
     assert st["completed"] == len(jobs)
     assert st["launches"] < len(jobs)                 # the 2D requests still share launches
     srv.close()
+
+
+def test_adjoint_requests_in_the_mix(ops):
+    """Adjoint requests (PC_SERVE_ADJOINT, the estimator's probes A~* Z)
+    among forward ones, 2D and 3D: runs of one direction share launches, and
+    every result equals the request applied alone, bit for bit; BF16x3
+    operators refuse adjoint requests."""
+    import paper_1805_06018_gb300 as pcg
+    shape = (30, 28, 26)
+    cells = workloads.regular_grid(shape, (3, 3, 3))
+    kern = workloads.Skewed([0.7, -0.4, 0.3], lambda x: 1.1 + 0.3 * np.sin(x[..., 0] / 6.0), 4)
+    op3 = make_pair(shape, cells, kern, "fp32")[0]
+    mix = [(ops[0], True), (ops[1], True), (ops[2], False), (ops[0], False), (op3, True), (ops[1], True),
+           (ops[2], True), (op3, False), (ops[0], True), (ops[1], False)]
+    srv = pcg.Server(context(), budget_bytes=32 << 30, streams=2, max_requests_per_launch=8)
+    rng = np.random.default_rng(2)
+    prepared = []
+    for q, (op, adj) in enumerate(mix * 2):
+        nrhs = int(rng.integers(1, 7))
+        x = torch.from_numpy(workloads.rhs(700 + q, nrhs, op.shape)).cuda()
+        prepared.append((op, adj, x, torch.full_like(x, float("nan"))))
+    torch.cuda.synchronize()
+    jobs = [(op, adj, x, y, srv.submit(op, x, y, adjoint=adj)) for op, adj, x, y in prepared]
+    done = _wait(srv, [j[4] for j in jobs], timeout=120.0)
+    for op, adj, x, y, t in jobs:
+        alone = op.apply_adjoint(x) if adj else op.apply(x)
+        torch.cuda.synchronize()
+        assert torch.equal(y, alone)
+        assert done[t]["status"] == 0
+    st = srv.stats()
+    assert st["launches"] < len(jobs)
+    op16 = make_pair(shape, cells, kern, "bf16x3")[0]
+    x = torch.zeros(1, *shape, device="cuda")
+    with pytest.raises(pcg.PCError) as e:
+        srv.submit(op16, x, torch.empty_like(x), adjoint=True)
+    assert e.value.status == pcg.binding.PC_ERR_UNSUPPORTED
+    srv.close()
