@@ -44,6 +44,9 @@ WORKLOAD = "fp32_512"
 WORKLOADS = {
     "fp32_512": ("512x512 regular 16x16 grid (r=256), anisotropic Gaussian R=24, 128^2 patch FFTs, 64 RHS",
                  "fft2d_kernel<float,128>", ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_overlap.cuh"]),
+    "fp64_64": ("FP64 64x64 regular 4x4 grid (r=16), isotropic Gaussian R=12, 64^2 patch FFTs, 1 RHS "
+                "(the correctness configuration: latency-bound)", "fft2d_kernel<double,64>",
+                ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_overlap.cuh"]),
     "fp32_128c": ("128^3 regular 8x8x8 grid (r=512), axis-aligned Gaussian R=12, 64^3 patch FFTs, 32 RHS",
                   "fft3d_kernel<false>", ["pc_fft3d.cu", "pc_fftcore.cuh", "pc_ptx.cuh"]),
     "bf16x3_128c": ("128^3 regular 8x8x8 grid (r=512), axis-aligned Gaussian R=12, 64^3 patches: plane FFTs in "
@@ -73,7 +76,7 @@ WORKLOADS = {
                       ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_overlap.cuh"]),
 }
 # workload name -> (operator configuration, precision)
-WORKLOAD_OPERATOR = {"fp32_512": ("fp32_512", "fp32"), "fp32_512_adjoint": ("fp32_512", "fp32"),
+WORKLOAD_OPERATOR = {"fp64_64": ("fp64_64", "fp64"), "fp32_512": ("fp32_512", "fp32"), "fp32_512_adjoint": ("fp32_512", "fp32"),
                      "fp32_512_estimator": ("fp32_512", "fp32"), "fp32_512_block": ("fp32_512", "fp32"),
                      "fp32_512_blocks": ("fp32_512", "fp32"),
                      "fp32_128c": ("fp32_128c", "fp32"), "bf16x3_128c": ("fp32_128c", "bf16x3"),
@@ -212,6 +215,25 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(x, world):
+    """The slowest rank's value, on every rank (one process: x itself).  The
+    reduction runs on the process group's own device: CUDA for NCCL, the
+    host for gloo."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / seconds
 
 
 def cpu_oracle_rate(wl, x, seconds, seed=0, adjoint=False):
@@ -373,10 +395,8 @@ def run_block(args, rank, world):
     tot_ms = float(step_ms.sum())
     if world > 1:
         dist.barrier()
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * args.steps * wl.nrhs / (tot_ms / 1e3)
+    tot_ms = max_over_ranks(tot_ms, world)
+    value = aggregate_rate(args.steps * wl.nrhs, world, tot_ms / 1e3)
 
     xh = torch.from_numpy(x_host).pin_memory()
     yh = torch.empty(y.shape, dtype=torch.float32).pin_memory()
@@ -388,8 +408,8 @@ def run_block(args, rank, world):
         step()
         yh.copy_(y, non_blocking=True)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = world * e2e_steps * wl.nrhs / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = aggregate_rate(e2e_steps * wl.nrhs, world, e2e_s)
 
     lo, hi = pcg.pc_neighbourhood_boxes(wl.shape, wl.cells)
     flops, nominal_terms = block_algorithmic_flops(lo, hi, wl.radius, wl.nrhs)
@@ -404,7 +424,8 @@ def run_block(args, rank, world):
     achieved = flops / (step_mean / 1e3) / 1e12
     line = {"metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32",
+            "data": "synthetic",
             "config": {"workload": desc, "global_batch": wl.nrhs * world, "per_gpu_batch": wl.nrhs,
                        "grid": list(wl.shape), "radius": wl.radius, "T": [list(tlo), list(thi)],
                        "S": [list(slo), list(shi)], "terms": terms, "tiles": tiles,
@@ -494,10 +515,8 @@ def run_blocks(args, rank, world):
     tot_ms = float(step_ms.sum())
     if world > 1:
         dist.barrier()
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * args.steps * wl.nrhs * nb / (tot_ms / 1e3)
+    tot_ms = max_over_ranks(tot_ms, world)
+    value = aggregate_rate(args.steps * wl.nrhs * nb, world, tot_ms / 1e3)
     # the same blocks as separate single-block plans
     singles = [pcg.BlockPlan(op, *b[0], *b[1]) for b in blocks]
     for pl, x, y, a, c in zip(singles, xp, yp, nS, nT):
@@ -528,7 +547,7 @@ def run_blocks(args, rank, world):
         for y, h in zip(ys, yph):
             h.copy_(y, non_blocking=True)
     torch.cuda.synchronize()
-    e2e_value = world * e2e_steps * wl.nrhs * nb / (time.perf_counter() - t0)
+    e2e_value = aggregate_rate(e2e_steps * wl.nrhs * nb, world, max_over_ranks(time.perf_counter() - t0, world))
     lo, hi = pcg.pc_neighbourhood_boxes(wl.shape, wl.cells)
     flops = 0.0
     nominal = 0
@@ -759,6 +778,8 @@ def main():
     staged = precision == "bf16x3"
     info = op.info()
     x_host = workloads.rhs(wl.rhs_seed, wl.nrhs, wl.shape)
+    if precision == "fp64":
+        x_host = x_host.astype(np.float64)
     x = torch.from_numpy(x_host).cuda()
     y = torch.empty_like(x)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -804,11 +825,8 @@ def main():
     launches_per_step = int(op.launches())
     step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
     tot_ms = float(step_ms.sum())
-    if world > 1:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * args.steps * wl.nrhs / (tot_ms / 1e3)
+    tot_ms = max_over_ranks(tot_ms, world)
+    value = aggregate_rate(args.steps * wl.nrhs, world, tot_ms / 1e3)
 
     # ---- end to end through the public API with host buffers
     xh = torch.from_numpy(x_host).pin_memory()
@@ -831,16 +849,13 @@ def main():
             op.pc_apply_host(wl.nrhs, xh.data_ptr(), N, yh.data_ptr(), N, is_adj, 0, sp)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * e2e_steps * wl.nrhs / e2e_s
+    e2e_s = max_over_ranks(e2e_s, world)
+    e2e_value = aggregate_rate(e2e_steps * wl.nrhs, world, e2e_s)
 
     # ---- plain per-vector path on the same operator
     plain = None
     adjoint = args.workload.endswith("_adjoint") or estimator
-    if not args.no_plain and wl.ndim == 2 and not adjoint:
+    if not args.no_plain and wl.ndim == 2 and not adjoint and precision == "fp32":
         yp = torch.empty_like(x)
         op.pc_apply_plain(wl.nrhs, x.data_ptr(), N, yp.data_ptr(), N, sp)
         torch.cuda.synchronize()
@@ -862,7 +877,8 @@ def main():
 
     # ---- roofline of the fused kernel (FP32 ALU bound)
     lo, hi = pcg.pc_neighbourhood_boxes(wl.shape, wl.cells)
-    flops, bytes_ = algorithmic_work(wl.shape, lo, hi, wl.radius, wl.nrhs, info["spectra_bytes"])
+    flops, bytes_ = algorithmic_work(wl.shape, lo, hi, wl.radius, wl.nrhs, info["spectra_bytes"],
+                                     elem=8 if precision == "fp64" else 4)
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
@@ -910,6 +926,10 @@ def main():
             peak, bound = fp32_peak, "alu"
             basis = "FP32 FMA pipe: SMs x 128 lanes x 2 x %.0f MHz" % sm_max
             work = f_stage[dom]
+    elif precision == "fp64":
+        kern_ms = float(np.mean(kms))
+        achieved, peak, bound, work = flops / (kern_ms / 1e3) / 1e12, 1.25, "alu", flops
+        basis = "nominal GB300 FP64 rate, 1.25 TFLOP/s (no measured FP64 peak)"
     else:
         kern_ms = float(np.mean(kms))
         achieved, peak, bound, work = flops / (kern_ms / 1e3) / 1e12, fp32_peak, "alu", flops
