@@ -424,7 +424,7 @@ def run_block(args, rank, world):
     achieved = flops / (step_mean / 1e3) / 1e12
     line = {"metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": desc, "global_batch": wl.nrhs * world, "per_gpu_batch": wl.nrhs,
                        "grid": list(wl.shape), "radius": wl.radius, "T": [list(tlo), list(thi)],
@@ -938,7 +938,8 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32",
+            "data": "synthetic",
             "config": {"workload": desc, "global_batch": wl.nrhs * world,
                        "per_gpu_batch": wl.nrhs, "grid": list(wl.shape), "radius": wl.radius, "fft": info["fft_size"],
                        "parallelism": "replicas%d" % world, "l2": "flushed between steps (256 MB write)"},
