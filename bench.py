@@ -245,12 +245,12 @@ def cpu_oracle_rate(wl, x, seconds, seed=0, adjoint=False):
     rng = np.random.default_rng(seed)
     done = 0
     t0 = time.perf_counter()
-    chunk = 512
+    chunk = min(512, wl.n)
     while time.perf_counter() - t0 < seconds:
         pts = rng.choice(wl.n, chunk, replace=False)
         fn(x, points=pts)
         done += chunk
-        chunk = min(chunk * 2, 16384)
+        chunk = min(chunk * 2, 16384, wl.n)
     el = time.perf_counter() - t0
     return wl.nrhs * (done / wl.n) / el, done, os.cpu_count(), el
 
