@@ -669,21 +669,35 @@ def run_serve(args):
     def make_requests(n):
         return [(int(rng.integers(0, len(ops))), int(rng.integers(1, 65))) for _ in range(n)]
 
+    # per operator, a bounded pool of 64-RHS output buffers (about 24 GB for
+    # the largest operator); a request takes one and returns it on completion
+    ybufs = []
+    for o, (_, op) in enumerate(ops):
+        per = 64 * op.N * 4
+        ybufs.append([torch.empty_like(pools[o]) for _ in range(max(4, min(64, (24 << 30) // per)))])
+
     def run(reqs, rate):
         srv = pcg.Server(ctx, budget_bytes=120 << 30, max_inflight=512, streams=2, max_requests_per_launch=32)
-        ys = [torch.empty_like(pools[o][:k]) for o, k in reqs]
+        free = [list(range(len(b))) for b in ybufs]
         torch.cuda.synchronize()
         gaps = rng.exponential(1.0 / rate, len(reqs)) if rate else np.zeros(len(reqs))
         t0 = time.perf_counter()
         due = t0
-        pending = []
-        for (o, k), y, g in zip(reqs, ys, gaps):
+        pending = {}
+
+        def reap():
+            for t in [t for t in pending if srv.poll(t) is not None]:
+                o, b = pending.pop(t)
+                free[o].append(b)
+
+        for (o, k), g in zip(reqs, gaps):
             due += g
-            while time.perf_counter() < due:
-                pending = [t for t in pending if srv.poll(t) is None]
-            pending.append(srv.submit(ops[o][1], pools[o][:k], y))
+            while time.perf_counter() < due or not free[o]:
+                reap()
+            b = free[o].pop()
+            pending[srv.submit(ops[o][1], pools[o][:k], ybufs[o][b][:k])] = (o, b)
         while pending:
-            pending = [t for t in pending if srv.poll(t) is None]
+            reap()
         st = srv.stats()
         srv.close()
         return st
