@@ -669,12 +669,12 @@ def run_serve(args):
     def make_requests(n):
         return [(int(rng.integers(0, len(ops))), int(rng.integers(1, 65))) for _ in range(n)]
 
-    # per operator, a bounded pool of 64-RHS output buffers (about 24 GB for
-    # the largest operator); a request takes one and returns it on completion
+    # per operator, a bounded pool of 64-RHS output buffers (48 GB shared by
+    # the operators); a request takes one and returns it on completion
     ybufs = []
     for o, (_, op) in enumerate(ops):
         per = 64 * op.N * 4
-        ybufs.append([torch.empty_like(pools[o]) for _ in range(max(4, min(64, (24 << 30) // per)))])
+        ybufs.append([torch.empty_like(pools[o]) for _ in range(max(4, min(64, (48 << 30) // len(ops) // per)))])
 
     def run(reqs, rate):
         srv = pcg.Server(ctx, budget_bytes=120 << 30, max_inflight=512, streams=2, max_requests_per_launch=32)
