@@ -126,3 +126,30 @@ def test_weights_match_oracle_with_hanging_nodes(which):
     ref = np.concatenate([w.ravel() for w in W])
     assert lw.size == ref.size
     assert np.max(np.abs(lw - ref)) < 1e-12
+
+
+def test_header_is_plain_c_and_links():
+    """include/pc.h compiles as pedantic C99, and a C program that takes the
+    address of every declared entry point links against libpc.so (C linkage,
+    no C++ name mangling)."""
+    import shutil
+    import subprocess
+    import tempfile
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    names = sorted(_declared())
+    src = "#include \"pc.h\"\n#include <stdio.h>\nint main(void) {\n"
+    src += "".join("    printf(\"%%p\\n\", (void *)%s);\n" % n for n in names)
+    src += "    return 0;\n}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "abi.c")
+        with open(c, "w") as fh:
+            fh.write(src)
+        libdir = os.path.dirname(pcb.LIB_PATH)
+        cmd = [gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-I", os.path.join(root, "include"),
+               c, "-o", os.path.join(d, "abi"), "-L", libdir, "-l:" + os.path.basename(pcb.LIB_PATH),
+               "-Wl,-rpath," + libdir, "-Wl,--unresolved-symbols=ignore-in-shared-libs"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
