@@ -45,6 +45,12 @@
 extern "C" {
 #endif
 
+/* libpc is built with hidden symbol visibility; these declarations are the
+ * library's only exported symbols. */
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
 typedef enum {
     PC_OK = 0,
     PC_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, misaligned ld) */
@@ -530,6 +536,10 @@ pc_status pc_operator_stage_time(pc_operator *op, int32_t stage, float *ms);
 pc_status pc_operator_launches(const pc_operator *op, int64_t *kernels_last_apply);
 
 pc_status pc_operator_destroy(pc_operator *op);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
 
 #ifdef __cplusplus
 }

@@ -45,8 +45,8 @@ def _compile(src: str, verbose: bool) -> str:
     deps = [src] + _headers()
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC, "-I", SRC,
-           "-c", src, "-o", obj + ".tmp"]
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+           "-I", INC, "-I", SRC, "-c", src, "-o", obj + ".tmp"]
     if src.endswith(".cu"):
         cmd[1:1] = ["--expt-relaxed-constexpr"]
         if verbose:

@@ -5,12 +5,17 @@
 #include <cstring>
 #include <mutex>
 
+#include "pc_api_util.h"
 #include "pc_internal.h"
 
 namespace {
 
 std::mutex g_err_mu;
 std::string g_err;  // last error of context-free calls
+
+}  // namespace
+
+namespace pc {
 
 pc_status fail(pc_context *ctx, pc_status st, const std::string &msg) {
     if (ctx) {
@@ -27,29 +32,14 @@ pc_status cuda_fail(pc_context *ctx, cudaError_t e, const char *what) {
                 std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-// Make ctx's device current for the duration of a call, then restore.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
+}  // namespace pc
 
-template <typename T>
-cudaError_t upload(T **dst, const T *src, size_t n, size_t &acct) {
-    *dst = nullptr;
-    if (n == 0) return cudaSuccess;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), sizeof(T) * n);
-    if (e != cudaSuccess) return e;
-    acct += sizeof(T) * n;
-    return cudaMemcpy(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice);
-}
+using pc::cuda_fail;
+using pc::DeviceGuard;
+using pc::fail;
+using pc::upload;
+
+namespace {
 
 // W_P^j = exp(-2 pi i j / P), j < P, from long-double cos/sin of the
 // first-octant-reduced angle.
@@ -110,92 +100,6 @@ const char *free_operator(pc_operator *op) {
     if (op->ev_begin) chk(cudaEventDestroy(op->ev_begin), "events");
     if (op->ev_end) chk(cudaEventDestroy(op->ev_end), "events");
     delete op;
-    return bad;
-}
-
-// Schedule of a block apply (Section 3.3), from the operator's schedule.
-// A tile convolves its input box (inside bbox(U_k)) with one sub-window of
-// phi_k^E; restricting x to a box C only clips that input box, and shifting
-// the input box by delta shifts the tile's output box by delta with the same
-// sub-window (the translation of Section 3.3), so the tile keeps its
-// spectrum.  Forward: C = S and the output box must meet T; adjoint (which
-// gathers x over the output box and adds into the input box): C = T and the
-// output box must meet S.  Kept tiles are re-expressed in block coordinates:
-// input boxes relative to C, output boxes relative to the other box.  A
-// subset of a proper colouring is proper, and a clipped tile overlaps only
-// tiles its original overlapped, so the colour order and the dependency
-// lists restricted to kept tiles still order every sum.
-struct BlockSchedule {
-    std::vector<pc::Tile> tiles;
-    std::vector<int32_t> color_start{0}, dep_start{0}, dep;
-    int terms = 0;
-};
-
-void build_block_schedule(const pc_operator *op, const int64_t *t_lo, const int64_t *t_hi, const int64_t *s_lo,
-                          const int64_t *s_hi, bool adjoint, BlockSchedule &b) {
-    const int d = op->d;
-    const int64_t *clo = adjoint ? t_lo : s_lo, *chi = adjoint ? t_hi : s_hi;
-    const int64_t *olo = adjoint ? s_lo : t_lo, *ohi = adjoint ? s_hi : t_hi;
-    std::vector<int32_t> remap(op->tiles_h.size(), -1);
-    std::vector<char> used(size_t(op->r), 0);
-    for (int c = 0; c < op->n_colors; ++c) {
-        for (int ti = op->color_start_h[size_t(c)]; ti < op->color_start_h[size_t(c) + 1]; ++ti) {
-            const pc::Tile &t = op->tiles_h[size_t(ti)];
-            int64_t delta[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
-            bool keep = true;
-            for (int a = 0; a < d && keep; ++a) {
-                const int64_t lo = std::max<int64_t>(t.in_lo[a], clo[a]);
-                const int64_t hi = std::min<int64_t>(int64_t(t.in_lo[a]) + t.in_ext[a] - 1, chi[a]);
-                delta[a] = lo - t.in_lo[a];
-                ext[a] = hi - lo + 1;
-                const int64_t o_lo = t.out_lo[a] + delta[a];
-                const int64_t o_hi = o_lo + ext[a] + t.kext[a] - 2;
-                keep = ext[a] > 0 && o_hi >= olo[a] && o_lo <= ohi[a];
-            }
-            if (!keep) continue;
-            pc::Tile u = t;
-            for (int a = 0; a < d; ++a) {
-                u.in_lo[a] = int32_t(t.in_lo[a] + delta[a] - clo[a]);
-                u.in_ext[a] = int32_t(ext[a]);
-                u.out_lo[a] = int32_t(t.out_lo[a] + delta[a] - olo[a]);
-            }
-            // weight strides: 2D {ext1, 1}; 3D {ext1 * ext2, ext2} with unit stride on the last axis
-            u.w_base = t.w_base + delta[0] * t.w_ld[0] + delta[1] * t.w_ld[1] + (d == 3 ? delta[2] : 0);
-            remap[size_t(ti)] = int32_t(b.tiles.size());
-            b.tiles.push_back(u);
-            for (int q = op->dep_start_h[size_t(ti)]; q < op->dep_start_h[size_t(ti) + 1]; ++q) {
-                const int32_t m = remap[size_t(op->dep_h[size_t(q)])];
-                if (m >= 0) b.dep.push_back(m);
-            }
-            b.dep_start.push_back(int32_t(b.dep.size()));
-            if (!used[size_t(t.patch)]) {
-                used[size_t(t.patch)] = 1;
-                ++b.terms;
-            }
-        }
-        if (int32_t(b.tiles.size()) > b.color_start.back()) b.color_start.push_back(int32_t(b.tiles.size()));
-    }
-}
-
-const char *free_block_plan(pc_block_plan *bp) {
-    if (!bp) return nullptr;
-    const char *bad = nullptr;
-    auto chk = [&](cudaError_t e, const char *what) {
-        if (e != cudaSuccess && !bad) bad = what;
-    };
-    chk(cudaFree(bp->d_tiles), "tiles");
-    chk(cudaFree(bp->d_color_start), "colours");
-    chk(cudaFree(bp->d_dep_start), "dependency starts");
-    chk(cudaFree(bp->d_dep), "dependencies");
-    chk(cudaFree(bp->d_done), "ordering flags");
-    chk(cudaFree(bp->d_ctrl), "control block");
-    for (pc::LaunchDesc *h : bp->h_desc) chk(cudaFreeHost(h), "launch descriptors");
-    for (char *h : bp->h_runs) chk(cudaFreeHost(h), "run tables");
-    chk(cudaFree(bp->d_runs), "run tables");
-    chk(cudaFree(bp->d_desc), "launch descriptors");
-    chk(cudaFree(bp->d_seg_done), "segment counters");
-    if (bp->desc_ev) chk(cudaEventDestroy(bp->desc_ev), "descriptor event");
-    delete bp;
     return bad;
 }
 
@@ -1189,539 +1093,6 @@ pc_status pc_apply_plain(pc_operator *op, int32_t nrhs, const void *x, int64_t l
     pc_status st = pc::plain_apply(op, nrhs, x, ldx, y, ldy, static_cast<cudaStream_t>(stream), err);
     if (st != PC_OK) return fail(ctx, st, err);
     op->last_stream = static_cast<cudaStream_t>(stream);
-    return PC_OK;
-}
-
-pc_status pc_estimator_create(pc_context *ctx, const pc_box *box, pc_precision prec, int32_t q, const void *z,
-                              int64_t ldz, const void *y, int64_t ldy, pc_estimator **est) {
-    if (!est) return fail(ctx, PC_ERR_ARG, "est is null");
-    *est = nullptr;
-    if (!ctx || !box || !z || !y) return fail(ctx, PC_ERR_ARG, "null context, box, z or y");
-    if (box->ndim != 2) return fail(ctx, PC_ERR_UNSUPPORTED, "the incremental estimator covers 2D boxes");
-    if (prec != PC_FP32 && prec != PC_FP64) return fail(ctx, PC_ERR_UNSUPPORTED, "precision must be PC_FP32 or PC_FP64");
-    if (q < 1) return fail(ctx, PC_ERR_ARG, "q must be >= 1");
-    const int64_t N = box->shape[0] * box->shape[1];
-    if (box->shape[0] < 2 || box->shape[1] < 2 || ldz < N || ldy < N)
-        return fail(ctx, PC_ERR_ARG, "bad box, or ldz / ldy < N");
-    const size_t elem = prec == PC_FP64 ? 8 : 4;
-    if (reinterpret_cast<uintptr_t>(z) % elem || reinterpret_cast<uintptr_t>(y) % elem)
-        return fail(ctx, PC_ERR_ARG, "z and y must be aligned to the element size");
-    DeviceGuard dg(ctx->device);
-    if (!dg.ok) return fail(ctx, PC_ERR_CUDA, "cannot select the context's device");
-    auto *e = new (std::nothrow) pc_estimator;
-    if (!e) return fail(ctx, PC_ERR_NOMEM, "out of host memory");
-    e->ctx = ctx;
-    e->prec = prec;
-    e->elem = elem;
-    e->shape[0] = box->shape[0];
-    e->shape[1] = box->shape[1];
-    e->N = N;
-    e->q = q;
-    e->z = z;
-    e->ldz = ldz;
-    e->y = y;
-    e->ldy = ldy;
-    const cudaError_t ce = cudaMalloc(&e->d_yt, elem * size_t(q) * size_t(N));
-    if (ce != cudaSuccess) {
-        delete e;
-        return cuda_fail(ctx, ce, "allocating the estimator scratch");
-    }
-    *est = e;
-    return PC_OK;
-}
-
-pc_status pc_estimator_update(pc_estimator *est, pc_operator *op, double *eta, int32_t *recomputed,
-                              pc_stream stream) {
-    if (!est) return fail(nullptr, PC_ERR_ARG, "estimator is null");
-    pc_context *ctx = est->ctx;
-    if (!op || !eta) return fail(ctx, PC_ERR_ARG, "null operator or eta");
-    if (op->d != 2 || op->shape[0] != est->shape[0] || op->shape[1] != est->shape[1])
-        return fail(ctx, PC_ERR_ARG, "the operator's box differs from the estimator's");
-    if (op->prec != est->prec) return fail(ctx, PC_ERR_ARG, "the operator's precision differs from the estimator's");
-    DeviceGuard dg(ctx->device);
-    if (!dg.ok) return fail(ctx, PC_ERR_CUDA, "cannot select the context's device");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int r = op->r;
-    const int32_t q = est->q, nsub = op->split.nsub, nsub2 = nsub * nsub;
-    // layout of the new arena; kept blocks and points to recompute
-    std::vector<int64_t> blk_off(size_t(std::max(r, 1)), 0), copies;
-    std::vector<char> marked(size_t(std::max(r, 1)), 0);
-    std::map<std::pair<int32_t, int32_t>, pc_estimator::Entry> next;
-    int64_t total = 0;
-    int32_t nmarked = 0;
-    for (int k = 0; k < r; ++k) {
-        pc_estimator::Entry ne{};
-        for (int a = 0; a < 2; ++a) {
-            ne.bb_lo[a] = op->bb_lo_h[size_t(k) * 3 + size_t(a)];
-            ne.bb_ext[a] = op->bb_ext_h[size_t(k) * 3 + size_t(a)];
-        }
-        ne.hash = op->phiE_hash[size_t(k)];
-        ne.P = op->P;
-        ne.T = op->T;
-        ne.nsub = nsub;
-        ne.off = total;
-        ne.len = int64_t(nsub2) * q * int64_t(ne.bb_ext[0]) * ne.bb_ext[1];
-        blk_off[size_t(k)] = total;
-        total += ne.len;
-        const std::pair<int32_t, int32_t> key{op->pts_h[size_t(k) * 3], op->pts_h[size_t(k) * 3 + 1]};
-        const auto it = est->cache.find(key);
-        const bool same = it != est->cache.end() && it->second.hash == ne.hash && it->second.P == ne.P &&
-                          it->second.T == ne.T && it->second.nsub == ne.nsub && it->second.len == ne.len &&
-                          std::equal(ne.bb_lo, ne.bb_lo + 2, it->second.bb_lo) &&
-                          std::equal(ne.bb_ext, ne.bb_ext + 2, it->second.bb_ext);
-        if (same) {
-            copies.insert(copies.end(), {it->second.off, ne.off, ne.len});
-        } else {
-            marked[size_t(k)] = 1;
-            ++nmarked;
-        }
-        next[key] = ne;
-    }
-    // the recomputed points' tiles, each storing its block (one colour, no ordering needed)
-    std::vector<pc::Tile> tiles;
-    std::vector<pc::StoreDesc> sds;
-    for (const pc::Tile &t : op->tiles_h) {
-        const int k = t.patch;
-        if (!marked[size_t(k)]) continue;
-        const int sw = t.spec - k * nsub2;
-        const int64_t lo0 = op->bb_lo_h[size_t(k) * 3], lo1 = op->bb_lo_h[size_t(k) * 3 + 1];
-        const int64_t e0 = op->bb_ext_h[size_t(k) * 3], e1 = op->bb_ext_h[size_t(k) * 3 + 1];
-        pc::StoreDesc sd{};
-        sd.off = blk_off[size_t(k)] + int64_t(sw) * q * e0 * e1 + (t.in_lo[0] - lo0) * e1 + (t.in_lo[1] - lo1);
-        sd.ld_rhs = e0 * e1;
-        sd.ld_row = int32_t(e1);
-        tiles.push_back(t);
-        sds.push_back(sd);
-    }
-    const int32_t nt = int32_t(tiles.size());
-    const int32_t npairs = (q + 1) / 2;
-    // device work; every buffer of this call is released before it returns
-    void *arena = nullptr;
-    pc::Tile *d_tiles = nullptr;
-    pc::StoreDesc *d_sd = nullptr;
-    int32_t *d_cs = nullptr, *d_ds = nullptr, *d_dep = nullptr, *d_ctrl = nullptr;
-    uint32_t *d_done = nullptr;
-    int64_t *d_blk = nullptr, *d_copies = nullptr;
-    double *d_sums = nullptr;
-    size_t acct = 0;
-    auto release = [&]() {
-        cudaFree(d_tiles);
-        cudaFree(d_sd);
-        cudaFree(d_cs);
-        cudaFree(d_ds);
-        cudaFree(d_dep);
-        cudaFree(d_ctrl);
-        cudaFree(d_done);
-        cudaFree(d_blk);
-        cudaFree(d_copies);
-        cudaFree(d_sums);
-    };
-    auto bail = [&](cudaError_t ce, const char *what) {
-        cudaStreamSynchronize(s);
-        release();
-        cudaFree(arena);
-        return cuda_fail(ctx, ce, what);
-    };
-    cudaError_t e = cudaMalloc(&arena, est->elem * size_t(std::max<int64_t>(total, 1)));
-    if (e != cudaSuccess) return bail(e, "allocating the correlation arena");
-    if (!copies.empty()) {
-        if ((e = upload(&d_copies, copies.data(), copies.size(), acct)) != cudaSuccess)
-            return bail(e, "uploading the block copies");
-        if ((e = pc::launch_block_copies(est->prec, d_copies, int32_t(copies.size() / 3), est->arena, arena, s)) !=
-            cudaSuccess)
-            return bail(e, "launching the block copies");
-    }
-    if (nt > 0) {
-        const std::vector<int32_t> cs{0, nt}, ds(size_t(nt) + 1, 0), dep{0};
-        if ((e = upload(&d_tiles, tiles.data(), tiles.size(), acct)) != cudaSuccess ||
-            (e = upload(&d_sd, sds.data(), sds.size(), acct)) != cudaSuccess ||
-            (e = upload(&d_cs, cs.data(), cs.size(), acct)) != cudaSuccess ||
-            (e = upload(&d_ds, ds.data(), ds.size(), acct)) != cudaSuccess ||
-            (e = upload(&d_dep, dep.data(), dep.size(), acct)) != cudaSuccess ||
-            (e = cudaMalloc(&d_done, sizeof(uint32_t) * size_t(nt) * size_t(npairs))) != cudaSuccess ||
-            (e = cudaMemset(d_done, 0, sizeof(uint32_t) * size_t(nt) * size_t(npairs))) != cudaSuccess ||
-            (e = cudaMalloc(&d_ctrl, 64)) != cudaSuccess || (e = cudaMemset(d_ctrl, 0, 64)) != cudaSuccess)
-            return bail(e, "uploading the correlation work list");
-        pc::ApplyParams p{};
-        p.x = est->z;
-        p.y = est->d_yt;   // not written in store mode
-        p.ldx = est->ldz;
-        p.ldy = est->N;
-        p.nrhs = q;
-        p.npairs = npairs;
-        p.n[0] = int32_t(est->shape[0]);
-        p.n[1] = int32_t(est->shape[1]);
-        p.n[2] = 1;
-        p.nx[0] = p.n[0];
-        p.nx[1] = p.n[1];
-        p.nx[2] = p.n[2];
-        p.R = op->R;
-        p.tiles = d_tiles;
-        p.color_start = d_cs;
-        p.n_colors = 1;
-        p.dep_start = d_ds;
-        p.dep = d_dep;
-        p.done = d_done;
-        p.done_ld = npairs;
-        p.epoch = 1u;
-        p.ctrl = d_ctrl;
-        p.spec = op->d_spec;
-        p.spec_stride = op->spec_stride;
-        p.w = op->d_w;
-        p.tw = op->d_tw;
-        p.total_items = int64_t(nt) * npairs;
-        p.store = d_sd;
-        p.store_base = arena;
-        const int ctas = int(std::min<int64_t>(op->ctas, p.total_items));
-        if ((e = pc::launch_fft2d(p, op->P, op->prec, ctas, s, true)) != cudaSuccess)
-            return bail(e, "launching the correlations");
-    }
-    if ((e = upload(&d_blk, blk_off.data(), blk_off.size(), acct)) != cudaSuccess)
-        return bail(e, "uploading the block offsets");
-    if ((e = pc::launch_corr_combine(est->prec, op->entry, op->d_w, arena, d_blk, nsub2, q, est->d_yt, est->N, s)) !=
-        cudaSuccess)
-        return bail(e, "launching the combination");
-    if ((e = cudaMalloc(&d_sums, sizeof(double) * size_t(std::max(op->n_cells, 1)))) != cudaSuccess)
-        return bail(e, "allocating the cell sums");
-    if ((e = pc::launch_cell_sqdiff(est->prec, est->d_yt, est->N, est->y, est->ldy, q, op->d_cells, op->n_cells,
-                                    est->shape[0], est->shape[1], d_sums, s)) != cudaSuccess)
-        return bail(e, "launching the cell reduction");
-    std::vector<double> sums(size_t(op->n_cells));
-    int32_t ctrl[4] = {0, 0, 0, 0};
-    if ((e = cudaMemcpyAsync(sums.data(), d_sums, sizeof(double) * sums.size(), cudaMemcpyDeviceToHost, s)) !=
-            cudaSuccess ||
-        (d_ctrl && (e = cudaMemcpyAsync(ctrl, d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
-        (e = cudaStreamSynchronize(s)) != cudaSuccess)
-        return bail(e, "reading the cell sums");
-    release();
-    if (ctrl[2]) {
-        // the new blocks are not trusted: keep the previous cache
-        cudaFree(arena);
-        return fail(ctx, PC_ERR_TIMEOUT, "a bounded wait in the correlation kernel timed out");
-    }
-    cudaFree(est->arena);
-    est->arena = arena;
-    est->cache.swap(next);
-    est->recomputed_total += nmarked;
-    if (recomputed) *recomputed = nmarked;
-    for (int c = 0; c < op->n_cells; ++c) eta[c] = std::sqrt(sums[size_t(c)] / double(q));
-    return PC_OK;
-}
-
-pc_status pc_estimator_destroy(pc_estimator *est) {
-    if (!est) return PC_OK;
-    pc_context *ctx = est->ctx;
-    DeviceGuard dg(ctx->device);
-    const cudaError_t se = cudaDeviceSynchronize();
-    const cudaError_t e1 = cudaFree(est->d_yt), e2 = cudaFree(est->arena);
-    delete est;
-    if (se != cudaSuccess) return cuda_fail(ctx, se, "synchronising before freeing the estimator");
-    if (e1 != cudaSuccess || e2 != cudaSuccess) return fail(ctx, PC_ERR_CUDA, "freeing the estimator");
-    return PC_OK;
-}
-
-pc_status pc_block_plan_create_many(pc_operator *op, int32_t nblocks, const int64_t *t_lo, const int64_t *t_hi,
-                                    const int64_t *s_lo, const int64_t *s_hi, int32_t adjoint, pc_block_plan **plan) {
-    if (!plan) return fail(op ? op->ctx : nullptr, PC_ERR_ARG, "plan is null");
-    *plan = nullptr;
-    if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
-    pc_context *ctx = op->ctx;
-    if (nblocks < 1) return fail(ctx, PC_ERR_ARG, "nblocks must be >= 1");
-    if (!t_lo || !t_hi || !s_lo || !s_hi) return fail(ctx, PC_ERR_ARG, "null box bound");
-    if (adjoint != 0 && adjoint != 1) return fail(ctx, PC_ERR_ARG, "adjoint must be 0 or 1");
-    if (op->prec == PC_BF16X3) return fail(ctx, PC_ERR_UNSUPPORTED, "block applies cover FP32 and FP64 operators");
-    const int d = op->d;
-    for (int32_t i = 0; i < nblocks; ++i)
-        for (int a = 0; a < d; ++a) {
-            const int64_t j = int64_t(i) * d + a;
-            if (t_lo[j] < 0 || t_lo[j] > t_hi[j] || t_hi[j] >= op->shape[size_t(a)])
-                return fail(ctx, PC_ERR_ARG, "target box T must satisfy 0 <= lo <= hi < shape");
-            if (s_lo[j] < 0 || s_lo[j] > s_hi[j] || s_hi[j] >= op->shape[size_t(a)])
-                return fail(ctx, PC_ERR_ARG, "source box S must satisfy 0 <= lo <= hi < shape");
-        }
-    auto *bp = new (std::nothrow) pc_block_plan;
-    if (!bp) return fail(ctx, PC_ERR_NOMEM, "out of host memory");
-    bp->op = op;
-    bp->adjoint = adjoint == 1;
-    std::vector<pc::Tile> tiles;
-    std::vector<int32_t> cs, ds, dep;
-    for (int32_t i = 0; i < nblocks; ++i) {
-        BlockSchedule b;
-        build_block_schedule(op, t_lo + d * i, t_hi + d * i, s_lo + d * i, s_hi + d * i, adjoint == 1, b);
-        pc_block_plan::Block blk{};
-        for (int a = 0; a < 3; ++a) {
-            blk.t_ext[a] = a < d ? t_hi[d * i + a] - t_lo[d * i + a] + 1 : 1;
-            blk.s_ext[a] = a < d ? s_hi[d * i + a] - s_lo[d * i + a] + 1 : 1;
-        }
-        blk.nT = blk.t_ext[0] * blk.t_ext[1] * blk.t_ext[2];
-        blk.nS = blk.s_ext[0] * blk.s_ext[1] * blk.s_ext[2];
-        blk.tile_off = int32_t(tiles.size());
-        blk.n_tiles = int32_t(b.tiles.size());
-        blk.cs_off = int32_t(cs.size());
-        blk.n_colors = int32_t(b.color_start.size()) - 1;
-        blk.ds_off = int32_t(ds.size());
-        blk.dep_off = int32_t(dep.size());
-        blk.terms = b.terms;
-        tiles.insert(tiles.end(), b.tiles.begin(), b.tiles.end());
-        cs.insert(cs.end(), b.color_start.begin(), b.color_start.end());
-        ds.insert(ds.end(), b.dep_start.begin(), b.dep_start.end());
-        dep.insert(dep.end(), b.dep.begin(), b.dep.end());
-        bp->blocks.push_back(blk);
-        bp->n_tiles += blk.n_tiles;
-        bp->terms += blk.terms;
-    }
-    if (dep.empty()) dep.push_back(0);
-    bp->cs_h = cs;
-    DeviceGuard dg(ctx->device);
-    if (!dg.ok) {
-        free_block_plan(bp);
-        return fail(ctx, PC_ERR_CUDA, "cannot select the context's device");
-    }
-    size_t acct = 0;
-    auto bail = [&](cudaError_t ee, const char *what) {
-        pc_status s2 = cuda_fail(ctx, ee, what);
-        free_block_plan(bp);
-        return s2;
-    };
-    cudaError_t e;
-    if (!tiles.empty() && (e = upload(&bp->d_tiles, tiles.data(), tiles.size(), acct)) != cudaSuccess)
-        return bail(e, "tiles");
-    if ((e = upload(&bp->d_color_start, cs.data(), cs.size(), acct)) != cudaSuccess ||
-        (e = upload(&bp->d_dep_start, ds.data(), ds.size(), acct)) != cudaSuccess ||
-        (e = upload(&bp->d_dep, dep.data(), dep.size(), acct)) != cudaSuccess)
-        return bail(e, "colours and dependencies");
-    if ((e = cudaMalloc(&bp->d_ctrl, 64)) != cudaSuccess) return bail(e, "control block");
-    if ((e = cudaMemset(bp->d_ctrl, 0, 64)) != cudaSuccess) return bail(e, "control block");
-    if (nblocks > 1 && d == 2) {
-        const int rounds = (nblocks + pc::kMaxSegments - 1) / pc::kMaxSegments;
-        for (int rnd = 0; rnd < rounds; ++rnd) {
-            int32_t runs = 0;
-            for (int32_t i = rnd * pc::kMaxSegments; i < std::min(nblocks, (rnd + 1) * pc::kMaxSegments); ++i)
-                runs += bp->blocks[size_t(i)].n_colors;
-            bp->run_cap = std::max(bp->run_cap, runs);
-        }
-        const size_t run_bytes = 8 * size_t(bp->run_cap + 1) + 8 * size_t(bp->run_cap);
-        for (int rnd = 0; rnd < rounds; ++rnd) {
-            pc::LaunchDesc *h = nullptr;
-            char *hr = nullptr;
-            if ((e = cudaHostAlloc(reinterpret_cast<void **>(&h), sizeof(pc::LaunchDesc), 0)) != cudaSuccess)
-                return bail(e, "launch descriptors");
-            bp->h_desc.push_back(h);
-            if ((e = cudaHostAlloc(reinterpret_cast<void **>(&hr), run_bytes, 0)) != cudaSuccess)
-                return bail(e, "run tables");
-            bp->h_runs.push_back(hr);
-        }
-        if ((e = cudaMalloc(&bp->d_runs, run_bytes * size_t(rounds))) != cudaSuccess) return bail(e, "run tables");
-        if ((e = cudaMalloc(&bp->d_desc, sizeof(pc::LaunchDesc) * size_t(rounds))) != cudaSuccess ||
-            (e = cudaMalloc(&bp->d_seg_done, sizeof(uint32_t) * pc::kMaxSegments)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&bp->desc_ev, cudaEventDisableTiming)) != cudaSuccess)
-            return bail(e, "launch descriptors");
-    }
-    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "synchronising after the plan's uploads");
-    *plan = bp;
-    return PC_OK;
-}
-
-pc_status pc_block_plan_create(pc_operator *op, const int64_t *t_lo, const int64_t *t_hi, const int64_t *s_lo,
-                               const int64_t *s_hi, int32_t adjoint, pc_block_plan **plan) {
-    return pc_block_plan_create_many(op, 1, t_lo, t_hi, s_lo, s_hi, adjoint, plan);
-}
-
-pc_status pc_block_apply_many(pc_block_plan *bp, int32_t nrhs, const void *const *x, const int64_t *ldx,
-                              void *const *y, const int64_t *ldy, pc_stream stream) {
-    if (!bp) return fail(nullptr, PC_ERR_ARG, "plan is null");
-    pc_operator *op = bp->op;
-    pc_context *ctx = op->ctx;
-    if (nrhs < 0) return fail(ctx, PC_ERR_ARG, "nrhs < 0");
-    if (nrhs == 0) return PC_OK;
-    if (!x || !ldx || !y || !ldy) return fail(ctx, PC_ERR_ARG, "null pointer array");
-    const int32_t nb = int32_t(bp->blocks.size());
-    const int64_t el = int64_t(op->elem);
-    std::vector<std::pair<uintptr_t, uintptr_t>> yr(static_cast<size_t>(nb));
-    for (int32_t i = 0; i < nb; ++i) {
-        const pc_block_plan::Block &b = bp->blocks[size_t(i)];
-        if (!x[i] || !y[i]) return fail(ctx, PC_ERR_ARG, "null x or y");
-        if (ldx[i] < b.nS || ldy[i] < b.nT) return fail(ctx, PC_ERR_ARG, "need ldx >= |S| and ldy >= |T|");
-        const uintptr_t xa = reinterpret_cast<uintptr_t>(x[i]), ya = reinterpret_cast<uintptr_t>(y[i]);
-        if (xa % op->elem || ya % op->elem) return fail(ctx, PC_ERR_ARG, "x and y must be aligned to the element size");
-        const uintptr_t xe = xa + uintptr_t((int64_t(nrhs - 1) * ldx[i] + b.nS) * el);
-        const uintptr_t ye = ya + uintptr_t((int64_t(nrhs - 1) * ldy[i] + b.nT) * el);
-        if (xa < ye && ya < xe) return fail(ctx, PC_ERR_ARG, "x and y overlap");
-        yr[size_t(i)] = {ya, ye};
-    }
-    if (nb > 1) {
-        std::sort(yr.begin(), yr.end());
-        for (size_t i = 1; i < yr.size(); ++i)
-            if (yr[i].first < yr[i - 1].second) return fail(ctx, PC_ERR_ARG, "the blocks' y arrays overlap");
-    }
-    DeviceGuard dg(ctx->device);
-    if (!dg.ok) return fail(ctx, PC_ERR_CUDA, "cannot select the context's device");
-    const int32_t npairs = (nrhs + 1) / 2;
-    cudaError_t e = cudaSuccess;
-    if (bp->n_tiles > 0 && npairs > bp->done_cap) {
-        if (bp->launched && (e = cudaDeviceSynchronize()) != cudaSuccess)
-            return cuda_fail(ctx, e, "synchronising before growing the plan's flags");
-        cudaFree(bp->d_done);
-        bp->d_done = nullptr;
-        bp->done_cap = 0;
-        const int32_t cap = std::max<int32_t>(npairs, 32);
-        const size_t bytes = sizeof(uint32_t) * size_t(bp->n_tiles) * size_t(cap);
-        if ((e = cudaMalloc(&bp->d_done, bytes)) != cudaSuccess) return cuda_fail(ctx, e, "allocating plan flags");
-        if ((e = cudaMemset(bp->d_done, 0, bytes)) != cudaSuccess) return cuda_fail(ctx, e, "clearing plan flags");
-        bp->done_cap = cap;
-        bp->epoch = 0;
-    }
-    if (++bp->epoch == 0) bp->epoch = 1;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    auto params = [&](int32_t i) {
-        const pc_block_plan::Block &b = bp->blocks[size_t(i)];
-        pc::ApplyParams p{};
-        p.x = x[i];
-        p.y = y[i];
-        p.ldx = ldx[i];
-        p.ldy = ldy[i];
-        p.nrhs = nrhs;
-        p.npairs = npairs;
-        for (int a = 0; a < 3; ++a) {
-            p.n[a] = int32_t(b.t_ext[a]);
-            p.nx[a] = int32_t(b.s_ext[a]);
-        }
-        p.R = op->R;
-        p.tiles = bp->d_tiles ? bp->d_tiles + b.tile_off : nullptr;
-        p.color_start = bp->d_color_start + b.cs_off;
-        p.n_colors = b.n_colors;
-        p.dep_start = bp->d_dep_start + b.ds_off;
-        p.dep = bp->d_dep + b.dep_off;
-        p.done = bp->d_done ? bp->d_done + int64_t(b.tile_off) * bp->done_cap : nullptr;
-        p.done_ld = bp->done_cap;
-        p.epoch = bp->epoch;
-        p.ctrl = bp->d_ctrl;
-        p.spec = op->d_spec;
-        p.spec_stride = op->spec_stride;
-        p.w = op->d_w;
-        p.tw = op->d_tw;
-        p.total_items = int64_t(b.n_tiles) * npairs;
-        return p;
-    };
-    int64_t launches = 0;
-    if (nb == 1 || op->d == 3) {
-        // one block per launch (3D: the patch kernel runs one block at a time, on
-        // the operator's per-CTA scratch volumes)
-        for (int32_t i = 0; i < nb; ++i) {
-            const pc::ApplyParams p = params(i);
-            if ((e = pc::launch_zero(p, bp->blocks[size_t(i)].nT, op->prec, s)) != cudaSuccess)
-                return cuda_fail(ctx, e, "launching the zero kernel");
-            ++launches;
-            if (p.total_items > 0) {
-                const int ctas = int(std::min<int64_t>(op->ctas, p.total_items));
-                e = op->d == 3 ? pc::launch_fft3d(p, ctas, op->d_scratch, s, bp->adjoint)
-                               : pc::launch_fft2d(p, op->P, op->prec, ctas, s, bp->adjoint);
-                if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the patch kernel");
-                ++launches;
-            }
-        }
-    } else {
-        size_t smem = 0;
-        if ((e = pc::fft2d_configure(op->P, op->prec, nullptr, &smem)) != cudaSuccess)
-            return cuda_fail(ctx, e, "configuring the patch kernel");
-        // the previous call's descriptor uploads have completed before the host descriptors are rewritten
-        if (bp->launched && (e = cudaEventSynchronize(bp->desc_ev)) != cudaSuccess)
-            return cuda_fail(ctx, e, "waiting for the previous descriptor upload");
-        for (int32_t b0 = 0, rnd = 0; b0 < nb; b0 += pc::kMaxSegments, ++rnd) {
-            const int32_t nseg = std::min<int32_t>(pc::kMaxSegments, nb - b0);
-            pc::LaunchDesc &d = *bp->h_desc[size_t(rnd)];
-            std::memset(&d, 0, sizeof(pc::LaunchDesc));
-            int32_t maxc = 0;
-            for (int32_t q = 0; q < nseg; ++q) {
-                pc::Segment &sg = d.seg[q];
-                sg.p = params(b0 + q);
-                sg.slot = -1;
-                maxc = std::max(maxc, bp->blocks[size_t(b0 + q)].n_colors);
-            }
-            // run table: colour-major across the round's blocks, so that every
-            // colour step holds work of all of them; each run's dependencies
-            // (lower colours of its own block) come earlier in the order
-            const size_t run_bytes = 8 * size_t(bp->run_cap + 1) + 8 * size_t(bp->run_cap);
-            char *hr = bp->h_runs[size_t(rnd)];
-            int64_t *run_begin = reinterpret_cast<int64_t *>(hr);
-            int32_t *run_segcol = reinterpret_cast<int32_t *>(hr + 8 * size_t(bp->run_cap + 1));
-            int32_t nrun = 0;
-            int64_t items = 0;
-            for (int32_t c = 0; c < maxc; ++c)
-                for (int32_t q = 0; q < nseg; ++q) {
-                    const pc_block_plan::Block &b = bp->blocks[size_t(b0 + q)];
-                    if (c >= b.n_colors) continue;
-                    const int32_t ntc = bp->cs_h[size_t(b.cs_off + c + 1)] - bp->cs_h[size_t(b.cs_off + c)];
-                    run_begin[nrun] = items;
-                    run_segcol[2 * nrun] = q;
-                    run_segcol[2 * nrun + 1] = c;
-                    items += int64_t(ntc) * npairs;
-                    ++nrun;
-                }
-            run_begin[nrun] = items;
-            char *dr = bp->d_runs + run_bytes * size_t(rnd);
-            d.nseg = nseg;
-            d.nrun = nrun;
-            d.total_items = items;
-            d.run_begin = reinterpret_cast<const int64_t *>(dr);
-            d.run_segcol = reinterpret_cast<const int32_t *>(dr + 8 * size_t(bp->run_cap + 1));
-            pc::LaunchDesc *dd = bp->d_desc + rnd;
-            if ((e = cudaMemcpyAsync(dd, &d, sizeof(pc::LaunchDesc), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-                (e = cudaMemcpyAsync(dr, hr, run_bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-                return cuda_fail(ctx, e, "uploading a launch descriptor");
-            const int ctas = int(std::max<int64_t>(1, std::min<int64_t>(op->ctas, items)));
-            if ((e = pc::launch_round(dd, reinterpret_cast<unsigned long long *>(bp->d_ctrl), bp->d_ctrl + 2,
-                                      bp->d_seg_done, nullptr, ctas, smem, s, op->P, op->prec, bp->adjoint)) !=
-                cudaSuccess)
-                return cuda_fail(ctx, e, "launching the blocks");
-            launches += 2;
-        }
-        cudaEventRecord(bp->desc_ev, s);
-    }
-    bp->last_stream = s;
-    bp->launched = true;
-    (void)launches;
-    return PC_OK;
-}
-
-pc_status pc_block_apply(pc_block_plan *bp, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
-                         pc_stream stream) {
-    if (bp && bp->blocks.size() != 1)
-        return fail(bp->op->ctx, PC_ERR_ARG, "the plan holds several blocks: use pc_block_apply_many");
-    return pc_block_apply_many(bp, nrhs, &x, &ldx, &y, &ldy, stream);
-}
-
-pc_status pc_block_plan_info(const pc_block_plan *bp, int32_t *terms, int32_t *tiles) {
-    if (!bp) return fail(nullptr, PC_ERR_ARG, "plan is null");
-    if (terms) *terms = bp->terms;
-    if (tiles) *tiles = bp->n_tiles;
-    return PC_OK;
-}
-
-pc_status pc_block_plan_check(pc_block_plan *bp) {
-    if (!bp) return fail(nullptr, PC_ERR_ARG, "plan is null");
-    pc_context *ctx = bp->op->ctx;
-    DeviceGuard dg(ctx->device);
-    cudaError_t e = cudaStreamSynchronize(bp->last_stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "asynchronous CUDA error");
-    int32_t ctrl[4] = {0, 0, 0, 0};
-    if ((e = cudaMemcpy(ctrl, bp->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost)) != cudaSuccess)
-        return cuda_fail(ctx, e, "reading the status word");
-    if (ctrl[2]) {
-        cudaMemset(bp->d_ctrl + 2, 0, sizeof(int32_t));
-        return fail(ctx, PC_ERR_TIMEOUT, "a bounded wait in the patch kernel timed out");
-    }
-    return PC_OK;
-}
-
-pc_status pc_block_plan_destroy(pc_block_plan *bp) {
-    if (!bp) return PC_OK;
-    pc_context *ctx = bp->op->ctx;
-    DeviceGuard dg(ctx->device);
-    const cudaError_t se = cudaDeviceSynchronize();
-    const char *bad = free_block_plan(bp);
-    if (se != cudaSuccess) return cuda_fail(ctx, se, "synchronising before freeing the plan");
-    if (bad) return fail(ctx, PC_ERR_CUDA, std::string("freeing the plan: ") + bad);
     return PC_OK;
 }
 
