@@ -18,8 +18,14 @@ the tensor product of these bases.  Dense matrix products only, no FFT.
 
 w_k on Omega is the union of its pieces on the cells of cells(p_k); pieces on
 shared facets agree because both cells solve the same lower-dimensional
-problems.  3D grids must be conforming (no hanging nodes): the recursion over
-broken 2D facets is not built, and such a grid raises NotImplementedError.
+problems.
+
+Broken facets (Section 2.4): a facet of a 3D leaf that finer leaves across
+it divide is replaced by its constituent smaller boxes, the intersections of
+the facet with the facets of the leaves across it.  Each piece gets the
+harmonic extension of its own (node-split) edges, and the leaf's interior the
+3D extension of the union of its pieces.  In 2D the facets are edges, and
+splitting them at every sample point on them is the same construction.
 """
 from __future__ import annotations
 
@@ -111,12 +117,12 @@ def harmonic_on_box(lo, hi, nodes: Dict[tuple, float]) -> np.ndarray:
         return np.full(shape, nodes[tuple(int(v) for v in lo)])
     if m == 1:
         return _segment_values(lo, hi, axes[0], nodes).reshape(shape)
-    inside = [p for p in nodes if all(lo[a] <= p[a] <= hi[a] for a in range(d))]
-    corner_set = set(box_corners(lo, hi))
-    if m >= 3 or (m == 2 and d == 3):
-        extra = [p for p in inside if p not in corner_set]
-        if extra:
-            raise NotImplementedError("3D harmonic weights with hanging nodes are not built")
+    # a sample point in the relative interior of a box of dimension >= 2 would
+    # make it a broken box: those are split into pieces before they get here
+    interior = [p for p in nodes if all(lo[a] <= p[a] <= hi[a] for a in range(d))
+                and all(lo[a] < p[a] < hi[a] for a in axes)]
+    if interior:
+        raise ValueError("a sample point inside a %d-dim box: split it into its constituent boxes" % m)
     V = np.full(shape, np.nan)
     # boundary facets: fix one non-degenerate axis at its min or max
     for a in axes:
@@ -137,6 +143,32 @@ def harmonic_on_box(lo, hi, nodes: Dict[tuple, float]) -> np.ndarray:
     return Vs.reshape(shape)
 
 
+def facet_pieces(grid: Grid, c: int, a: int, side: int) -> List[Tuple[np.ndarray, np.ndarray]]:
+    """The boxes that make up facet (axis a, side 0 = min, 1 = max) of leaf c
+    (Section 2.4): the facet itself on the boundary of Omega, else its
+    intersections, of positive area, with the facets of the leaves across it."""
+    lo, hi = (np.array(v, dtype=np.int64) for v in grid.cells[c])
+    plane = int(hi[a] if side else lo[a])
+    flo, fhi = lo.copy(), hi.copy()
+    flo[a] = fhi[a] = plane
+    if (side == 0 and plane == 0) or (side == 1 and plane == grid.shape[a] - 1):
+        return [(flo, fhi)]
+    others = [b for b in range(grid.d) if b != a]
+    out = []
+    for n, (nlo, nhi) in enumerate(grid.cells):
+        if n == c or (side == 1 and nlo[a] != plane) or (side == 0 and nhi[a] != plane):
+            continue
+        plo, phi = flo.copy(), fhi.copy()
+        for b in others:
+            plo[b], phi[b] = max(lo[b], nlo[b]), min(hi[b], nhi[b])
+        if all(plo[b] < phi[b] for b in others):
+            out.append((plo, phi))
+    area = sum(int(np.prod([phi[b] - plo[b] for b in others])) for plo, phi in out)
+    if area != int(np.prod([hi[b] - lo[b] for b in others])):
+        raise ValueError("the leaves across a facet do not tile it")
+    return out
+
+
 def cell_weights(grid: Grid, c: int) -> Dict[int, np.ndarray]:
     """w_k restricted to leaf c, for every sample point p_k in c."""
     lo, hi = grid.cells[c]
@@ -144,7 +176,18 @@ def cell_weights(grid: Grid, c: int) -> Dict[int, np.ndarray]:
     out = {}
     for k in ks:
         nodes = {tuple(int(v) for v in grid.points[j]): (1.0 if j == k else 0.0) for j in ks}
-        out[int(k)] = harmonic_on_box(lo, hi, nodes)
+        if grid.d == 3:
+            # facets as their constituent boxes, then the 3D interior
+            shape = tuple(int(h - l + 1) for l, h in zip(lo, hi))
+            V = np.full(shape, np.nan)
+            for a in range(3):
+                for side in (0, 1):
+                    for plo, phi in facet_pieces(grid, c, a, side):
+                        sl = tuple(slice(int(x - o), int(y - o) + 1) for x, y, o in zip(plo, phi, lo))
+                        V[sl] = harmonic_on_box(plo, phi, nodes)
+            out[int(k)] = dirichlet_laplace(V)
+        else:
+            out[int(k)] = harmonic_on_box(lo, hi, nodes)
     return out
 
 

@@ -26,8 +26,10 @@ Y~ = A~* Z is updated incrementally, as Algorithm 1 does (`incremental`,
 the default): the correlations flip(phi_k^E) * Z of sample points whose
 phi_k^E and bbox(U_k) are unchanged are kept from the previous pass, and
 only new points and points with a new neighbour are recomputed
-(pc_estimator_update).  With incremental=False every pass recomputes all of
-them (pc_estimate_cell_errors).
+(pc_estimator_update).  With incremental=False, and for 3D boxes, every
+pass recomputes all of them (pc_estimate_cell_errors).  3D leaves with
+hanging nodes get their harmonic weights through the facet pieces of
+Section 2.4 (the library handles them when it builds each pass's operator).
 """
 from __future__ import annotations
 
@@ -87,7 +89,8 @@ def construct(ctx, shape, impulse: Callable[[np.ndarray], np.ndarray], R: int, Z
     points whose correlations each pass computed."""
     shape = tuple(int(n) for n in shape)
     q = Z.shape[0]
-    est = Estimator(ctx, shape, Z, Y, precision) if incremental else None
+    # the incremental estimator covers 2D boxes; 3D passes re-estimate in full
+    est = Estimator(ctx, shape, Z, Y, precision) if incremental and len(shape) == 2 else None
     recomputed = []
     ynorm = float(np.linalg.norm(Y.reshape(q, -1).double().cpu().numpy())) / np.sqrt(q)
     cells = _first_cells(shape)

@@ -26,6 +26,10 @@
 namespace pc {
 
 pc_status harmonic_cell_2d(const Geometry &g, int c, int k, std::vector<double> &vals, std::string &err);
+// 3D leaf with hanging nodes: its facets as their constituent boxes (the
+// intersections with the leaves across them), each with the 2D harmonic
+// extension of its node-split edges, then the 3D interior (Section 2.4).
+pc_status harmonic_cell_3d(const Geometry &g, int c, int k, std::vector<double> &vals, std::string &err);
 
 static bool lex_less(const I3 &a, const I3 &b) {
     for (int i = 0; i < 3; ++i)
@@ -183,17 +187,22 @@ pc_status build_weights(const Geometry &g, std::vector<double> &w, std::vector<i
                             }
                             wk[((i0 - bl[0]) * e1 + (i1 - bl[1])) * e2 + (i2 - bl[2])] = v;
                         }
-            } else {
-                if (g.d != 2) {
-                    err = "3D grids with hanging nodes are not supported";
-                    return PC_ERR_UNSUPPORTED;
-                }
+            } else if (g.d == 2) {
                 pc_status st = harmonic_cell_2d(g, c, k, vals, err);
                 if (st != PC_OK) return st;
                 const int64_t m1 = hi[1] - lo[1] + 1;
                 for (int64_t i0 = lo[0]; i0 <= hi[0]; ++i0)
                     for (int64_t i1 = lo[1]; i1 <= hi[1]; ++i1)
                         wk[(i0 - bl[0]) * e1 + (i1 - bl[1])] = vals[(i0 - lo[0]) * m1 + (i1 - lo[1])];
+            } else {
+                pc_status st = harmonic_cell_3d(g, c, k, vals, err);
+                if (st != PC_OK) return st;
+                const int64_t m1 = hi[1] - lo[1] + 1, m2 = hi[2] - lo[2] + 1;
+                for (int64_t i0 = lo[0]; i0 <= hi[0]; ++i0)
+                    for (int64_t i1 = lo[1]; i1 <= hi[1]; ++i1)
+                        for (int64_t i2 = lo[2]; i2 <= hi[2]; ++i2)
+                            wk[((i0 - bl[0]) * e1 + (i1 - bl[1])) * e2 + (i2 - bl[2])] =
+                                vals[size_t(((i0 - lo[0]) * m1 + (i1 - lo[1])) * m2 + (i2 - lo[2]))];
             }
         }
     }

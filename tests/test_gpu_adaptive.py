@@ -104,3 +104,33 @@ def test_ring_blur_refines_near_the_ring():
         e[x] = 1.0
         col = orc.apply(e[None]).ravel()
         assert np.max(np.abs(At[:, x] - col)) <= 1e-6 * np.abs(col).max()
+
+
+def test_3d_construction():
+    """Algorithm 1 in 3D (hanging nodes from the second split on), FP32: every
+    split follows the axis of change, the estimate reaches tau, and the final
+    leaves' estimates agree with the oracle's on the same leaves."""
+    from paper_1805_06018_gb300 import adaptive
+    from oracle.estimator import eta_from_adjoints
+    shape = (11, 12, 17)
+    L = 17.0
+    kern = workloads.GaussianAxis3D(lambda x: 1.0 + 0 * x[..., 0], lambda x: 1.0 + 0 * x[..., 0],
+                                    lambda x: 0.8 + 1.6 * x[..., 2] / L, 3)
+    A = workloads.dense_operator(shape, kern)
+    q = 4
+    Z = workloads.rhs(33, q, shape).reshape(q, -1).astype(np.float64)
+    Y = (Z @ A).astype(np.float32)
+    impulse = lambda pts: workloads.impulse_windows(shape, pts, kern)  # noqa: E731
+    op, cells, hist = adaptive.construct(context(), shape, impulse, 3,
+                                         torch.from_numpy(Z.astype(np.float32).reshape((q,) + shape)).cuda(),
+                                         torch.from_numpy(Y.reshape((q,) + shape)).cuda(), tau=0.06,
+                                         precision="fp32", max_passes=12, batch=2)
+    assert hist[-1][1] <= 0.06 < hist[0][1] and len(cells) > 8
+    for lo, hi in cells:
+        assert (lo[0], hi[0]) in ((0, 5), (5, 10)) and (lo[1], hi[1]) in ((0, 5), (5, 11))
+    g = Grid(shape, cells)
+    orc = PCOracle(shape, cells, workloads.impulse_windows(shape, g.points, kern), 3)
+    ref = eta_from_adjoints(g, orc.apply_adjoint(Z.reshape((q,) + shape)), Y.astype(np.float64).reshape(q, -1))
+    eta = op.estimate_cell_errors(torch.from_numpy(Z.astype(np.float32).reshape((q,) + shape)).cuda(),
+                                  torch.from_numpy(Y.reshape((q,) + shape)).cuda(), len(cells))
+    assert np.max(np.abs(eta - ref)) <= 1e-4 * ref.max()

@@ -256,3 +256,15 @@ def test_3d_workload_128_sampled():
     ref = orc.apply(x, points=pts)
     err = np.linalg.norm(y[:, pts] - ref, axis=1) / np.linalg.norm(ref, axis=1)
     assert np.all(err <= TOL["fp32"]), err
+
+
+def test_3d_hanging_nodes():
+    """A 3D grid with broken facets (octants of 13^3, one octant split again):
+    the library's facet-piece weights and the apply against the oracle."""
+    from test_oracle_geometry import _broken_grid
+    shape, cells = _broken_grid(1)
+    kern = workloads.Skewed([0.7, -0.4, 0.3], lambda x: 1.1 + 0.3 * np.sin(x[..., 0] / 4.0), 3)
+    op, orc = make_pair(shape, np.array(cells), kern, "fp32")
+    x = workloads.rhs(124, 3, shape)
+    err = rel_l2(run(op, x), orc.apply(x))
+    assert np.all(err <= TOL["fp32"]), err

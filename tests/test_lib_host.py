@@ -110,16 +110,22 @@ def test_grid_validation(cells, why):
     assert ei.value.status == pcb.PC_ERR_GRID, why
 
 
-@pytest.mark.parametrize("which", ["small", "adaptive_1024"])
+@pytest.mark.parametrize("which", ["small", "adaptive_1024", "3d_broken_facet", "3d_octants"])
 def test_weights_match_oracle_with_hanging_nodes(which):
-    """The library solves hanging-node leaves by bilinear + per-edge separation
-    of variables; the oracle by a full sine-eigenbasis solve.  Both are exact
-    discrete harmonic extensions, so they agree to rounding."""
+    """The library solves 2D hanging-node leaves by bilinear + per-edge
+    separation of variables, and 3D ones by facet pieces + a sine-basis
+    interior solve written separately; the oracle by its recursive sine-basis
+    solves.  Both are exact discrete harmonic extensions, so they agree to
+    rounding."""
+    from test_oracle_geometry import _broken_grid
     if which == "small":
         shape, cells = ADAPTIVE_SHAPE, np.array(ADAPTIVE_CELLS)
-    else:
+    elif which == "adaptive_1024":
         wl = configs.adaptive_1024()
         shape, cells = wl.shape, wl.cells
+    else:
+        shape, cells = _broken_grid(0 if which == "3d_broken_facet" else 1)
+        cells = np.array(cells)
     g = Grid(shape, cells)
     W = harmonic_weights(g)
     lw = pcb.pc_harmonic_weights(shape, cells)

@@ -141,3 +141,22 @@ def test_update_reuses_exactly_the_unaffected_correlations():
     assert 0 < affected < gb.r
     ref = ob.apply_adjoint(z)
     assert np.max(np.abs(yt - ref)) <= 1e-12 * np.abs(ref).max()
+
+
+def test_3d_refinement_follows_the_axis_of_change():
+    """3D (hanging nodes appear from the second split on): when the impulse
+    responses change along one axis only, every split is along that axis, and
+    the estimate falls to tau."""
+    shape = (11, 12, 17)
+    L = 17.0
+    kern = workloads.GaussianAxis3D(lambda x: 1.0 + 0 * x[..., 0], lambda x: 1.0 + 0 * x[..., 0],
+                                    lambda x: 0.8 + 1.6 * x[..., 2] / L, 3)
+    A = workloads.dense_operator(shape, kern)
+    Z, Y = _probes(shape, A, q=4)
+    cells, hist = construct(shape, _impulse(shape, kern), 3, Z, Y, tau=0.06, max_passes=12, batch=2)
+    assert hist[-1][1] <= 0.06 < hist[0][1]
+    for lo, hi in cells:
+        # leaves differ from the first subdivision only along axis 2
+        for a in (0, 1):
+            assert (lo[a], hi[a]) in (((0, 5), (5, 10)) if a == 0 else ((0, 5), (5, 11)))
+    assert len(cells) > 8

@@ -194,11 +194,123 @@ def test_sine_solver_against_dense_solve():
         assert np.array_equal(U[mask], V[mask])
 
 
-def test_3d_hanging_nodes_refused():
-    cells = [[[0, 0, 0], [4, 4, 4]], [[4, 0, 0], [8, 4, 2]], [[4, 0, 2], [8, 4, 4]]]
-    g = Grid((9, 5, 5), cells)
-    with pytest.raises(NotImplementedError):
-        harmonic_weights(g)
+# 3D leaves with hanging nodes (broken facets, Section 2.4)
+BROKEN_3D = [
+    # a coarse leaf beside two finer ones: its facet x0 = 4 is broken at z = 2
+    ((9, 5, 5), [[[0, 0, 0], [4, 4, 4]], [[4, 0, 0], [8, 4, 2]], [[4, 0, 2], [8, 4, 4]]]),
+    # octants of 13^3, one octant split again into octants: hanging nodes on
+    # facets (centres of broken facets) and on edges
+    ((13, 13, 13), None),
+]
+
+
+def _octants(lo, hi):
+    mid = [(a + b) // 2 for a, b in zip(lo, hi)]
+    out = []
+    for side in itertools.product((0, 1), repeat=3):
+        out.append([[lo[a] if s == 0 else mid[a] for a, s in enumerate(side)],
+                    [mid[a] if s == 0 else hi[a] for a, s in enumerate(side)]])
+    return out
+
+
+def _broken_grid(i):
+    shape, cells = BROKEN_3D[i]
+    if cells is None:
+        cells = _octants([0, 0, 0], [12, 12, 12])
+        fine = cells.pop(0)
+        cells += _octants(fine[0], fine[1])
+    return shape, cells
+
+
+@pytest.mark.parametrize("i", [0, 1])
+def test_3d_hanging_nodes_partition_delta_support_maximum(i):
+    shape, cells = _broken_grid(i)
+    g = Grid(shape, cells)
+    W = harmonic_weights(g)       # also asserts that the leaves agree on shared facets
+    S = np.zeros(shape)
+    for k in range(g.r):
+        wk = weight_on_omega(g, W, k)
+        S += wk
+        for j in range(g.r):
+            assert wk[tuple(g.points[j])] == (1.0 if j == k else 0.0)
+        assert np.all(wk[~g.U_mask_full(k)] == 0.0)
+        assert wk.min() >= -1e-15 and wk.max() <= 1 + 1e-15
+    assert np.max(np.abs(S - 1.0)) < 1e-13
+
+
+def _residual(V):
+    """Graph-Laplacian residual at the interior nodes of an array of any dimension."""
+    m = V.ndim
+    inner = tuple(slice(1, -1) for _ in range(m))
+    res = 2 * m * V[inner]
+    for a in range(m):
+        lo = [slice(1, -1)] * m
+        hi = [slice(1, -1)] * m
+        lo[a] = slice(0, -2)
+        hi[a] = slice(2, None)
+        res = res - V[tuple(lo)] - V[tuple(hi)]
+    return res
+
+
+@pytest.mark.parametrize("i", [0, 1])
+def test_3d_hanging_nodes_harmonic_on_every_piece(i):
+    """The weight is discrete-harmonic inside every leaf and on every facet
+    piece (the constituent boxes of broken facets), and linear on every edge
+    between consecutive sample points."""
+    from oracle.weights import facet_pieces
+    shape, cells = _broken_grid(i)
+    g = Grid(shape, cells)
+    W = harmonic_weights(g)
+    pts = {tuple(p) for p in g.points}
+    nbroken = 0
+    for k in range(g.r):
+        wk = weight_on_omega(g, W, k)
+        for c, (lo, hi) in enumerate(g.cells):
+            V = wk[tuple(slice(a, b + 1) for a, b in zip(lo, hi))]
+            if min(V.shape) > 2:
+                assert np.max(np.abs(_residual(V))) < 1e-13
+            for a in range(3):
+                for side in (0, 1):
+                    pieces = facet_pieces(g, c, a, side)
+                    nbroken += len(pieces) > 1
+                    for plo, phi in pieces:
+                        F = wk[tuple(slice(x, y + 1) for x, y in zip(plo, phi))].squeeze(axis=a)
+                        if min(F.shape) > 2:
+                            assert np.max(np.abs(_residual(F))) < 1e-13
+                        # its four edges: linear between consecutive sample points
+                        for b in [x for x in range(3) if x != a]:
+                            for e in (plo[b], phi[b]):
+                                elo, ehi = plo.copy(), phi.copy()
+                                elo[b] = ehi[b] = e
+                                free = [x for x in range(3) if elo[x] != ehi[x]][0]
+                                line = []
+                                for t in range(elo[free], ehi[free] + 1):
+                                    q = list(elo)
+                                    q[free] = t
+                                    line.append(tuple(q))
+                                vals = np.array([wk[q] for q in line])
+                                nodes = [j for j, q in enumerate(line) if q in pts]
+                                for j0, j1 in zip(nodes[:-1], nodes[1:]):
+                                    lin = np.linspace(vals[j0], vals[j1], j1 - j0 + 1)
+                                    assert np.max(np.abs(vals[j0:j1 + 1] - lin)) < 1e-14
+    assert nbroken > 0
+
+
+def test_3d_broken_facet_as_one_box_is_caught(monkeypatch):
+    """Planted mistake: solving a broken facet as one box (ignoring the finer
+    leaves across it) gives the two sides different facet values."""
+    from oracle import weights as ow
+    shape, cells = _broken_grid(0)
+    g = Grid(shape, cells)
+
+    def whole(grid, c, a, side):
+        lo, hi = (np.array(v, dtype=np.int64) for v in grid.cells[c])
+        flo, fhi = lo.copy(), hi.copy()
+        flo[a] = fhi[a] = hi[a] if side else lo[a]
+        return [(flo, fhi)]
+    monkeypatch.setattr(ow, "facet_pieces", whole)
+    with pytest.raises((AssertionError, ValueError)):
+        ow.harmonic_weights(g)
 
 
 # ---------------------------------------------------------------- extension (2.5)
