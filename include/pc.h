@@ -177,8 +177,11 @@ pc_status pc_neighbourhood_boxes(const pc_box *box, const pc_grid *grid, int32_t
 /* The harmonic partition-of-unity weights of Section 2.4 as the library
  * builds them (host computation, FP64, no GPU needed): on a leaf whose only
  * sample points are its corners the recursive Laplace construction gives the
- * multilinear hat; leaves with hanging nodes (2D) solve the discrete Laplace
- * equation with piecewise-linear edge data.  *count receives the number of
+ * multilinear hat; 2D leaves with hanging nodes solve the discrete Laplace
+ * equation with piecewise-linear edge data; 3D leaves with hanging nodes
+ * first solve it on each piece of their facets (a facet broken by finer
+ * leaves across it is replaced by its intersections with their facets),
+ * then in the interior.  *count receives the number of
  * values (sum over k of |bbox(U_k)|); if weights is not NULL it must hold
  * that many doubles and receives w_k on bbox(U_k), C order, k ascending
  * (zero outside U_k). */
@@ -204,7 +207,8 @@ pc_status pc_extend_impulse(const pc_box *box, const pc_grid *grid, int32_t radi
  *            on Omega - p_k; Section 2.5 fills that region from neighbours).
  *   weights  NULL: the library builds the harmonic weights of Section 2.4
  *            (closed-form multilinear hats on cells without hanging nodes,
- *            a discrete Laplace solve on 2D cells with hanging nodes).
+ *            discrete Laplace solves on cells with hanging nodes, 2D and 3D,
+ *            as pc_harmonic_weights describes).
  *            Otherwise host FP64, w_k on bbox(U_k) (pc_neighbourhood_boxes),
  *            C order, concatenated for k = 0..r-1; entries outside U_k must
  *            be 0.

@@ -43,8 +43,9 @@ harmonicity, Lemma 4.1, Lemma 4.2, Proposition 4.3, Proposition 4.4,
 Theorem 4.5, exactness at sample points, exact reproduction of a
 translation-invariant operator against an independent library convolution,
 A~ = A when every point is a sample point, and entry-formula vs direct-sum
-agreement).  3D harmonic weights are built only for conforming cells (no
-hanging nodes); that restriction is enforced, not silently skipped.
+agreement).  3D leaves with hanging nodes take their weights through the
+pieces of their broken facets (Section 2.4), pinned by harmonicity on every
+leaf and piece, partition of unity and agreement across shared facets.
 """
 from .grid import Grid  # noqa: F401
 from .weights import harmonic_weights  # noqa: F401
