@@ -264,7 +264,11 @@ pc_status pc_apply_adjoint_batched(pc_operator *op, int32_t nrhs, const void *x,
  *     copy stream.  The call therefore BLOCKS until the kernel has
  *     finished (at most 60 s after the work queued earlier on `stream`,
  *     else PC_ERR_TIMEOUT); the copies out of the last chunks may still be
- *     in flight when it returns.
+ *     in flight when it returns.  Where launches block the calling thread
+ *     (CUDA_LAUNCH_BLOCKING non-zero), and where the environment sets
+ *     PC_HOST_PIPELINE=chunked (for tools that serialise launches, such as
+ *     profilers), 2D operators take the chunked pipeline below instead,
+ *     with the same chunks and the same bitwise result.
  *   - 3D operators (chunk 0: the whole batch, as their patch kernels gain
  *     little from smaller batches): chunk i is copied in, applied on
  *     `stream` and copied out

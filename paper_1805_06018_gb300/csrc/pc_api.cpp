@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -978,6 +979,19 @@ pc_status apply_host_chunked(pc_operator *op, int32_t nrhs, const void *x, int64
 
 extern "C" {
 
+// The segmented launch needs the calling thread to run beside the kernel: it
+// marks chunks ready while the kernel's CTAs wait for them.  Where a launch
+// blocks the host until the kernel ends (CUDA_LAUNCH_BLOCKING set to a
+// non-zero value), every CTA would wait out its bound; there, and where the
+// caller asks for it (PC_HOST_PIPELINE=chunked, e.g. under a profiler that
+// serialises launches), 2D operators take the chunked pipeline instead.
+static bool segmented_host_apply() {
+    const char *blocking = std::getenv("CUDA_LAUNCH_BLOCKING");
+    if (blocking && blocking[0] && std::strcmp(blocking, "0") != 0) return false;
+    const char *mode = std::getenv("PC_HOST_PIPELINE");
+    return !(mode && std::strcmp(mode, "chunked") == 0);
+}
+
 pc_status pc_apply_host(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
                         int32_t adjoint, int32_t chunk, pc_stream stream) {
     if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
@@ -1008,7 +1022,8 @@ pc_status pc_apply_host(pc_operator *op, int32_t nrhs, const void *x, int64_t ld
         // longer), at most kMaxSegments of them
         int32_t c = even(std::max<int32_t>(chunk > 0 ? chunk : (nrhs + 3) / 4,
                                            (nrhs + pc::kMaxSegments - 1) / pc::kMaxSegments));
-        return apply_host_segmented(op, nrhs, x, ldx, y, ldy, adjoint == 1, c, s);
+        if (segmented_host_apply()) return apply_host_segmented(op, nrhs, x, ldx, y, ldy, adjoint == 1, c, s);
+        return apply_host_chunked(op, nrhs, x, ldx, y, ldy, adjoint == 1, c, s);
     }
     // 3D: the chunked pipeline, by default in one chunk (the 3D patch kernels
     // take nearly as long for a quarter of a batch as for all of it)

@@ -88,3 +88,32 @@ def test_host_apply_bad_arguments():
         with pytest.raises(pcg.PCError) as ei:
             op.pc_apply_host(*args, 0)
         assert ei.value.status == PC_ERR_ARG
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_host_apply_with_blocking_launches_takes_the_chunked_pipeline(monkeypatch, adjoint):
+    """Where launches block the calling thread (CUDA_LAUNCH_BLOCKING), the
+    segmented launch could not be fed its chunks; 2D operators then take the
+    chunked pipeline (one zero and one patch launch per chunk) with the same
+    bitwise result, as they do on request (PC_HOST_PIPELINE=chunked).  CUDA
+    itself reads CUDA_LAUNCH_BLOCKING only when it starts, so here it steers
+    the library alone."""
+    shape = (48, 44)
+    op, _ = make_pair(shape, workloads.regular_grid(shape, (4, 4)), _kernel(shape, 6), "fp32")
+    xh = torch.from_numpy(workloads.rhs(79, 9, shape)).pin_memory()
+    seg = op.apply_host(xh, adjoint=adjoint, chunk=2)
+    assert op.launches() == 2
+    monkeypatch.setenv("CUDA_LAUNCH_BLOCKING", "0")
+    assert torch.equal(op.apply_host(xh, adjoint=adjoint, chunk=2), seg)
+    assert op.launches() == 2
+    monkeypatch.setenv("CUDA_LAUNCH_BLOCKING", "1")
+    chunked = op.apply_host(xh, adjoint=adjoint, chunk=2)
+    op.check()
+    assert op.launches() == 2 * 5
+    assert torch.equal(chunked, seg)
+    monkeypatch.delenv("CUDA_LAUNCH_BLOCKING")
+    monkeypatch.setenv("PC_HOST_PIPELINE", "chunked")
+    assert torch.equal(op.apply_host(xh, adjoint=adjoint, chunk=2), seg)
+    assert op.launches() == 2 * 5
+    yd = op.apply_adjoint(xh.cuda()) if adjoint else op.apply(xh.cuda())
+    assert torch.equal(chunked, yd.cpu())
