@@ -488,6 +488,9 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
         if (e == cudaSuccess) e = pc::tc3d_build_operands(op->tc_k1cap, &op->d_tc_ops);
         if (e == cudaSuccess) acct += size_t(op->tc_k1cap) * 512 + 65536;
     }
+    // every upload and spectrum kernel above has landed before the operator
+    // is handed out (its applies run on the caller's streams)
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(d_psi);
     cudaFree(d_tw64);
     if (e != cudaSuccess) return bail(e, "building spectra");
@@ -532,7 +535,7 @@ static pc_status ensure_done_capacity(pc_operator *op, int32_t npairs) {
         return cuda_fail(op->ctx, e, "allocating ordering flags");
     }
     op->device_bytes += bytes;
-    e = cudaMemset(op->d_done, 0, bytes);
+    e = pc::zero_now(op->d_done, bytes);
     if (e != cudaSuccess) return cuda_fail(op->ctx, e, "clearing ordering flags");
     op->done_cap = cap;
     op->epoch = 0;
@@ -596,7 +599,9 @@ static pc_status apply_split3d(pc_operator *op, const pc::ApplyParams &p, cudaSt
         }
         if ((e = cudaMalloc(&order, ord.size() * sizeof(int32_t))) != cudaSuccess)
             return cuda_fail(ctx, e, "allocating the unit order");
-        if ((e = cudaMemcpy(order, ord.data(), ord.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        // ordered on s (a pageable source is staged before the call returns)
+        if ((e = cudaMemcpyAsync(order, ord.data(), ord.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess) {
             cudaFree(order);
             return cuda_fail(ctx, e, "uploading the unit order");
         }
@@ -1120,7 +1125,7 @@ pc_status pc_operator_check(pc_operator *op) {
     e = cudaMemcpy(ctrl, op->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(op->ctx, e, "reading the status word");
     if (ctrl[2]) {
-        cudaMemset(op->d_ctrl + 2, 0, sizeof(int32_t));
+        pc::zero_now(op->d_ctrl + 2, sizeof(int32_t));
         return fail(op->ctx, PC_ERR_TIMEOUT, "a bounded wait in the patch kernel timed out");
     }
     return PC_OK;

@@ -29,7 +29,18 @@ struct DeviceGuard {
     }
 };
 
-// cudaMalloc n elements at *dst, copy src there (synchronous), count the bytes in acct.
+// Zero n device bytes at p and wait until the zeros have landed.  The
+// synchronous cudaMemset (like cudaMemcpy from pageable host memory) may still
+// be in flight on the legacy default stream when it returns, and kernels on
+// non-blocking streams are not ordered after that stream.
+inline cudaError_t zero_now(void *p, size_t n) {
+    const cudaError_t e = cudaMemset(p, 0, n);
+    return e == cudaSuccess ? cudaDeviceSynchronize() : e;
+}
+
+// cudaMalloc n elements at *dst, copy src there, count the bytes in acct.  The
+// copy may still be in flight when this returns (see zero_now): callers
+// synchronise the device before work on a caller's stream reads *dst.
 template <typename T>
 cudaError_t upload(T **dst, const T *src, size_t n, size_t &acct) {
     *dst = nullptr;
@@ -38,6 +49,18 @@ cudaError_t upload(T **dst, const T *src, size_t n, size_t &acct) {
     if (e != cudaSuccess) return e;
     acct += sizeof(T) * n;
     return cudaMemcpy(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice);
+}
+
+// upload, with the copy ordered on stream s instead (src must stay valid until
+// the copy has run on s).
+template <typename T>
+cudaError_t upload_on(T **dst, const T *src, size_t n, size_t &acct, cudaStream_t s) {
+    *dst = nullptr;
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), sizeof(T) * n);
+    if (e != cudaSuccess) return e;
+    acct += sizeof(T) * n;
+    return cudaMemcpyAsync(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice, s);
 }
 
 }  // namespace pc

@@ -251,7 +251,7 @@ pc_status pc_block_apply_many(pc_block_plan *bp, int32_t nrhs, const void *const
         const int32_t cap = std::max<int32_t>(npairs, 32);
         const size_t bytes = sizeof(uint32_t) * size_t(bp->n_tiles) * size_t(cap);
         if ((e = cudaMalloc(&bp->d_done, bytes)) != cudaSuccess) return cuda_fail(ctx, e, "allocating plan flags");
-        if ((e = cudaMemset(bp->d_done, 0, bytes)) != cudaSuccess) return cuda_fail(ctx, e, "clearing plan flags");
+        if ((e = pc::zero_now(bp->d_done, bytes)) != cudaSuccess) return cuda_fail(ctx, e, "clearing plan flags");
         bp->done_cap = cap;
         bp->epoch = 0;
     }
@@ -392,7 +392,7 @@ pc_status pc_block_plan_check(pc_block_plan *bp) {
     if ((e = cudaMemcpy(ctrl, bp->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(ctx, e, "reading the status word");
     if (ctrl[2]) {
-        cudaMemset(bp->d_ctrl + 2, 0, sizeof(int32_t));
+        pc::zero_now(bp->d_ctrl + 2, sizeof(int32_t));
         return fail(ctx, PC_ERR_TIMEOUT, "a bounded wait in the patch kernel timed out");
     }
     return PC_OK;

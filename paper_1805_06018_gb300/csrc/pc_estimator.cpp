@@ -11,7 +11,7 @@
 using pc::cuda_fail;
 using pc::DeviceGuard;
 using pc::fail;
-using pc::upload;
+using pc::upload_on;
 
 extern "C" {
 
@@ -118,7 +118,8 @@ pc_status pc_estimator_update(pc_estimator *est, pc_operator *op, double *eta, i
     }
     const int32_t nt = int32_t(tiles.size());
     const int32_t npairs = (q + 1) / 2;
-    // device work; every buffer of this call is released before it returns
+    // device work, all of it ordered on s (the host vectors outlive it: the
+    // call ends by synchronising s); every buffer is released before it returns
     void *arena = nullptr;
     pc::Tile *d_tiles = nullptr;
     pc::StoreDesc *d_sd = nullptr;
@@ -148,7 +149,7 @@ pc_status pc_estimator_update(pc_estimator *est, pc_operator *op, double *eta, i
     cudaError_t e = cudaMalloc(&arena, est->elem * size_t(std::max<int64_t>(total, 1)));
     if (e != cudaSuccess) return bail(e, "allocating the correlation arena");
     if (!copies.empty()) {
-        if ((e = upload(&d_copies, copies.data(), copies.size(), acct)) != cudaSuccess)
+        if ((e = upload_on(&d_copies, copies.data(), copies.size(), acct, s)) != cudaSuccess)
             return bail(e, "uploading the block copies");
         if ((e = pc::launch_block_copies(est->prec, d_copies, int32_t(copies.size() / 3), est->arena, arena, s)) !=
             cudaSuccess)
@@ -156,14 +157,14 @@ pc_status pc_estimator_update(pc_estimator *est, pc_operator *op, double *eta, i
     }
     if (nt > 0) {
         const std::vector<int32_t> cs{0, nt}, ds(size_t(nt) + 1, 0), dep{0};
-        if ((e = upload(&d_tiles, tiles.data(), tiles.size(), acct)) != cudaSuccess ||
-            (e = upload(&d_sd, sds.data(), sds.size(), acct)) != cudaSuccess ||
-            (e = upload(&d_cs, cs.data(), cs.size(), acct)) != cudaSuccess ||
-            (e = upload(&d_ds, ds.data(), ds.size(), acct)) != cudaSuccess ||
-            (e = upload(&d_dep, dep.data(), dep.size(), acct)) != cudaSuccess ||
+        if ((e = upload_on(&d_tiles, tiles.data(), tiles.size(), acct, s)) != cudaSuccess ||
+            (e = upload_on(&d_sd, sds.data(), sds.size(), acct, s)) != cudaSuccess ||
+            (e = upload_on(&d_cs, cs.data(), cs.size(), acct, s)) != cudaSuccess ||
+            (e = upload_on(&d_ds, ds.data(), ds.size(), acct, s)) != cudaSuccess ||
+            (e = upload_on(&d_dep, dep.data(), dep.size(), acct, s)) != cudaSuccess ||
             (e = cudaMalloc(&d_done, sizeof(uint32_t) * size_t(nt) * size_t(npairs))) != cudaSuccess ||
-            (e = cudaMemset(d_done, 0, sizeof(uint32_t) * size_t(nt) * size_t(npairs))) != cudaSuccess ||
-            (e = cudaMalloc(&d_ctrl, 64)) != cudaSuccess || (e = cudaMemset(d_ctrl, 0, 64)) != cudaSuccess)
+            (e = cudaMemsetAsync(d_done, 0, sizeof(uint32_t) * size_t(nt) * size_t(npairs), s)) != cudaSuccess ||
+            (e = cudaMalloc(&d_ctrl, 64)) != cudaSuccess || (e = cudaMemsetAsync(d_ctrl, 0, 64, s)) != cudaSuccess)
             return bail(e, "uploading the correlation work list");
         pc::ApplyParams p{};
         p.x = est->z;
@@ -199,7 +200,7 @@ pc_status pc_estimator_update(pc_estimator *est, pc_operator *op, double *eta, i
         if ((e = pc::launch_fft2d(p, op->P, op->prec, ctas, s, true)) != cudaSuccess)
             return bail(e, "launching the correlations");
     }
-    if ((e = upload(&d_blk, blk_off.data(), blk_off.size(), acct)) != cudaSuccess)
+    if ((e = upload_on(&d_blk, blk_off.data(), blk_off.size(), acct, s)) != cudaSuccess)
         return bail(e, "uploading the block offsets");
     if ((e = pc::launch_corr_combine(est->prec, op->entry, op->d_w, arena, d_blk, nsub2, q, est->d_yt, est->N, s)) !=
         cudaSuccess)

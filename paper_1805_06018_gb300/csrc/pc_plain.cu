@@ -122,6 +122,8 @@ static pc_status plain_init(pc_operator *op, std::string &err) {
     if (e == cudaSuccess) e = cudaMalloc(&st->blk_tiles, sizeof(int32_t) * flat.size());
     if (e == cudaSuccess) e = cudaMemcpy(st->blk_start, start.data(), sizeof(int32_t) * start.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(st->blk_tiles, flat.data(), sizeof(int32_t) * flat.size(), cudaMemcpyHostToDevice);
+    // the copies have landed before any apply on a caller's stream reads them
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         destroy_state(st);
         err = std::string("plain path tables: ") + cudaGetErrorString(e);

@@ -417,7 +417,7 @@ pc_status pc_serve_create(pc_context *ctx, const pc_serve_config *cfg, pc_server
         if (e == cudaSuccess) e = cudaMalloc(&sl.d_seg_done, sizeof(uint32_t) * pc::kMaxSegments);
         if (e == cudaSuccess) e = cudaMalloc(&sl.d_counter, sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMalloc(&sl.d_status, sizeof(int32_t));
-        if (e == cudaSuccess) e = cudaMemset(sl.d_status, 0, sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMemsetAsync(sl.d_status, 0, sizeof(int32_t), sl.stream);
         if (e == cudaSuccess) std::memset(sl.h_desc, 0, sizeof(pc::LaunchDesc));
         // capture, forward and adjoint: descriptor upload, zero-fill, persistent fused kernel
         for (int adj = 0; adj < 2 && e == cudaSuccess; ++adj) {
