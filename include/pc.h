@@ -184,7 +184,10 @@ pc_status pc_neighbourhood_boxes(const pc_box *box, const pc_grid *grid, int32_t
  * then in the interior.  *count receives the number of
  * values (sum over k of |bbox(U_k)|); if weights is not NULL it must hold
  * that many doubles and receives w_k on bbox(U_k), C order, k ascending
- * (zero outside U_k). */
+ * (zero outside U_k).  A 3D grid in which some facet piece has a corner that
+ * is no sample point (the two sides of a facet split along different axes)
+ * has no weights under Section 2.4's recursion: PC_ERR_GRID, as from
+ * pc_build_spectra. */
 pc_status pc_harmonic_weights(const pc_box *box, const pc_grid *grid, int64_t *count, double *weights);
 
 /* The extended impulse responses phi_k^E of Section 2.5 (Eqs. vj_def,

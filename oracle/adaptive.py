@@ -19,6 +19,15 @@ adjoint apply and estimator, in the algorithm's order:
    Values within a relative 1e-9 of the largest count as a tie, won by the
    lowest direction index.
 
+   In 3D a split can break the two sides of a facet crosswise (one side
+   split along one axis, the other side along another); the pieces of that
+   facet then have corners that are no cell's corner, where the recursive
+   construction of Section 2.4 has no value.  Such a split is skipped: the
+   cell takes the next direction in the order above whose split leaves every
+   facet piece with sample points at its corners, and a cell with none is
+   passed over for the next cell by eta_C.  (In 2D a facet is a segment and
+   its pieces end at sample points, so every split qualifies.)
+
 `batch` > 1 refines up to that many cells per pass (largest eta_C first),
 all chosen from one pass's estimates; batch = 1 is Algorithm 1 as printed.
 """
@@ -32,11 +41,14 @@ import numpy as np
 from .apply import PCOracle
 from .estimator import eta_from_adjoints
 from .grid import Grid, box_midpoint
+from .weights import facet_pieces
 
 
-def split_direction(grid: Grid, phiE: np.ndarray, R: int, c: int) -> int:
-    """Section 2.7: the subdivision direction of leaf cell c, or -1 if no
-    direction is big enough to refine."""
+def split_directions(grid: Grid, phiE: np.ndarray, R: int, c: int) -> List[int]:
+    """Section 2.7: the directions in which leaf cell c may be subdivided
+    (extent > 2), best first: each is the one of largest
+    || phi^{i+} - phi^{i-} || among those not yet listed, values within a
+    relative 1e-9 of it counting as a tie won by the lowest index."""
     lo, hi = grid.cells[c]
     d = grid.d
     W = 2 * R + 1
@@ -59,10 +71,37 @@ def split_direction(grid: Grid, phiE: np.ndarray, R: int, c: int) -> int:
                 minus += phiE[k]
         diff = (plus - minus) / 2 ** (d - 1)
         vals.append(float(np.sqrt(np.sum(diff[inside] ** 2))))
-    top = max((v for v in vals if v is not None), default=None)
-    if top is None:
-        return -1
-    return next(i for i, v in enumerate(vals) if v is not None and v >= top - 1e-9 * top)
+    left = [i for i, v in enumerate(vals) if v is not None]
+    order = []
+    while left:
+        top = max(vals[i] for i in left)
+        best = min(i for i in left if vals[i] >= top - 1e-9 * top)
+        order.append(best)
+        left.remove(best)
+    return order
+
+
+def split_direction(grid: Grid, phiE: np.ndarray, R: int, c: int) -> int:
+    """The best subdivision direction of leaf cell c, or -1 if no direction
+    is big enough to refine."""
+    order = split_directions(grid, phiE, R, c)
+    return order[0] if order else -1
+
+
+def pieces_have_sample_corners(shape, cells) -> bool:
+    """Whether every facet piece of every leaf (Section 2.4: a facet, or its
+    intersections with the facets of the leaves across it) has sample points
+    at all its corners."""
+    grid = Grid(shape, cells)
+    points = {tuple(int(v) for v in p) for p in grid.points}
+    for c in range(len(grid.cells)):
+        for a in range(grid.d):
+            for side in (0, 1):
+                for plo, phi in facet_pieces(grid, c, a, side):
+                    for corner in product(*[(int(plo[b]), int(phi[b])) for b in range(grid.d)]):
+                        if corner not in points:
+                            return False
+    return True
 
 
 def subdivide(cells: np.ndarray, c: int, i: int) -> np.ndarray:
@@ -91,8 +130,11 @@ def initial_cells(shape) -> np.ndarray:
 
 
 def construct(shape, impulse: Callable[[np.ndarray], np.ndarray], R: int, Z: np.ndarray, Y: np.ndarray,
-              tau: float, max_passes: int = 100, batch: int = 1):
-    """Returns (cells, history) with history = [(r, eta_Omega)] per pass."""
+              tau: float, max_passes: int = 100, batch: int = 1, stats: dict = None):
+    """Returns (cells, history) with history = [(r, eta_Omega)] per pass.  If
+    `stats` is a dict it counts "skipped_splits" (a direction whose split
+    would break a facet crosswise) and "fallbacks" (cells split in a later
+    direction than their first)."""
     Z = np.asarray(Z, dtype=np.float64).reshape(len(Z), -1)
     Y = np.asarray(Y, dtype=np.float64).reshape(len(Y), -1)
     q = Z.shape[0]
@@ -116,10 +158,19 @@ def construct(shape, impulse: Callable[[np.ndarray], np.ndarray], R: int, Z: np.
             break
         order = sorted(range(len(cells)), key=lambda c: (-eta_c[c], c))
         chosen = []
+        trial = cells          # the cells as split so far this pass
         for c in order:
-            i = split_direction(grid, orc.phiE, R, c)
-            if i >= 0:
-                chosen.append((c, i))
+            for i in split_directions(grid, orc.phiE, R, c):
+                at = next(j for j, box in enumerate(trial) if np.array_equal(box, cells[c]))
+                nxt = subdivide(trial, at, i)
+                if grid.d == 2 or pieces_have_sample_corners(shape, nxt):
+                    trial = nxt
+                    chosen.append((c, i))
+                    if stats is not None and i != split_direction(grid, orc.phiE, R, c):
+                        stats["fallbacks"] = stats.get("fallbacks", 0) + 1
+                    break
+                if stats is not None:
+                    stats["skipped_splits"] = stats.get("skipped_splits", 0) + 1
             if len(chosen) == batch:
                 break
         if not chosen:

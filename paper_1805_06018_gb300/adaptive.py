@@ -21,6 +21,15 @@ the largest are a tie, won by the lowest i.  The split is at
 floor((c_min + c_max) / 2).  batch > 1 splits up to that many leaves per
 pass (largest eta_C first); batch = 1 is Algorithm 1 as printed.
 
+In 3D a split can break the two sides of a facet crosswise (one side split
+along one axis, the other along another): the facet's pieces then meet at a
+point that is no cell's corner, where the recursive weights of Section 2.4
+have no value (libpc refuses such grids with PC_ERR_GRID).  A leaf therefore
+takes its directions in the order above (each the best of those left) and
+splits in the first one that keeps every facet piece's corners at sample
+points; a leaf with none is passed over for the next by eta_C.  In 2D facets
+are segments and every split qualifies.
+
 Each pass rebuilds the operator (geometry, weights and spectra in libpc).
 Y~ = A~* Z is updated incrementally, as Algorithm 1 does (`incremental`,
 the default): the correlations flip(phi_k^E) * Z of sample points whose
@@ -52,7 +61,7 @@ def _first_cells(shape) -> List[Tuple[List[int], List[int]]]:
     return out
 
 
-def _direction(shape, lo, hi, point_index, phiE, R) -> int:
+def _directions(shape, lo, hi, point_index, phiE, R) -> List[int]:
     d = len(shape)
     W = 2 * R + 1
     cmid = [(a + b) // 2 for a, b in zip(lo, hi)]
@@ -75,10 +84,52 @@ def _direction(shape, lo, hi, point_index, phiE, R) -> int:
                 back += phiE[k]
         delta = (front - back) * (2.0 ** (1 - d))
         scores[i] = float(np.linalg.norm(delta[mask]))
-    if not scores:
-        return -1
-    top = max(scores.values())
-    return min(i for i, v in scores.items() if v >= top - 1e-9 * top)
+    out = []
+    while scores:
+        top = max(scores.values())
+        i = min(j for j, v in scores.items() if v >= top - 1e-9 * top)
+        out.append(i)
+        del scores[i]
+    return out
+
+
+def _split(cells, box, i):
+    """cells with leaf `box` replaced by its halves along axis i."""
+    lo, hi = box
+    m = (lo[i] + hi[i]) // 2
+    out = [c for c in cells if not (list(c[0]) == list(lo) and list(c[1]) == list(hi))]
+    out.append((list(lo), [m if a == i else hi[a] for a in range(len(lo))]))
+    out.append(([m if a == i else lo[a] for a in range(len(lo))], list(hi)))
+    return out
+
+
+def _pieces_end_at_points(cells, new_boxes) -> bool:
+    """Whether every facet piece of the leaves `new_boxes` (their facets'
+    intersections of positive area with the facets of the leaves across)
+    has cell corners at its corners.  Pieces away from them are unchanged by
+    a split."""
+    d = len(cells[0][0])
+    corners = set()
+    for lo, hi in cells:
+        corners.update(product(*[(lo[a], hi[a]) for a in range(d)]))
+    for lo, hi in new_boxes:
+        for a in range(d):
+            for plane, far in ((lo[a], 1), (hi[a], 0)):
+                for nlo, nhi in cells:
+                    # a leaf across: its opposite facet lies on the same plane
+                    if (nhi[a] if far else nlo[a]) != plane or (nlo[a] if far else nhi[a]) == plane:
+                        continue
+                    plo = [max(lo[b], nlo[b]) for b in range(d)]
+                    phi = [min(hi[b], nhi[b]) for b in range(d)]
+                    plo[a] = phi[a] = plane
+                    if any(plo[b] >= phi[b] for b in range(d) if b != a):
+                        continue
+                    for corner in product(*[(plo[b], phi[b]) for b in range(d)]):
+                        if corner not in corners:
+                            return False
+    return True
+
+
 
 
 def construct(ctx, shape, impulse: Callable[[np.ndarray], np.ndarray], R: int, Z, Y, tau: float,
@@ -120,12 +171,16 @@ def construct(ctx, shape, impulse: Callable[[np.ndarray], np.ndarray], R: int, Z
         phiE = pc_extend_impulse(shape, arr, R, phi)
         point_index = {tuple(int(v) for v in p): k for k, p in enumerate(pts)}
         picks = []
+        trial = list(cells)   # the leaves as split so far this pass
         for c in sorted(range(len(cells)), key=lambda c: (-eta_c[c], c)):
-            i = _direction(shape, cells[c][0], cells[c][1], point_index, phiE, R)
-            if i >= 0:
-                picks.append((c, i))
-                if len(picks) == batch:
+            for i in _directions(shape, cells[c][0], cells[c][1], point_index, phiE, R):
+                nxt = _split(trial, cells[c], i)
+                if len(shape) == 2 or _pieces_end_at_points(nxt, nxt[-2:]):
+                    trial = nxt
+                    picks.append((c, i))
                     break
+            if len(picks) == batch:
+                break
         if not picks:
             break
         for c, i in sorted(picks, key=lambda ci: -ci[0]):

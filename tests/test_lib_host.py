@@ -159,3 +159,155 @@ def test_header_is_plain_c_and_links():
                "-Wl,-rpath," + libdir, "-Wl,--unresolved-symbols=ignore-in-shared-libs"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def _random_tree_3d(seed, shape=(17, 15, 13), splits=10):
+    """Random one-axis splits of random leaves (the anisotropic refinement of
+    Section 2.7), starting from the box split once per axis; splits that
+    would break a facet crosswise (no weights defined, Section 2.4) are
+    redrawn."""
+    from oracle.adaptive import initial_cells, pieces_have_sample_corners, subdivide
+    rng = np.random.default_rng(seed)
+    cells = initial_cells(shape)
+    for _ in range(splits):
+        while True:
+            c, a = int(rng.integers(len(cells))), int(rng.integers(3))
+            if cells[c][1][a] - cells[c][0][a] > 2:
+                nxt = subdivide(cells, c, a)
+                if pieces_have_sample_corners(shape, nxt):
+                    break
+        cells = nxt
+    return shape, cells
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_3d_weights_on_random_anisotropic_trees_match_oracle(seed):
+    """One-axis splits break facets into T-junctions and put several hanging
+    nodes on one edge; the library's weights (facet pieces, then a sine-basis
+    interior solve) still equal the oracle's recursive solves, and form a
+    partition of unity with the delta property."""
+    shape, cells = _random_tree_3d(seed)
+    g = Grid(shape, cells)
+    W = harmonic_weights(g)       # asserts that the leaves agree on shared facets
+    ref = np.concatenate([w.ravel() for w in W])
+    lw = pcb.pc_harmonic_weights(shape, cells)
+    assert lw.size == ref.size
+    assert np.max(np.abs(lw - ref)) < 1e-12
+    S = np.zeros(shape)
+    for k in range(g.r):
+        sl = tuple(slice(a, b + 1) for a, b in zip(g.bbox_lo[k], g.bbox_hi[k]))
+        S[sl] += W[k]
+    assert np.max(np.abs(S - 1.0)) < 1e-13
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 4, 5])
+def test_adaptive_split_admissibility_matches_oracle(seed):
+    """The adaptive construction's check that a split keeps every facet
+    piece's corners at sample points (written locally, around the new
+    leaves) agrees with the oracle's check of the whole grid, on every
+    candidate split of random anisotropic 3D trees, crosswise ones included."""
+    from paper_1805_06018_gb300 import adaptive as lib_adaptive
+    from oracle.adaptive import pieces_have_sample_corners
+    shape, cells = _random_tree_3d(seed, splits=6)
+    boxes = [(list(map(int, lo)), list(map(int, hi))) for lo, hi in cells]
+    seen = {True: 0, False: 0}
+    for box in boxes:
+        for i in range(3):
+            if box[1][i] - box[0][i] <= 2:
+                continue
+            nxt = lib_adaptive._split(boxes, box, i)
+            got = lib_adaptive._pieces_end_at_points(nxt, nxt[-2:])
+            want = pieces_have_sample_corners(shape, np.array([[lo, hi] for lo, hi in nxt]))
+            assert got == want, (box, i)
+            seen[got] += 1
+    assert seen[True] > 0 and seen[False] > 0
+
+
+def test_adaptive_crosswise_split_is_refused_by_both_sides():
+    from paper_1805_06018_gb300 import adaptive as lib_adaptive
+    from test_oracle_adaptive import _crosswise_grid
+    for axis, ok in [(2, False), (1, True)]:
+        shape, cells = _crosswise_grid(axis)
+        boxes = [(list(map(int, lo)), list(map(int, hi))) for lo, hi in cells]
+        assert lib_adaptive._pieces_end_at_points(boxes, boxes[-2:]) == ok
+        if ok:
+            pcb.pc_harmonic_weights(shape, np.array(cells))
+        else:
+            with pytest.raises(pcb.PCError) as ei:
+                pcb.pc_harmonic_weights(shape, np.array(cells))
+            assert ei.value.status == pcb.PC_ERR_GRID
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_adaptive_direction_order_matches_oracle(seed):
+    """Section 2.7's directions, best first, from the library's extension
+    (pc_extend_impulse) and from the oracle's, on every leaf of random 3D
+    trees with a kernel that changes along all three axes."""
+    import workloads
+    from paper_1805_06018_gb300 import adaptive as lib_adaptive
+    from oracle import PCOracle
+    from oracle.adaptive import split_directions
+    shape, cells = _random_tree_3d(seed, splits=5)
+    kern = workloads.GaussianAxis3D(lambda x: 1.0 + 0.05 * x[..., 0], lambda x: 1.2 + 0.04 * x[..., 1],
+                                    lambda x: 0.9 + 0.06 * x[..., 2], 3)
+    g = Grid(shape, cells)
+    phi = workloads.impulse_windows(shape, g.points, kern)
+    orc = PCOracle(shape, cells, phi, 3)
+    lib_phiE = pcb.pc_extend_impulse(shape, cells, 3, phi)
+    index = {tuple(int(v) for v in p): k for k, p in enumerate(g.points)}
+    for c, (lo, hi) in enumerate(cells):
+        got = lib_adaptive._directions(shape, list(map(int, lo)), list(map(int, hi)), index, lib_phiE, 3)
+        assert got == split_directions(g, orc.phiE, 3, c)
+
+
+class _OracleBackedOperator:
+    """Stands in for the library operator inside the adaptive construction's
+    host loop: the per-cell estimates come from the oracle, so the loop's
+    choices (cells, directions, crosswise skips, batches) can be compared
+    with the oracle's construction without a GPU."""
+
+    def __init__(self, ctx, shape, cells, R, phi, precision="fp64", **tune):
+        from oracle import PCOracle
+        self.grid = Grid(shape, cells)
+        self.orc = PCOracle(shape, cells, phi, R)
+
+    def estimate_cell_errors(self, Z, Y, num_cells):
+        from oracle.estimator import eta_from_adjoints
+        z = Z.double().numpy()
+        return eta_from_adjoints(self.grid, self.orc.apply_adjoint(z), Y.double().numpy().reshape(len(z), -1))
+
+    def close(self):
+        pass
+
+
+@pytest.mark.parametrize("case", ["2d", "3d_crosswise"])
+def test_adaptive_host_loop_matches_the_oracle_construction(monkeypatch, case):
+    import torch
+    import workloads
+    from paper_1805_06018_gb300 import adaptive as lib_adaptive
+    from oracle.adaptive import construct as oracle_construct
+    if case == "2d":
+        shape, R, batch, passes = (40, 36), 4, 2, 6
+        kern = workloads.Skewed([0.6, -0.3], lambda x: 1.0 + 0.4 * np.sin(x[..., 0] / 6.0), R)
+    else:
+        shape, R, batch, passes = (13, 13, 13), 3, 2, 6
+        kern = workloads.GaussianAxis3D(lambda x: 1.0 + 0 * x[..., 0],
+                                        lambda x: 0.8 + 1.6 * (x[..., 0] < 6) * x[..., 1] / 13.0,
+                                        lambda x: 0.8 + 1.6 * (x[..., 0] >= 6) * x[..., 2] / 13.0, R)
+    A = workloads.dense_operator(shape, kern)
+    q = 4
+    Z = workloads.rhs(35, q, shape).reshape(q, -1).astype(np.float64)
+    Y = Z @ A
+    impulse = lambda pts: workloads.impulse_windows(shape, pts, kern)  # noqa: E731
+    stats = {}
+    ref_cells, ref_hist = oracle_construct(shape, impulse, R, Z, Y, tau=1e-6, max_passes=passes, batch=batch,
+                                           stats=stats)
+    monkeypatch.setattr(lib_adaptive, "Operator", _OracleBackedOperator)
+    _, cells, hist = lib_adaptive.construct(None, shape, impulse, R, torch.from_numpy(Z.reshape((q,) + shape)),
+                                            torch.from_numpy(Y.reshape((q,) + shape)), tau=1e-6,
+                                            precision="fp64", max_passes=passes, batch=batch, incremental=False)
+    assert np.array_equal(np.asarray(cells), np.asarray(ref_cells))
+    assert [r for r, _ in hist] == [r for r, _ in ref_hist]
+    assert np.allclose([e for _, e in hist], [e for _, e in ref_hist], rtol=1e-12, atol=0)
+    if case == "3d_crosswise":
+        assert stats.get("skipped_splits", 0) >= 1

@@ -10,9 +10,10 @@
   anisotropy pin.
 """
 import numpy as np
+import pytest
 
 import workloads
-from oracle import adaptive, Grid
+from oracle import adaptive, Grid, harmonic_weights
 from oracle.adaptive import construct, split_direction
 from oracle.dense import dense_pc
 from oracle.apply import PCOracle
@@ -81,15 +82,13 @@ def test_planted_direction_mistake_is_caught(monkeypatch):
     g = Grid(shape, adaptive.initial_cells(shape))
     orc = PCOracle(shape, g.cells, workloads.impulse_windows(shape, g.points, kern), 6)
     assert all(split_direction(g, orc.phiE, 6, c) == 0 for c in range(4))
-    real = adaptive.split_direction
+    real = adaptive.split_directions
 
     def least_change(grid, phiE, R, c):
-        best = real(grid, phiE, R, c)
-        lo, hi = grid.cells[c]
-        others = [i for i in range(grid.d) if i != best and hi[i] - lo[i] > 2]
-        return others[0] if others else best
+        order = real(grid, phiE, R, c)
+        return order[1:] + order[:1]
 
-    monkeypatch.setattr(adaptive, "split_direction", least_change)
+    monkeypatch.setattr(adaptive, "split_directions", least_change)
     A = workloads.dense_operator(shape, kern)
     Z, Y = _probes(shape, A)
     cells, _ = construct(shape, _impulse(shape, kern), 6, Z, Y, tau=1e-3, max_passes=8)
@@ -160,3 +159,53 @@ def test_3d_refinement_follows_the_axis_of_change():
         for a in (0, 1):
             assert (lo[a], hi[a]) in (((0, 5), (5, 10)) if a == 0 else ((0, 5), (5, 11)))
     assert len(cells) > 8
+
+
+def _crosswise_grid(second_axis):
+    """Octants of 9^3; the octant at the origin split along axis 1, then its
+    neighbour across x0 = 4 split along `second_axis`."""
+    from oracle.adaptive import initial_cells, subdivide
+    shape = (9, 9, 9)
+    cells = initial_cells(shape)
+    left = next(j for j, c in enumerate(cells) if tuple(c[0]) == (0, 0, 0))
+    cells = subdivide(cells, left, 1)
+    right = next(j for j, c in enumerate(cells) if tuple(c[0]) == (4, 0, 0))
+    return shape, subdivide(cells, right, second_axis)
+
+
+def test_crosswise_broken_facet_has_no_value_at_the_crossing():
+    """Section 2.4 builds w_k on the pieces of broken facets down to their
+    corners.  When the two sides of a facet are split along different axes
+    (here y on one side, z on the other), the pieces meet at (4, 2, 2), which
+    is no cell's corner: the recursion has no value there, and the oracle's
+    weights refuse the grid.  Splitting both sides along the same axis leaves
+    hanging nodes only, and is fine."""
+    from oracle.adaptive import pieces_have_sample_corners
+    shape, cells = _crosswise_grid(2)
+    assert not pieces_have_sample_corners(shape, cells)
+    assert (4, 2, 2) not in {tuple(int(v) for v in p) for p in Grid(shape, cells).points}
+    with pytest.raises(ValueError):
+        harmonic_weights(Grid(shape, cells))
+    shape, cells = _crosswise_grid(1)
+    assert pieces_have_sample_corners(shape, cells)
+    harmonic_weights(Grid(shape, cells))
+
+
+def test_3d_construction_skips_crosswise_splits():
+    """A 3D kernel that changes along y on one side of x0 = 6 and along z on
+    the other: Section 2.7 asks for crosswise splits across that plane.  Each
+    is skipped for the cell's next direction, the construction goes on, every
+    pass's grid is one Section 2.4 defines weights on, and the estimate
+    falls."""
+    shape = (13, 13, 13)
+    L = 13.0
+    kern = workloads.GaussianAxis3D(lambda x: 1.0 + 0 * x[..., 0],
+                                    lambda x: 0.8 + 1.6 * (x[..., 0] < 6) * x[..., 1] / L,
+                                    lambda x: 0.8 + 1.6 * (x[..., 0] >= 6) * x[..., 2] / L, 3)
+    A = workloads.dense_operator(shape, kern)
+    Z, Y = _probes(shape, A, q=4)
+    stats = {}
+    cells, hist = construct(shape, _impulse(shape, kern), 3, Z, Y, tau=0.02, max_passes=6, batch=2, stats=stats)
+    assert stats.get("skipped_splits", 0) >= 1 and stats.get("fallbacks", 0) >= 1
+    assert hist[-1][1] < 0.6 * hist[0][1]
+    harmonic_weights(Grid(shape, cells))
