@@ -28,13 +28,21 @@ What it computes, step by step, in the paper's order and notation:
 6. Blocks A~[T, S] and (A~*)[T, S] applied to vectors (Section 3.3): the
    restricted definition, and the translated small convolution per term.
    -> :mod:`oracle.block`
+7. The randomized a-posteriori estimator (Section 2.6, Eq.
+   randomized_estimator_ec): eta_C from A~* Z and the caller's Y = A* Z.
+   -> :mod:`oracle.estimator`
+8. The adaptive construction (Algorithm 1) with anisotropic splits (Section
+   2.7).  -> :mod:`oracle.adaptive`
 
 Readings where the paper is silent (each one is listed with its reason in the
 design notes): n-point regular grids include the box corners, midpoints round
 down, truncation is Euclidean |y - x|_2 <= R, a neighbour contributes to the
 extension wherever its domain Omega - p_j contains z (Section 1.3's meaning of
-support), the extension uses the plain average, data are real, and the oracle
-consumes the FP32-rounded right-hand side promoted to FP64.
+support), the extension uses the plain average, data are real, the oracle
+consumes the FP32-rounded right-hand side promoted to FP64, and in 3D a split
+that would break a facet crosswise (its pieces meeting at a point that is no
+cell's corner, where Section 2.4's recursion gives no value) is skipped for
+the cell's next direction.
 
 Parity pins: every function here is checked by the ``-m "not gpu"`` tests
 against closed forms and invariants the paper fixes (partition of unity,
