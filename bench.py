@@ -301,9 +301,11 @@ def run_reference(args, rank, world):
     rng = np.random.default_rng(1)
     # each step is one oracle call on random output pixels.  A call also lays
     # out the whole input batch (a fixed cost that a full apply pays once), so
-    # steps take as many pixels as the run allows: about 16 full applies'
-    # worth over the K + W steps, at least 2048 per step
-    per_step = int(min(wl.n, max(2048, 16 * wl.n // max(1, args.steps + args.warmup))))
+    # steps are as large as the run allows: the warm-up steps size the sample
+    # so that a step takes about 120 s / (K + W) (0.5 s to 30 s), which keeps
+    # the whole run near two minutes whatever the workload's cost per pixel
+    target = min(30.0, max(0.5, 120.0 / (args.steps + args.warmup)))
+    per_step = min(2048, wl.n)
     times = []
     for i in range(args.warmup + args.steps):
         pts = rng.choice(wl.n, per_step, replace=False)
@@ -312,6 +314,8 @@ def run_reference(args, rank, world):
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
+        elif dt > 0:
+            per_step = int(min(wl.n, max(min(2048, wl.n), per_step * target / dt)))
     tot = sum(times)
     value = args.steps * wl.nrhs * (per_step / wl.n) / tot
     sample = ("%d random output pixels x %d RHS per step (of %d pixels), one oracle call each, which also "
