@@ -294,7 +294,8 @@ def run_reference(args, rank, world):
     wl = configs.get(WORKLOAD_OPERATOR[args.workload][0])
     if args.workload.endswith("_block") or args.workload.endswith("_blocks"):
         return run_reference_block(args, wl)
-    x = workloads.rhs(wl.rhs_seed, wl.nrhs, wl.shape)
+    # the FP32 right-hand sides, promoted to the oracle's FP64 before timing
+    x = workloads.rhs(wl.rhs_seed, wl.nrhs, wl.shape).astype(np.float64)
     from oracle import PCOracle
     orc = PCOracle.from_workload(wl)
     fn = orc.apply_adjoint if args.workload.endswith("_adjoint") else orc.apply
