@@ -236,9 +236,10 @@ def aggregate_rate(units_per_rank, world, seconds):
     return world * units_per_rank / seconds
 
 
-def cpu_oracle_rate(wl, x, seconds, seed=0, adjoint=False):
+def cpu_oracle_rate(wl, x, seconds, seed=0, adjoint=False, keep=None):
     """Time the oracle on random output pixels until `seconds` have passed;
-    returns (RHS/s-equivalent, pixels, threads, elapsed)."""
+    returns (RHS/s-equivalent, pixels, threads, elapsed).  If `keep` is a
+    dict it receives the last call's "points" and oracle "values" [B][n]."""
     from oracle import PCOracle
     orc = PCOracle.from_workload(wl)
     fn = orc.apply_adjoint if adjoint else orc.apply
@@ -248,11 +249,25 @@ def cpu_oracle_rate(wl, x, seconds, seed=0, adjoint=False):
     chunk = min(512, wl.n)
     while time.perf_counter() - t0 < seconds:
         pts = rng.choice(wl.n, chunk, replace=False)
-        fn(x, points=pts)
+        out = fn(x, points=pts)
+        if keep is not None:
+            keep["points"], keep["values"] = pts, out
         done += chunk
         chunk = min(chunk * 2, 65536, wl.n)   # large calls: each also transposes the whole input batch
     el = time.perf_counter() - t0
     return wl.nrhs * (done / wl.n) / el, done, os.cpu_count(), el
+
+
+def sampled_error(y, points, values):
+    """Largest relative l2 error over the right-hand sides of the device
+    result y [B][*box] at the oracle's sampled output pixels (FP64 values
+    [B][len(points)])."""
+    import torch
+    idx = torch.as_tensor(np.asarray(points, dtype=np.int64), device=y.device)
+    got = y.reshape(y.shape[0], -1).index_select(1, idx).double().cpu().numpy()
+    ref = np.asarray(values, dtype=np.float64).reshape(got.shape)
+    den = np.maximum(np.linalg.norm(ref, axis=1), np.finfo(np.float64).tiny)
+    return float(np.max(np.linalg.norm(got - ref, axis=1) / den))
 
 
 def run_reference_block(args, wl):
@@ -985,9 +1000,18 @@ def main():
         line["roofline_tensor"] = roof_tensor
         line["dtype"] = "f32+bf16x3"
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
-        rate, pix, cores, el = cpu_oracle_rate(wl, x_host, args.cpu_seconds, adjoint=adjoint)
+        kept = {}
+        rate, pix, cores, el = cpu_oracle_rate(wl, x_host, args.cpu_seconds, adjoint=adjoint, keep=kept)
         line["cpu_baseline"] = {"value": rate, "unit": "RHS/s", "cores": cores, "kind": "oracle",
                                 "sample": "%d random output pixels x %d RHS in %.1f s" % (pix, wl.nrhs, el)}
+        if not estimator and kept:
+            # the timed result against the FP64 oracle at the last sample's pixels
+            try:
+                err = sampled_error(y, kept["points"], kept["values"])
+                line["accuracy"] = {"rel_l2_vs_fp64_oracle": err, "pixels": int(len(kept["points"])),
+                                    "rhs": wl.nrhs, "per": "max over right-hand sides"}
+            except Exception as e:   # a report, never a reason to lose the line
+                line["accuracy"] = {"unavailable": "%s: %s" % (type(e).__name__, e)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     op.close()
