@@ -58,14 +58,20 @@ class Grid:
         self.bbox_hi = np.array([self.cells[self.cells_of[k], 1, :].max(axis=0) for k in range(self.r)])
 
     def _validate(self):
-        cnt = np.zeros(self.shape, dtype=np.int64)
+        """The leaves tile Omega (Section 2.2): boxes of positive extent
+        inside it, every unit cube of Omega in exactly one leaf, so that
+        leaves meet only on facets."""
+        cnt = np.zeros(tuple(int(n) - 1 for n in self.shape), dtype=np.int64)
         for lo, hi in self.cells:
-            if np.any(lo < 0) or np.any(hi >= np.array(self.shape)) or np.any(hi < lo):
+            if np.any(lo < 0) or np.any(hi >= np.array(self.shape)):
                 raise ValueError("leaf cell outside the box")
-            sl = tuple(slice(int(a), int(b) + 1) for a, b in zip(lo, hi))
-            cnt[sl] += 1
+            if np.any(hi <= lo):
+                raise ValueError("degenerate leaf cell")
+            cnt[tuple(slice(int(a), int(b)) for a, b in zip(lo, hi))] += 1
         if np.any(cnt == 0):
             raise ValueError("leaves do not cover the box")
+        if np.any(cnt > 1):
+            raise ValueError("leaves overlap")
 
     def bbox_shape(self, k):
         return tuple(int(h - l + 1) for l, h in zip(self.bbox_lo[k], self.bbox_hi[k]))

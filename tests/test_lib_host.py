@@ -311,3 +311,51 @@ def test_adaptive_host_loop_matches_the_oracle_construction(monkeypatch, case):
     assert np.allclose([e for _, e in hist], [e for _, e in ref_hist], rtol=1e-12, atol=0)
     if case == "3d_crosswise":
         assert stats.get("skipped_splits", 0) >= 1
+
+
+def _mutations(cells, rng):
+    """Invalid variants of a valid leaf list: a leaf grown into its
+    neighbour, a leaf dropped, a degenerate leaf, a leaf past the box, a
+    duplicated leaf."""
+    cells = [np.array(c, dtype=np.int64) for c in cells]
+    d = cells[0].shape[1]
+    out = []
+    c = int(rng.integers(len(cells)))
+    a = int(rng.integers(d))
+    grown = [x.copy() for x in cells]
+    grown[c][1][a] += 1
+    out.append(("overlap or outside", grown))
+    out.append(("gap", [x for j, x in enumerate(cells) if j != c]))
+    flat = [x.copy() for x in cells]
+    flat[c][1][a] = flat[c][0][a]
+    out.append(("degenerate", flat))
+    shifted = [x.copy() for x in cells]
+    shifted[c][0][a] -= 1
+    out.append(("negative or overlap", shifted))
+    out.append(("duplicate", cells + [cells[c].copy()]))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_invalid_grids_are_refused_without_harm(seed):
+    """Leaf lists that do not tile the box (overlaps, gaps, degenerate or
+    out-of-box leaves, duplicates) are refused with PC_ERR_GRID by every host
+    entry point that reads a grid; the oracle's grid refuses them too."""
+    rng = np.random.default_rng(100 + seed)
+    if seed % 2:
+        shape, cells = _random_tree_3d(seed, splits=4)
+    else:
+        shape = (int(rng.integers(8, 40)), int(rng.integers(8, 40)))
+        cells = workloads.regular_grid(shape, (int(rng.integers(2, 5)), int(rng.integers(2, 5))))
+    for why, bad in _mutations(cells, rng):
+        bad = np.array(bad, dtype=np.int64)
+        for call in (lambda: pcb.pc_sample_points(shape, bad),
+                     lambda: pcb.pc_neighbourhood_boxes(shape, bad),
+                     lambda: pcb.pc_harmonic_weights(shape, bad)):
+            with pytest.raises(pcb.PCError) as ei:
+                call()
+            assert ei.value.status == pcb.PC_ERR_GRID, why
+        with pytest.raises(Exception):
+            Grid(shape, bad)
+    # and the valid grid still goes through
+    assert np.array_equal(pcb.pc_sample_points(shape, np.array(cells)), Grid(shape, cells).points)
