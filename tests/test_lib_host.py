@@ -359,3 +359,17 @@ def test_invalid_grids_are_refused_without_harm(seed):
             Grid(shape, bad)
     # and the valid grid still goes through
     assert np.array_equal(pcb.pc_sample_points(shape, np.array(cells)), Grid(shape, cells).points)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_extension_matches_oracle_on_random_3d_trees(seed):
+    """phi_k^E (Section 2.5) on random anisotropic 3D trees, where sample
+    points have uneven neighbour sets and the counting functions c_k vary."""
+    shape, cells = _random_tree_3d(seed, splits=8)
+    g = Grid(shape, cells)
+    R = 4
+    rng = np.random.default_rng(300 + seed)
+    phi = rng.standard_normal((g.r, (2 * R + 1) ** 3))
+    ref = extend_impulse_responses(g, workloads_mask(shape, g.points, R) * phi, R)
+    got = pcb.pc_extend_impulse(shape, np.array(cells), R, phi)
+    assert np.max(np.abs(got - ref)) < 4e-15 * max(1.0, np.abs(ref).max())
