@@ -373,3 +373,12 @@ def test_extension_matches_oracle_on_random_3d_trees(seed):
     ref = extend_impulse_responses(g, workloads_mask(shape, g.points, R) * phi, R)
     got = pcb.pc_extend_impulse(shape, np.array(cells), R, phi)
     assert np.max(np.abs(got - ref)) < 4e-15 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_points_and_boxes_match_oracle_on_random_3d_trees(seed):
+    shape, cells = _random_tree_3d(seed, splits=12)
+    g = Grid(shape, cells)
+    assert np.array_equal(pcb.pc_sample_points(shape, np.array(cells)), g.points)
+    lo, hi = pcb.pc_neighbourhood_boxes(shape, np.array(cells))
+    assert np.array_equal(lo, g.bbox_lo) and np.array_equal(hi, g.bbox_hi)
