@@ -382,3 +382,34 @@ def test_points_and_boxes_match_oracle_on_random_3d_trees(seed):
     assert np.array_equal(pcb.pc_sample_points(shape, np.array(cells)), g.points)
     lo, hi = pcb.pc_neighbourhood_boxes(shape, np.array(cells))
     assert np.array_equal(lo, g.bbox_lo) and np.array_equal(hi, g.bbox_hi)
+
+
+def _random_tree_2d(seed, shape=(41, 37), splits=25):
+    from oracle.adaptive import initial_cells, subdivide
+    rng = np.random.default_rng(seed)
+    cells = initial_cells(shape)
+    for _ in range(splits):
+        while True:
+            c, a = int(rng.integers(len(cells))), int(rng.integers(2))
+            if cells[c][1][a] - cells[c][0][a] > 2:
+                break
+        cells = subdivide(cells, c, a)
+    return shape, cells
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_2d_random_anisotropic_trees_match_oracle(seed):
+    """Random one-axis splits in 2D: edges with several hanging nodes, leaves
+    of very different sizes side by side.  Sample points, boxes, weights (to
+    1e-12) and phi_k^E (to rounding) against the oracle."""
+    shape, cells = _random_tree_2d(seed)
+    g = Grid(shape, cells)
+    arr = np.array(cells)
+    assert np.array_equal(pcb.pc_sample_points(shape, arr), g.points)
+    W = harmonic_weights(g)
+    ref = np.concatenate([w.ravel() for w in W])
+    assert np.max(np.abs(pcb.pc_harmonic_weights(shape, arr) - ref)) < 1e-12
+    R = 6
+    phi = np.random.default_rng(400 + seed).standard_normal((g.r, (2 * R + 1) ** 2))
+    ext = extend_impulse_responses(g, workloads_mask(shape, g.points, R) * phi, R)
+    assert np.max(np.abs(pcb.pc_extend_impulse(shape, arr, R, phi) - ext)) < 4e-15 * max(1.0, np.abs(ext).max())
