@@ -413,3 +413,24 @@ def test_2d_random_anisotropic_trees_match_oracle(seed):
     phi = np.random.default_rng(400 + seed).standard_normal((g.r, (2 * R + 1) ** 2))
     ext = extend_impulse_responses(g, workloads_mask(shape, g.points, R) * phi, R)
     assert np.max(np.abs(pcb.pc_extend_impulse(shape, arr, R, phi) - ext)) < 4e-15 * max(1.0, np.abs(ext).max())
+
+
+def test_library_weights_match_the_hand_worked_fixture():
+    """The library's weights on the hand-worked 5 x 3 box with one hanging
+    node (tests/golden/hanging_2d_5x3.txt)."""
+    from conftest import load_golden_sections
+    from test_oracle_geometry import HANGING_5x3
+    fx = load_golden_sections("hanging_2d_5x3.txt")
+    shape, cells = HANGING_5x3
+    arr = np.array(cells)
+    pts = pcb.pc_sample_points(shape, arr)
+    lo, hi = pcb.pc_neighbourhood_boxes(shape, arr)
+    flat = pcb.pc_harmonic_weights(shape, arr)
+    off = 0
+    for k, p in enumerate(pts):
+        ext = tuple(int(b - a + 1) for a, b in zip(lo[k], hi[k]))
+        full = np.zeros(shape)
+        full[lo[k][0]:hi[k][0] + 1, lo[k][1]:hi[k][1] + 1] = flat[off:off + int(np.prod(ext))].reshape(ext)
+        off += int(np.prod(ext))
+        assert np.max(np.abs(full - fx["w_%d_%d" % (int(p[0]), int(p[1]))])) < 1e-15
+    assert off == flat.size

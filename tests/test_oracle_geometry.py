@@ -348,3 +348,21 @@ def test_extension_keeps_own_values_and_averages_neighbours():
             js = [j for j in g.nbrs[k] if j != k and ind[j][z]]
             want = np.mean([phi[j][z] for j in js]) if js else 0.0
             assert abs(E[k][z] - want) < 1e-15
+
+
+HANGING_5x3 = ((5, 3), [[[0, 0], [2, 2]], [[2, 0], [4, 1]], [[2, 1], [4, 2]]])
+
+
+def test_hanging_node_weights_match_the_hand_worked_fixture(golden):
+    """tests/golden/hanging_2d_5x3.txt: the weights of a 5 x 3 box with one
+    hanging node, worked out by hand from Section 2.4 (linear edges split at
+    sample points, the 5-point mean at the one interior point)."""
+    fx = golden("hanging_2d_5x3.txt")
+    shape, cells = HANGING_5x3
+    g = Grid(shape, np.array(cells))
+    W = harmonic_weights(g)
+    assert [tuple(int(v) for v in p) for p in g.points] == [(0, 0), (0, 2), (2, 0), (2, 1), (2, 2), (4, 0), (4, 1),
+                                                            (4, 2)]
+    for k, p in enumerate(g.points):
+        want = fx["w_%d_%d" % (int(p[0]), int(p[1]))]
+        assert np.max(np.abs(weight_on_omega(g, W, k) - want)) < 1e-15
