@@ -434,3 +434,16 @@ def test_library_weights_match_the_hand_worked_fixture():
         off += int(np.prod(ext))
         assert np.max(np.abs(full - fx["w_%d_%d" % (int(p[0]), int(p[1]))])) < 1e-15
     assert off == flat.size
+
+
+def test_library_extension_matches_the_hand_worked_fixture():
+    """pc_extend_impulse on the hand-worked 3 x 3 example
+    (tests/golden/extension_2d_3x3.txt); values outside Omega - p_k in the
+    input are ignored by the library."""
+    from conftest import load_golden_sections
+    from test_oracle_geometry import _hand_extension_inputs
+    fx = load_golden_sections("extension_2d_3x3.txt")
+    shape, cells, phi = _hand_extension_inputs()
+    got = pcb.pc_extend_impulse(shape, cells, 1, phi)
+    for k in range(4):
+        assert np.array_equal(got[k].reshape(3, 3), fx["phiE_%d" % k])

@@ -366,3 +366,25 @@ def test_hanging_node_weights_match_the_hand_worked_fixture(golden):
     for k, p in enumerate(g.points):
         want = fx["w_%d_%d" % (int(p[0]), int(p[1]))]
         assert np.max(np.abs(weight_on_omega(g, W, k) - want)) < 1e-15
+
+
+def _hand_extension_inputs():
+    shape = (3, 3)
+    cells = np.array([[[0, 0], [2, 2]]])
+    a, b = np.meshgrid(np.arange(3), np.arange(3), indexing="ij")
+    phi = np.stack([10.0 * (j + 1) + 3 * a + b for j in range(4)]).reshape(4, 9)
+    return shape, cells, phi
+
+
+def test_extension_matches_the_hand_worked_fixture(golden):
+    """tests/golden/extension_2d_3x3.txt: phi_k^E on a 3 x 3 box with its four
+    corners as sample points, worked out by hand from Section 2.5."""
+    from oracle.extension import extend_impulse_responses
+    fx = golden("extension_2d_3x3.txt")
+    shape, cells, phi = _hand_extension_inputs()
+    g = Grid(shape, cells)
+    offs = np.stack(np.meshgrid(np.arange(-1, 2), np.arange(-1, 2), indexing="ij"), -1).reshape(-1, 2)
+    mask = np.array([[np.all((p + z >= 0) & (p + z < 3)) for z in offs] for p in g.points], dtype=float)
+    got = extend_impulse_responses(g, mask * phi, 1)
+    for k in range(4):
+        assert np.array_equal(got[k].reshape(3, 3), fx["phiE_%d" % k])
