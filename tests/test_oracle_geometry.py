@@ -388,3 +388,20 @@ def test_extension_matches_the_hand_worked_fixture(golden):
     got = extend_impulse_responses(g, mask * phi, 1)
     for k in range(4):
         assert np.array_equal(got[k].reshape(3, 3), fx["phiE_%d" % k])
+
+
+def test_hand_worked_column_of_the_approximation(golden):
+    """The column x = (1,1) of A~ on the hand-worked 3 x 3 example, from the
+    oracle's direct-sum apply of e_(1,1) and from its entry-formula matrix."""
+    from oracle import PCOracle
+    from oracle.dense import dense_pc
+    fx = golden("extension_2d_3x3.txt")
+    shape, cells, phi = _hand_extension_inputs()
+    g = Grid(shape, cells)
+    offs = np.stack(np.meshgrid(np.arange(-1, 2), np.arange(-1, 2), indexing="ij"), -1).reshape(-1, 2)
+    mask = np.array([[np.all((p + z >= 0) & (p + z < 3)) for z in offs] for p in g.points], dtype=float)
+    orc = PCOracle(shape, cells, mask * phi, 1)
+    e = np.zeros((1, 3, 3))
+    e[0, 1, 1] = 1.0
+    assert np.max(np.abs(orc.apply(e)[0] - fx["Atilde_col_1_1"])) < 1e-13
+    assert np.max(np.abs(dense_pc(orc)[:, 4].reshape(3, 3) - fx["Atilde_col_1_1"])) < 1e-13
