@@ -447,3 +447,21 @@ def test_library_extension_matches_the_hand_worked_fixture():
     got = pcb.pc_extend_impulse(shape, cells, 1, phi)
     for k in range(4):
         assert np.array_equal(got[k].reshape(3, 3), fx["phiE_%d" % k])
+
+
+def test_library_3d_hanging_node_weight_matches_the_hand_worked_fixture():
+    from conftest import load_golden_sections
+    from test_oracle_geometry import HANGING_5x3x3
+    want = load_golden_sections("hanging_3d_5x3x3.txt")["w_2_1_0"].reshape(5, 3, 3)
+    shape, cells = HANGING_5x3x3
+    arr = np.array(cells)
+    pts = [tuple(int(v) for v in p) for p in pcb.pc_sample_points(shape, arr)]
+    lo, hi = pcb.pc_neighbourhood_boxes(shape, arr)
+    flat = pcb.pc_harmonic_weights(shape, arr)
+    k = pts.index((2, 1, 0))
+    sizes = [int(np.prod(h - l + 1)) for l, h in zip(lo, hi)]
+    off = int(np.sum(sizes[:k]))
+    ext = tuple(int(v) for v in hi[k] - lo[k] + 1)
+    full = np.zeros(shape)
+    full[tuple(slice(int(a), int(b) + 1) for a, b in zip(lo[k], hi[k]))] = flat[off:off + sizes[k]].reshape(ext)
+    assert np.max(np.abs(full - want)) < 1e-15

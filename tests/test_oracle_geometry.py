@@ -405,3 +405,19 @@ def test_hand_worked_column_of_the_approximation(golden):
     e[0, 1, 1] = 1.0
     assert np.max(np.abs(orc.apply(e)[0] - fx["Atilde_col_1_1"])) < 1e-13
     assert np.max(np.abs(dense_pc(orc)[:, 4].reshape(3, 3) - fx["Atilde_col_1_1"])) < 1e-13
+
+
+HANGING_5x3x3 = ((5, 3, 3), [[[0, 0, 0], [2, 2, 2]], [[2, 0, 0], [4, 1, 2]], [[2, 1, 0], [4, 2, 2]]])
+
+
+def test_3d_hanging_node_weight_matches_the_hand_worked_fixture(golden):
+    """tests/golden/hanging_3d_5x3x3.txt: the weight of a hanging node on a
+    broken facet, worked out by hand from Section 2.4 (edges, then the facet
+    pieces and facets, then the interiors, each by its discrete Laplace
+    mean)."""
+    want = golden("hanging_3d_5x3x3.txt")["w_2_1_0"].reshape(5, 3, 3)
+    shape, cells = HANGING_5x3x3
+    g = Grid(shape, np.array(cells))
+    W = harmonic_weights(g)
+    k = [tuple(int(v) for v in p) for p in g.points].index((2, 1, 0))
+    assert np.max(np.abs(weight_on_omega(g, W, k) - want)) < 1e-15
