@@ -130,8 +130,6 @@ def _pieces_end_at_points(cells, new_boxes) -> bool:
     return True
 
 
-
-
 def construct(ctx, shape, impulse: Callable[[np.ndarray], np.ndarray], R: int, Z, Y, tau: float,
               precision: str = "fp32", max_passes: int = 100, batch: int = 1, incremental: bool = True,
               stats: dict = None, **tune):
