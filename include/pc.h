@@ -90,13 +90,24 @@ typedef struct {
     const int32_t *cells;
 } pc_grid;
 
-/* Launch-shape knobs; a NULL pc_tuning, or a field of 0, means "choose". */
+/* Launch-shape knobs of an operator.  pc_build_spectra with a NULL
+ * pc_tuning autotunes them (times candidate shapes on the device and keeps
+ * the fastest); in a non-NULL pc_tuning a field of 0 means "the library's
+ * model choice" (no timing). */
 typedef struct {
-    int32_t fft_size;        /* padded FFT extent P per axis: 64, 128 (2D) */
+    int32_t fft_size;        /* padded FFT extent P per axis: 64, 128 (2D); 64 (3D) */
     int32_t tile;            /* input tile extent T <= min(P - W + 1, 2P/3), W the kernel
                                 (sub-)window extent (2R+1 unless split) (0: that bound) */
     int32_t ctas_per_sm;     /* persistent CTAs per SM (0: occupancy limit) */
-    int32_t reserved[5];
+    int32_t wait_limit_us;   /* limit of every device-side wait of an apply (ordering flags,
+                                copy completion, host-written ready words), microseconds
+                                (0: 2 s).  A wait that runs out ends the launch early: every
+                                other wait of the launch then gives up at once, the result is
+                                invalid, and the apply's status query reports PC_ERR_TIMEOUT */
+    int32_t window_split;    /* kernel sub-windows per axis: [-R, R] cut into window_split
+                                pieces with their own spectra, an exact rewrite of the sum
+                                (0: the count that minimises FFT work per input pixel) */
+    int32_t reserved[3];
 } pc_tuning;
 
 /* Read-only description of a built operator. */
@@ -113,7 +124,12 @@ typedef struct {
     int64_t spectra_bytes;   /* device bytes of the stored spectra */
     int64_t device_bytes;    /* all device bytes owned by the operator, including the
                                 buffers its applies have grown so far */
-    double build_seconds;
+    double build_seconds;    /* including the autotuner's candidates when it ran */
+    int32_t window_split;    /* kernel sub-windows per axis */
+    int32_t ctas_per_sm;     /* persistent CTAs per SM of the apply */
+    int32_t autotuned;       /* 1 if the launch shape came from the autotuner */
+    int32_t tuned_candidates;   /* candidate shapes the autotuner timed */
+    double tuned_ms;         /* its time of the chosen shape per timed batch (ms) */
 } pc_operator_info;
 
 typedef struct pc_context pc_context;
@@ -330,6 +346,50 @@ pc_status pc_estimator_update(pc_estimator *est, pc_operator *op, double *eta, i
 pc_status pc_estimator_destroy(pc_estimator *est);
 
 /* ---------------------------------------------------------------------
+ * Refinement of the adaptive construction (Algorithm 1, Section 2.7), host
+ * code on the leaf cells of pc_grid.  With pc_build_spectra and
+ * pc_estimate_cell_errors (or pc_estimator_update) a C caller runs the whole
+ * construction: build, estimate, pc_refine, repeat until eta_Omega <= tau.
+ * impulse: phi_k of the current sample points, as for pc_build_spectra.
+ * --------------------------------------------------------------------- */
+
+/* One pass of Algorithm 1's refinement.  eta_Omega = sqrt(sum_C eta_C^2) /
+ * y_rms (the overall estimator as a relative estimate: y_rms = ||Y||_F /
+ * sqrt(q) of the caller's Y = A* Z; eta_c[C] from pc_estimate_cell_errors,
+ * one per leaf in grid order).  If eta_Omega > tau, up to `batch` leaves are
+ * split, largest eta_C first (ties: lower leaf index), each in its first
+ * admissible direction of pc_split_directions (in 3D a direction is
+ * admissible when pc_split_is_admissible says so, on the leaves as split so
+ * far this pass; a leaf with none is passed over).  A split halves the leaf
+ * at floor((c_min + c_max) / 2).  cells_out receives the new leaf list
+ * (the unsplit leaves in their order, then each split leaf's two halves,
+ * highest split leaf index first; layout as pc_grid.cells), room for
+ * num_cells + batch leaves; *num_cells_out its length (num_cells when
+ * eta_Omega <= tau or no leaf could be split).  batch = 1 is Algorithm 1 as
+ * printed. */
+pc_status pc_refine(const pc_box *box, const pc_grid *grid, int32_t radius, const double *impulse,
+                    const double *eta_c, double y_rms, double tau, int32_t batch, double *eta_omega,
+                    int32_t *cells_out, int32_t *num_cells_out);
+
+/* Subdivision directions of leaf `cell` (Section 2.7), best first: the axes
+ * i with c_max^i - c_min^i > 2, ordered by || phi^{i+} - phi^{i-} ||, the
+ * l2 norm over the window offsets z with c_mid + z in Omega of the
+ * difference between the averages of phi_k^E (Eq. def_varphiE) over the
+ * leaf's corners on its front and its back face along i; scores within a
+ * relative 1e-9 of the best are a tie, won by the lowest axis.  dirs:
+ * room for ndim entries; *ndirs the number written. */
+pc_status pc_split_directions(const pc_box *box, const pc_grid *grid, int32_t radius, const double *impulse,
+                              int32_t cell, int32_t *dirs, int32_t *ndirs);
+
+/* Whether halving leaf `cell` along `axis` keeps every facet piece of the
+ * two halves (their facets' intersections of positive area with the facets
+ * of the leaves across) with sample points at its corners, which the
+ * recursive weights of Section 2.4 need; always 1 in 2D.  A 3D split that
+ * breaks a facet crosswise gives 0.  PC_ERR_ARG if the leaf is thinner than
+ * 2 along the axis. */
+pc_status pc_split_is_admissible(const pc_box *box, const pc_grid *grid, int32_t cell, int32_t axis, int32_t *ok);
+
+/* ---------------------------------------------------------------------
  * Block apply (Section 3.3).  For closed boxes T (targets) and S (sources)
  * inside Omega, and x_S extended by zero outside S:
  *   forward  y_T = A~[T, S] x_S
@@ -444,23 +504,38 @@ pc_status pc_apply_plain(pc_operator *op, int32_t nrhs, const void *x, int64_t l
  * sides) plus a 64-byte control block - lives in a statically sized device
  * array of 1 MiB inside libpc that every GPU which loads the library holds
  * until the process exits.
- *   - Same arguments, layout and result as pc_apply_batched (y overwritten).
+ *   - Same arguments, layout and result as pc_apply_batched (y overwritten),
+ *     for 2D operators; a 3D operator is refused with PC_ERR_UNSUPPORTED.
  *     The operator (spectra, weights, tiles) was allocated by
  *     pc_build_spectra; the caller owns x and y.
  *   - Limit: num_tiles * ceil(nrhs/2) <= 262128 (pc_operator_info gives
  *     num_tiles); larger batches fail with PC_ERR_ARG and a message, before
  *     anything is launched.  Split such batches.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress with that device current) and caches it; make that
- *     first call before any stream capture.
- *   - Every call, on every operator, shares the one array; the call clears the
- *     part it uses before its kernel reads it.  Calls whose work overlaps on
- *     the GPU (different streams, or another thread) race on the array and
- *     give wrong results: serialise them, e.g. on one stream.
- *   - Device-side wait timeouts are not reported by this path (use
- *     pc_apply_batched with pc_operator_check for that). */
+ *   - The first call on a device sets the path up: it looks up the array's
+ *     device address (cudaGetSymbolAddress with that device current), which
+ *     also loads the library's module and with it the array, and loads this
+ *     path's kernels; the result is cached.  A call with nrhs == 0 does this
+ *     set-up and launches nothing: make such a call first, before the caller
+ *     reserves its device memory and before any stream capture.
+ *   - Every call, on every operator, shares the one array and it keeps the
+ *     last call's contents; each call clears the part it uses before its
+ *     kernel reads it.  Calls whose work overlaps on the GPU (different
+ *     streams, or another thread) race on the array and give wrong results:
+ *     serialise them, e.g. on one stream.
+ *   - Device-side wait timeouts set a status word in the array, which
+ *     pc_noalloc_check reads; the next call clears it.  The operator's own
+ *     queries (pc_operator_check, pc_operator_kernel_time,
+ *     pc_operator_launches) describe its last pc_apply* call and ignore the
+ *     calls made here. */
 pc_status pc_apply_batched_noalloc(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx,
                                    void *y, int64_t ldy, pc_stream stream);
+
+/* Status of the last pc_apply_batched_noalloc call on ctx's device, which the
+ * caller issued on `stream`: synchronises that stream, then returns
+ * PC_ERR_TIMEOUT (and clears the word) if one of the call's device-side waits
+ * ran out, else PC_OK.  Call it before the next allocation-free apply, which
+ * clears the word.  Allocates nothing; the paper has no counterpart. */
+pc_status pc_noalloc_check(pc_context *ctx, pc_stream stream);
 
 /* ---------------------------------------------------------------------
  * Serving.  The paper's use of A~ is many applications to vectors that
@@ -473,11 +548,11 @@ pc_status pc_apply_batched_noalloc(pc_operator *op, int32_t nrhs, const void *x,
  * from a CUDA graph captured at creation.  Launch slots run on separate
  * streams, so a new launch starts while earlier ones finish.  Each request
  * is computed exactly as pc_apply_batched would compute it alone.
- * Supported operators: 2D PC_FP32 with fft_size 128 (batched together as
- * above) and 3D PC_FP32 / PC_BF16X3.  A 3D request runs alone on a launch
- * slot through the operator's own apply, one request per 3D operator at a
- * time; 3D requests of different operators, and 2D launches, overlap on the
- * other slots.
+ * 2D PC_FP32 operators with fft_size 128 are batched together as above.
+ * Any other operator (2D with fft_size 64 or PC_FP64, 3D PC_FP32 /
+ * PC_BF16X3) runs each request alone on a launch slot through the operator's
+ * own apply, one request per such operator at a time; requests of different
+ * operators, and the batched launches, overlap on the other slots.
  * --------------------------------------------------------------------- */
 
 /* Create a server on ctx's device: a scheduler thread, `streams` launch
@@ -515,10 +590,14 @@ pc_status pc_serve_stats_get(pc_server *srv, pc_serve_stats *stats);
  * server's resources.  Requests still queued are dropped. */
 pc_status pc_serve_destroy(pc_server *srv);
 
-/* Autotuner: builds candidate launch shapes of the operator (FFT size,
- * tile extent), times a batch of nrhs vectors on each with CUDA events, and
- * writes the fastest into *best (*best_ms: its time per batch).  Same
- * operator arguments as pc_build_spectra. */
+/* Autotuner: enumerates the operator's launch shapes (FFT size P, kernel
+ * sub-windows per axis, tile extent T, persistent CTAs per SM for 3D), ranks
+ * them by a model of their line-FFT work, builds the best few and times a
+ * batch of nrhs vectors on each with CUDA events on a private stream; a
+ * candidate whose build, apply or device status fails is dropped.  Writes the
+ * fastest into *best (*best_ms: its time per batch).  Same operator arguments
+ * as pc_build_spectra, which runs the same search (nrhs = 8 in 2D, 4 in 3D)
+ * when its pc_tuning is NULL and keeps the winning operator. */
 pc_status pc_autotune(pc_context *ctx, const pc_box *box, const pc_grid *grid, int32_t radius, const double *impulse,
                       const double *weights, pc_precision prec, int32_t nrhs, pc_tuning *best, double *best_ms);
 

@@ -10,25 +10,17 @@ weights w_k, extended impulse responses phi_k^E and spectra in libpc),
 estimates eta_C for every leaf (pc_estimate_cell_errors: A~* Z on the GPU,
 FP64 cell norms) and refines.
 
-Overall estimator: eta_Omega = sqrt(sum_C eta_C^2) / (||Y||_F / sqrt(q)),
-a relative error estimate (a point on a shared facet counts in each cell
-that holds it).  While eta_Omega > tau, the leaf with the largest eta_C is
-split (Section 2.7) in the direction i, among those with c_max^i - c_min^i
-> 2, that maximises || phi^{i+} - phi^{i-} || over the window offsets z with
-c_mid + z in Omega, where phi^{i+-} averages phi_k^E over the cell's corners
-on its front / back face in direction i; values within a relative 1e-9 of
-the largest are a tie, won by the lowest i.  The split is at
-floor((c_min + c_max) / 2).  batch > 1 splits up to that many leaves per
-pass (largest eta_C first); batch = 1 is Algorithm 1 as printed.
-
-In 3D a split can break the two sides of a facet crosswise (one side split
-along one axis, the other along another): the facet's pieces then meet at a
-point that is no cell's corner, where the recursive weights of Section 2.4
-have no value (libpc refuses such grids with PC_ERR_GRID).  A leaf therefore
-takes its directions in the order above (each the best of those left) and
-splits in the first one that keeps every facet piece's corners at sample
-points; a leaf with none is passed over for the next by eta_C.  In 2D facets
-are segments and every split qualifies.
+Each pass then calls pc_refine, which computes the overall estimator
+eta_Omega = sqrt(sum_C eta_C^2) / (||Y||_F / sqrt(q)) (a relative error
+estimate; a point on a shared facet counts in each cell that holds it) and,
+while eta_Omega > tau, splits the leaf with the largest eta_C (Section 2.7)
+in the direction of largest change of phi^E, at floor((c_min + c_max) / 2);
+batch > 1 splits up to that many leaves per pass (largest eta_C first),
+batch = 1 is Algorithm 1 as printed.  In 3D a split that would break the two
+sides of a facet crosswise is skipped for the leaf's next direction
+(pc_split_is_admissible): the facet's pieces would meet at a point that is
+no cell's corner, where the recursive weights of Section 2.4 have no value.
+All of this is libpc's host code; this module only marshals.
 
 Each pass rebuilds the operator (geometry, weights and spectra in libpc).
 Y~ = A~* Z is updated incrementally, as Algorithm 1 does (`incremental`,
@@ -47,10 +39,11 @@ from typing import Callable, List, Tuple
 
 import numpy as np
 
-from .binding import Estimator, Operator, pc_extend_impulse, pc_sample_points
+from .binding import Estimator, Operator, pc_refine, pc_sample_points
 
 
 def _first_cells(shape) -> List[Tuple[List[int], List[int]]]:
+    """Omega split once along every axis at floor((0 + n - 1) / 2)."""
     d = len(shape)
     mids = [(n - 1) // 2 for n in shape]
     out = []
@@ -59,75 +52,6 @@ def _first_cells(shape) -> List[Tuple[List[int], List[int]]]:
         hi = [mids[a] if s == 0 else shape[a] - 1 for a, s in enumerate(side)]
         out.append((lo, hi))
     return out
-
-
-def _directions(shape, lo, hi, point_index, phiE, R) -> List[int]:
-    d = len(shape)
-    W = 2 * R + 1
-    cmid = [(a + b) // 2 for a, b in zip(lo, hi)]
-    grids = np.meshgrid(*[np.arange(-R, R + 1)] * d, indexing="ij")
-    mask = np.ones((W,) * d, dtype=bool)
-    for a in range(d):
-        mask &= (cmid[a] + grids[a] >= 0) & (cmid[a] + grids[a] < shape[a])
-    mask = mask.ravel()
-    scores = {}
-    for i in range(d):
-        if hi[i] - lo[i] <= 2:
-            continue
-        front = np.zeros(W ** d)
-        back = np.zeros(W ** d)
-        for corner in product(*[(lo[a], hi[a]) for a in range(d)]):
-            k = point_index[corner]
-            if corner[i] == hi[i]:
-                front += phiE[k]
-            else:
-                back += phiE[k]
-        delta = (front - back) * (2.0 ** (1 - d))
-        scores[i] = float(np.linalg.norm(delta[mask]))
-    out = []
-    while scores:
-        top = max(scores.values())
-        i = min(j for j, v in scores.items() if v >= top - 1e-9 * top)
-        out.append(i)
-        del scores[i]
-    return out
-
-
-def _split(cells, box, i):
-    """cells with leaf `box` replaced by its halves along axis i."""
-    lo, hi = box
-    m = (lo[i] + hi[i]) // 2
-    out = [c for c in cells if not (list(c[0]) == list(lo) and list(c[1]) == list(hi))]
-    out.append((list(lo), [m if a == i else hi[a] for a in range(len(lo))]))
-    out.append(([m if a == i else lo[a] for a in range(len(lo))], list(hi)))
-    return out
-
-
-def _pieces_end_at_points(cells, new_boxes) -> bool:
-    """Whether every facet piece of the leaves `new_boxes` (their facets'
-    intersections of positive area with the facets of the leaves across)
-    has cell corners at its corners.  Pieces away from them are unchanged by
-    a split."""
-    d = len(cells[0][0])
-    corners = set()
-    for lo, hi in cells:
-        corners.update(product(*[(lo[a], hi[a]) for a in range(d)]))
-    for lo, hi in new_boxes:
-        for a in range(d):
-            for plane, far in ((lo[a], 1), (hi[a], 0)):
-                for nlo, nhi in cells:
-                    # a leaf across: its opposite facet lies on the same plane
-                    if (nhi[a] if far else nlo[a]) != plane or (nlo[a] if far else nhi[a]) == plane:
-                        continue
-                    plo = [max(lo[b], nlo[b]) for b in range(d)]
-                    phi = [min(hi[b], nhi[b]) for b in range(d)]
-                    plo[a] = phi[a] = plane
-                    if any(plo[b] >= phi[b] for b in range(d) if b != a):
-                        continue
-                    for corner in product(*[(plo[b], phi[b]) for b in range(d)]):
-                        if corner not in corners:
-                            return False
-    return True
 
 
 def construct(ctx, shape, impulse: Callable[[np.ndarray], np.ndarray], R: int, Z, Y, tau: float,
@@ -141,14 +65,14 @@ def construct(ctx, shape, impulse: Callable[[np.ndarray], np.ndarray], R: int, Z
     # the incremental estimator covers 2D boxes; 3D passes re-estimate in full
     est = Estimator(ctx, shape, Z, Y, precision) if incremental and len(shape) == 2 else None
     recomputed = []
-    ynorm = float(np.linalg.norm(Y.reshape(q, -1).double().cpu().numpy())) / np.sqrt(q)
-    cells = _first_cells(shape)
+    # y_rms = ||Y||_F / sqrt(q), from the caller's A* Z
+    y_rms = float(np.linalg.norm(Y.reshape(q, -1).double().cpu().numpy())) / np.sqrt(q)
+    cells = np.array(_first_cells(shape), dtype=np.int32)
     known = {}
     history = []
     op = None
     for _ in range(max_passes):
-        arr = np.array(cells, dtype=np.int32)
-        pts = pc_sample_points(shape, arr)
+        pts = pc_sample_points(shape, cells)
         fresh = [tuple(int(v) for v in p) for p in pts if tuple(int(v) for v in p) not in known]
         if fresh:
             for p, ph in zip(fresh, impulse(np.array(fresh))):
@@ -156,38 +80,20 @@ def construct(ctx, shape, impulse: Callable[[np.ndarray], np.ndarray], R: int, Z
         phi = np.stack([known[tuple(int(v) for v in p)] for p in pts])
         if op is not None:
             op.close()
-        op = Operator(ctx, shape, arr, R, phi, precision=precision, **tune)
+        op = Operator(ctx, shape, cells, R, phi, precision=precision, **tune)
         if est is not None:
             eta_c, nrec = est.update(op, len(cells))
         else:
             eta_c, nrec = op.estimate_cell_errors(Z, Y, len(cells)), len(pts)
         recomputed.append(nrec)
-        eta_o = float(np.sqrt(np.sum(eta_c ** 2))) / ynorm
+        # eta_Omega and the refinement (leaf choice, direction, admissibility): libpc
+        eta_o, nxt = pc_refine(shape, cells, R, phi, eta_c, y_rms, tau, batch)
         history.append((len(pts), eta_o))
-        if eta_o <= tau:
+        if eta_o <= tau or len(nxt) == len(cells):
             break
-        phiE = pc_extend_impulse(shape, arr, R, phi)
-        point_index = {tuple(int(v) for v in p): k for k, p in enumerate(pts)}
-        picks = []
-        trial = list(cells)   # the leaves as split so far this pass
-        for c in sorted(range(len(cells)), key=lambda c: (-eta_c[c], c)):
-            for i in _directions(shape, cells[c][0], cells[c][1], point_index, phiE, R):
-                nxt = _split(trial, cells[c], i)
-                if len(shape) == 2 or _pieces_end_at_points(nxt, nxt[-2:]):
-                    trial = nxt
-                    picks.append((c, i))
-                    break
-            if len(picks) == batch:
-                break
-        if not picks:
-            break
-        for c, i in sorted(picks, key=lambda ci: -ci[0]):
-            lo, hi = cells.pop(c)
-            m = (lo[i] + hi[i]) // 2
-            cells.append((lo, [m if a == i else hi[a] for a in range(len(shape))]))
-            cells.append(([m if a == i else lo[a] for a in range(len(shape))], hi))
+        cells = nxt
     if est is not None:
         est.close()
     if stats is not None:
         stats["recomputed"] = recomputed
-    return op, np.array(cells), history
+    return op, np.asarray(cells), history

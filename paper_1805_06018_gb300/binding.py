@@ -46,7 +46,7 @@ class pc_grid(ctypes.Structure):
 
 class pc_tuning(ctypes.Structure):
     _fields_ = [("fft_size", ctypes.c_int32), ("tile", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("wait_limit_us", ctypes.c_int32), ("window_split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class pc_operator_info(ctypes.Structure):
@@ -54,7 +54,8 @@ class pc_operator_info(ctypes.Structure):
                 ("r", ctypes.c_int32), ("fft_size", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("num_tiles", ctypes.c_int32), ("num_colors", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("spectra_bytes", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("build_seconds", ctypes.c_double)]
+                ("build_seconds", ctypes.c_double), ("window_split", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("autotuned", ctypes.c_int32), ("tuned_candidates", ctypes.c_int32), ("tuned_ms", ctypes.c_double)]
 
 
 class pc_serve_config(ctypes.Structure):
@@ -95,6 +96,7 @@ _PROTOS = {
     "pc_apply_batched": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
     "pc_apply_batched_noalloc": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64,
                                                  _VP]),
+    "pc_noalloc_check": (ctypes.c_int, [_VP, _VP]),
     "pc_apply_plain": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
     "pc_operator_check": (ctypes.c_int, [_VP]),
     "pc_operator_kernel_time": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
@@ -109,6 +111,13 @@ _PROTOS = {
     "pc_estimator_update": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
                                            _VP]),
     "pc_estimator_destroy": (ctypes.c_int, [_VP]),
+    "pc_refine": (ctypes.c_int, [ctypes.POINTER(pc_box), ctypes.POINTER(pc_grid), ctypes.c_int32, _VP, _VP,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                 _VP, ctypes.POINTER(ctypes.c_int32)]),
+    "pc_split_directions": (ctypes.c_int, [ctypes.POINTER(pc_box), ctypes.POINTER(pc_grid), ctypes.c_int32, _VP,
+                                           ctypes.c_int32, _VP, ctypes.POINTER(ctypes.c_int32)]),
+    "pc_split_is_admissible": (ctypes.c_int, [ctypes.POINTER(pc_box), ctypes.POINTER(pc_grid), ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "pc_block_plan_create": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(_VP)]),
     "pc_block_apply": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
     "pc_block_plan_create_many": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, ctypes.c_int32,
@@ -219,11 +228,56 @@ def pc_extend_impulse(shape, cells, radius: int, impulse: np.ndarray) -> np.ndar
     return out
 
 
+def pc_refine(shape, cells, radius: int, impulse: np.ndarray, eta_c, y_rms: float, tau: float, batch: int = 1):
+    """One refinement pass of Algorithm 1: (eta_Omega, new leaf cells [n][2][d])."""
+    b = _box(shape)
+    g, keep = _grid(cells)
+    d = len(shape)
+    imp = np.ascontiguousarray(impulse, dtype=np.float64)
+    eta = np.ascontiguousarray(eta_c, dtype=np.float64)
+    out = np.zeros((len(cells) + batch, 2, d), dtype=np.int32)
+    eo = ctypes.c_double()
+    n = ctypes.c_int32()
+    _check(lib().pc_refine(ctypes.byref(b), ctypes.byref(g), ctypes.c_int32(radius), _ptr(imp), _ptr(eta),
+                           ctypes.c_double(y_rms), ctypes.c_double(tau), ctypes.c_int32(batch), ctypes.byref(eo),
+                           _ptr(out), ctypes.byref(n)))
+    del keep
+    return eo.value, out[:n.value]
+
+
+def pc_split_directions(shape, cells, radius: int, impulse: np.ndarray, cell: int):
+    """Section 2.7's subdivision directions of leaf `cell`, best first."""
+    b = _box(shape)
+    g, keep = _grid(cells)
+    imp = np.ascontiguousarray(impulse, dtype=np.float64)
+    dirs = np.zeros(3, dtype=np.int32)
+    n = ctypes.c_int32()
+    _check(lib().pc_split_directions(ctypes.byref(b), ctypes.byref(g), ctypes.c_int32(radius), _ptr(imp),
+                                     ctypes.c_int32(cell), _ptr(dirs), ctypes.byref(n)))
+    del keep
+    return [int(v) for v in dirs[:n.value]]
+
+
+def pc_split_is_admissible(shape, cells, cell: int, axis: int) -> bool:
+    """Whether halving leaf `cell` along `axis` keeps facet pieces at sample points."""
+    b = _box(shape)
+    g, keep = _grid(cells)
+    ok = ctypes.c_int32()
+    _check(lib().pc_split_is_admissible(ctypes.byref(b), ctypes.byref(g), ctypes.c_int32(cell), ctypes.c_int32(axis),
+                                        ctypes.byref(ok)))
+    del keep
+    return bool(ok.value)
+
+
 class Context:
     def __init__(self, device: int = 0):
         h = _VP()
         _check(lib().pc_context_create(ctypes.c_int32(device), ctypes.byref(h)))
         self.handle = h
+
+    def noalloc_check(self, stream=None):
+        """pc_noalloc_check: status of the last allocation-free apply on this device."""
+        _check(lib().pc_noalloc_check(self.handle, _VP(_stream_ptr(stream))), self.handle)
 
     def close(self):
         if self.handle:
@@ -248,7 +302,8 @@ class Operator:
     """A built product-convolution operator (pc_build_spectra)."""
 
     def __init__(self, ctx: Context, shape, cells, radius: int, impulse: np.ndarray, precision: str = "fp32",
-                 weights: Optional[np.ndarray] = None, fft_size: int = 0, tile: int = 0, ctas_per_sm: int = 0):
+                 weights: Optional[np.ndarray] = None, fft_size: int = 0, tile: int = 0, ctas_per_sm: int = 0,
+                 wait_limit_us: int = 0, window_split: int = 0, autotune: bool = False):
         self.ctx = ctx
         self.shape = tuple(int(s) for s in shape)
         self.N = int(np.prod(self.shape))
@@ -259,10 +314,12 @@ class Operator:
         wts = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
         tune = pc_tuning()
         tune.fft_size, tune.tile, tune.ctas_per_sm = fft_size, tile, ctas_per_sm
+        tune.wait_limit_us, tune.window_split = wait_limit_us, window_split
         h = _VP()
+        # autotune: a NULL pc_tuning asks the library to time candidate launch shapes
         _check(lib().pc_build_spectra(ctx.handle, ctypes.byref(b), ctypes.byref(g), ctypes.c_int32(radius),
-                                      _ptr(imp), _ptr(wts), PRECISIONS[precision], ctypes.byref(tune),
-                                      ctypes.byref(h)), ctx.handle)
+                                      _ptr(imp), _ptr(wts), PRECISIONS[precision],
+                                      None if autotune else ctypes.byref(tune), ctypes.byref(h)), ctx.handle)
         del keep
         self.handle = h
 
@@ -552,7 +609,8 @@ def pc_autotune(ctx: Context, shape, cells, radius: int, impulse: np.ndarray, pr
                              _ptr(wts), PRECISIONS[precision], ctypes.c_int32(nrhs), ctypes.byref(best),
                              ctypes.byref(ms)), ctx.handle)
     del keep
-    return {"fft_size": best.fft_size, "tile": best.tile, "ctas_per_sm": best.ctas_per_sm}, ms.value
+    return {"fft_size": best.fft_size, "tile": best.tile, "ctas_per_sm": best.ctas_per_sm,
+            "window_split": best.window_split}, ms.value
 
 
 class Server:

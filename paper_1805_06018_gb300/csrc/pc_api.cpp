@@ -42,8 +42,8 @@ using pc::upload;
 
 namespace {
 
-// W_P^j = exp(-2 pi i j / P), j < P, from long-double cos/sin of the
-// first-octant-reduced angle.
+// W_P^j = exp(-2 pi i j / P), j < P, from long-double cos/sin of the full
+// angle 2 pi j / P, rounded once to double; exact values on the axes.
 std::vector<double> twiddles64(int P) {
     std::vector<double> tw(2 * size_t(P));
     const long double pi = 3.141592653589793238462643383279502884L;
@@ -204,9 +204,9 @@ pc_status pc_extend_impulse(const pc_box *box, const pc_grid *grid, int32_t radi
     return PC_OK;
 }
 
-pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *grid, int32_t radius,
-                           const double *impulse, const double *weights, pc_precision prec,
-                           const pc_tuning *tune, pc_operator **out) {
+static pc_status build_operator(pc_context *ctx, const pc_box *box, const pc_grid *grid, int32_t radius,
+                                const double *impulse, const double *weights, pc_precision prec,
+                                const pc_tuning *tune, pc_operator **out) {
     const auto t0 = std::chrono::steady_clock::now();
     if (!ctx) return fail(nullptr, PC_ERR_ARG, "ctx is null");
     if (!out || !impulse) return fail(ctx, PC_ERR_ARG, "null impulse or output handle");
@@ -239,12 +239,15 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     const int cap = three ? (prec == PC_BF16X3 ? pc::kTc3dMaxTile : P) : (2 * P) / 3;
     pc::WindowSplit split;
     int T = 0;
+    const int forced_split = tune && tune->window_split > 0 ? tune->window_split : 0;
+    if (forced_split > 8) return fail(ctx, PC_ERR_ARG, "window_split must be in [1, 8]");
     {
         double best = 1e300;
         for (int nsub = 1; nsub <= 8; ++nsub) {
+            if (forced_split && nsub != forced_split) continue;
             const int ws = (Wfull + nsub - 1) / nsub;
             const int t = std::min(P - ws + 1, cap);
-            if (t < 1 || (nsub == 1 && t < 16 && Wfull > 16)) continue;
+            if (t < 1 || (!forced_split && nsub == 1 && t < 16 && Wfull > 16)) continue;
             const double cost = double(nsub) * nsub / (double(t) * t);
             if (cost < best * 0.999) {
                 best = cost;
@@ -309,6 +312,8 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     op->n_tiles = int(sch.tiles.size());
     op->n_colors = int(sch.color_start.size()) - 1;
     op->ctas = ctx->num_sms * ctas_per_sm;
+    op->ctas_per_sm = ctas_per_sm;
+    op->wait_ns = tune && tune->wait_limit_us > 0 ? int64_t(tune->wait_limit_us) * 1000 : 0;
     op->color_start_h = sch.color_start;
     op->tiles_h = sch.tiles;
     op->dep_start_h = sch.dep_start;
@@ -501,6 +506,13 @@ pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *gr
     return PC_OK;
 }
 
+pc_status pc_build_spectra(pc_context *ctx, const pc_box *box, const pc_grid *grid, int32_t radius,
+                           const double *impulse, const double *weights, pc_precision prec,
+                           const pc_tuning *tune, pc_operator **out) {
+    if (tune) return build_operator(ctx, box, grid, radius, impulse, weights, prec, tune, out);
+    return pc::autotune_build(ctx, box, grid, radius, impulse, weights, prec, out);
+}
+
 pc_status pc_operator_info_get(const pc_operator *op, pc_operator_info *info) {
     if (!op || !info) return fail(nullptr, PC_ERR_ARG, "null operator or info");
     std::memset(info, 0, sizeof(*info));
@@ -516,6 +528,11 @@ pc_status pc_operator_info_get(const pc_operator *op, pc_operator_info *info) {
     info->spectra_bytes = int64_t(op->spec_bytes);
     info->device_bytes = int64_t(op->device_bytes);
     info->build_seconds = op->build_seconds;
+    info->window_split = op->split.nsub;
+    info->ctas_per_sm = op->ctas_per_sm;
+    info->autotuned = op->autotuned ? 1 : 0;
+    info->tuned_candidates = op->tuned_candidates;
+    info->tuned_ms = op->tuned_ms;
     return PC_OK;
 }
 
@@ -705,6 +722,7 @@ static pc_status apply_batched(pc_operator *op, int32_t nrhs, const void *x, int
     p.spec_stride = op->spec_stride;
     p.w = op->d_w;
     p.tw = op->d_tw;
+    p.wait_ns = op->wait_ns;
     p.total_items = int64_t(op->n_tiles) * npairs;
     if (!op->ev_begin) {
         cudaError_t e = cudaEventCreate(&op->ev_begin);
@@ -850,6 +868,7 @@ pc_status apply_host_segmented(pc_operator *op, int32_t nrhs, const void *x, int
         p.spec_stride = op->spec_stride;
         p.w = op->d_w;
         p.tw = op->d_tw;
+        p.wait_ns = op->wait_ns;
         p.total_items = int64_t(op->n_tiles) * np;
         sg.item_begin = items;
         sg.ready = op->d_host_ready + i;
@@ -894,6 +913,11 @@ pc_status apply_host_segmented(pc_operator *op, int32_t nrhs, const void *x, int
     // mark each segment ready once its copy in has completed, and copy each
     // segment out once the kernel has finished it
     if ((e = cudaEventSynchronize(ev[6])) != cudaSuccess) return cuda_fail(ctx, e, "waiting for earlier work");
+    // Failure-path tests set PC_TEST_WITHHOLD_READY=1: every segment after the
+    // first is then never marked ready, so the kernel's bounded wait for it
+    // runs out and the call must come back with PC_ERR_TIMEOUT.
+    const char *withhold_env = std::getenv("PC_TEST_WITHHOLD_READY");
+    const bool withhold = withhold_env && withhold_env[0] == '1';
     volatile uint32_t *hr = op->h_host_ready;
     const auto deadline = std::chrono::steady_clock::now() + std::chrono::seconds(60);
     int32_t next_in = 0, next_out = 0;
@@ -902,7 +926,7 @@ pc_status apply_host_segmented(pc_operator *op, int32_t nrhs, const void *x, int
             const cudaError_t q = cudaEventQuery(op->host_in_ev[size_t(next_in)]);
             if (q == cudaErrorNotReady) break;
             if (q != cudaSuccess) return cuda_fail(ctx, q, "copying a chunk in");
-            hr[next_in] = ep;   // the kernel reads it with a system-scope acquire
+            if (!withhold || next_in == 0) hr[next_in] = ep;   // the kernel reads it with a system-scope acquire
             ++next_in;
         }
         bool progressed = false;
@@ -918,8 +942,22 @@ pc_status apply_host_segmented(pc_operator *op, int32_t nrhs, const void *x, int
         if (progressed || (polls & 1023) != 1023) continue;
         const cudaError_t q = cudaStreamQuery(s);
         if (q != cudaSuccess && q != cudaErrorNotReady) return cuda_fail(ctx, q, "the segmented patch kernel");
-        if (q == cudaSuccess && next_out < nch && next_in == nch && hf[next_out] == 0u)
+        if (q == cudaSuccess && next_out < nch && next_in == nch && hf[next_out] == 0u) {
+            // the launch ended early: a bounded device-side wait gave up (status word set)
+            // or the kernel failed; let the copies already queued finish either way
+            int32_t flag = 0;
+            cudaError_t e2 = cudaStreamSynchronize(op->s_d2h);
+            if (e2 == cudaSuccess) e2 = cudaMemcpy(&flag, op->d_ctrl + 2, sizeof(flag), cudaMemcpyDeviceToHost);
+            if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "reading the launch status");
+            if (flag != 0) {
+                if ((e2 = pc::zero_now(op->d_ctrl + 2, sizeof(flag))) != cudaSuccess)
+                    return cuda_fail(ctx, e2, "clearing the launch status");
+                return fail(ctx, PC_ERR_TIMEOUT,
+                            "a device-side wait of the segmented launch ran out (limit " +
+                                std::to_string(op->wait_ns > 0 ? op->wait_ns / 1000 : 2000000) + " us)");
+            }
             return fail(ctx, PC_ERR_CUDA, "the patch kernel ended without finishing a segment");
+        }
         if (std::chrono::steady_clock::now() > deadline)
             return fail(ctx, PC_ERR_TIMEOUT, "the host apply did not finish within 60 s");
     }

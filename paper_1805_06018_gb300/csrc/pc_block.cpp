@@ -284,6 +284,7 @@ pc_status pc_block_apply_many(pc_block_plan *bp, int32_t nrhs, const void *const
         p.spec_stride = op->spec_stride;
         p.w = op->d_w;
         p.tw = op->d_tw;
+        p.wait_ns = op->wait_ns;
         p.total_items = int64_t(b.n_tiles) * npairs;
         return p;
     };

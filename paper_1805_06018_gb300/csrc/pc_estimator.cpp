@@ -193,6 +193,7 @@ pc_status pc_estimator_update(pc_estimator *est, pc_operator *op, double *eta, i
         p.spec_stride = op->spec_stride;
         p.w = op->d_w;
         p.tw = op->d_tw;
+        p.wait_ns = op->wait_ns;
         p.total_items = int64_t(nt) * npairs;
         p.store = d_sd;
         p.store_base = arena;

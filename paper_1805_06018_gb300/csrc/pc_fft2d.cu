@@ -45,28 +45,22 @@ constexpr int kThreads2d = 512;
 template <typename T, int P> struct KCfg {
     static constexpr int threads = kThreads2d;
 };
-// acquire load at system scope (a ready word the host writes in mapped memory)
-__device__ __forceinline__ uint32_t ld_acquire_sys_u32(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 
-constexpr long long kSpinLimit = 1ll << 24;   // x >= 64 ns per spin: about a second at least
-constexpr long long kMbarLimit = 1ll << 24;   // try_wait rounds for the spectrum copy
-
-
-// Shared memory: the P x P complex workspace, then the patch's half spectrum
-// ([P/2+1] columns of P values, rows padded to P + 8 values), then an mbarrier.
+// Shared memory: the P x P complex workspace (padded rows, PadLayout), then
+// the patch's half spectrum ([P/2+1] columns of P values, each followed by a
+// copy of its value 0 at index P, so that the mirrored read of phase B,
+// index P - k for k = 0 .. P-1, needs no wrap; rows padded to P + 8 values),
+// then an mbarrier.
 template <typename T, int P> struct Smem2d {
     using C = typename Cx<T>::type;
+    static constexpr int PITCH = PadLayout<P>::pitch;
     static constexpr int SPLD = P + 8;
     // phase C reuses the spectrum region as one FP32 staging row per line:
     // re part [0, P+4), im part [P+12, 2P+16); the stride 2P+24 is 24 banks
     // mod 32, so the four lines of a warp write disjoint banks
     static constexpr int STAGE = 2 * P + 24;
     static constexpr int IMOFF = P + 12;
-    static constexpr size_t ws = size_t(P) * P * sizeof(C);
+    static constexpr size_t ws = size_t(P) * PITCH * sizeof(C);
     static constexpr size_t spec = size_t(P / 2 + 1) * SPLD * sizeof(C);
     static constexpr size_t stage = size_t(KCfg<T, P>::threads / FftShape<P>::R2) * STAGE * sizeof(float);
     static constexpr size_t sp = spec > stage ? spec : stage;
@@ -74,6 +68,14 @@ template <typename T, int P> struct Smem2d {
 };
 
 constexpr int kMaxColorsCached = 63;
+
+// Column that line `line` transforms in phase B (round `rnd`): the two lines
+// of a half-warp take columns c and c + 4, whose padded-workspace walks fall
+// in disjoint banks (PadLayout).  A bijection of [0, LINES) for each round.
+template <int LINES>
+__device__ __forceinline__ int phase_b_col(int line, int rnd) {
+    return rnd * LINES + (line & ~7) + ((line >> 1) & 3) + 4 * (line & 1);
+}
 
 // colour-major order: item -> (tile index, right-hand-side pair).  `cs` holds
 // the colour offsets (shared-memory copy when there are few colours).
@@ -177,10 +179,13 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
     __shared__ int64_t s_runbase;
     __shared__ __align__(16) Segment s_seg;          // the current item's request
     __shared__ int s_cstart_buf[kMaxColorsCached + 1];
+    // set once a wait of this launch has given up: the CTA takes no more items
+    __shared__ int s_stop;
 
     const int nseg = lp.desc ? lp.desc->nseg : 1;
     const int nrun = MULTI && lp.desc ? lp.desc->nrun : 0;
     const int64_t total = lp.desc ? lp.desc->total_items : lp.one.p.total_items;
+    constexpr int PITCH = L::PITCH;
     const int t = threadIdx.x % R2;
     const int line = threadIdx.x / R2;
     const unsigned lmask = FftShape<P>::line_mask();
@@ -229,11 +234,12 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
     if (threadIdx.x == 0) {
         s_next = int64_t(atomicAdd(counter, 1ull));
         s_run = 0;
+        s_stop = 0;
     }
     for (;;) {
         __syncthreads();
         const int64_t gitem = s_next;
-        if (gitem >= total) break;
+        if (gitem >= total || s_stop) break;
         // the request (segment) this item belongs to (a single-apply launch has one)
         int segidx = 0;
         if (lp.desc) {
@@ -265,22 +271,17 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
                 s_seg = lp.one;
             }
             __syncthreads();
-            // a segment whose input is still being copied in: wait (bounded) for its ready word
-            if (threadIdx.x == 0 && s_seg.ready) {
-                long long spins = 0;
-                while (ld_acquire_sys_u32(s_seg.ready) != s_seg.ready_val) {
-                    if (++spins > kSpinLimit) {
-                        atomicExch(lp.status, 1);   // timeout flag; result of this apply is invalid
-                        break;
-                    }
-                    __nanosleep(128);
-                }
-            }
+            // a segment whose input is still being copied in: wait (bounded) for its ready
+            // word; if the wait gives up, the launch's result is invalid and the CTA stops
+            if (threadIdx.x == 0 && s_seg.ready &&
+                !wait_flag_eq<true>(s_seg.ready, s_seg.ready_val, lp.status, wait_limit_ns(s_seg.p.wait_ns), 1, 128))
+                s_stop = 1;
             const int nc = s_seg.p.n_colors;
             s_cstart = nc <= kMaxColorsCached ? s_cstart_buf : s_seg.p.color_start;
             for (int c = threadIdx.x; c <= nc && c <= kMaxColorsCached; c += blockDim.x)
                 s_cstart_buf[c] = s_seg.p.color_start[c];
             __syncthreads();
+            if (s_stop) break;
         }
         const ApplyParams &p = s_seg.p;
         const int64_t item = gitem - s_seg.item_begin;
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
             decode_item(p, s_cstart, item, ti, pair);
         }
         const Tile tile = p.tiles[ti];
-        if (threadIdx.x == 0) mbar_arrive_expect_tx(mbar, uint32_t(H * P * sizeof(C)));
+        if (threadIdx.x == 0) mbar_arrive_expect_tx(mbar, uint32_t(H * (P * sizeof(C) + 16)));
         __syncthreads();   // everyone has read s_next; the spectrum copy is announced
         if (threadIdx.x == NT - 1) s_next = int64_t(atomicAdd(counter, 1ull));
         const int n1 = tile.in_ext[0], n2 = tile.in_ext[1];
@@ -316,18 +317,20 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
         // copies, one per stored column) while phase A runs
         if (threadIdx.x < H) {
             const int col = threadIdx.x;
+            const C *src = spec + int64_t(tile.spec) * p.spec_stride + int64_t(col) * P;
             fence_proxy_async_smem();
-            bulk_g2s(SP + col * L::SPLD, spec + int64_t(tile.spec) * p.spec_stride + int64_t(col) * P,
-                     uint32_t(P * sizeof(C)), mbar);
+            bulk_g2s(SP + col * L::SPLD, src, uint32_t(P * sizeof(C)), mbar);
+            bulk_g2s(SP + col * L::SPLD + P, src, 16u, mbar);   // value 0 again, at index P
         }
 
         // ---------------- phase A: stage w, x0, x1 rows (cp.async), weight, row FFTs
         // rows of one warp sit 2P reals apart (same banks): shift each row's staging
         // by (row & 3) * 8 reals when the three arrays leave room
         if constexpr (!ADJ) {
-            const int shmul = 3 * n2 + 24 <= 2 * P ? 8 : 0;
+            // staging of row i: the first 2 PITCH reals of the workspace row
+            const int shmul = 3 * n2 + 24 <= 2 * PITCH ? 8 : 0;
             for (int i = line; i < n1; i += LINES) {
-                T *row = Sf + i * 2 * P + (i & 3) * shmul;
+                T *row = Sf + i * 2 * PITCH + (i & 3) * shmul;
                 const int64_t xr = int64_t(i0 + i) * p.nx[1] + j0;
                 const T *wr = wt + int64_t(i) * tile.w_ld[0];
 #pragma unroll
@@ -343,7 +346,7 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
             cp_async_wait_all();
             __syncwarp(lmask);
             for (int i = line; i < n1; i += LINES) {
-                const T *row = Sf + i * 2 * P + (i & 3) * shmul;
+                const T *row = Sf + i * 2 * PITCH + (i & 3) * shmul;
                 C a[R1];
 #pragma unroll
                 for (int j = 0; j < R1; ++j) {
@@ -355,10 +358,11 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
                         a[j] = zero;
                     }
                 }
-                RowScratch<P, C> scr{S, i};
+                C *Srow = S + i * PITCH + pad_shift(i);
+                PadScratch<P, C, false> scr(Srow, t);
                 fft_line<P, false>(a, tw, t, scr, lmask);
 #pragma unroll
-                for (int j = 0; j < R1; ++j) S[i * P + ((t + R2 * j) ^ swz(i))] = a[j];
+                for (int j = 0; j < R1; ++j) Srow[t + R2 * j] = a[j];
             }
         } else {
             // adjoint: x over the output box (L1 x L2 at (o0, o1)), zero outside
@@ -366,7 +370,7 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
             for (int i = line; i < L1; i += LINES) {
                 const int gr = o0 + i;
                 if (gr < 0 || gr >= p.nx[0]) continue;
-                T *row = Sf + i * 2 * P;
+                T *row = Sf + i * 2 * PITCH;
                 const int64_t xr = int64_t(gr) * p.nx[1] + o1;
 #pragma unroll
                 for (int j = 0; j < R1; ++j) {
@@ -383,7 +387,7 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
             for (int i = line; i < L1; i += LINES) {
                 const int gr = o0 + i;
                 const bool rin = gr >= 0 && gr < p.nx[0];
-                const T *row = Sf + i * 2 * P;
+                const T *row = Sf + i * 2 * PITCH;
                 C a[R1];
 #pragma unroll
                 for (int j = 0; j < R1; ++j) {
@@ -392,10 +396,11 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
                     a[j] = rin && col < L2 && gc >= 0 && gc < p.nx[1] ? C{row[col], has1 ? row[L2 + col] : T(0)}
                                                                     : zero;
                 }
-                RowScratch<P, C> scr{S, i};
+                C *Srow = S + i * PITCH + pad_shift(i);
+                PadScratch<P, C, false> scr(Srow, t);
                 fft_line<P, false>(a, tw, t, scr, lmask);
 #pragma unroll
-                for (int j = 0; j < R1; ++j) S[i * P + ((t + R2 * j) ^ swz(i))] = a[j];
+                for (int j = 0; j < R1; ++j) Srow[t + R2 * j] = a[j];
             }
         }
         // the previous item's bulk reductions have landed: it can report done
@@ -412,42 +417,47 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
             prefetch_item<T, ADJ>(p, s_cstart, s_next - s_seg.item_begin);
 
         // ---------------- phase B: column FFT, spectral product, inverse column FFT
-        if (!mbar_wait_bounded(mbar, phase, kMbarLimit)) {
-            atomicExch(lp.status, 2);   // copy did not land; wait once more, then carry on
-            mbar_wait_bounded(mbar, phase, kMbarLimit);
+        // If the spectrum copy does not land within the limit, the item is
+        // abandoned: the warp waits once more (the copy writes into this CTA's
+        // shared memory) and skips phase B; the CTA then stops before adding.
+        const int64_t lim = wait_limit_ns(p.wait_ns);
+        bool bad = !mbar_wait_ns(mbar, phase, lim);
+        if (bad) {
+            atomicCAS(lp.status, 0, 2);
+            (void)mbar_wait_ns(mbar, phase, lim);
         }
+        bad = __any_sync(0xffffffffu, bad);
         phase ^= 1u;
-        for (int col = line; col < P; col += LINES) {
+        for (int rnd = 0; rnd < P / LINES && !bad; ++rnd) {
+            const int col = phase_b_col<LINES>(line, rnd);
             C a[R1];
-            // rows in: n1 (forward) or L1 (adjoint); rows kept: the other
+            // rows in: n1 (forward) or L1 (adjoint); rows kept: the other.
+            // Row t + R2 j of the column: (t + R2 j) * PITCH + col + pad_shift(t)
             const int rows_in = ADJ ? L1 : n1, rows_out = ADJ ? n1 : L1;
+            C *Scol = S + t * PITCH + pad_shift(t) + col;
 #pragma unroll
-            for (int j = 0; j < R1; ++j) {
-                const int row = t + R2 * j;
-                a[j] = row < rows_in ? S[row * P + (col ^ swz(row))] : zero;
-            }
-            ColScratch<P, C> scr{S, col};
+            for (int j = 0; j < R1; ++j) a[j] = t + R2 * j < rows_in ? Scol[j * R2 * PITCH] : zero;
+            PadScratch<P, C, true> scr(S + col, t);
             fft_line<P, false>(a, tw, t, scr, lmask);
             // Hermitian half spectrum stored as [k2 <= P/2][k1]; the adjoint
-            // multiplies by the conjugate
+            // multiplies by the conjugate.  Mirrored columns read index
+            // P - k1 (index P holds value 0 again).
             if (col <= P / 2) {
-                const C *sc = SP + col * L::SPLD;
+                const C *sc = SP + col * L::SPLD + t;
 #pragma unroll
-                for (int j = 0; j < R1; ++j) a[j] = ADJ ? cmulc(a[j], sc[t + R2 * j]) : cmul(a[j], sc[t + R2 * j]);
+                for (int j = 0; j < R1; ++j) a[j] = ADJ ? cmulc(a[j], sc[R2 * j]) : cmul(a[j], sc[R2 * j]);
             } else {
-                const C *sc = SP + (P - col) * L::SPLD;
+                const C *sc = SP + (P - col) * L::SPLD + (P - t);
 #pragma unroll
                 for (int j = 0; j < R1; ++j) {
-                    const C v = sc[(P - (t + R2 * j)) & (P - 1)];
+                    const C v = sc[-R2 * j];
                     a[j] = ADJ ? cmul(a[j], v) : cmulc(a[j], v);
                 }
             }
             fft_line<P, true>(a, tw, t, scr, lmask);
 #pragma unroll
-            for (int j = 0; j < R1; ++j) {
-                const int row = t + R2 * j;
-                if (row < rows_out) S[row * P + (col ^ swz(row))] = a[j];
-            }
+            for (int j = 0; j < R1; ++j)
+                if (t + R2 * j < rows_out) Scol[j * R2 * PITCH] = a[j];
         }
 
         // ---------------- ordered overlap-add: wait for lower colours
@@ -455,20 +465,16 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
         // after the polls also ends phase B
         {
             const int d0 = p.dep_start[ti], nd = p.dep_start[ti + 1] - d0;
-            for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+            for (int d = threadIdx.x; d < nd && !bad; d += blockDim.x) {
                 const uint32_t *f = p.done + int64_t(p.dep[d0 + d]) * p.done_ld + pair;
-                long long spins = 0;
-                while (ld_acquire_u32(f) != p.epoch) {
-                    if (++spins > kSpinLimit) {
-                        atomicExch(lp.status, 1);   // timeout flag; result of this apply is invalid
-                        break;
-                    }
-                    __nanosleep(64);
-                }
+                // timeout (or another wait of the launch gave up): result invalid
+                bad = !wait_flag_eq<false>(f, p.epoch, lp.status, lim, 1, 64);
                 __threadfence();
             }
         }
-        __syncthreads();
+        // an abandoned item adds nothing and is not reported done; the CTA
+        // stops (its earlier, finished item is still published at exit)
+        if (__syncthreads_or(bad)) break;
 
         // ---------------- phase C: inverse row FFTs and overlap-add (fire-and-forget
         // reductions: no two tiles that overlap add at the same time, so each pixel
@@ -481,9 +487,10 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
                 const int oy = o0 + n;
                 if (oy < 0 || oy >= p.n[0]) continue;
                 C a[R1];
+                C *Srow = S + n * PITCH + pad_shift(n);
 #pragma unroll
-                for (int j = 0; j < R1; ++j) a[j] = S[n * P + ((t + R2 * j) ^ swz(n))];
-                RowScratch<P, C> scr{S, n};
+                for (int j = 0; j < R1; ++j) a[j] = Srow[t + R2 * j];
+                PadScratch<P, C, false> scr(Srow, t);
                 fft_line<P, true>(a, tw, t, scr, lmask);
                 add_row<T, P>(a, t, lmask, reinterpret_cast<float *>(SP) + line * L::STAGE,
                               y0 + int64_t(oy) * p.n[1], y1 + int64_t(oy) * p.n[1], has1, o1, L2, p.n[1]);
@@ -497,9 +504,10 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
 #pragma unroll
                 for (int j = 0; j < R1; ++j) wv[j] = t + R2 * j < n2 ? __ldg(wr + t + R2 * j) : T(0);
                 C a[R1];
+                C *Srow = S + n * PITCH + pad_shift(n);
 #pragma unroll
-                for (int j = 0; j < R1; ++j) a[j] = S[n * P + ((t + R2 * j) ^ swz(n))];
-                RowScratch<P, C> scr{S, n};
+                for (int j = 0; j < R1; ++j) a[j] = Srow[t + R2 * j];
+                PadScratch<P, C, false> scr(Srow, t);
                 fft_line<P, true>(a, tw, t, scr, lmask);
                 if (p.store) {
                     const StoreDesc sd = p.store[ti];
@@ -530,6 +538,7 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
         __syncthreads();
         pend_flag_any = true;
         if (threadIdx.x == 0) {
+            if (ld_volatile_s32(lp.status) != 0) s_stop = 1;
             pend_flag = p.done + int64_t(ti) * p.done_ld + pair;
             pend_epoch = p.epoch;
             pend_seg_done = lp.seg_done ? lp.seg_done + cur_seg : nullptr;

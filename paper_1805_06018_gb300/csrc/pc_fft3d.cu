@@ -30,7 +30,6 @@ namespace pc {
 
 constexpr int kThreads3d = 256;
 constexpr int kP3 = 64;
-constexpr long long kSpinLimit3 = 1ll << 24;
 constexpr int kSmem3 = kP3 * kP3 * int(sizeof(float2));
 
 // One work item: tile `ti` of the schedule and right-hand-side pair `pair`
@@ -201,22 +200,19 @@ __device__ __forceinline__ void phase2_3d(const ApplyParams &p, const Item3 &it,
 // ordered overlap-add: wait (bounded) until every overlapping tile of a lower
 // colour has published its contribution for this pair.  A tile's flags for
 // the pair are `ng` consecutive words (one per output-plane group) starting
-// at done[tile * done_ld + pair * ng].
-__device__ __forceinline__ void wait_deps_3d(const ApplyParams &p, const Item3 &it, int ng) {
+// at done[tile * done_ld + pair * ng].  Returns false (for the whole CTA) if
+// a wait gave up - a timeout, or another wait of the launch gave up first
+// (the status word p.ctrl[2] is then non-zero): the item must be abandoned.
+__device__ __forceinline__ bool wait_deps_3d(const ApplyParams &p, const Item3 &it, int ng) {
     const int d0 = p.dep_start[it.ti], nd = p.dep_start[it.ti + 1] - d0;
-    for (int d = threadIdx.x; d < nd * ng; d += blockDim.x) {
+    const int64_t lim = wait_limit_ns(p.wait_ns);
+    bool bad = false;
+    for (int d = threadIdx.x; d < nd * ng && !bad; d += blockDim.x) {
         const uint32_t *f = p.done + int64_t(p.dep[d0 + d / ng]) * p.done_ld + int64_t(it.pair) * ng + d % ng;
-        long long spins = 0;
-        while (ld_acquire_u32(f) != p.epoch) {
-            if (++spins > kSpinLimit3) {
-                atomicExch(p.ctrl + 2, 1);
-                break;
-            }
-            __nanosleep(64);
-        }
+        bad = !wait_flag_eq<false>(f, p.epoch, p.ctrl + 2, lim, 1, 64);
         __threadfence();
     }
-    __syncthreads();
+    return !__syncthreads_or(bad);
 }
 
 // phase 3: inverse 2D FFT of the output planes o0 in [ob, oe) (of the L0
@@ -309,14 +305,18 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_kernel(const ApplyParams 
     const Lines3 L(static_cast<const float2 *>(p.tw));
     float2 *G = scratch + int64_t(blockIdx.x) * kP3 * kP3 * kP3;
     for (;;) {
-        if (threadIdx.x == 0) s_item = int64_t(atomicAdd(reinterpret_cast<unsigned long long *>(p.ctrl), 1ull));
+        // a launch whose waits have given up (status word set) takes no more items
+        if (threadIdx.x == 0)
+            s_item = ld_volatile_s32(p.ctrl + 2) != 0
+                         ? p.total_items
+                         : int64_t(atomicAdd(reinterpret_cast<unsigned long long *>(p.ctrl), 1ull));
         __syncthreads();
         const int64_t item = s_item;
         if (item >= p.total_items) break;
         const Item3 it = decode_item3(p, item);
         phase1_3d<ADJ>(p, it, G, S, L);
         phase2_3d<ADJ>(p, it, G, S, L);
-        wait_deps_3d(p, it, 1);
+        if (!wait_deps_3d(p, it, 1)) break;
         // planes kept: the L0 of the output box, or the n0 of the input box (adjoint)
         const int m0 = ADJ ? it.tile.in_ext[0] : it.tile.in_ext[0] + it.tile.kext[0] - 1;
         phase3_3d<ADJ>(p, it, G, S, L, 0, m0, p.done + int64_t(it.ti) * p.done_ld + it.pair);
@@ -351,14 +351,16 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase3_kernel(const Apply
     const Lines3 L(static_cast<const float2 *>(p.tw));
     for (;;) {
         if (threadIdx.x == 0)
-            s_piece = c0 * NG + int64_t(atomicAdd(reinterpret_cast<unsigned long long *>(p.ctrl), 1ull));
+            s_piece = ld_volatile_s32(p.ctrl + 2) != 0
+                          ? c1 * NG
+                          : c0 * NG + int64_t(atomicAdd(reinterpret_cast<unsigned long long *>(p.ctrl), 1ull));
         __syncthreads();
         const int64_t piece = s_piece;
         if (piece >= c1 * NG) break;
         const int64_t item = piece / NG;
         const int g = int(piece % NG);
         const Item3 it = decode_item3(p, item);
-        wait_deps_3d(p, it, NG);
+        if (!wait_deps_3d(p, it, NG)) break;
         const int L0 = it.tile.in_ext[0] + it.tile.kext[0] - 1;
         phase3_3d<false>(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L, (L0 * g) / NG, (L0 * (g + 1)) / NG,
                   p.done + int64_t(it.ti) * p.done_ld + int64_t(it.pair) * NG + g);

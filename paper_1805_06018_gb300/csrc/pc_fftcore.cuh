@@ -166,9 +166,11 @@ template <int P> struct FftShape {
 };
 
 // One line FFT.  `a` holds x[t + R2 j]; `tw` holds W_P^{t m} for m < R1;
-// Scratch provides ld(pos)/st(pos, v) for positions 0..P-1 private to the
-// line; `mask` names the line's lanes (lines of one warp may diverge).
-// On return a[j'] = X[t + R2 j'].
+// Scratch holds P slots private to the line: st_m(m, t, v) stores register m
+// of thread t at slot m R2 + (t ^ (m mod R2)) and ld_e(e, t2, t) loads slot
+// (t + R2 e) R2 + (t2 ^ t), the value thread t2 stored as register t + R2 e
+// (the transpose of step 3).  `mask` names the line's lanes (lines of one
+// warp may diverge).  On return a[j'] = X[t + R2 j'].
 template <int P, bool INV, typename C, typename Scratch>
 __device__ __forceinline__ void fft_line(C *a, const C *tw, int t, Scratch &scr, unsigned mask) {
     constexpr int R1 = FftShape<P>::R1, R2 = FftShape<P>::R2, E = R1 / R2;
@@ -178,12 +180,12 @@ __device__ __forceinline__ void fft_line(C *a, const C *tw, int t, Scratch &scr,
     // the scratch may be the storage the line just read its input from
     __syncwarp(mask);
 #pragma unroll
-    for (int m = 0; m < R1; ++m) scr.st(m * R2 + (t ^ (m & (R2 - 1))), a[m]);
+    for (int m = 0; m < R1; ++m) scr.st_m(m, t, a[m]);
     __syncwarp(mask);
 #pragma unroll
     for (int e = 0; e < E; ++e)
 #pragma unroll
-        for (int t2 = 0; t2 < R2; ++t2) a[e * R2 + t2] = scr.ld((t + R2 * e) * R2 + (t2 ^ t));
+        for (int t2 = 0; t2 < R2; ++t2) a[e * R2 + t2] = scr.ld_e(e, t2, t);
     __syncwarp(mask);
     C b[R1];
 #pragma unroll
@@ -199,16 +201,60 @@ __device__ __forceinline__ void fft_line(C *a, const C *tw, int t, Scratch &scr,
 // Line scratch inside a P x P shared workspace laid out row * P + (col ^ swz(row)):
 // a row, or a column (positions are then row indices).
 template <int P, typename C> struct RowScratch {
+    static constexpr int R2 = FftShape<P>::R2;
     C *S;
     int row;
     __device__ __forceinline__ C ld(int s) const { return S[row * P + (s ^ swz(row))]; }
     __device__ __forceinline__ void st(int s, C v) const { S[row * P + (s ^ swz(row))] = v; }
+    __device__ __forceinline__ void st_m(int m, int t, C v) const { st(m * R2 + (t ^ (m & (R2 - 1))), v); }
+    __device__ __forceinline__ C ld_e(int e, int t2, int t) const { return ld((t + R2 * e) * R2 + (t2 ^ t)); }
 };
 template <int P, typename C> struct ColScratch {
+    static constexpr int R2 = FftShape<P>::R2;
     C *S;
     int col;
     __device__ __forceinline__ C ld(int s) const { return S[s * P + (col ^ swz(s))]; }
     __device__ __forceinline__ void st(int s, C v) const { S[s * P + (col ^ swz(s))] = v; }
+    __device__ __forceinline__ void st_m(int m, int t, C v) const { st(m * R2 + (t ^ (m & (R2 - 1))), v); }
+    __device__ __forceinline__ C ld_e(int e, int t2, int t) const { return ld((t + R2 * e) * R2 + (t2 ^ t)); }
+};
+
+// Padded workspace of the 2D patch kernel: element (r, c) of a P x P complex
+// field sits at r * pitch + c + pad_shift(r), pitch = P + 8.  A pitch of 8
+// mod 16 eight-byte units puts consecutive rows in opposite halves of the
+// banks, and the shift (r mod 8) / 2 spreads the 8 rows r = 8u + x (x < 8)
+// that a column walk or a column transpose touches at once over distinct
+// banks.  Unlike a swizzle, every address is a per-thread base plus a
+// compile-time offset.
+template <int P> struct PadLayout {
+    static constexpr int pitch = P + 8;
+};
+__device__ __forceinline__ int pad_shift(int r) { return (r & 7) >> 1; }
+
+// Line scratch in the padded workspace, for R2 = 8 threads per line: slot
+// s = 8 u + x lives at base + u * A + x * B (+ pad_shift(x) for a column,
+// whose slots are rows).  q[c] is the address of slot x = t ^ c of group 0, so
+// the transpose's stores and loads are q[c] plus compile-time offsets.
+//   row r:     base = &ws[r * pitch + pad_shift(r)], A = 8,         B = 1
+//   column c:  base = &ws[c],                        A = 8 * pitch, B = pitch
+template <int P, typename C, bool COL> struct PadScratch {
+    static constexpr int R2 = FftShape<P>::R2;
+    static_assert(R2 == 8, "padded line scratch assumes 8 threads per line");
+    static constexpr int A = COL ? 8 * PadLayout<P>::pitch : 8;
+    static constexpr int B = COL ? PadLayout<P>::pitch : 1;
+    C *q[8];
+    int tA;
+    __device__ __forceinline__ PadScratch(C *base, int t) : tA(t * A) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int x = t ^ c;
+            q[c] = base + x * B + (COL ? (x >> 1) : 0);
+        }
+    }
+    // slot m * 8 + (t ^ (m mod 8)): group m, x = t ^ (m mod 8)
+    __device__ __forceinline__ void st_m(int m, int, C v) const { q[m & 7][m * A] = v; }
+    // slot (t + 8 e) * 8 + (t2 ^ t): group t + 8 e, x = t ^ t2
+    __device__ __forceinline__ C ld_e(int e, int t2, int) const { return q[t2][tA + 8 * e * A]; }
 };
 
 }  // namespace pc

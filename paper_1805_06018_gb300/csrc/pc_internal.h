@@ -131,6 +131,9 @@ struct ApplyParams {
     // input box is stored unweighted (incremental estimator), not added to y
     const StoreDesc *store;
     void *store_base;
+    // limit of each device-side wait of the apply, ns (0: 2 s); once one wait
+    // gives up, the others of the launch give up at once
+    int64_t wait_ns;
 };
 
 // One request on one operator inside a launch.
@@ -256,7 +259,11 @@ struct pc_operator {
     cudaStream_t last_stream = nullptr;
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;   // around the fused kernel of the last apply
     bool timed = false;
-    int ctas = 0;
+    int64_t wait_ns = 0;         // limit of each device-side wait of an apply (0: the kernels' default, 2 s)
+    int ctas = 0, ctas_per_sm = 0;
+    bool autotuned = false;      // launch shape chosen by timing candidates (pc_build_spectra, tune NULL)
+    int tuned_candidates = 0;
+    double tuned_ms = 0;
     int64_t launches_last = 0;
     size_t device_bytes = 0;
     double build_seconds = 0;
@@ -386,6 +393,9 @@ cudaError_t launch_entries(pc_precision prec, int64_t n, const int64_t *rows, co
                            const EntryData &e, const void *w, cudaStream_t s);
 // grow the on-demand device buffers of an apply of nrhs vectors (pc_api.cpp)
 pc_status prepare_batch(pc_operator *op, int32_t nrhs);
+// autotuner (pc_autotune.cpp): pc_build_spectra with a NULL pc_tuning
+pc_status autotune_build(pc_context *ctx, const pc_box *box, const pc_grid *grid, int32_t radius,
+                         const double *impulse, const double *weights, pc_precision prec, pc_operator **out);
 // error estimator (pc_estimate.cu): out[c] = sum over cell c and q columns of (yt - y)^2, FP64
 // incremental estimator (pc_incremental.cu): copy kept correlation blocks
 // (copies[i] = {src, dst, len} in elements) and form

@@ -23,25 +23,6 @@ constexpr int64_t kNoAllocFlagWords = kNoAllocWords - kNoAllocCtrlWords;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
 
-// Device address of g_noalloc_scratch, looked up once per device.  In host
-// code the symbol itself is only a host-side handle; kernels must be given the
-// address cudaGetSymbolAddress returns with the device current.
-std::mutex g_mu;
-uint32_t *g_addr[64] = {};
-
-cudaError_t scratch_address(int device, uint32_t **out) {
-    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[device]) {
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[device] = static_cast<uint32_t *>(ptr);
-    }
-    *out = g_addr[device];
-    return cudaSuccess;
-}
-
 // y = 0 for the batch, flags of this call cleared, work counter reset.
 template <typename T>
 __global__ void noalloc_prepare(T *y, int64_t ldy, int32_t nrhs, int64_t N, uint32_t *scratch, int64_t nflags) {
@@ -60,7 +41,73 @@ __global__ void noalloc_prepare(T *y, int64_t ldy, int32_t nrhs, int64_t N, uint
     }
 }
 
+// Device address of g_noalloc_scratch, looked up once per device.  In host
+// code the symbol itself is only a host-side handle; kernels must be given the
+// address cudaGetSymbolAddress returns with the device current.  The same
+// set-up loads this path's kernels (under lazy module loading a kernel's
+// module is otherwise loaded, and its device memory taken, at its first
+// launch), so that later calls take no device memory at all.
+std::mutex g_mu;
+uint32_t *g_addr[64] = {};
+
+cudaError_t scratch_address(int device, uint32_t **out) {
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, noalloc_prepare<float>)) != cudaSuccess ||
+            (e = cudaFuncGetAttributes(&fa, noalloc_prepare<double>)) != cudaSuccess)
+            return e;
+        g_addr[device] = static_cast<uint32_t *>(ptr);
+    }
+    *out = g_addr[device];
+    return cudaSuccess;
+}
+
+// Select `device` for the lifetime of the guard (restored afterwards).
+struct DeviceSel {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceSel(int device) {
+        if (cudaGetDevice(&prev) != cudaSuccess) return;
+        ok = prev == device || cudaSetDevice(device) == cudaSuccess;
+    }
+    ~DeviceSel() {
+        if (ok && prev >= 0) cudaSetDevice(prev);
+    }
+};
+
 }  // namespace
+
+extern "C" pc_status pc_noalloc_check(pc_context *ctx, pc_stream stream) {
+    if (!ctx) return PC_ERR_ARG;
+    DeviceSel sel(ctx->device);
+    if (!sel.ok) {
+        ctx->last_error = "cannot select the context's device";
+        return PC_ERR_CUDA;
+    }
+    uint32_t *scratch = nullptr;
+    cudaError_t e = scratch_address(ctx->device, &scratch);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    uint32_t flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, scratch + 2, sizeof(flag), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && flag != 0) {
+        e = cudaMemset(scratch + 2, 0, sizeof(flag));
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    if (e != cudaSuccess) {
+        ctx->last_error = std::string("reading the allocation-free apply's status: ") + cudaGetErrorString(e);
+        return PC_ERR_CUDA;
+    }
+    if (flag != 0) {
+        ctx->last_error = "a device-side wait of the last allocation-free apply ran out";
+        return PC_ERR_TIMEOUT;
+    }
+    return PC_OK;
+}
 
 extern "C" pc_status pc_apply_batched_noalloc(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y,
                                               int64_t ldy, pc_stream stream) {
@@ -72,6 +119,12 @@ extern "C" pc_status pc_apply_batched_noalloc(pc_operator *op, int32_t nrhs, con
     };
     if (nrhs < 0) return fail(PC_ERR_ARG, "nrhs < 0");
     if (op->d != 2) return fail(PC_ERR_UNSUPPORTED, "the allocation-free apply covers 2D operators");
+    DeviceSel sel(ctx->device);
+    if (!sel.ok) return fail(PC_ERR_CUDA, "cannot select the context's device");
+    // set-up first, so that a call with nrhs == 0 serves as the warm-up call
+    uint32_t *scratch = nullptr;
+    cudaError_t e = scratch_address(ctx->device, &scratch);
+    if (e != cudaSuccess) return fail(PC_ERR_CUDA, std::string("setting up the static scratch: ") + cudaGetErrorString(e));
     if (nrhs == 0) return PC_OK;
     if (!x || !y) return fail(PC_ERR_ARG, "null x or y");
     if (ldx < op->N || ldy < op->N) return fail(PC_ERR_ARG, "ldx and ldy must be >= N");
@@ -86,16 +139,8 @@ extern "C" pc_status pc_apply_batched_noalloc(pc_operator *op, int32_t nrhs, con
         return fail(PC_ERR_ARG, "tiles x ceil(nrhs/2) = " + std::to_string(nflags) +
                                     " exceeds the static scratch of pc_apply_batched_noalloc (" +
                                     std::to_string(kNoAllocFlagWords) + " flags); split the batch");
-    int prev = -1;
-    if (cudaGetDevice(&prev) != cudaSuccess) return fail(PC_ERR_CUDA, "cudaGetDevice failed");
-    if (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess)
-        return fail(PC_ERR_CUDA, "cannot select the context's device");
     pc_status st = PC_OK;
-    uint32_t *scratch = nullptr;
-    cudaError_t e = scratch_address(ctx->device, &scratch);
-    if (e != cudaSuccess) {
-        st = fail(PC_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    } else {
+    {
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         const int64_t total = std::max<int64_t>(nflags, int64_t(nrhs) * op->N);
         const int blocks = int(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4096)));
@@ -132,12 +177,12 @@ extern "C" pc_status pc_apply_batched_noalloc(pc_operator *op, int32_t nrhs, con
             p.spec_stride = op->spec_stride;
             p.w = op->d_w;
             p.tw = op->d_tw;
+            p.wait_ns = op->wait_ns;
             p.total_items = int64_t(op->n_tiles) * npairs;
             const int ctas = int(std::min<int64_t>(op->ctas, p.total_items));
             e = pc::launch_fft2d(p, op->P, op->prec, ctas, s);
         }
         if (e != cudaSuccess) st = fail(PC_ERR_CUDA, std::string("launching the apply: ") + cudaGetErrorString(e));
     }
-    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
     return st;
 }

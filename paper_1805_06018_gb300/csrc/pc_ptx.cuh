@@ -43,6 +43,30 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// Device wall clock in nanoseconds (for waits bounded in time).
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait limit of an apply's device-side waits when the operator sets none: 2 s.
+constexpr int64_t kDefaultWaitNs = 2000000000ll;
+__device__ __forceinline__ int64_t wait_limit_ns(int64_t ns) { return ns > 0 ? ns : kDefaultWaitNs; }
+
+// Wait for phase `parity` of an mbarrier for at most limit_ns: false if it
+// gave up.  Only time bounds it: an asynchronous copy into this CTA's shared
+// memory must land before the CTA reuses the buffer or exits.
+__device__ __forceinline__ bool mbar_wait_ns(uint64_t *bar, uint32_t parity, int64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (int64_t(global_ns() - t0) > limit_ns) return false;
+    }
+}
+
 // Bulk global -> shared copy completing on an mbarrier (16-byte aligned
 // addresses, size a multiple of 16).
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -83,6 +107,44 @@ __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
 // release store at system scope (the host reads the word through mapped memory)
 __device__ __forceinline__ void st_release_sys_u32(uint32_t *p, uint32_t v) {
     asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// acquire load at system scope (a word the host writes in mapped memory)
+__device__ __forceinline__ uint32_t ld_acquire_sys_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int32_t ld_volatile_s32(const int32_t *p) {
+    int32_t v;
+    asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Wait until *f == want (acquire; system scope for a host-written word),
+// for at most limit_ns.  The launch's status word makes the waits sticky:
+// once any wait of the launch has given up (status != 0) every other wait
+// gives up at once, so a failed launch ends within about one limit.  On a
+// timeout the first waiter to give up records `code` in the status word.
+// Returns true if the flag arrived.
+template <bool SYS>
+__device__ __forceinline__ bool wait_flag_eq(const uint32_t *f, uint32_t want, int32_t *status, int64_t limit_ns,
+                                             int32_t code, unsigned sleep_ns) {
+    auto ld = [&]() { return SYS ? ld_acquire_sys_u32(f) : ld_acquire_u32(f); };
+    if (ld() == want) return true;
+    const uint64_t t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+        __nanosleep(sleep_ns);
+        if (ld() == want) return true;
+        if ((it & 7u) == 0u) {
+            if (ld_volatile_s32(status) != 0) return false;
+            if (int64_t(global_ns() - t0) > limit_ns) {
+                atomicCAS(status, 0, code);
+                return false;
+            }
+        }
+    }
 }
 
 }  // namespace pc

@@ -13,12 +13,12 @@
 // drains: requests that arrive while others run are admitted as soon as a
 // slot and memory free up.
 //
-// 3D operators (FP32, or BF16x3 with the tensor-core first axis) do not fit
-// the multi-request 2D kernel: a 3D request at the head of the queue takes a
-// free slot on its own and runs the operator's own apply on that slot's
-// stream.  A 3D operator has at most one request in flight (its ordering
-// flags and scratch volumes are per operator); different operators run
-// concurrently on different slots.  The buffers such an apply grows on demand
+// Operators the multi-request kernel does not cover (3D FP32 or BF16x3, 2D
+// with fft_size 64 or FP64) run each request alone: a request at the head of
+// the queue takes a free slot on its own and runs the operator's own apply
+// on that slot's stream.  Such an operator has at most one request in flight
+// (its ordering flags and scratch volumes are per operator); different
+// operators run concurrently on different slots.  The buffers such an apply grows on demand
 // are grown by the scheduler thread just before the launch (the only thread
 // that touches a served operator), which may synchronise the device once.
 #include <algorithm>
@@ -53,7 +53,7 @@ struct Request {
     int status = PC_OK;
     int hslot = -1;     // host completion flag index
     int launch_requests = 0;
-    bool solo = false;  // 3D: runs alone through the operator's own apply
+    bool solo = false;  // runs alone through the operator's own apply (not a batched 2D operator)
     bool adjoint = false;   // Y = A~* X (Eq. adjoint_random_z)
     std::string error;
 };
@@ -70,7 +70,7 @@ struct LaunchSlot {
     int32_t *d_status = nullptr;
     cudaEvent_t done = nullptr;
     bool busy = false;
-    bool solo = false;                  // running one 3D request
+    bool solo = false;                  // running one request through its operator's own apply
     std::vector<Request *> reqs;
 };
 
@@ -136,7 +136,7 @@ void reap(pc_server *s) {
         const double t = s->now();
         for (Request *r : sl.reqs) {
             // early completion through the mapped flag (batched 2D requests
-            // only: a 3D request has no flag slot and completes with its launch)
+            // only: a solo request has no flag slot and completes with its launch)
             if (r->state != 1 || r->hslot < 0) continue;
             if (reinterpret_cast<volatile uint32_t *>(s->h_flags)[r->hslot] != 0u) {
                 r->state = 2;
@@ -149,7 +149,7 @@ void reap(pc_server *s) {
         }
         const cudaError_t q = cudaEventQuery(sl.done);
         if (q == cudaErrorNotReady) continue;
-        // the launch has ended: anything not flagged failed.  A 3D request
+        // the launch has ended: anything not flagged failed.  A solo request
         // reports through its operator's timeout flag.
         int32_t status = 0;
         int32_t *d_status = sl.solo ? sl.reqs.front()->op->d_ctrl + 2 : sl.d_status;
@@ -186,11 +186,11 @@ void reap(pc_server *s) {
     }
 }
 
-// A 3D request at the head of the queue, alone on slot sl.  Returns false if
+// A solo request at the head of the queue, alone on slot sl.  Returns false if
 // it has to wait (FIFO: nothing behind it overtakes).
 bool launch_solo(pc_server *s, LaunchSlot &sl) {
     Request *r = s->queue.front();
-    if (s->op_inflight.count(r->op)) return false;              // one request per 3D operator
+    if (s->op_inflight.count(r->op)) return false;              // one request per solo operator
     if (s->inflight >= s->cfg.max_inflight) return false;
     // Grow the operator's ordering flags and scratch for this request here,
     // on the scheduler thread, the only thread that touches a served
@@ -243,7 +243,7 @@ void try_launch(pc_server *s) {
         std::unordered_map<pc_operator *, int> seen;
         const bool adj = s->queue.front()->adjoint;
         for (Request *r : s->queue) {
-            if (r->solo) break;   // the 3D request takes a slot of its own next
+            if (r->solo) break;   // the solo request takes a slot of its own next
             if (r->adjoint != adj) break;   // one direction per launch (FIFO: no overtaking)
             if (int(take.size()) >= s->cfg.max_requests_per_launch) break;
             if (s->inflight + int(take.size()) >= s->cfg.max_inflight) break;
@@ -294,6 +294,7 @@ void try_launch(pc_server *s) {
             p.spec_stride = op->spec_stride;
             p.w = op->d_w;
             p.tw = op->d_tw;
+            p.wait_ns = op->wait_ns;
             p.total_items = int64_t(op->n_tiles) * npairs;
             sg.item_begin = items;
             r->hslot = s->free_hslots.back();
@@ -457,11 +458,11 @@ pc_status pc_serve_submit(pc_server *s, pc_operator *op, int32_t nrhs, const voi
     if (adjoint && op->prec == PC_BF16X3)
         return srv_fail(s, PC_ERR_UNSUPPORTED, "adjoint requests need an FP32 operator");
     if (op->ctx->device != s->ctx->device) return srv_fail(s, PC_ERR_ARG, "operator lives on another device");
-    const bool solo = op->d == 3;
-    if (!solo && (op->d != 2 || op->prec != PC_FP32 || op->P != 128))
-        return srv_fail(s, PC_ERR_UNSUPPORTED, "served 2D operators are FP32 with fft_size 128");
-    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) % 4)
-        return srv_fail(s, PC_ERR_ARG, "x and y must be 4-byte aligned");
+    // the multi-request kernel covers 2D FP32 operators with fft_size 128;
+    // every other operator runs its requests alone through its own apply
+    const bool solo = op->d != 2 || op->prec != PC_FP32 || op->P != 128;
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) % op->elem)
+        return srv_fail(s, PC_ERR_ARG, "x and y must be aligned to the element size");
     auto *r = new Request;
     r->op = op;
     r->nrhs = nrhs;
@@ -554,72 +555,6 @@ pc_status pc_serve_destroy(pc_server *s) {
     s->cv.notify_one();
     if (s->th.joinable()) s->th.join();
     free_server(s);
-    return PC_OK;
-}
-
-pc_status pc_autotune(pc_context *ctx, const pc_box *box, const pc_grid *grid, int32_t radius, const double *impulse,
-                      const double *weights, pc_precision prec, int32_t nrhs, pc_tuning *best, double *best_ms) {
-    if (!ctx || !best || nrhs < 1) return PC_ERR_ARG;
-    std::vector<pc_tuning> cands;
-    for (int P : {64, 128}) {
-        if (prec == PC_FP64 && P != 64) continue;
-        const int Wfull = 2 * radius + 1;
-        if (Wfull + 15 > P && P == 64) continue;   // no useful tile without splitting at P = 64
-        for (int frac : {4, 3}) {
-            pc_tuning t{};
-            t.fft_size = P;
-            const int tmax = std::min(P - Wfull + 1, (2 * P) / 3);
-            t.tile = frac == 4 ? 0 : std::max(8, tmax * 3 / 4);
-            if (frac == 3 && (tmax < 16 || t.tile >= tmax)) continue;
-            cands.push_back(t);
-        }
-    }
-    double bms = 1e300;
-    pc_tuning bt{};
-    std::string last_err;
-    void *x = nullptr, *y = nullptr;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaSetDevice(ctx->device);
-    for (const pc_tuning &t : cands) {
-        pc_operator *op = nullptr;
-        if (pc_build_spectra(ctx, box, grid, radius, impulse, weights, prec, &t, &op) != PC_OK) {
-            last_err = ctx->last_error;
-            continue;
-        }
-        const size_t bytes = size_t(nrhs) * op->N * op->elem;
-        if (!x) {
-            if (cudaMalloc(&x, bytes) != cudaSuccess || cudaMalloc(&y, bytes) != cudaSuccess ||
-                cudaMemset(x, 0, bytes) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
-                cudaEventCreate(&e1) != cudaSuccess) {
-                pc_operator_destroy(op);
-                break;
-            }
-        }
-        for (int q = 0; q < 2; ++q) pc_apply_batched(op, nrhs, x, op->N, y, op->N, nullptr);
-        cudaEventRecord(e0, nullptr);
-        const int reps = 5;
-        for (int q = 0; q < reps; ++q) pc_apply_batched(op, nrhs, x, op->N, y, op->N, nullptr);
-        cudaEventRecord(e1, nullptr);
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        const double per = double(ms) / reps;
-        if (per < bms) {
-            bms = per;
-            bt = t;
-        }
-        pc_operator_destroy(op);
-    }
-    cudaFree(x);
-    cudaFree(y);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    if (bms >= 1e300) {
-        ctx->last_error = "no candidate launch shape could be built: " + last_err;
-        return PC_ERR_UNSUPPORTED;
-    }
-    *best = bt;
-    if (best_ms) *best_ms = bms;
     return PC_OK;
 }
 

@@ -202,49 +202,53 @@ def test_3d_weights_on_random_anisotropic_trees_match_oracle(seed):
 
 @pytest.mark.parametrize("seed", [0, 1, 2, 3, 4, 5])
 def test_adaptive_split_admissibility_matches_oracle(seed):
-    """The adaptive construction's check that a split keeps every facet
-    piece's corners at sample points (written locally, around the new
+    """The library's check that a split keeps every facet piece's corners at
+    sample points (pc_split_is_admissible, written locally around the new
     leaves) agrees with the oracle's check of the whole grid, on every
     candidate split of random anisotropic 3D trees, crosswise ones included."""
-    from paper_1805_06018_gb300 import adaptive as lib_adaptive
-    from oracle.adaptive import pieces_have_sample_corners
+    from oracle.adaptive import pieces_have_sample_corners, subdivide
     shape, cells = _random_tree_3d(seed, splits=6)
-    boxes = [(list(map(int, lo)), list(map(int, hi))) for lo, hi in cells]
+    arr = np.array(cells, dtype=np.int32)
     seen = {True: 0, False: 0}
-    for box in boxes:
+    for c in range(len(cells)):
         for i in range(3):
-            if box[1][i] - box[0][i] <= 2:
+            if cells[c][1][i] - cells[c][0][i] <= 2:
                 continue
-            nxt = lib_adaptive._split(boxes, box, i)
-            got = lib_adaptive._pieces_end_at_points(nxt, nxt[-2:])
-            want = pieces_have_sample_corners(shape, np.array([[lo, hi] for lo, hi in nxt]))
-            assert got == want, (box, i)
+            got = pcb.pc_split_is_admissible(shape, arr, c, i)
+            want = pieces_have_sample_corners(shape, subdivide(cells, c, i))
+            assert got == want, (c, i)
             seen[got] += 1
     assert seen[True] > 0 and seen[False] > 0
 
 
 def test_adaptive_crosswise_split_is_refused_by_both_sides():
-    from paper_1805_06018_gb300 import adaptive as lib_adaptive
-    from test_oracle_adaptive import _crosswise_grid
+    """The octant beside a leaf split along y: splitting it along z breaks
+    their facet crosswise (refused by the library's check and by its
+    weights), along y only leaves hanging nodes."""
+    from oracle.adaptive import initial_cells, subdivide
+    shape = (9, 9, 9)
+    cells = initial_cells(shape)
+    left = next(j for j, c in enumerate(cells) if tuple(c[0]) == (0, 0, 0))
+    cells = subdivide(cells, left, 1)
+    right = next(j for j, c in enumerate(cells) if tuple(c[0]) == (4, 0, 0))
     for axis, ok in [(2, False), (1, True)]:
-        shape, cells = _crosswise_grid(axis)
-        boxes = [(list(map(int, lo)), list(map(int, hi))) for lo, hi in cells]
-        assert lib_adaptive._pieces_end_at_points(boxes, boxes[-2:]) == ok
+        assert pcb.pc_split_is_admissible(shape, np.array(cells, dtype=np.int32), right, axis) == ok
+        split = np.array(subdivide(cells, right, axis))
         if ok:
-            pcb.pc_harmonic_weights(shape, np.array(cells))
+            pcb.pc_harmonic_weights(shape, split)
         else:
             with pytest.raises(pcb.PCError) as ei:
-                pcb.pc_harmonic_weights(shape, np.array(cells))
+                pcb.pc_harmonic_weights(shape, split)
             assert ei.value.status == pcb.PC_ERR_GRID
 
 
 @pytest.mark.parametrize("seed", [0, 1])
 def test_adaptive_direction_order_matches_oracle(seed):
-    """Section 2.7's directions, best first, from the library's extension
-    (pc_extend_impulse) and from the oracle's, on every leaf of random 3D
-    trees with a kernel that changes along all three axes."""
+    """Section 2.7's directions, best first, from the library
+    (pc_split_directions on its own extension) and from the oracle's
+    extension, on every leaf of random 3D trees with a kernel that changes
+    along all three axes."""
     import workloads
-    from paper_1805_06018_gb300 import adaptive as lib_adaptive
     from oracle import PCOracle
     from oracle.adaptive import split_directions
     shape, cells = _random_tree_3d(seed, splits=5)
@@ -253,10 +257,9 @@ def test_adaptive_direction_order_matches_oracle(seed):
     g = Grid(shape, cells)
     phi = workloads.impulse_windows(shape, g.points, kern)
     orc = PCOracle(shape, cells, phi, 3)
-    lib_phiE = pcb.pc_extend_impulse(shape, cells, 3, phi)
-    index = {tuple(int(v) for v in p): k for k, p in enumerate(g.points)}
-    for c, (lo, hi) in enumerate(cells):
-        got = lib_adaptive._directions(shape, list(map(int, lo)), list(map(int, hi)), index, lib_phiE, 3)
+    arr = np.array(cells, dtype=np.int32)
+    for c in range(len(cells)):
+        got = pcb.pc_split_directions(shape, arr, 3, phi, c)
         assert got == split_directions(g, orc.phiE, 3, c)
 
 
