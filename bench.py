@@ -270,6 +270,13 @@ def sampled_error(y, points, values):
     return float(np.max(np.linalg.norm(got - ref, axis=1) / den))
 
 
+def workload_config(wl, desc, world, fft):
+    """The `config` dict of a bench line; both arms print the same one."""
+    return {"workload": desc, "global_batch": wl.nrhs * world, "per_gpu_batch": wl.nrhs, "grid": list(wl.shape),
+            "radius": wl.radius, "fft": fft, "parallelism": "replicas%d" % world,
+            "l2": "flushed between steps (256 MB write)"}
+
+
 def run_reference_block(args, wl):
     """Reference arm of the block workload: the oracle's translated block
     apply, one right-hand side per step (a bounded sample of the 64)."""
@@ -339,8 +346,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][0],
-                                            "global_batch": wl.nrhs, "parallelism": "cpu"},
+            "data": "synthetic", "config": workload_config(wl, WORKLOADS[args.workload][0], world, wl.fft),
             "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -674,31 +680,30 @@ def serve_operators(pcg, ctx, with_3d=True):
     return ops
 
 
-def run_serve(args):
-    """Serving: Poisson arrivals of requests (operator uniform over the mix,
-    RHS uniform in [1, 64]) at 50/80/95 % of the saturated rate, 120 GB budget."""
+def serve_measure(pcg, ctx, ops, n_requests, rng, levels=(0.5, 0.8, 0.95), rhs_max=64, sat_requests=None,
+                  plain=True):
+    """Serving measurement over `ops` [(name, operator)]: requests pick an
+    operator uniformly and U[1, rhs_max] right-hand sides; a saturated run
+    (all submitted at once), then Poisson arrivals at each load level (a
+    fraction of the saturated RHS/s) with n_requests requests each, 120 GB
+    budget.  Returns the stats and, if `plain`, the plain per-vector path's
+    RHS/s on the saturated request set (2D requests)."""
     import torch
     import workloads
-    import paper_1805_06018_gb300 as pcg
-    from paper_1805_06018_gb300 import build as libbuild
-    libbuild.build()
-    ctx = pcg.Context(0)
-    ops = serve_operators(pcg, ctx, with_3d=not args.serve_2d)
     by_shape = {}
     for i, (_, op) in enumerate(ops):
         if op.shape not in by_shape:
-            by_shape[op.shape] = torch.from_numpy(workloads.rhs(7000 + i, 64, op.shape)).cuda()
+            by_shape[op.shape] = torch.from_numpy(workloads.rhs(7000 + i, rhs_max, op.shape)).cuda()
     pools = [by_shape[op.shape] for _, op in ops]
-    rng = np.random.default_rng(17)
 
     def make_requests(n):
-        return [(int(rng.integers(0, len(ops))), int(rng.integers(1, 65))) for _ in range(n)]
+        return [(int(rng.integers(0, len(ops))), int(rng.integers(1, rhs_max + 1))) for _ in range(n)]
 
-    # per operator, a bounded pool of 64-RHS output buffers (48 GB shared by
-    # the operators); a request takes one and returns it on completion
+    # per operator, a bounded pool of rhs_max-RHS output buffers (48 GB shared
+    # by the operators); a request takes one and returns it on completion
     ybufs = []
     for o, (_, op) in enumerate(ops):
-        per = 64 * op.N * 4
+        per = rhs_max * op.N * 4
         ybufs.append([torch.empty_like(pools[o]) for _ in range(max(4, min(64, (48 << 30) // len(ops) // per)))])
 
     def run(reqs, rate):
@@ -727,43 +732,250 @@ def run_serve(args):
         srv.close()
         return st
 
-    warm = make_requests(16)
-    run(warm, None)
-    sat_reqs = make_requests(max(32, args.serve_requests // 2))
+    run(make_requests(16), None)   # warm-up
+    sat_reqs = make_requests(sat_requests or max(32, n_requests // 2))
     sat = run(sat_reqs, None)
-    mean_rhs = 32.5
+    mean_rhs = (1 + rhs_max) / 2.0
     loads = []
-    for f in (0.5, 0.8, 0.95):
-        reqs = make_requests(args.serve_requests)
+    for f in levels:
+        reqs = make_requests(n_requests)
         st = run(reqs, f * sat["rhs_per_s"] / mean_rhs)
         loads.append({"load": f, "requests": st["completed"], "rhs_per_s": st["rhs_per_s"],
                       "p50_ms": 1e3 * st["p50_latency_s"], "p99_ms": 1e3 * st["p99_latency_s"],
                       "launches": st["launches"], "peak_budget_bytes": st["peak_bytes"]})
-    # the plain per-vector path on the saturated request set, one request after
-    # another (2D requests: the plain path is 2D only)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    rhs = 0
-    for o, k in sat_reqs:
-        if len(ops[o][1].shape) != 2:
-            continue
-        y = torch.empty_like(pools[o][:k])
-        ops[o][1].apply_plain(pools[o][:k], y)
-        rhs += k
-    torch.cuda.synchronize()
-    plain = rhs / (time.perf_counter() - t0)
+    out = {"saturated": {"requests": sat["completed"], "rhs_per_s": sat["rhs_per_s"],
+                         "p50_ms": 1e3 * sat["p50_latency_s"], "p99_ms": 1e3 * sat["p99_latency_s"],
+                         "launches": sat["launches"]},
+           "loads": loads, "requests_after_warmup": sat["completed"] + sum(lv["requests"] for lv in loads)}
+    if plain:
+        # the plain per-vector path on the saturated request set, one request after another
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rhs = 0
+        for o, k in sat_reqs:
+            y = torch.empty_like(pools[o][:k])
+            ops[o][1].apply_plain(pools[o][:k], y)
+            rhs += k
+        torch.cuda.synchronize()
+        out["plain_gpu_rhs_per_s"] = rhs / (time.perf_counter() - t0)
+    return out
+
+
+def run_serve(args):
+    """Serving: Poisson arrivals of requests (operator uniform over the mix,
+    RHS uniform in [1, 64]) at 50/80/95 % of the saturated rate, 120 GB budget."""
+    import paper_1805_06018_gb300 as pcg
+    from paper_1805_06018_gb300 import build as libbuild
+    libbuild.build()
+    ctx = pcg.Context(0)
+    ops = serve_operators(pcg, ctx, with_3d=not args.serve_2d)
+    m = serve_measure(pcg, ctx, ops, args.serve_requests, np.random.default_rng(17))
     line = {"metric": "served product-convolution RHS/s; p50/p99 latency", "mode": "serve",
-            "value": sat["rhs_per_s"], "unit": "RHS/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
-            "data": "synthetic", "saturated": {"requests": sat["completed"], "rhs_per_s": sat["rhs_per_s"],
-                                               "p50_ms": 1e3 * sat["p50_latency_s"],
-                                               "p99_ms": 1e3 * sat["p99_latency_s"], "launches": sat["launches"]},
-            "loads": loads, "plain_gpu_rhs_per_s": plain,
+            "value": m["saturated"]["rhs_per_s"], "unit": "RHS/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic", "saturated": m["saturated"], "loads": m["loads"],
+            "plain_gpu_rhs_per_s": m.get("plain_gpu_rhs_per_s"),
             "config": {"operators": [n for n, _ in ops], "rhs_per_request": "U[1,64]", "budget_bytes": 120 << 30,
                        "arrivals": "Poisson at 50/80/95% of the saturated rate",
                        "modes": "2D FP32" if args.serve_2d else "2D FP32; 3D FP32 and BF16x3 (tensor-core first axis)",
-                       "requests_after_warmup": sat["completed"] + sum(lv["requests"] for lv in loads),
-                       "plain_gpu": "2D requests of the saturated set only"}}
+                       "requests_after_warmup": m["requests_after_warmup"],
+                       "plain_gpu": "the saturated request set, one request after another"}}
     print(json.dumps(line), flush=True)
+
+
+def roofline_of(pcg, wl, info, precision, kms, workload):
+    """Roofline of the dominant kernel of one apply: nominal FLOPs (or, for the
+    tensor-core stage, executed MMA FLOPs) over its event-timed duration
+    (kms: per-step kernel ms, or per-step [stage0, stage1, stage2] ms for the
+    BF16x3 split path), against the FP32 FMA pipe, the FP64 rate or the
+    measured BF16 peak.  Returns (roofline, roofline_tensor or None, kernel
+    name, kernel ms)."""
+    import torch
+    staged = precision == "bf16x3"
+    kname = WORKLOADS[workload][1]
+    lo, hi = pcg.pc_neighbourhood_boxes(wl.shape, wl.cells)
+    flops, bytes_ = algorithmic_work(wl.shape, lo, hi, wl.radius, wl.nrhs, info["spectra_bytes"],
+                                     elem=8 if precision == "fp64" else 4)
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+    roof_tensor = None
+    if staged:
+        # three kernels per chunk; nominal flops split by transform axis:
+        # phase 1 = forward axes 1, 2; tensor stage = axis 0 forward + inverse
+        # + product; phase 3 = inverse axes 1, 2.  Executed tensor-core flops
+        # count the MMAs the tensor stage issues (3 split products per step).
+        stage_names = ["fft3d_phase1_kernel", "tc3d_axis0_kernel", "fft3d_phase3_kernel"]
+        st_ms = np.mean(np.array(kms), axis=0)
+        npairs = (wl.nrhs + 1) // 2
+        f_stage = [0.0, 0.0, 0.0]
+        mma_flops = 0.0
+        assert info["num_tiles"] == len(lo), "one tile per patch expected"
+        for a, b in zip(lo, hi):
+            n = [bb - aa + 1 for aa, bb in zip(a, b)]
+            Ls = [v + 2 * wl.radius for v in n]
+            L = float(np.prod(Ls))
+            f_stage[0] += 2.5 * L * (math.log2(Ls[1]) + math.log2(Ls[2]))
+            f_stage[1] += 5.0 * L * math.log2(Ls[0]) + 3.0 * L
+            f_stage[2] += 2.5 * L * (math.log2(Ls[1]) + math.log2(Ls[2]))
+            mma_flops += npairs * 32 * 3 * ((2 * n[0] + 15) // 16 + 8) * 2.0 * 128 * 128 * 16
+        f_stage = [f * wl.nrhs for f in f_stage]
+        bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+        tc_ach = mma_flops / (st_ms[1] / 1e3) / 1e12
+        roof_tensor = {"bound": "tensor", "kernel": stage_names[1], "kernel_ms": float(st_ms[1]),
+                       "executed_mma_flop_per_apply": mma_flops, "achieved": tc_ach, "peak": bf16_peak,
+                       "unit": "TFLOP/s", "frac": tc_ach / bf16_peak,
+                       "peak_basis": "measured cuBLAS bf16 GEMM (burst)",
+                       "nominal_fft_tflops": f_stage[1] / (st_ms[1] / 1e3) / 1e12,
+                       "stage_ms": {nm: float(t) for nm, t in zip(stage_names, st_ms)}}
+        dom = int(np.argmax(st_ms))
+        kname = stage_names[dom]
+        kern_ms = float(st_ms[dom])
+        if dom == 1:
+            achieved, peak, bound, basis = tc_ach, bf16_peak, "tensor", roof_tensor["peak_basis"]
+            work = mma_flops
+        else:
+            achieved = f_stage[dom] / (kern_ms / 1e3) / 1e12
+            peak, bound = fp32_peak, "alu"
+            basis = "FP32 FMA pipe: SMs x 128 lanes x 2 x %.0f MHz" % sm_max
+            work = f_stage[dom]
+    elif precision == "fp64":
+        kern_ms = float(np.mean(kms))
+        achieved, peak, bound, work = flops / (kern_ms / 1e3) / 1e12, 1.25, "alu", flops
+        basis = "nominal GB300 FP64 rate, 1.25 TFLOP/s (no measured FP64 peak)"
+    else:
+        kern_ms = float(np.mean(kms))
+        achieved, peak, bound, work = flops / (kern_ms / 1e3) / 1e12, fp32_peak, "alu", flops
+        basis = "FP32 FMA pipe: SMs x 128 lanes x 2 x %.0f MHz" % sm_max
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": kname, "kernel_ms": kern_ms, "algorithmic_flop_per_launch": work,
+            "algorithmic_bytes_per_launch": bytes_, "peak_basis": basis}
+    return roof, roof_tensor, kname, kern_ms
+
+
+def suite_apply(pcg, ctx, name, steps, warmup, flush, plain_steps=2, accuracy_points=2048):
+    """One sub-workload of the default run: its batched apply timed on the
+    device (L2 flushed between steps), its result against the FP64 oracle at
+    sampled output points, its roofline, and the plain per-vector path on the
+    same operator where it applies.  Returns the entry and the operator."""
+    import torch
+    import workloads
+    from workloads import configs
+    from oracle import PCOracle
+    cfg_name, precision = WORKLOAD_OPERATOR[name]
+    wl = configs.get(cfg_name)
+    desc = WORKLOADS[name][0]
+    pts = pcg.pc_sample_points(wl.shape, wl.cells)
+    op = pcg.Operator(ctx, wl.shape, wl.cells, wl.radius, workloads.impulse_windows(wl.shape, pts, wl.kernel),
+                      precision=precision)
+    info = op.info()
+    x_host = workloads.rhs(wl.rhs_seed, wl.nrhs, wl.shape)
+    x = torch.from_numpy(x_host).cuda()
+    if precision == "fp64":
+        x = x.double()
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    staged = precision == "bf16x3"
+    for _ in range(warmup):
+        op.pc_apply_batched(wl.nrhs, x.data_ptr(), wl.n, y.data_ptr(), wl.n, stream.cuda_stream)
+    torch.cuda.synchronize()
+    op.check()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    kms = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        op.pc_apply_batched(wl.nrhs, x.data_ptr(), wl.n, y.data_ptr(), wl.n, stream.cuda_stream)
+        ev[i][1].record(stream)
+        kms.append([op.stage_ms(k) for k in range(3)] if staged else op.kernel_ms())
+    torch.cuda.synchronize()
+    op.check()
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    entry = {"config": desc, "value": wl.nrhs * steps / (step_ms.sum() / 1e3), "unit": "RHS/s",
+             "ms_per_step": float(step_ms.mean()), "steps": steps, "warmup": warmup,
+             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                            "per": "apply of %d RHS" % wl.nrhs},
+             "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "f32+bf16x3"}[precision],
+             "fft": info["fft_size"], "tile": info["tile"], "num_tiles": info["num_tiles"],
+             "num_colors": info["num_colors"], "window_split": info["window_split"]}
+    # accuracy: the oracle (FP64, direct sums) at sampled output points, all RHS
+    rng = np.random.default_rng(5)
+    npts = min(wl.n, accuracy_points)
+    sel = np.sort(rng.choice(wl.n, npts, replace=False))
+    orc = PCOracle.from_workload(wl)
+    t0 = time.perf_counter()
+    ref = orc.apply(x_host.astype(np.float64), points=sel)
+    entry["accuracy"] = {"rel_l2_vs_fp64_oracle": sampled_error(y, sel, ref), "points": int(npts), "rhs": wl.nrhs,
+                         "per": "max over right-hand sides", "oracle_s": time.perf_counter() - t0}
+    roof, roof_tensor, kname, _ = roofline_of(pcg, wl, info, precision, kms, name)
+    roof["traffic"] = profiled_traffic(name) if kname == WORKLOADS[name][1] else None
+    entry["roofline"] = roof
+    if roof_tensor is not None:
+        entry["roofline_tensor"] = roof_tensor
+    if precision != "fp64" and plain_steps > 0:
+        yp = torch.empty_like(x)
+        op.pc_apply_plain(wl.nrhs, x.data_ptr(), wl.n, yp.data_ptr(), wl.n, stream.cuda_stream)
+        torch.cuda.synchronize()
+        pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(plain_steps)]
+        for a, b in pe:
+            flush.fill_(1.0)
+            a.record(stream)
+            op.pc_apply_plain(wl.nrhs, x.data_ptr(), wl.n, yp.data_ptr(), wl.n, stream.cuda_stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        pms = [a.elapsed_time(b) for a, b in pe]
+        entry["plain_gpu"] = {"value": wl.nrhs / (np.mean(pms) / 1e3), "unit": "RHS/s", "ms_per_apply": float(np.mean(pms)),
+                              "accuracy_rel_l2_vs_fp64_oracle": sampled_error(yp, sel, ref),
+                              "path": "per vector: gather, cuFFT R2C, product, cuFFT C2R, overlap-add (FP32)"}
+        del yp
+    del x, y
+    return entry, op
+
+
+def suite(pcg, ctx, args):
+    """The other configurations, measured on the same run: the FP64 64^2
+    correctness workload, the 3D 128^3 workload in FP32 and with the
+    tensor-core first axis (BF16x3), the adaptive 1024^2 workload (batched,
+    and as 256 served requests of U[1,32] right-hand sides), and serving of
+    the 2D operator mix with Poisson arrivals."""
+    import torch
+    import workloads
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    plan = [("fp64_64", 30, 3), ("fp32_128c", 8, 3), ("bf16x3_128c", 8, 3), ("adaptive_1024", 8, 3)]
+    for name, steps, warm in plan:
+        try:
+            entry, op = suite_apply(pcg, ctx, name, steps, warm, flush,
+                                    plain_steps=0 if name == "adaptive_1024" else 2,
+                                    accuracy_points=512 if name.endswith("128c") else 2048)
+            if name == "adaptive_1024":
+                # the adaptive workload as written: 256 requests of U[1,32] RHS through the server
+                m = serve_measure(pcg, ctx, [("adaptive_1024", op)], 256, np.random.default_rng(31), levels=(),
+                                  rhs_max=32, sat_requests=256, plain=False)
+                entry["served_256_requests"] = dict(m["saturated"], rhs_per_request="U[1,32]",
+                                                    arrivals="all 256 submitted at once")
+            op.close()
+            out[name] = entry
+        except Exception as e:   # a report, never a reason to lose the line
+            out[name] = {"unavailable": "%s: %s" % (type(e).__name__, e)}
+        torch.cuda.empty_cache()
+    del flush
+    if args.suite_serve_requests > 0:
+        try:
+            ops = serve_operators(pcg, ctx, with_3d=False)
+            m = serve_measure(pcg, ctx, ops, args.suite_serve_requests, np.random.default_rng(17))
+            m["config"] = {"operators": [n for n, _ in ops], "rhs_per_request": "U[1,64]", "budget_bytes": 120 << 30,
+                           "arrivals": "Poisson at 50/80/95% of the saturated rate",
+                           "plain_gpu": "the saturated request set, one request after another"}
+            out["serving_2d_mix"] = m
+            for _, op in ops:
+                op.close()
+        except Exception as e:
+            out["serving_2d_mix"] = {"unavailable": "%s: %s" % (type(e).__name__, e)}
+    return out
 
 
 def main():
@@ -780,6 +992,10 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--nrhs", type=int, default=0,
                     help="override the workload's batch (smaller cases for profiler captures)")
+    ap.add_argument("--no-suite", action="store_true",
+                    help="skip the other configurations that the default run adds under 'workloads'")
+    ap.add_argument("--suite-serve-requests", type=int, default=2000,
+                    help="requests per load level of the default run's serving measurement (0: skip it)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -915,73 +1131,14 @@ def main():
         step()  # leave the operator's last launch = the fused path
 
     # ---- roofline of the fused kernel (FP32 ALU bound)
-    lo, hi = pcg.pc_neighbourhood_boxes(wl.shape, wl.cells)
-    flops, bytes_ = algorithmic_work(wl.shape, lo, hi, wl.radius, wl.nrhs, info["spectra_bytes"],
-                                     elem=8 if precision == "fp64" else 4)
-    peaks = {}
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        peaks = json.load(open(pk_path))
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    props = torch.cuda.get_device_properties(torch.cuda.current_device())
-    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
-    roof_tensor = None
-    if staged:
-        # three kernels per chunk; nominal flops split by transform axis:
-        # phase 1 = forward axes 1, 2; tensor stage = axis 0 forward + inverse
-        # + product; phase 3 = inverse axes 1, 2.  Executed tensor-core flops
-        # count the MMAs the tensor stage issues (3 split products per step).
-        stage_names = ["fft3d_phase1_kernel", "tc3d_axis0_kernel", "fft3d_phase3_kernel"]
-        st_ms = np.mean(np.array(kms), axis=0)
-        npairs = (wl.nrhs + 1) // 2
-        f_stage = [0.0, 0.0, 0.0]
-        mma_flops = 0.0
-        assert info["num_tiles"] == len(lo), "one tile per patch expected"
-        for a, b in zip(lo, hi):
-            n = [bb - aa + 1 for aa, bb in zip(a, b)]
-            Ls = [v + 2 * wl.radius for v in n]
-            L = float(np.prod(Ls))
-            f_stage[0] += 2.5 * L * (math.log2(Ls[1]) + math.log2(Ls[2]))
-            f_stage[1] += 5.0 * L * math.log2(Ls[0]) + 3.0 * L
-            f_stage[2] += 2.5 * L * (math.log2(Ls[1]) + math.log2(Ls[2]))
-            mma_flops += npairs * 32 * 3 * ((2 * n[0] + 15) // 16 + 8) * 2.0 * 128 * 128 * 16
-        f_stage = [f * wl.nrhs for f in f_stage]
-        bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
-        tc_ach = mma_flops / (st_ms[1] / 1e3) / 1e12
-        roof_tensor = {"bound": "tensor", "kernel": stage_names[1], "kernel_ms": float(st_ms[1]),
-                       "executed_mma_flop_per_apply": mma_flops, "achieved": tc_ach, "peak": bf16_peak,
-                       "unit": "TFLOP/s", "frac": tc_ach / bf16_peak,
-                       "peak_basis": "measured cuBLAS bf16 GEMM (burst)",
-                       "nominal_fft_tflops": f_stage[1] / (st_ms[1] / 1e3) / 1e12,
-                       "stage_ms": {nm: float(t) for nm, t in zip(stage_names, st_ms)}}
-        dom = int(np.argmax(st_ms))
-        kname = stage_names[dom]
-        kern_ms = float(st_ms[dom])
-        if dom == 1:
-            achieved, peak, bound, basis = tc_ach, bf16_peak, "tensor", roof_tensor["peak_basis"]
-            work = mma_flops
-        else:
-            achieved = f_stage[dom] / (kern_ms / 1e3) / 1e12
-            peak, bound = fp32_peak, "alu"
-            basis = "FP32 FMA pipe: SMs x 128 lanes x 2 x %.0f MHz" % sm_max
-            work = f_stage[dom]
-    elif precision == "fp64":
-        kern_ms = float(np.mean(kms))
-        achieved, peak, bound, work = flops / (kern_ms / 1e3) / 1e12, 1.25, "alu", flops
-        basis = "nominal GB300 FP64 rate, 1.25 TFLOP/s (no measured FP64 peak)"
-    else:
-        kern_ms = float(np.mean(kms))
-        achieved, peak, bound, work = flops / (kern_ms / 1e3) / 1e12, fp32_peak, "alu", flops
-        basis = "FP32 FMA pipe: SMs x 128 lanes x 2 x %.0f MHz" % sm_max
-    traffic = profiled_traffic(args.workload) if kname == WORKLOADS[args.workload][1] else None
+    roof, roof_tensor, kname, kern_ms = roofline_of(pcg, wl, info, precision, kms, args.workload)
+    roof["traffic"] = profiled_traffic(args.workload) if kname == WORKLOADS[args.workload][1] else None
 
     line = {"metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32",
             "data": "synthetic",
-            "config": {"workload": desc, "global_batch": wl.nrhs * world,
-                       "per_gpu_batch": wl.nrhs, "grid": list(wl.shape), "radius": wl.radius, "fft": info["fft_size"],
-                       "parallelism": "replicas%d" % world, "l2": "flushed between steps (256 MB write)"},
+            "config": workload_config(wl, desc, world, info["fft_size"]),
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                            "per": "apply of %d RHS" % wl.nrhs},
             "plain_gpu": plain,
@@ -990,11 +1147,7 @@ def main():
                     "call": "pc_estimate_cell_errors after a host-to-device copy of Z" if estimator else
                     "pc_apply_host (pinned host x, y; chunked copies overlapped with the kernels)"},
             "gpu_launches": launches_per_step * args.steps,
-            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": kname, "kernel_ms": kern_ms,
-                         "algorithmic_flop_per_launch": work, "algorithmic_bytes_per_launch": bytes_,
-                         "peak_basis": basis},
+            "roofline": roof,
             "clocks": clk.summary()}
     if roof_tensor is not None:
         line["roofline_tensor"] = roof_tensor
@@ -1012,9 +1165,16 @@ def main():
                                     "rhs": wl.nrhs, "per": "max over right-hand sides"}
             except Exception as e:   # a report, never a reason to lose the line
                 line["accuracy"] = {"unavailable": "%s: %s" % (type(e).__name__, e)}
+    if rank == 0 and world == 1 and args.workload == WORKLOAD and not args.no_suite:
+        op.close()
+        op = None
+        del x, y, flush
+        torch.cuda.empty_cache()
+        line["workloads"] = suite(pcg, ctx, args)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    op.close()
+    if op is not None:
+        op.close()
     ctx.close()
     if world > 1:
         dist.destroy_process_group()

@@ -484,9 +484,11 @@ pc_status pc_estimate_cell_errors(pc_operator *op, int32_t q, const void *z, int
                                   int64_t ldy, double *eta, pc_stream stream);
 
 /* Plain path for comparison: the same operator applied one vector at a time
- * through a gather kernel, a library FFT (cuFFT) of each padded patch, a
- * spectral product kernel, an inverse library FFT and an output-stationary
- * overlap-add kernel.  FP32 operators only.  Same arguments as
+ * through a gather kernel, a library FFT (cuFFT, 2D P x P or 3D P x P x P)
+ * of each padded patch, a spectral product kernel, an inverse library FFT
+ * and an output-stationary overlap-add kernel, all in FP32.  2D and 3D
+ * operators with FP32 spectra (PC_FP32, and PC_BF16X3, whose spectra are
+ * FP32); PC_FP64 gives PC_ERR_UNSUPPORTED.  Same arguments as
  * pc_apply_batched; it allocates its scratch on first use. */
 pc_status pc_apply_plain(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx,
                          void *y, int64_t ldy, pc_stream stream);

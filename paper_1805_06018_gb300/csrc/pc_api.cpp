@@ -1140,7 +1140,7 @@ pc_status pc_apply_plain(pc_operator *op, int32_t nrhs, const void *x, int64_t l
                          pc_stream stream) {
     if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
     pc_context *ctx = op->ctx;
-    if (op->prec != PC_FP32 || op->d != 2) return fail(ctx, PC_ERR_UNSUPPORTED, "the plain path is 2D FP32 only");
+    if (op->prec == PC_FP64) return fail(ctx, PC_ERR_UNSUPPORTED, "the plain path covers FP32 spectra (FP32, BF16X3)");
     if (nrhs < 0) return fail(ctx, PC_ERR_ARG, "nrhs < 0");
     if (nrhs == 0) return PC_OK;
     if (!x || !y) return fail(ctx, PC_ERR_ARG, "null x or y");

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
     T *Sf = reinterpret_cast<T *>(smem_raw);
     C *SP = reinterpret_cast<C *>(smem_raw + L::ws);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw + L::ws + L::sp);
-    __shared__ int64_t s_next;
+    __shared__ int64_t s_next_buf[2];   // claim of the next item, by item parity
     __shared__ int s_segidx;
     __shared__ int s_run, s_runcol;
     __shared__ int64_t s_runbase;
@@ -221,8 +221,9 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
         pend_flag = nullptr;
     };
 
+    // one arrival per spectrum column: each copying thread announces its own bytes
     if (threadIdx.x == 0) {
-        mbar_init(mbar, 1);
+        mbar_init(mbar, H);
         fence_mbar_init();
     }
 
@@ -232,13 +233,14 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
     // CTA is working on, so every dependency wait ends.
     unsigned long long *counter = lp.counter;
     if (threadIdx.x == 0) {
-        s_next = int64_t(atomicAdd(counter, 1ull));
+        s_next_buf[0] = int64_t(atomicAdd(counter, 1ull));
         s_run = 0;
         s_stop = 0;
     }
-    for (;;) {
-        __syncthreads();
-        const int64_t gitem = s_next;
+    __syncthreads();
+    for (int par = 0;; par ^= 1) {
+        // s_next_buf[par] and s_stop were written before the barrier that ended the previous item
+        const int64_t gitem = s_next_buf[par];
         if (gitem >= total || s_stop) break;
         // the request (segment) this item belongs to (a single-apply launch has one)
         int segidx = 0;
@@ -300,9 +302,7 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
             decode_item(p, s_cstart, item, ti, pair);
         }
         const Tile tile = p.tiles[ti];
-        if (threadIdx.x == 0) mbar_arrive_expect_tx(mbar, uint32_t(H * (P * sizeof(C) + 16)));
-        __syncthreads();   // everyone has read s_next; the spectrum copy is announced
-        if (threadIdx.x == NT - 1) s_next = int64_t(atomicAdd(counter, 1ull));
+        if (threadIdx.x == NT - 1) s_next_buf[par ^ 1] = int64_t(atomicAdd(counter, 1ull));
         const int n1 = tile.in_ext[0], n2 = tile.in_ext[1];
         const int i0 = tile.in_lo[0], j0 = tile.in_lo[1];
         const int L1 = n1 + tile.kext[0] - 1, L2 = n2 + tile.kext[1] - 1;   // <= P
@@ -319,6 +319,7 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
             const int col = threadIdx.x;
             const C *src = spec + int64_t(tile.spec) * p.spec_stride + int64_t(col) * P;
             fence_proxy_async_smem();
+            mbar_arrive_expect_tx(mbar, uint32_t(P * sizeof(C) + 16));
             bulk_g2s(SP + col * L::SPLD, src, uint32_t(P * sizeof(C)), mbar);
             bulk_g2s(SP + col * L::SPLD + P, src, 16u, mbar);   // value 0 again, at index P
         }
@@ -413,8 +414,8 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
         __syncthreads();
         if (threadIdx.x == 0) publish_pending();
 
-        if ((!MULTI || nrun == 0) && s_next - s_seg.item_begin < p.total_items)
-            prefetch_item<T, ADJ>(p, s_cstart, s_next - s_seg.item_begin);
+        if ((!MULTI || nrun == 0) && s_next_buf[par ^ 1] - s_seg.item_begin < p.total_items)
+            prefetch_item<T, ADJ>(p, s_cstart, s_next_buf[par ^ 1] - s_seg.item_begin);
 
         // ---------------- phase B: column FFT, spectral product, inverse column FFT
         // If the spectrum copy does not land within the limit, the item is
@@ -535,7 +536,6 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
             // phase A (or at exit), and only then is this item reported done.
             if (t == 0) bulk_wait_read();
         }
-        __syncthreads();
         pend_flag_any = true;
         if (threadIdx.x == 0) {
             if (ld_volatile_s32(lp.status) != 0) s_stop = 1;
@@ -545,6 +545,7 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
             pend_total = p.total_items;
             pend_slot = s_seg.slot;
         }
+        __syncthreads();
     }
     if constexpr (sizeof(T) == 4) {
         if (t == 0 && pend_flag_any) {
