@@ -107,7 +107,15 @@ typedef struct {
     int32_t window_split;    /* kernel sub-windows per axis: [-R, R] cut into window_split
                                 pieces with their own spectra, an exact rewrite of the sum
                                 (0: the count that minimises FFT work per input pixel) */
-    int32_t reserved[3];
+    int32_t per_patch;       /* 2D: 1 = each patch takes the FFT size (64 or 128) and
+                                window split that a model of the line-FFT work prefers for
+                                its own bbox(U_k); the patches of each shape form a part,
+                                applied by its own launch (fft_size, tile and window_split
+                                are then ignored).  Such operators support the applies, the
+                                host-buffer apply, serving (alone on a slot), the estimator
+                                and the entries; block plans, the incremental estimator
+                                and the plain path refuse them (PC_ERR_UNSUPPORTED) */
+    int32_t reserved[2];
 } pc_tuning;
 
 /* Read-only description of a built operator. */
@@ -130,6 +138,8 @@ typedef struct {
     int32_t autotuned;       /* 1 if the launch shape came from the autotuner */
     int32_t tuned_candidates;   /* candidate shapes the autotuner timed */
     double tuned_ms;         /* its time of the chosen shape per timed batch (ms) */
+    int32_t num_parts;       /* launch shapes (parts) of a per_patch operator; 1 otherwise */
+    int32_t reserved;
 } pc_operator_info;
 
 typedef struct pc_context pc_context;

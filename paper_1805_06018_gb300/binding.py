@@ -46,7 +46,8 @@ class pc_grid(ctypes.Structure):
 
 class pc_tuning(ctypes.Structure):
     _fields_ = [("fft_size", ctypes.c_int32), ("tile", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("wait_limit_us", ctypes.c_int32), ("window_split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("wait_limit_us", ctypes.c_int32), ("window_split", ctypes.c_int32), ("per_patch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class pc_operator_info(ctypes.Structure):
@@ -55,7 +56,8 @@ class pc_operator_info(ctypes.Structure):
                 ("num_tiles", ctypes.c_int32), ("num_colors", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("spectra_bytes", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("build_seconds", ctypes.c_double), ("window_split", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("autotuned", ctypes.c_int32), ("tuned_candidates", ctypes.c_int32), ("tuned_ms", ctypes.c_double)]
+                ("autotuned", ctypes.c_int32), ("tuned_candidates", ctypes.c_int32), ("tuned_ms", ctypes.c_double),
+                ("num_parts", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class pc_serve_config(ctypes.Structure):
@@ -303,7 +305,7 @@ class Operator:
 
     def __init__(self, ctx: Context, shape, cells, radius: int, impulse: np.ndarray, precision: str = "fp32",
                  weights: Optional[np.ndarray] = None, fft_size: int = 0, tile: int = 0, ctas_per_sm: int = 0,
-                 wait_limit_us: int = 0, window_split: int = 0, autotune: bool = False):
+                 wait_limit_us: int = 0, window_split: int = 0, per_patch: bool = False, autotune: bool = False):
         self.ctx = ctx
         self.shape = tuple(int(s) for s in shape)
         self.N = int(np.prod(self.shape))
@@ -314,7 +316,7 @@ class Operator:
         wts = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
         tune = pc_tuning()
         tune.fft_size, tune.tile, tune.ctas_per_sm = fft_size, tile, ctas_per_sm
-        tune.wait_limit_us, tune.window_split = wait_limit_us, window_split
+        tune.wait_limit_us, tune.window_split, tune.per_patch = wait_limit_us, window_split, int(per_patch)
         h = _VP()
         # autotune: a NULL pc_tuning asks the library to time candidate launch shapes
         _check(lib().pc_build_spectra(ctx.handle, ctypes.byref(b), ctypes.byref(g), ctypes.c_int32(radius),

@@ -33,6 +33,21 @@ pc_status cuda_fail(pc_context *ctx, cudaError_t e, const char *what) {
                 std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+ApplyParams part_params(const pc_operator *op, const Part &pt, const ApplyParams &p) {
+    ApplyParams q = p;
+    q.tiles = op->d_tiles + pt.tile_off;
+    q.color_start = op->d_color_start + pt.cs_off;
+    q.n_colors = pt.n_colors;
+    q.dep_start = op->d_dep_start + pt.ds_off;
+    q.dep = op->d_dep + pt.dep_off;
+    q.done = p.done + int64_t(pt.tile_off) * p.done_ld;
+    q.spec = static_cast<const char *>(op->d_spec) + size_t(pt.spec_off) * 2 * op->elem;
+    q.spec_stride = pt.spec_stride;
+    q.tw = pt.d_tw;
+    q.total_items = int64_t(pt.n_tiles) * p.npairs;
+    return q;
+}
+
 }  // namespace pc
 
 using pc::cuda_fail;
@@ -78,8 +93,11 @@ const char *free_operator(pc_operator *op) {
     chk(cudaFree(op->d_dep), "dependencies");
     chk(cudaFree(op->d_done), "ordering flags");
     chk(cudaFree(op->d_ctrl), "control block");
+    for (pc::Part &pt : op->parts)
+        if (pt.d_tw && pt.d_tw != op->d_tw) chk(cudaFree(pt.d_tw), "twiddles");
     chk(cudaFree(op->d_tw), "twiddles");
     chk(cudaFree(op->d_scratch), "scratch volumes");
+    chk(cudaFree(op->d_big_scratch), "256^2 scratch fields");
     chk(cudaFree(op->d_tc_ops), "tensor-core operands");
     for (auto &kv : op->tc_orders) chk(cudaFree(kv.second), "unit orders");
     chk(cudaFree(op->d_cells), "cells");
@@ -274,6 +292,47 @@ static pc_status build_operator(pc_context *ctx, const pc_box *box, const pc_gri
 
     const int r = int(g.pts.size());
     const int64_t W = 2 * radius + 1, wsz = three ? W * W * W : W * W;
+    // launch shapes: one for the whole operator, or (per_patch) one part per
+    // (P, window split) that the work model picks for the patches
+    struct Spec {
+        int P, T;
+        pc::WindowSplit split;
+        std::vector<int32_t> patches;   // empty: every patch
+    };
+    std::vector<Spec> specs;
+    if (!three && tune && tune->per_patch) {
+        std::vector<std::array<int, 2>> shapes;
+        pc::choose_patch_shapes(g, radius, prec, shapes);
+        std::map<std::pair<int, int>, std::vector<int32_t>> groups;
+        for (int k = 0; k < r; ++k) {
+            if (shapes[size_t(k)][0] == 0) return fail(ctx, PC_ERR_UNSUPPORTED, "radius too large for the FFT sizes");
+            groups[{shapes[size_t(k)][0], shapes[size_t(k)][1]}].push_back(int32_t(k));
+        }
+        for (auto &kv : groups) {
+            Spec sp;
+            sp.P = kv.first.first;
+            sp.split.nsub = kv.first.second;
+            sp.split.ws = (Wfull + sp.split.nsub - 1) / sp.split.nsub;
+            sp.T = std::min(sp.P - sp.split.ws + 1, pc::tile_cap(sp.P));
+            if (groups.size() > 1) sp.patches = kv.second;
+            specs.push_back(sp);
+        }
+        if (specs.size() == 1) {
+            P = specs[0].P;
+            split = specs[0].split;
+            T = specs[0].T;
+        }
+        for (const Spec &sp : specs) {
+            int n = 0;
+            if ((e = sp.P == pc::kBigFft ? pc::fft2d_big_configure(&n) : pc::fft2d_configure(sp.P, prec, &n, nullptr)) !=
+                cudaSuccess)
+                return cuda_fail(ctx, e, "configuring the patch kernel");
+            ctas_per_sm = std::min(ctas_per_sm, n);
+        }
+        if (ctas_per_sm < 1) return fail(ctx, PC_ERR_UNSUPPORTED, "patch kernel does not fit on an SM");
+    } else {
+        specs.push_back(Spec{P, T, split, {}});
+    }
     // weights
     std::vector<double> w;
     std::vector<int64_t> woff;
@@ -292,9 +351,30 @@ static pc_status build_operator(pc_context *ctx, const pc_box *box, const pc_gri
     // extension (Section 2.5)
     std::vector<double> phiE;
     pc::build_extension(g, radius, impulse, phiE);
-    // schedule
+    // schedule: one per launch shape, concatenated (colour classes and
+    // dependency lists local to each part)
     pc::Schedule sch;
-    pc::build_schedule(g, radius, T, split, woff, sch);
+    std::vector<pc::Part> parts;
+    for (const Spec &sp : specs) {
+        pc::Schedule one;
+        pc::build_schedule(g, radius, sp.T, sp.split, woff, one, sp.patches);
+        pc::Part pt;
+        pt.P = sp.P;
+        pt.T = sp.T;
+        pt.split = sp.split;
+        pt.patches = sp.patches;
+        pt.tile_off = int(sch.tiles.size());
+        pt.n_tiles = int(one.tiles.size());
+        pt.cs_off = int(sch.color_start.size());
+        pt.n_colors = int(one.color_start.size()) - 1;
+        pt.ds_off = int(sch.dep_start.size());
+        pt.dep_off = int(sch.dep.size());
+        sch.tiles.insert(sch.tiles.end(), one.tiles.begin(), one.tiles.end());
+        sch.color_start.insert(sch.color_start.end(), one.color_start.begin(), one.color_start.end());
+        sch.dep_start.insert(sch.dep_start.end(), one.dep_start.begin(), one.dep_start.end());
+        sch.dep.insert(sch.dep.end(), one.dep.begin(), one.dep.end());
+        parts.push_back(pt);
+    }
 
     auto *op = new (std::nothrow) pc_operator;
     if (!op) return fail(ctx, PC_ERR_NOMEM, "out of host memory");
@@ -310,7 +390,14 @@ static pc_status build_operator(pc_context *ctx, const pc_box *box, const pc_gri
     op->prec = prec;
     op->elem = prec == PC_FP64 ? 8 : 4;
     op->n_tiles = int(sch.tiles.size());
-    op->n_colors = int(sch.color_start.size()) - 1;
+    op->n_colors = specs.size() > 1 ? 0 : int(sch.color_start.size()) - 1;
+    if (specs.size() > 1) {
+        op->parts = parts;
+        for (const pc::Part &pt : parts) {
+            op->n_colors += pt.n_colors;
+            op->P = std::max(op->P, pt.P);
+        }
+    }
     op->ctas = ctx->num_sms * ctas_per_sm;
     op->ctas_per_sm = ctas_per_sm;
     op->wait_ns = tune && tune->wait_limit_us > 0 ? int64_t(tune->wait_limit_us) * 1000 : 0;
@@ -443,43 +530,94 @@ static pc_status build_operator(pc_context *ctx, const pc_box *box, const pc_gri
         return bail(e, "twiddles");
     }
     // spectra (FP64 on the device, rounded once), one per (patch, sub-window):
-    // sub-window (s0, s1) of phi_k^E placed at [0, ws)^2, zero-padded
-    const int ns = split.nsub, ws = split.ws;
-    const int nsd = three ? ns * ns * ns : ns * ns;
-    const int nspec = r * nsd;
-    const size_t wvol = three ? size_t(ws) * ws * ws : size_t(ws) * ws;
-    std::vector<double> psi;
-    const double *psi_src = phiE.data();
-    if (ns > 1) {
-        psi.assign(size_t(nspec) * wvol, 0.0);
-        const int ns2 = three ? ns : 1, ws2 = three ? ws : 1, Wf2 = three ? Wfull : 1;
-        for (int k = 0; k < r; ++k)
-            for (int s0 = 0; s0 < ns; ++s0)
-                for (int s1 = 0; s1 < ns; ++s1)
-                    for (int s2 = 0; s2 < ns2; ++s2) {
-                        double *dst = psi.data() + (size_t(k) * nsd + (s0 * ns + s1) * ns2 + s2) * wvol;
-                        for (int a = 0; a < ws && s0 * ws + a < Wfull; ++a)
-                            for (int b = 0; b < ws && s1 * ws + b < Wfull; ++b)
-                                for (int c = 0; c < ws2 && s2 * ws2 + c < Wf2; ++c)
-                                    dst[(size_t(a) * ws + b) * ws2 + c] =
-                                        phiE[size_t(k) * wsz + ((size_t(s0 * ws + a) * Wfull + (s1 * ws + b)) * Wf2 +
-                                                                (s2 * ws2 + c))];
-                    }
-        psi_src = psi.data();
-    }
+    // sub-window (s0, s1) of phi_k^E placed at [0, ws)^2, zero-padded; per
+    // launch shape, for the shape's patches in ascending order
     op->spec_stride = three ? int64_t(P / 2 + 1) * P * P : int64_t(P / 2 + 1) * P;
-    op->spec_bytes = size_t(nspec) * op->spec_stride * 2 * op->elem;
-    double *d_psi = nullptr;
-    const size_t psi_elems = size_t(nspec) * wvol;
-    e = cudaMalloc(&op->d_spec, op->spec_bytes);
-    if (e == cudaSuccess) {
-        acct += op->spec_bytes;
-        e = cudaMalloc(&d_psi, sizeof(double) * psi_elems);
+    op->spec_bytes = 0;
+    std::vector<int64_t> spec_off(specs.size(), 0);
+    for (size_t q = 0; q < specs.size(); ++q) {
+        const Spec &sp = specs[q];
+        const int nk = sp.patches.empty() ? r : int(sp.patches.size());
+        const int nsd = three ? sp.split.nsub * sp.split.nsub * sp.split.nsub : sp.split.nsub * sp.split.nsub;
+        const int64_t stride = three ? int64_t(sp.P / 2 + 1) * sp.P * sp.P : int64_t(sp.P / 2 + 1) * sp.P;
+        spec_off[q] = int64_t(op->spec_bytes / (2 * op->elem));
+        op->spec_bytes += size_t(nk) * size_t(nsd) * size_t(stride) * 2 * op->elem;
+        if (!op->parts.empty()) {
+            op->parts[q].spec_off = spec_off[q];
+            op->parts[q].spec_stride = stride;
+        }
     }
-    if (e == cudaSuccess) e = cudaMemcpy(d_psi, psi_src, sizeof(double) * psi_elems, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = three ? pc::build_spectra_3d(d_psi, nspec, ws, P, op->d_spec, d_tw64, nullptr)
-                  : pc::build_spectra_2d(d_psi, nspec, ws, P, prec, op->d_spec, d_tw64, nullptr);
+    double *d_psi = nullptr;
+    e = cudaMalloc(&op->d_spec, op->spec_bytes);
+    if (e == cudaSuccess) acct += op->spec_bytes;
+    for (size_t q = 0; q < specs.size() && e == cudaSuccess; ++q) {
+        const Spec &sp = specs[q];
+        const int ns = sp.split.nsub, ws = sp.split.ws;
+        const int nk = sp.patches.empty() ? r : int(sp.patches.size());
+        const int nsd = three ? ns * ns * ns : ns * ns;
+        const int nspec = nk * nsd;
+        const size_t wvol = three ? size_t(ws) * ws * ws : size_t(ws) * ws;
+        std::vector<double> psi;
+        const double *psi_src = phiE.data();
+        if (ns > 1 || !sp.patches.empty()) {
+            psi.assign(size_t(nspec) * wvol, 0.0);
+            const int ns2 = three ? ns : 1, ws2 = three ? ws : 1, Wf2 = three ? Wfull : 1;
+            for (int qk = 0; qk < nk; ++qk) {
+                const int k = sp.patches.empty() ? qk : sp.patches[size_t(qk)];
+                for (int s0 = 0; s0 < ns; ++s0)
+                    for (int s1 = 0; s1 < ns; ++s1)
+                        for (int s2 = 0; s2 < ns2; ++s2) {
+                            double *dst = psi.data() + (size_t(qk) * nsd + (s0 * ns + s1) * ns2 + s2) * wvol;
+                            for (int a = 0; a < ws && s0 * ws + a < Wfull; ++a)
+                                for (int b = 0; b < ws && s1 * ws + b < Wfull; ++b)
+                                    for (int c = 0; c < ws2 && s2 * ws2 + c < Wf2; ++c)
+                                        dst[(size_t(a) * ws + b) * ws2 + c] =
+                                            phiE[size_t(k) * wsz + ((size_t(s0 * ws + a) * Wfull + (s1 * ws + b)) *
+                                                                        Wf2 +
+                                                                    (s2 * ws2 + c))];
+                        }
+            }
+            psi_src = psi.data();
+        }
+        const size_t psi_elems = size_t(nspec) * wvol;
+        cudaFree(d_psi);
+        d_psi = nullptr;
+        e = cudaMalloc(&d_psi, sizeof(double) * psi_elems);
+        // the twiddles of this shape's P (FP64 for the build; compute precision for the kernel)
+        double2 *tw64 = d_tw64;
+        std::vector<double> twq;
+        if (e == cudaSuccess && sp.P != P) {
+            twq = twiddles64(sp.P);
+            size_t dummy = 0;
+            e = upload(reinterpret_cast<double **>(&tw64), twq.data(), twq.size(), dummy);
+            if (e == cudaSuccess && !op->parts.empty()) {
+                if (prec == PC_FP64) {
+                    e = upload(reinterpret_cast<double **>(&op->parts[q].d_tw), twq.data(), twq.size(), acct);
+                } else {
+                    std::vector<float> twf(twq.begin(), twq.end());
+                    e = upload(reinterpret_cast<float **>(&op->parts[q].d_tw), twf.data(), twf.size(), acct);
+                }
+            }
+        } else if (!op->parts.empty()) {
+            op->parts[q].d_tw = op->d_tw;
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(d_psi, psi_src, sizeof(double) * psi_elems, cudaMemcpyHostToDevice);
+        char *dst = static_cast<char *>(op->d_spec) + size_t(spec_off[q]) * 2 * op->elem;
+        if (e == cudaSuccess)
+            e = three ? pc::build_spectra_3d(d_psi, nspec, ws, sp.P, dst, tw64, nullptr)
+                      : pc::build_spectra_2d(d_psi, nspec, ws, sp.P, prec, dst, tw64, nullptr);
+        if (tw64 != d_tw64) {
+            const cudaError_t e2 = cudaDeviceSynchronize();
+            cudaFree(tw64);
+            if (e == cudaSuccess) e = e2;
+        }
+    }
+    for (const pc::Part &pt : op->parts)
+        if (e == cudaSuccess && pt.P == pc::kBigFft && !op->d_big_scratch) {
+            const size_t sb = pc::fft2d_big_scratch_bytes(op->ctas);
+            e = cudaMalloc(&op->d_big_scratch, sb);
+            if (e == cudaSuccess) acct += sb;
+        }
     if (e == cudaSuccess && three && prec == PC_FP32) {
         const size_t sb = pc::fft3d_scratch_bytes(op->ctas);
         e = cudaMalloc(&op->d_scratch, sb);
@@ -533,6 +671,7 @@ pc_status pc_operator_info_get(const pc_operator *op, pc_operator_info *info) {
     info->autotuned = op->autotuned ? 1 : 0;
     info->tuned_candidates = op->tuned_candidates;
     info->tuned_ms = op->tuned_ms;
+    info->num_parts = op->parts.empty() ? 1 : int32_t(op->parts.size());
     return PC_OK;
 }
 
@@ -671,6 +810,29 @@ static pc_status prepare_batch_impl(pc_operator *op, int32_t nrhs) {
     return st;
 }
 
+// The parts of a per_patch operator, one launch each after the zero-fill
+// (which also reset the claim counter for the first): each part's items run
+// in its own colour order, and the parts add one after another, so y is
+// still summed in a fixed order.
+static pc_status apply_parts(pc_operator *op, const pc::ApplyParams &p, cudaStream_t s, bool adjoint) {
+    cudaError_t e = cudaEventRecord(op->ev_begin, s);
+    for (size_t q = 0; q < op->parts.size() && e == cudaSuccess; ++q) {
+        const pc::ApplyParams pq = pc::part_params(op, op->parts[q], p);
+        if (q > 0) e = cudaMemsetAsync(p.ctrl, 0, sizeof(unsigned long long), s);   // claim counter
+        if (e != cudaSuccess) break;
+        const int ctas = int(std::min<int64_t>(op->ctas, pq.total_items));
+        if (ctas > 0)
+            e = op->parts[q].P == pc::kBigFft ? pc::launch_fft2d_big(pq, ctas, op->d_big_scratch, s, adjoint)
+                                              : pc::launch_fft2d(pq, op->parts[q].P, op->prec, ctas, s, adjoint);
+    }
+    if (e != cudaSuccess) return cuda_fail(op->ctx, e, "launching the patch kernel");
+    cudaEventRecord(op->ev_end, s);
+    op->timed = true;
+    op->last_stream = s;
+    op->launches_last = 1 + int64_t(op->parts.size());
+    return PC_OK;
+}
+
 static pc_status apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
                                pc_stream stream, bool adjoint) {
     if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
@@ -732,6 +894,7 @@ static pc_status apply_batched(pc_operator *op, int32_t nrhs, const void *x, int
     if (split3d) return apply_split3d(op, p, s);
     cudaError_t e = pc::launch_zero(p, op->N, op->prec, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the zero kernel");
+    if (!op->parts.empty()) return apply_parts(op, p, s, adjoint);
     const int ctas = int(std::min<int64_t>(op->ctas, p.total_items));
     cudaEventRecord(op->ev_begin, s);
     e = op->d == 3 ? pc::launch_fft3d(p, ctas, op->d_scratch, s, adjoint)
@@ -1065,7 +1228,8 @@ pc_status pc_apply_host(pc_operator *op, int32_t nrhs, const void *x, int64_t ld
         // longer), at most kMaxSegments of them
         int32_t c = even(std::max<int32_t>(chunk > 0 ? chunk : (nrhs + 3) / 4,
                                            (nrhs + pc::kMaxSegments - 1) / pc::kMaxSegments));
-        if (segmented_host_apply()) return apply_host_segmented(op, nrhs, x, ldx, y, ldy, adjoint == 1, c, s);
+        if (segmented_host_apply() && op->parts.empty())
+            return apply_host_segmented(op, nrhs, x, ldx, y, ldy, adjoint == 1, c, s);
         return apply_host_chunked(op, nrhs, x, ldx, y, ldy, adjoint == 1, c, s);
     }
     // 3D: the chunked pipeline, by default in one chunk (the 3D patch kernels
@@ -1141,6 +1305,8 @@ pc_status pc_apply_plain(pc_operator *op, int32_t nrhs, const void *x, int64_t l
     if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
     pc_context *ctx = op->ctx;
     if (op->prec == PC_FP64) return fail(ctx, PC_ERR_UNSUPPORTED, "the plain path covers FP32 spectra (FP32, BF16X3)");
+    if (!op->parts.empty())
+        return fail(ctx, PC_ERR_UNSUPPORTED, "the plain path covers operators with one launch shape");
     if (nrhs < 0) return fail(ctx, PC_ERR_ARG, "nrhs < 0");
     if (nrhs == 0) return PC_OK;
     if (!x || !y) return fail(ctx, PC_ERR_ARG, "null x or y");

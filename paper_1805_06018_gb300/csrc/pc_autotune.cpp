@@ -66,7 +66,22 @@ double model_cost(const Geometry &g, int R, int P, int nsub, int T) {
     return lines * line;
 }
 
-// Candidate launch shapes, best modelled first, at most `keep` of them.
+// Modelled line-FFT work of patch k alone at shape (P, nsub, T), 2D.
+double patch_cost(const Geometry &g, int k, int R, int P, int nsub, int T) {
+    const int W = 2 * R + 1, ws = (W + nsub - 1) / nsub;
+    const auto t0 = tile_extents(g.bb_hi[k][0] - g.bb_lo[k][0] + 1, T);
+    const auto t1 = tile_extents(g.bb_hi[k][1] - g.bb_lo[k][1] + 1, T);
+    double lines = 0;
+    for (int64_t a0 : t0)
+        for (int s = 0; s < nsub; ++s) {
+            const int w0 = std::min(ws, W - s * ws);
+            lines += double(t1.size()) * nsub * double(a0 + 2 * P + (a0 + w0 - 1));
+        }
+    return lines * double(P) * std::log2(double(P));
+}
+
+// Candidate launch shapes, best modelled first, at most `keep` of them, and
+// in 2D the per-patch shape choice when the patches differ.
 std::vector<Candidate> candidates(const Geometry &g, int R, pc_precision prec, int keep) {
     std::vector<Candidate> out;
     const bool three = g.d == 3;
@@ -94,6 +109,18 @@ std::vector<Candidate> candidates(const Geometry &g, int R, pc_precision prec, i
         }
     std::stable_sort(out.begin(), out.end(), [](const Candidate &a, const Candidate &b) { return a.cost < b.cost; });
     if (int(out.size()) > keep) out.resize(size_t(keep));
+    if (!three) {
+        // one shape per patch (a part per shape), when the patches differ in their best shape
+        std::vector<std::array<int, 2>> shapes;
+        choose_patch_shapes(g, R, prec, shapes);
+        bool mixed = false;
+        for (const auto &sh : shapes) mixed = mixed || sh != shapes[0];
+        if (mixed) {
+            Candidate c;
+            c.t.per_patch = 1;
+            out.push_back(c);
+        }
+    }
     return out;
 }
 
@@ -192,6 +219,26 @@ pc_status search(pc_context *ctx, const pc_box *box, const pc_grid *grid, int32_
 }
 
 }  // namespace
+
+void choose_patch_shapes(const Geometry &g, int R, pc_precision prec, std::vector<std::array<int, 2>> &shape) {
+    const int W = 2 * R + 1;
+    shape.assign(g.pts.size(), {0, 0});
+    std::vector<int> Ps = prec == PC_FP64 ? std::vector<int>{64} : std::vector<int>{64, 128, kBigFft};
+    for (size_t k = 0; k < g.pts.size(); ++k) {
+        double best = 1e300;
+        for (int P : Ps)
+            for (int nsub = 1; nsub <= 8; ++nsub) {
+                const int ws = (W + nsub - 1) / nsub;
+                const int T = std::min(P - ws + 1, tile_cap(P));
+                if (T < 8) continue;
+                const double c = patch_cost(g, int(k), R, P, nsub, T);
+                if (c < best * 0.999) {
+                    best = c;
+                    shape[k] = {P, nsub};
+                }
+            }
+    }
+}
 
 pc_status autotune_build(pc_context *ctx, const pc_box *box, const pc_grid *grid, int32_t radius,
                          const double *impulse, const double *weights, pc_precision prec, pc_operator **out) {

@@ -113,6 +113,7 @@ pc_status pc_block_plan_create_many(pc_operator *op, int32_t nblocks, const int6
     if (nblocks < 1) return fail(ctx, PC_ERR_ARG, "nblocks must be >= 1");
     if (!t_lo || !t_hi || !s_lo || !s_hi) return fail(ctx, PC_ERR_ARG, "null box bound");
     if (adjoint != 0 && adjoint != 1) return fail(ctx, PC_ERR_ARG, "adjoint must be 0 or 1");
+    if (!op->parts.empty()) return fail(ctx, PC_ERR_UNSUPPORTED, "block plans cover operators with one launch shape");
     if (op->prec == PC_BF16X3) return fail(ctx, PC_ERR_UNSUPPORTED, "block applies cover FP32 and FP64 operators");
     const int d = op->d;
     for (int32_t i = 0; i < nblocks; ++i)

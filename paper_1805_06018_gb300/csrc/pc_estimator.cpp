@@ -61,6 +61,8 @@ pc_status pc_estimator_update(pc_estimator *est, pc_operator *op, double *eta, i
     if (op->d != 2 || op->shape[0] != est->shape[0] || op->shape[1] != est->shape[1])
         return fail(ctx, PC_ERR_ARG, "the operator's box differs from the estimator's");
     if (op->prec != est->prec) return fail(ctx, PC_ERR_ARG, "the operator's precision differs from the estimator's");
+    if (!op->parts.empty())
+        return fail(ctx, PC_ERR_UNSUPPORTED, "the incremental estimator covers operators with one launch shape");
     DeviceGuard dg(ctx->device);
     if (!dg.ok) return fail(ctx, PC_ERR_CUDA, "cannot select the context's device");
     cudaStream_t s = static_cast<cudaStream_t>(stream);

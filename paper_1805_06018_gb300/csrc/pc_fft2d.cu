@@ -78,9 +78,12 @@ __device__ __forceinline__ int phase_b_col(int line, int rnd) {
 }
 
 // colour-major order: item -> (tile index, right-hand-side pair).  `cs` holds
-// the colour offsets (shared-memory copy when there are few colours).
-__device__ __forceinline__ void decode_item(const ApplyParams &p, const int *cs, int64_t item, int &ti, int &pair) {
-    int c = 0;
+// the colour offsets (shared-memory copy when there are few colours).  The
+// search starts at colour `c` (in: a colour <= the item's, out: the item's):
+// a CTA's claims only increase, so its previous item's colour is a valid
+// start and the search is a step or two even with hundreds of colours.
+__device__ __forceinline__ void decode_item(const ApplyParams &p, const int *cs, int64_t item, int &ti, int &pair,
+                                            int &c) {
     while (int64_t(cs[c + 1]) * p.npairs <= item) ++c;
     const int64_t base = int64_t(cs[c]) * p.npairs;
     const int ntc = cs[c + 1] - cs[c];
@@ -97,10 +100,10 @@ __device__ __forceinline__ void prefetch_l2(const void *ptr) {
 // (forward), or the right-hand sides over the output box clipped to the box x
 // lives on (adjoint).
 template <typename T, bool ADJ>
-__device__ __forceinline__ void prefetch_item(const ApplyParams &p, const int *cs, int64_t item) {
+__device__ __forceinline__ void prefetch_item(const ApplyParams &p, const int *cs, int64_t item, int c) {
     if (item >= p.total_items) return;
     int ti, pair;
-    decode_item(p, cs, item, ti, pair);
+    decode_item(p, cs, item, ti, pair, c);
     const Tile tile = p.tiles[ti];
     constexpr int per_line = 128 / int(sizeof(T));
     const int b0 = 2 * pair;
@@ -197,6 +200,7 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
     const C zero{T(0), T(0)};
     uint32_t phase = 0;
     int cur_seg = -1;
+    int chint = 0;   // colour of this CTA's last item in the current segment
     const int *s_cstart = s_cstart_buf;
     // the last finished item's flag, published (by thread 0) once its
     // reductions have landed
@@ -265,6 +269,7 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
         }
         if (segidx != cur_seg) {
             cur_seg = segidx;
+            chint = 0;
             if (lp.desc) {
                 const uint32_t *src = reinterpret_cast<const uint32_t *>(lp.desc->seg + cur_seg);
                 for (int q = threadIdx.x; q < int(sizeof(Segment) / 4); q += blockDim.x)
@@ -299,7 +304,7 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
             pair = int(local / ntc);
             ti = s_cstart[c] + int(local % ntc);
         } else {
-            decode_item(p, s_cstart, item, ti, pair);
+            decode_item(p, s_cstart, item, ti, pair, chint);
         }
         const Tile tile = p.tiles[ti];
         if (threadIdx.x == NT - 1) s_next_buf[par ^ 1] = int64_t(atomicAdd(counter, 1ull));
@@ -415,7 +420,7 @@ __global__ void __launch_bounds__(KCfg<T, P>::threads, 1) fft2d_kernel(const Lau
         if (threadIdx.x == 0) publish_pending();
 
         if ((!MULTI || nrun == 0) && s_next_buf[par ^ 1] - s_seg.item_begin < p.total_items)
-            prefetch_item<T, ADJ>(p, s_cstart, s_next_buf[par ^ 1] - s_seg.item_begin);
+            prefetch_item<T, ADJ>(p, s_cstart, s_next_buf[par ^ 1] - s_seg.item_begin, chint);
 
         // ---------------- phase B: column FFT, spectral product, inverse column FFT
         // If the spectrum copy does not land within the limit, the item is

@@ -39,8 +39,9 @@ struct Item3 {
     Tile tile;
 };
 
-__device__ __forceinline__ Item3 decode_item3(const ApplyParams &p, int64_t item) {
-    int c = 0;
+// `c`: a colour <= the item's to start the search from (a CTA's claims only
+// increase, so its previous item's colour); updated to the item's colour
+__device__ __forceinline__ Item3 decode_item3(const ApplyParams &p, int64_t item, int &c) {
     while (int64_t(p.color_start[c + 1]) * p.npairs <= item) ++c;
     const int64_t base = int64_t(p.color_start[c]) * p.npairs;
     const int ntc = p.color_start[c + 1] - p.color_start[c];
@@ -304,6 +305,7 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_kernel(const ApplyParams 
     __shared__ int64_t s_item;
     const Lines3 L(static_cast<const float2 *>(p.tw));
     float2 *G = scratch + int64_t(blockIdx.x) * kP3 * kP3 * kP3;
+    int chint = 0;
     for (;;) {
         // a launch whose waits have given up (status word set) takes no more items
         if (threadIdx.x == 0)
@@ -313,7 +315,7 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_kernel(const ApplyParams 
         __syncthreads();
         const int64_t item = s_item;
         if (item >= p.total_items) break;
-        const Item3 it = decode_item3(p, item);
+        const Item3 it = decode_item3(p, item, chint);
         phase1_3d<ADJ>(p, it, G, S, L);
         phase2_3d<ADJ>(p, it, G, S, L);
         if (!wait_deps_3d(p, it, 1)) break;
@@ -330,8 +332,9 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase1_kernel(const Apply
                                                                      int64_t c0, int64_t c1) {
     __shared__ __align__(16) float2 S[kP3 * kP3];
     const Lines3 L(static_cast<const float2 *>(p.tw));
+    int chint = 0;
     for (int64_t item = c0 + blockIdx.x; item < c1; item += gridDim.x) {
-        const Item3 it = decode_item3(p, item);
+        const Item3 it = decode_item3(p, item, chint);
         phase1_3d<false>(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L);
     }
 }
@@ -349,6 +352,7 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase3_kernel(const Apply
     __shared__ int64_t s_piece;
     constexpr int NG = kPhase3Groups;
     const Lines3 L(static_cast<const float2 *>(p.tw));
+    int chint = 0;
     for (;;) {
         if (threadIdx.x == 0)
             s_piece = ld_volatile_s32(p.ctrl + 2) != 0
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase3_kernel(const Apply
         if (piece >= c1 * NG) break;
         const int64_t item = piece / NG;
         const int g = int(piece % NG);
-        const Item3 it = decode_item3(p, item);
+        const Item3 it = decode_item3(p, item, chint);
         if (!wait_deps_3d(p, it, NG)) break;
         const int L0 = it.tile.in_ext[0] + it.tile.kext[0] - 1;
         phase3_3d<false>(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L, (L0 * g) / NG, (L0 * (g + 1)) / NG,

@@ -248,13 +248,15 @@ void build_extension(const Geometry &g, int R, const double *phi, std::vector<do
 }
 
 void build_schedule(const Geometry &g, int R, int T, const WindowSplit &wsp, const std::vector<int64_t> &w_off,
-                    Schedule &s) {
+                    Schedule &s, const std::vector<int32_t> &patches) {
     const int r = int(g.pts.size());
     const int W = 2 * R + 1;
     int nsubd = 1;
     for (int a = 0; a < g.d; ++a) nsubd *= wsp.nsub;
     std::vector<Tile> tiles;
-    for (int k = 0; k < r; ++k) {
+    const int nk = patches.empty() ? r : int(patches.size());
+    for (int q = 0; q < nk; ++q) {
+        const int k = patches.empty() ? q : patches[size_t(q)];
         int64_t ext[3] = {1, 1, 1}, nt[3] = {1, 1, 1};
         for (int a = 0; a < g.d; ++a) {
             ext[a] = g.bb_hi[k][a] - g.bb_lo[k][a] + 1;
@@ -287,7 +289,7 @@ void build_schedule(const Geometry &g, int R, int T, const WindowSplit &wsp, con
                     // one work unit per kernel sub-window
                     for (int sidx = 0; sidx < nsubd; ++sidx) {
                         Tile u = t;
-                        u.spec = k * nsubd + sidx;
+                        u.spec = q * nsubd + sidx;
                         int rest = sidx;
                         for (int a = g.d - 1; a >= 0; --a) {
                             const int sa = rest % wsp.nsub;

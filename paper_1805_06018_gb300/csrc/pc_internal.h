@@ -89,8 +89,28 @@ struct Schedule {
 // overlapping tiles of lower colour.  Output pixels of the forward apply (and
 // of the adjoint, which adds into the input boxes) then receive their
 // contributions in colour order.
+// With a non-empty `patches`, only those patches are tiled, and tile.spec
+// numbers their spectra by position in the list (q * nsub^d + sub-window).
 void build_schedule(const Geometry &g, int R, int T, const WindowSplit &ws, const std::vector<int64_t> &w_off,
-                    Schedule &s);
+                    Schedule &s, const std::vector<int32_t> &patches = {});
+
+// One launch shape of an operator whose patches use different ones: its
+// tiles are [tile_off, tile_off + n_tiles) of the operator's tile array (with
+// the tiles' own colour classes and dependency lists, indices local to the
+// part), its spectra start at spec_off complex values into the operator's
+// spectra.  Each part is one launch of the patch kernel.
+struct Part {
+    int P = 0, T = 0;
+    WindowSplit split;
+    std::vector<int32_t> patches;    // the sample points k of the part, ascending
+    int tile_off = 0, n_tiles = 0;
+    int cs_off = 0, n_colors = 0;    // colour offsets at d_color_start + cs_off ([n_colors + 1])
+    int ds_off = 0;                  // dependency starts at d_dep_start + ds_off ([n_tiles + 1])
+    int dep_off = 0;                 // dependencies at d_dep + dep_off
+    int64_t spec_off = 0, spec_stride = 0;
+    void *d_tw = nullptr;            // W_P^j in compute precision (owned by the operator)
+    int ctas = 0;
+};
 
 // Where the 2D adjoint kernel's store mode writes a tile's unweighted
 // correlation block: element (b, row, col) of the tile's input box goes to
@@ -277,6 +297,10 @@ struct pc_operator {
     std::vector<uint64_t> phiE_hash;
     // plain-path scratch (lazily allocated)
     void *plain = nullptr;
+    // launch shapes per patch group (2D, pc_tuning.per_patch): empty for an
+    // operator with one shape, which its own fields describe
+    std::vector<pc::Part> parts;
+    void *d_big_scratch = nullptr;   // per-CTA 256^2 scratch fields of a part with P = 256
 };
 
 // Incremental randomized estimator (Algorithm 1): the probes Z and Y = A* Z
@@ -355,6 +379,12 @@ cudaError_t launch_round(const LaunchDesc *d_desc, unsigned long long *counter, 
                          uint32_t *host_flags, int ctas, size_t smem, cudaStream_t s, int P = 128,
                          pc_precision prec = PC_FP32, bool adjoint = false);
 cudaError_t fft2d_configure(int P, pc_precision prec, int *ctas_per_sm, size_t *smem);
+// 256 x 256 patch FFTs (pc_fft2d_big.cu), FP32, single launches: the three
+// phases around a per-CTA scratch field of fft2d_big_scratch_bytes(1) bytes
+cudaError_t fft2d_big_configure(int *ctas_per_sm);
+size_t fft2d_big_scratch_bytes(int ctas);
+cudaError_t launch_fft2d_big(const ApplyParams &p, int ctas, void *scratch, cudaStream_t s, bool adjoint);
+constexpr int kBigFft = 256;
 // d_psi: [nspec][W][W] FP64 windows placed at [0, W)^2; spectra [nspec][P/2+1][P]
 cudaError_t build_spectra_2d(const double *d_psi, int nspec, int W, int P, pc_precision prec, void *d_spec,
                              const double2 *d_tw64, cudaStream_t s);
@@ -393,6 +423,17 @@ cudaError_t launch_entries(pc_precision prec, int64_t n, const int64_t *rows, co
                            const EntryData &e, const void *w, cudaStream_t s);
 // grow the on-demand device buffers of an apply of nrhs vectors (pc_api.cpp)
 pc_status prepare_batch(pc_operator *op, int32_t nrhs);
+// The apply parameters of one part of a per_patch operator: `p` with the
+// part's tiles, colour classes, dependency lists, ordering flags, spectra,
+// twiddles and item count (pc_api.cpp).
+ApplyParams part_params(const pc_operator *op, const Part &pt, const ApplyParams &p);
+// Per-patch launch shape (pc_autotune.cpp): for each sample point k the FFT
+// size and kernel-window split that the line-FFT work model prefers for
+// bbox(U_k) (2D; P in {64, 128}, and 256 for FP32); shape[k] = {P, nsub}.
+// Tile extent of a window split ws at FFT size P: min(P - ws + 1, cap), cap
+// = 2P/3 for the fused kernel's row staging, P for the 256^2 kernel.
+inline int tile_cap(int P) { return P == kBigFft ? P : (2 * P) / 3; }
+void choose_patch_shapes(const Geometry &g, int R, pc_precision prec, std::vector<std::array<int, 2>> &shape);
 // autotuner (pc_autotune.cpp): pc_build_spectra with a NULL pc_tuning
 pc_status autotune_build(pc_context *ctx, const pc_box *box, const pc_grid *grid, int32_t radius,
                          const double *impulse, const double *weights, pc_precision prec, pc_operator **out);

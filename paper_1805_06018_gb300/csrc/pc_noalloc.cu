@@ -179,8 +179,20 @@ extern "C" pc_status pc_apply_batched_noalloc(pc_operator *op, int32_t nrhs, con
             p.tw = op->d_tw;
             p.wait_ns = op->wait_ns;
             p.total_items = int64_t(op->n_tiles) * npairs;
-            const int ctas = int(std::min<int64_t>(op->ctas, p.total_items));
-            e = pc::launch_fft2d(p, op->P, op->prec, ctas, s);
+            if (op->parts.empty()) {
+                const int ctas = int(std::min<int64_t>(op->ctas, p.total_items));
+                e = pc::launch_fft2d(p, op->P, op->prec, ctas, s);
+            }
+            // a per_patch operator: its parts one after another, the claim
+            // counter reset between them (noalloc_prepare reset it for the first)
+            for (size_t q = 0; q < op->parts.size() && e == cudaSuccess; ++q) {
+                const pc::ApplyParams pq = pc::part_params(op, op->parts[q], p);
+                if (q > 0) e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), s);
+                const int ctas = int(std::min<int64_t>(op->ctas, pq.total_items));
+                if (e == cudaSuccess && ctas > 0)
+                    e = op->parts[q].P == pc::kBigFft ? pc::launch_fft2d_big(pq, ctas, op->d_big_scratch, s, false)
+                                                      : pc::launch_fft2d(pq, op->parts[q].P, op->prec, ctas, s);
+            }
         }
         if (e != cudaSuccess) st = fail(PC_ERR_CUDA, std::string("launching the apply: ") + cudaGetErrorString(e));
     }

@@ -460,7 +460,7 @@ pc_status pc_serve_submit(pc_server *s, pc_operator *op, int32_t nrhs, const voi
     if (op->ctx->device != s->ctx->device) return srv_fail(s, PC_ERR_ARG, "operator lives on another device");
     // the multi-request kernel covers 2D FP32 operators with fft_size 128;
     // every other operator runs its requests alone through its own apply
-    const bool solo = op->d != 2 || op->prec != PC_FP32 || op->P != 128;
+    const bool solo = op->d != 2 || op->prec != PC_FP32 || op->P != 128 || !op->parts.empty();
     if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) % op->elem)
         return srv_fail(s, PC_ERR_ARG, "x and y must be aligned to the element size");
     auto *r = new Request;
