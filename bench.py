@@ -71,10 +71,13 @@ WORKLOADS = {
                         "operator for a 4x4 partition into 128^2 boxes (every pair of boxes that touch, itself "
                         "included), 64 RHS per block, one plan in two launches", "fft2d_kernel<float,128>",
                         ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_overlap.cuh"]),
-    "adaptive_1024": ("1024x1024 adaptive quadtree (r=1579), heavy-tailed R=64 (2x2 kernel sub-windows), "
-                      "128^2 patch FFTs, 32 RHS", "fft2d_kernel<float,128>",
+    "adaptive_1024": ("1024x1024 adaptive quadtree (r=1579), heavy-tailed R=64, per-patch FFT sizes "
+                      "(128^2 with 2x2 kernel sub-windows, 256^2) chosen by the work model, 32 RHS",
+                      "fft2d_kernel<float,128>",
                       ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_overlap.cuh"]),
 }
+# launch-shape arguments of a workload's operator (the rest take the defaults)
+WORKLOAD_TUNING = {"adaptive_1024": {"per_patch": True}}
 # workload name -> (operator configuration, precision)
 WORKLOAD_OPERATOR = {"fp64_64": ("fp64_64", "fp64"), "fp32_512": ("fp32_512", "fp32"), "fp32_512_adjoint": ("fp32_512", "fp32"),
                      "fp32_512_estimator": ("fp32_512", "fp32"), "fp32_512_block": ("fp32_512", "fp32"),
@@ -662,8 +665,11 @@ def serve_operators(pcg, ctx, with_3d=True):
     ops = []
     for name, shape, cells, kern, R in wls:
         pts = pcg.pc_sample_points(shape, cells)
+        # regular grids: 128^2 patch FFTs, batched with the other requests; the
+        # adaptive operator: per-patch FFT sizes (its requests then run alone)
+        tune = WORKLOAD_TUNING.get(name, {"fft_size": 128})
         ops.append((name, pcg.Operator(ctx, shape, cells, R, workloads.impulse_windows(shape, pts, kern),
-                                       precision="fp32", fft_size=128)))
+                                       precision="fp32", **tune)))
     if with_3d:
         # 3D: 64^3 (5^3 grid), 96^3 (7^3), 128^3 (8^3, the 3D workload), 160^3
         # (10^3); axis-aligned Gaussian, sigma in [1.5, 5], R = 12, 64^3 patches;
@@ -775,6 +781,8 @@ def run_serve(args):
             "dtype": "f32", "data": "synthetic", "saturated": m["saturated"], "loads": m["loads"],
             "plain_gpu_rhs_per_s": m.get("plain_gpu_rhs_per_s"),
             "config": {"operators": [n for n, _ in ops], "rhs_per_request": "U[1,64]", "budget_bytes": 120 << 30,
+                       "shapes": {n: {k: op.info()[k] for k in ("fft_size", "window_split", "num_parts")}
+                                  for n, op in ops},
                        "arrivals": "Poisson at 50/80/95% of the saturated rate",
                        "modes": "2D FP32" if args.serve_2d else "2D FP32; 3D FP32 and BF16x3 (tensor-core first axis)",
                        "requests_after_warmup": m["requests_after_warmup"],
@@ -792,6 +800,8 @@ def roofline_of(pcg, wl, info, precision, kms, workload):
     import torch
     staged = precision == "bf16x3"
     kname = WORKLOADS[workload][1]
+    if info.get("num_parts", 1) > 1:
+        kname = "fft2d kernels of the %d per-patch parts (one launch each)" % info["num_parts"]
     lo, hi = pcg.pc_neighbourhood_boxes(wl.shape, wl.cells)
     flops, bytes_ = algorithmic_work(wl.shape, lo, hi, wl.radius, wl.nrhs, info["spectra_bytes"],
                                      elem=8 if precision == "fp64" else 4)
@@ -870,7 +880,7 @@ def suite_apply(pcg, ctx, name, steps, warmup, flush, plain_steps=2, accuracy_po
     desc = WORKLOADS[name][0]
     pts = pcg.pc_sample_points(wl.shape, wl.cells)
     op = pcg.Operator(ctx, wl.shape, wl.cells, wl.radius, workloads.impulse_windows(wl.shape, pts, wl.kernel),
-                      precision=precision)
+                      precision=precision, **WORKLOAD_TUNING.get(name, {}))
     info = op.info()
     x_host = workloads.rhs(wl.rhs_seed, wl.nrhs, wl.shape)
     x = torch.from_numpy(x_host).cuda()
@@ -900,7 +910,7 @@ def suite_apply(pcg, ctx, name, steps, warmup, flush, plain_steps=2, accuracy_po
                             "per": "apply of %d RHS" % wl.nrhs},
              "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "f32+bf16x3"}[precision],
              "fft": info["fft_size"], "tile": info["tile"], "num_tiles": info["num_tiles"],
-             "num_colors": info["num_colors"], "window_split": info["window_split"]}
+             "num_colors": info["num_colors"], "window_split": info["window_split"], "num_parts": info["num_parts"]}
     # accuracy: the oracle (FP64, direct sums) at sampled output points, all RHS
     rng = np.random.default_rng(5)
     npts = min(wl.n, accuracy_points)
@@ -968,6 +978,8 @@ def suite(pcg, ctx, args):
             ops = serve_operators(pcg, ctx, with_3d=False)
             m = serve_measure(pcg, ctx, ops, args.suite_serve_requests, np.random.default_rng(17))
             m["config"] = {"operators": [n for n, _ in ops], "rhs_per_request": "U[1,64]", "budget_bytes": 120 << 30,
+                           "shapes": {n: {k: op.info()[k] for k in ("fft_size", "window_split", "num_parts")}
+                                      for n, op in ops},
                            "arrivals": "Poisson at 50/80/95% of the saturated rate",
                            "plain_gpu": "the saturated request set, one request after another"}
             out["serving_2d_mix"] = m
@@ -1029,7 +1041,8 @@ def main():
     pts = pcg.pc_sample_points(wl.shape, wl.cells)
     phi = workloads.impulse_windows(wl.shape, pts, wl.kernel)
     ctx = pcg.Context(local)
-    op = pcg.Operator(ctx, wl.shape, wl.cells, wl.radius, phi, precision=precision)
+    op = pcg.Operator(ctx, wl.shape, wl.cells, wl.radius, phi, precision=precision,
+                      **WORKLOAD_TUNING.get(args.workload, {}))
     staged = precision == "bf16x3"
     info = op.info()
     x_host = workloads.rhs(wl.rhs_seed, wl.nrhs, wl.shape)

@@ -107,7 +107,7 @@ typedef struct {
     int32_t window_split;    /* kernel sub-windows per axis: [-R, R] cut into window_split
                                 pieces with their own spectra, an exact rewrite of the sum
                                 (0: the count that minimises FFT work per input pixel) */
-    int32_t per_patch;       /* 2D: 1 = each patch takes the FFT size (64 or 128) and
+    int32_t per_patch;       /* 2D: 1 = each patch takes the FFT size (FP32: 128 or 256) and
                                 window split that a model of the line-FFT work prefers for
                                 its own bbox(U_k); the patches of each shape form a part,
                                 applied by its own launch (fft_size, tile and window_split
@@ -608,7 +608,7 @@ pc_status pc_serve_destroy(pc_server *srv);
  * batch of nrhs vectors on each with CUDA events on a private stream; a
  * candidate whose build, apply or device status fails is dropped.  Writes the
  * fastest into *best (*best_ms: its time per batch).  Same operator arguments
- * as pc_build_spectra, which runs the same search (nrhs = 8 in 2D, 4 in 3D)
+ * as pc_build_spectra, which runs the same search (nrhs = 32 in 2D, 8 in 3D)
  * when its pc_tuning is NULL and keeps the winning operator. */
 pc_status pc_autotune(pc_context *ctx, const pc_box *box, const pc_grid *grid, int32_t radius, const double *impulse,
                       const double *weights, pc_precision prec, int32_t nrhs, pc_tuning *best, double *best_ms);

@@ -390,8 +390,10 @@ static pc_status build_operator(pc_context *ctx, const pc_box *box, const pc_gri
     op->prec = prec;
     op->elem = prec == PC_FP64 ? 8 : 4;
     op->n_tiles = int(sch.tiles.size());
-    op->n_colors = specs.size() > 1 ? 0 : int(sch.color_start.size()) - 1;
-    if (specs.size() > 1) {
+    // parts: several shapes, or the 256^2 kernel (which runs as a part of its own)
+    const bool use_parts = specs.size() > 1 || specs[0].P == pc::kBigFft;
+    op->n_colors = use_parts ? 0 : int(sch.color_start.size()) - 1;
+    if (use_parts) {
         op->parts = parts;
         for (const pc::Part &pt : parts) {
             op->n_colors += pt.n_colors;

@@ -223,7 +223,11 @@ pc_status search(pc_context *ctx, const pc_box *box, const pc_grid *grid, int32_
 void choose_patch_shapes(const Geometry &g, int R, pc_precision prec, std::vector<std::array<int, 2>> &shape) {
     const int W = 2 * R + 1;
     shape.assign(g.pts.size(), {0, 0});
-    std::vector<int> Ps = prec == PC_FP64 ? std::vector<int>{64} : std::vector<int>{64, 128, kBigFft};
+    // FP32 patches take 128^2 or 256^2: 64^2 items do so little FFT work each
+    // that their fixed cost (claim, barriers, spectrum copy, ordering wait)
+    // dominates; measured on the adaptive 1024^2 workload, a {64, 128, 256}
+    // choice ran 20.0 ms per 32 RHS against 16.0 ms for {128, 256}.  FP64: 64^2.
+    std::vector<int> Ps = prec == PC_FP64 ? std::vector<int>{64} : std::vector<int>{128, kBigFft};
     for (size_t k = 0; k < g.pts.size(); ++k) {
         double best = 1e300;
         for (int P : Ps)
@@ -248,7 +252,9 @@ pc_status autotune_build(pc_context *ctx, const pc_box *box, const pc_grid *grid
     pc_operator *op = nullptr;
     double ms = 0;
     int timed = 0;
-    const int32_t nrhs = box && box->ndim == 3 ? 4 : 8;
+    // batches as large as the workloads' (small batches favour shapes with
+    // fewer, larger launches, which a 32-RHS apply no longer needs)
+    const int32_t nrhs = box && box->ndim == 3 ? 8 : 32;
     pc_status st = search(ctx, box, grid, radius, impulse, weights, prec, nrhs, &op, nullptr, &ms, &timed);
     if (st != PC_OK) return st;
     op->autotuned = true;

@@ -429,7 +429,7 @@ pc_status prepare_batch(pc_operator *op, int32_t nrhs);
 ApplyParams part_params(const pc_operator *op, const Part &pt, const ApplyParams &p);
 // Per-patch launch shape (pc_autotune.cpp): for each sample point k the FFT
 // size and kernel-window split that the line-FFT work model prefers for
-// bbox(U_k) (2D; P in {64, 128}, and 256 for FP32); shape[k] = {P, nsub}.
+// bbox(U_k) (2D; P in {128, 256} for FP32, 64 for FP64); shape[k] = {P, nsub}.
 // Tile extent of a window split ws at FFT size P: min(P - ws + 1, cap), cap
 // = 2P/3 for the fused kernel's row staging, P for the 256^2 kernel.
 inline int tile_cap(int P) { return P == kBigFft ? P : (2 * P) / 3; }
