@@ -219,13 +219,18 @@ def test_split_kernel_window(precision, R):
     assert np.all(err <= TOL[precision]), err
 
 
-def test_adaptive_workload_1024_sampled():
+@pytest.mark.parametrize("tune", [{}, {"per_patch": True}])
+def test_adaptive_workload_1024_sampled(tune):
     """The adaptive 1024^2 quadtree (r = 1579, hanging nodes, heavy-tailed
-    kernel, R = 64): 4 right-hand sides, 4096 seeded pixels each."""
-    wl = configs.adaptive_1024(4)
-    op, orc = make_pair(wl.shape, wl.cells, wl.kernel, "fp32")
-    x = workloads.rhs(wl.rhs_seed, 4, wl.shape)
-    y = run(op, x).reshape(4, -1)
+    kernel, R = 64), with one launch shape and with per-patch shapes (128^2
+    with split windows and 256^2, the benchmark's): 4096 seeded pixels of
+    every right-hand side of a 32-RHS batch."""
+    wl = configs.adaptive_1024(32)
+    op, orc = make_pair(wl.shape, wl.cells, wl.kernel, "fp32", **tune)
+    if tune:
+        assert op.info()["num_parts"] == 2
+    x = workloads.rhs(wl.rhs_seed, 32, wl.shape)
+    y = run(op, x).reshape(32, -1)
     pts = np.random.default_rng(9).choice(wl.n, 4096, replace=False)
     ref = orc.apply(x, points=pts)
     err = np.linalg.norm(y[:, pts] - ref, axis=1) / np.linalg.norm(ref, axis=1)
