@@ -73,8 +73,8 @@ WORKLOADS = {
                         ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_overlap.cuh"]),
     "adaptive_1024": ("1024x1024 adaptive quadtree (r=1579), heavy-tailed R=64, per-patch FFT sizes "
                       "(128^2 with 2x2 kernel sub-windows, 256^2) chosen by the work model, 32 RHS",
-                      "fft2d_kernel<float,128>",
-                      ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_overlap.cuh"]),
+                      "fft2d_parts<float,128|256>",
+                      ["pc_fft2d.cu", "pc_fft2d_big.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_overlap.cuh"]),
 }
 # launch-shape arguments of a workload's operator (the rest take the defaults)
 WORKLOAD_TUNING = {"adaptive_1024": {"per_patch": True}}
@@ -754,11 +754,15 @@ def serve_measure(pcg, ctx, ops, n_requests, rng, levels=(0.5, 0.8, 0.95), rhs_m
                          "launches": sat["launches"]},
            "loads": loads, "requests_after_warmup": sat["completed"] + sum(lv["requests"] for lv in loads)}
     if plain:
-        # the plain per-vector path on the saturated request set, one request after another
+        # the plain per-vector path on the saturated request set, one request
+        # after another (operators with per-patch shapes have no plain path:
+        # their requests are left out)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rhs = 0
         for o, k in sat_reqs:
+            if ops[o][1].info()["num_parts"] > 1:
+                continue
             y = torch.empty_like(pools[o][:k])
             ops[o][1].apply_plain(pools[o][:k], y)
             rhs += k
@@ -786,7 +790,8 @@ def run_serve(args):
                        "arrivals": "Poisson at 50/80/95% of the saturated rate",
                        "modes": "2D FP32" if args.serve_2d else "2D FP32; 3D FP32 and BF16x3 (tensor-core first axis)",
                        "requests_after_warmup": m["requests_after_warmup"],
-                       "plain_gpu": "the saturated request set, one request after another"}}
+                       "plain_gpu": "the saturated request set, one request after another, without "
+                                    "requests of per-patch operators (no plain path)"}}
     print(json.dumps(line), flush=True)
 
 
@@ -800,8 +805,8 @@ def roofline_of(pcg, wl, info, precision, kms, workload):
     import torch
     staged = precision == "bf16x3"
     kname = WORKLOADS[workload][1]
-    if info.get("num_parts", 1) > 1:
-        kname = "fft2d kernels of the %d per-patch parts (one launch each)" % info["num_parts"]
+    if info.get("num_parts", 1) > 1 and not kname.startswith("fft2d_parts"):
+        kname = "fft2d_parts<%d per-patch launch shapes>" % info["num_parts"]
     lo, hi = pcg.pc_neighbourhood_boxes(wl.shape, wl.cells)
     flops, bytes_ = algorithmic_work(wl.shape, lo, hi, wl.radius, wl.nrhs, info["spectra_bytes"],
                                      elem=8 if precision == "fp64" else 4)
@@ -981,7 +986,8 @@ def suite(pcg, ctx, args):
                            "shapes": {n: {k: op.info()[k] for k in ("fft_size", "window_split", "num_parts")}
                                       for n, op in ops},
                            "arrivals": "Poisson at 50/80/95% of the saturated rate",
-                           "plain_gpu": "the saturated request set, one request after another"}
+                           "plain_gpu": "the saturated request set, one request after another, "
+                                        "without the per-patch operator's requests (no plain path)"}
             out["serving_2d_mix"] = m
             for _, op in ops:
                 op.close()

@@ -55,6 +55,10 @@ struct Request {
     int launch_requests = 0;
     bool solo = false;  // runs alone through the operator's own apply (not a batched 2D operator)
     bool adjoint = false;   // Y = A~* X (Eq. adjoint_random_z)
+    // a launch slot still lists the request (until its launch ends); a
+    // request polled before that is deleted by the slot, not by the poll
+    bool attached = false;
+    bool collected = false;
     std::string error;
 };
 
@@ -180,6 +184,10 @@ void reap(pc_server *s) {
             release_budget(s, r);
         }
         if (status) cudaMemsetAsync(d_status, 0, sizeof(int32_t), sl.stream);
+        for (Request *r : sl.reqs) {
+            r->attached = false;
+            if (r->collected) delete r;   // polled while the launch still ran
+        }
         sl.reqs.clear();
         sl.busy = false;
         sl.solo = false;
@@ -225,6 +233,7 @@ bool launch_solo(pc_server *s, LaunchSlot &sl) {
         return true;
     }
     sl.reqs.assign(1, r);
+    r->attached = true;
     sl.busy = true;
     sl.solo = true;
     ++s->launches;
@@ -333,6 +342,7 @@ void try_launch(pc_server *s) {
             continue;
         }
         sl.reqs = take;
+        for (Request *r : take) r->attached = true;
         sl.busy = true;
         ++s->launches;
     }
@@ -518,7 +528,12 @@ pc_status pc_serve_poll(pc_server *s, uint64_t ticket, pc_request_info *info) {
     const pc_status st = r->state == 2 ? PC_OK : pc_status(r->status);
     const std::string msg = r->error;
     s->all.erase(it);
-    delete r;
+    // a request that completed early (its flag in mapped memory) is still on
+    // its slot's list until the launch ends: the slot deletes it then
+    if (r->attached)
+        r->collected = true;
+    else
+        delete r;
     if (st != PC_OK) return srv_fail(s, st, msg);
     return PC_OK;
 }

@@ -185,3 +185,49 @@ def test_adjoint_requests_in_the_mix(ops):
         srv.submit(op16, x, torch.empty_like(x), adjoint=True)
     assert e.value.status == pcg.binding.PC_ERR_UNSUPPORTED
     srv.close()
+
+
+def test_early_completions_polled_while_their_launch_runs():
+    """Requests that complete early (their last item raises a flag in mapped
+    memory) are polled, and so released, while their launch still runs other
+    requests; an operator with per-patch shapes runs its requests alone on the
+    other slot meanwhile.  The slot keeps each request until its launch ends,
+    so nothing it still lists is freed: every result must equal the request
+    applied alone."""
+    import paper_1805_06018_gb300 as pcg
+    shape = (160, 150)
+    cells = workloads.quadtree_grid(shape, 1, 4, lambda lo, hi: lo[0] < 50 and lo[1] < 50)
+    pp, _ = make_pair(shape, cells, workloads.HeavyTailed(lambda x: 2.0 + 2.0 * (x[..., 0] / 160.0), 30), "fp32",
+                      per_patch=True)
+    assert pp.info()["num_parts"] >= 2
+    small = []
+    for shp, npts in [((96, 80), (4, 3)), ((128, 112), (5, 4))]:
+        kern = workloads.GaussianAniso2D(lambda x: 1.5 + 0 * x[..., 0], lambda x: 2.0 + np.sin(x[..., 0] / 15.0),
+                                         lambda x: 0.3 + 0 * x[..., 0], 8)
+        small.append(make_pair(shp, workloads.regular_grid(shp, npts), kern, "fp32", fft_size=128)[0])
+    ops = small + [pp]
+    srv = pcg.Server(context(), budget_bytes=8 << 30, streams=2, max_requests_per_launch=16)
+    rng = np.random.default_rng(3)
+    jobs = []
+    for q in range(120):
+        op = ops[int(rng.integers(0, len(ops)))]
+        nrhs = int(rng.integers(1, 9))
+        x = torch.from_numpy(workloads.rhs(900 + q, nrhs, op.shape)).cuda()
+        jobs.append((op, x, torch.full_like(x, float("nan"))))
+    torch.cuda.synchronize()
+    pending = {}
+    for op, x, y in jobs:
+        pending[srv.submit(op, x, y)] = (op, x, y)
+        # poll in between submissions: early completions are collected at once
+        for t in [t for t in pending if srv.poll(t) is not None]:
+            pending.pop(t)
+    t0 = time.time()
+    while pending:
+        for t in [t for t in pending if srv.poll(t) is not None]:
+            pending.pop(t)
+        assert time.time() - t0 < 120, "requests did not finish"
+    srv.close()
+    for op, x, y in jobs:
+        alone = op.apply(x)
+        torch.cuda.synchronize()
+        assert torch.equal(y, alone)
