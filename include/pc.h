@@ -425,7 +425,7 @@ typedef struct pc_block_plan pc_block_plan;
  * closed boxes with 0 <= lo <= hi < shape per axis, else PC_ERR_ARG.
  * adjoint: 0 (A~[T,S]) or 1 ((A~*)[T,S]).  PC_FP32 and PC_FP64 operators,
  * 2D and 3D; PC_BF16X3 operators return PC_ERR_UNSUPPORTED.  A 3D plan runs
- * on the operator's per-CTA scratch volumes: its applies must not overlap
+ * on the operator's scratch volumes: its applies must not overlap
  * the operator's own applies or other 3D plans of the same operator (one
  * stream serialises them).  The plan allocates its device
  * tables (kept tiles, colour offsets, dependency lists, ordering flags,

@@ -712,12 +712,12 @@ static pc_status ensure_split3d_scratch(pc_operator *op, int64_t total) {
         return cuda_fail(op->ctx, e, "synchronising before growing the scratch volumes");
     cudaFree(op->d_scratch);
     op->d_scratch = nullptr;
-    op->device_bytes -= size_t(op->scratch_items) * pc::fft3d_scratch_bytes(1);
+    op->device_bytes -= size_t(op->scratch_items) * pc::fft3d_volume_bytes();
     op->scratch_items = 0;
-    if ((e = cudaMalloc(&op->d_scratch, size_t(chunk) * pc::fft3d_scratch_bytes(1))) != cudaSuccess)
+    if ((e = cudaMalloc(&op->d_scratch, size_t(chunk) * pc::fft3d_volume_bytes())) != cudaSuccess)
         return cuda_fail(op->ctx, e, "allocating the 3D scratch volumes");
     op->scratch_items = chunk;
-    op->device_bytes += size_t(chunk) * pc::fft3d_scratch_bytes(1);
+    op->device_bytes += size_t(chunk) * pc::fft3d_volume_bytes();
     return PC_OK;
 }
 
@@ -807,7 +807,7 @@ static pc_status prepare_batch_impl(pc_operator *op, int32_t nrhs) {
     if (!dg.ok) return fail(op->ctx, PC_ERR_CUDA, "cannot select the context's device");
     const int32_t npairs = (nrhs + 1) / 2;
     const bool split3d = op->d == 3 && op->prec == PC_BF16X3;
-    pc_status st = ensure_done_capacity(op, split3d ? npairs * pc::kPhase3Groups : npairs);
+    pc_status st = ensure_done_capacity(op, npairs * pc::flag_groups(op->d, op->prec));
     if (st == PC_OK && split3d) st = ensure_split3d_scratch(op, int64_t(op->n_tiles) * npairs);
     return st;
 }
@@ -853,9 +853,9 @@ static pc_status apply_batched(pc_operator *op, int32_t nrhs, const void *x, int
     DeviceGuard dg(ctx->device);
     if (!dg.ok) return fail(ctx, PC_ERR_CUDA, "cannot select the context's device");
     const int32_t npairs = (nrhs + 1) / 2;
-    // the split 3D path keeps one flag per output-plane group of phase 3
+    // 3D paths keep one flag per output-plane group
     const bool split3d = op->d == 3 && op->prec == PC_BF16X3;
-    pc_status st = ensure_done_capacity(op, split3d ? npairs * pc::kPhase3Groups : npairs);
+    pc_status st = ensure_done_capacity(op, npairs * pc::flag_groups(op->d, op->prec));
     if (st != PC_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (++op->epoch == 0) op->epoch = 1;
@@ -899,7 +899,7 @@ static pc_status apply_batched(pc_operator *op, int32_t nrhs, const void *x, int
     if (!op->parts.empty()) return apply_parts(op, p, s, adjoint);
     const int ctas = int(std::min<int64_t>(op->ctas, p.total_items));
     cudaEventRecord(op->ev_begin, s);
-    e = op->d == 3 ? pc::launch_fft3d(p, ctas, op->d_scratch, s, adjoint)
+    e = op->d == 3 ? pc::launch_fft3d(p, op->ctas, op->d_scratch, s, adjoint)
                    : pc::launch_fft2d(p, op->P, op->prec, ctas, s, adjoint);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the patch kernel");
     cudaEventRecord(op->ev_end, s);

@@ -242,14 +242,16 @@ pc_status pc_block_apply_many(pc_block_plan *bp, int32_t nrhs, const void *const
     DeviceGuard dg(ctx->device);
     if (!dg.ok) return fail(ctx, PC_ERR_CUDA, "cannot select the context's device");
     const int32_t npairs = (nrhs + 1) / 2;
+    // flags per (tile, pair): one per output-plane group of a 3D apply
+    const int32_t nflags = npairs * pc::flag_groups(op->d, op->prec);
     cudaError_t e = cudaSuccess;
-    if (bp->n_tiles > 0 && npairs > bp->done_cap) {
+    if (bp->n_tiles > 0 && nflags > bp->done_cap) {
         if (bp->launched && (e = cudaDeviceSynchronize()) != cudaSuccess)
             return cuda_fail(ctx, e, "synchronising before growing the plan's flags");
         cudaFree(bp->d_done);
         bp->d_done = nullptr;
         bp->done_cap = 0;
-        const int32_t cap = std::max<int32_t>(npairs, 32);
+        const int32_t cap = std::max<int32_t>(nflags, 32);
         const size_t bytes = sizeof(uint32_t) * size_t(bp->n_tiles) * size_t(cap);
         if ((e = cudaMalloc(&bp->d_done, bytes)) != cudaSuccess) return cuda_fail(ctx, e, "allocating plan flags");
         if ((e = pc::zero_now(bp->d_done, bytes)) != cudaSuccess) return cuda_fail(ctx, e, "clearing plan flags");
@@ -292,7 +294,7 @@ pc_status pc_block_apply_many(pc_block_plan *bp, int32_t nrhs, const void *const
     int64_t launches = 0;
     if (nb == 1 || op->d == 3) {
         // one block per launch (3D: the patch kernel runs one block at a time, on
-        // the operator's per-CTA scratch volumes)
+        // the operator's scratch volumes)
         for (int32_t i = 0; i < nb; ++i) {
             const pc::ApplyParams p = params(i);
             if ((e = pc::launch_zero(p, bp->blocks[size_t(i)].nT, op->prec, s)) != cudaSuccess)
@@ -300,7 +302,7 @@ pc_status pc_block_apply_many(pc_block_plan *bp, int32_t nrhs, const void *const
             ++launches;
             if (p.total_items > 0) {
                 const int ctas = int(std::min<int64_t>(op->ctas, p.total_items));
-                e = op->d == 3 ? pc::launch_fft3d(p, ctas, op->d_scratch, s, bp->adjoint)
+                e = op->d == 3 ? pc::launch_fft3d(p, op->ctas, op->d_scratch, s, bp->adjoint)
                                : pc::launch_fft2d(p, op->P, op->prec, ctas, s, bp->adjoint);
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the patch kernel");
                 ++launches;

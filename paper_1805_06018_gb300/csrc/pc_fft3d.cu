@@ -2,7 +2,7 @@
 //
 // A 64^3 complex field (2 MB) does not fit in one CTA's shared memory, so a
 // work item (tile, pair of right-hand sides) runs in three phases around a
-// per-CTA scratch volume G in global memory, laid out [plane][k2][k1]:
+// scratch volume G in global memory, laid out [plane][k2][k1]:
 //
 //   phase 1  for each of the n0 non-zero input planes: gather w . x, 2D FFT
 //            (rows, then columns) in a 64 x 64 shared workspace, store the
@@ -13,6 +13,13 @@
 //            (in place in G: a line only touches its own column of G)
 //   phase 3  for each needed output plane: inverse 2D FFT (columns, then
 //            rows) and the overlap-add of its L1 x L2 box into y
+//
+// In the fused kernel a cluster of CTAs works on one item at a time through
+// one scratch volume: each CTA takes every n-th plane or line of phases 1
+// and 2 and one contiguous group of the output planes in phase 3, and
+// cluster barriers separate the phases.  Shorter items (in time) shorten the
+// chain of ordering waits through the colours, which bounds the forward
+// apply; the adjoint, whose chain is shorter, runs clusters of one CTA.
 //
 // Overlap-add order, termination and determinism are those of the 2D kernel:
 // colour-ordered tiles, claims in increasing order, bounded waits.  The same
@@ -74,9 +81,10 @@ struct Lines3 {
 // Adjoint: of the L0 planes of the output box, x unweighted and zero outside
 // Omega (rows and columns L1 x L2 at out_lo); planes outside Omega are
 // skipped here and read as zero by phase 2.
+// The planes i0 = first, first + step, ... of the phase: a CTA's share.
 template <bool ADJ>
 __device__ __forceinline__ void phase1_3d(const ApplyParams &p, const Item3 &it, float2 *G, float2 *S,
-                                          const Lines3 &L) {
+                                          const Lines3 &L, int first, int step) {
     using C = float2;
     constexpr int P = Lines3::P, R1 = Lines3::R1, R2 = Lines3::R2, LINES = Lines3::LINES, PP = Lines3::PP;
     const C zero{0.0f, 0.0f};
@@ -95,7 +103,7 @@ __device__ __forceinline__ void phase1_3d(const ApplyParams &p, const Item3 &it,
     const float *x1 = has1 ? x0 + p.ldx : x0;
     const float *wt = static_cast<const float *>(p.w) + tile.w_base;
     const int64_t plane_box = int64_t(p.nx[1]) * p.nx[2];   // x lives on the box nx
-    for (int i0 = 0; i0 < m0; ++i0) {
+    for (int i0 = first; i0 < m0; i0 += step) {
         if (ADJ && (g0 + i0 < 0 || g0 + i0 >= p.nx[0])) continue;   // uniform across the CTA
         const float *wp = wt + int64_t(i0) * tile.w_ld[0];
         const int64_t xp = int64_t(g0 + i0) * plane_box;
@@ -148,10 +156,11 @@ __device__ __forceinline__ void phase1_3d(const ApplyParams &p, const Item3 &it,
 // keeping the L0 needed output planes.  Stored spectrum: Hermitian half in
 // k2, layout [k2 <= P/2][k1][k0].
 // Adjoint: the L0 output-box planes in (those outside Omega read as zero),
-// the conjugate spectrum, the n0 input-box planes kept.
+// the conjugate spectrum, the n0 input-box planes kept.  The CTA takes the
+// lines of the line groups first, first + step, ... (LINES lines a group).
 template <bool ADJ>
 __device__ __forceinline__ void phase2_3d(const ApplyParams &p, const Item3 &it, float2 *G, float2 *S,
-                                          const Lines3 &L) {
+                                          const Lines3 &L, int first, int step) {
     using C = float2;
     constexpr int P = Lines3::P, R1 = Lines3::R1, R2 = Lines3::R2, LINES = Lines3::LINES, PP = Lines3::PP;
     const C zero{0.0f, 0.0f};
@@ -159,7 +168,7 @@ __device__ __forceinline__ void phase2_3d(const ApplyParams &p, const Item3 &it,
     const int rows_in = ADJ ? L0 : n0, rows_out = ADJ ? n0 : L0;
     const int g0 = it.tile.out_lo[0];
     const C *sp = static_cast<const C *>(p.spec) + int64_t(it.tile.spec) * p.spec_stride;
-    for (int l = L.line; l < PP; l += LINES) {
+    for (int l = first * LINES + L.line; l < PP; l += step * LINES) {
         const int k2 = l / P, k1 = l % P;
         C a[R1];
         C *g = G + k2 * P + k1;
@@ -198,31 +207,50 @@ __device__ __forceinline__ void phase2_3d(const ApplyParams &p, const Item3 &it,
     __syncthreads();
 }
 
+// First-axis range [b, e) (in y) of output-plane group g of ng of a tile:
+// the planes kept by phase 3 (the L0 of the output box, or the n0 of the
+// input box for the adjoint) split into ng contiguous groups.
+template <bool ADJ>
+__device__ __forceinline__ void group_span(const Tile &t, int g, int ng, int &b, int &e) {
+    const int base = ADJ ? t.in_lo[0] : t.out_lo[0];
+    const int m0 = ADJ ? t.in_ext[0] : t.in_ext[0] + t.kext[0] - 1;
+    b = base + (m0 * g) / ng;
+    e = base + (m0 * (g + 1)) / ng;
+}
+
 // ordered overlap-add: wait (bounded) until every overlapping tile of a lower
-// colour has published its contribution for this pair.  A tile's flags for
-// the pair are `ng` consecutive words (one per output-plane group) starting
-// at done[tile * done_ld + pair * ng].  Returns false (for the whole CTA) if
-// a wait gave up - a timeout, or another wait of the launch gave up first
-// (the status word p.ctrl[2] is then non-zero): the item must be abandoned.
-__device__ __forceinline__ bool wait_deps_3d(const ApplyParams &p, const Item3 &it, int ng) {
+// colour has published, for this pair, each of its `ng` output-plane groups
+// whose planes meet [zb, ze), the planes this CTA is about to add.  A tile's
+// flags for the pair are `ng` consecutive words (one per group) starting at
+// done[tile * done_ld + pair * ng].  Waiting per group, not per tile, lets a
+// tile's groups follow the lower colours' groups plane range by plane range.
+// Returns false (for the whole CTA) if a wait gave up - a timeout, or
+// another wait of the launch gave up first (the status word p.ctrl[2] is
+// then non-zero): the item must be abandoned.
+template <bool ADJ>
+__device__ __forceinline__ bool wait_deps_3d(const ApplyParams &p, const Item3 &it, int ng, int zb, int ze) {
     const int d0 = p.dep_start[it.ti], nd = p.dep_start[it.ti + 1] - d0;
     const int64_t lim = wait_limit_ns(p.wait_ns);
     bool bad = false;
-    for (int d = threadIdx.x; d < nd * ng && !bad; d += blockDim.x) {
-        const uint32_t *f = p.done + int64_t(p.dep[d0 + d / ng]) * p.done_ld + int64_t(it.pair) * ng + d % ng;
+    for (int d = threadIdx.x; d < nd * ng && !bad && zb < ze; d += blockDim.x) {
+        const int dt = p.dep[d0 + d / ng], g = d % ng;
+        int gb, ge;
+        group_span<ADJ>(p.tiles[dt], g, ng, gb, ge);
+        if (gb >= ge || ge <= zb || gb >= ze) continue;   // no plane in common
+        const uint32_t *f = p.done + int64_t(dt) * p.done_ld + int64_t(it.pair) * ng + g;
         bad = !wait_flag_eq<false>(f, p.epoch, p.ctrl + 2, lim, 1, 64);
         __threadfence();
     }
     return !__syncthreads_or(bad);
 }
 
-// phase 3: inverse 2D FFT of the output planes o0 in [ob, oe) (of the L0
-// needed) and the overlap-add of their L1 x L2 boxes into y; then publish
-// `flag`.  Adjoint: the planes are the n0 of the input box, each n1 x n2,
-// weighted by w_k and added at the tile's origin.
+// phase 3: inverse 2D FFT of the output planes o0 = ob, ob + step, ... < oe
+// (of the L0 needed) and the overlap-add of their L1 x L2 boxes into y; then
+// publish `flag` (if not null).  Adjoint: the planes are the n0 of the input
+// box, each n1 x n2, weighted by w_k and added at the tile's origin.
 template <bool ADJ>
 __device__ __forceinline__ void phase3_3d(const ApplyParams &p, const Item3 &it, const float2 *G, float2 *S,
-                                          const Lines3 &L, int ob, int oe, uint32_t *flag) {
+                                          const Lines3 &L, int ob, int oe, int step, uint32_t *flag) {
     using C = float2;
     constexpr int P = Lines3::P, R1 = Lines3::R1, R2 = Lines3::R2, LINES = Lines3::LINES, PP = Lines3::PP;
     const Tile &tile = it.tile;
@@ -240,7 +268,7 @@ __device__ __forceinline__ void phase3_3d(const ApplyParams &p, const Item3 &it,
     const int n2box = p.n[2];
     const int64_t plane_box = int64_t(p.n[1]) * n2box;
     (void)n0;
-    for (int o0 = ob; o0 < oe; ++o0) {
+    for (int o0 = ob; o0 < oe; o0 += step) {
         const int gy0 = h0 + o0;
         if (gy0 < 0 || gy0 >= p.n[0]) continue;   // uniform across the CTA
         // inverse along k1 for each k2: rows o1 of S
@@ -290,39 +318,61 @@ __device__ __forceinline__ void phase3_3d(const ApplyParams &p, const Item3 &it,
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
+    if (flag && threadIdx.x == 0) {
         __threadfence();
         st_release_u32(flag, p.epoch);
     }
 }
 
-// The fused FP32 kernel: persistent CTAs claim items in increasing order and
-// run the three phases through their own scratch volume.
-template <bool ADJ>
+// The fused FP32 kernel: persistent clusters of NR CTAs claim items in
+// increasing order and run the three phases through the cluster's scratch
+// volume, each CTA on its share of every phase.  In phase 3 CTA r adds the
+// r-th contiguous group of the item's output planes and publishes that
+// group's ordering flag.  NR = 1 is the one-CTA form (no cluster barriers).
+template <bool ADJ, int NR>
 __global__ void __launch_bounds__(kThreads3d, 3) fft3d_kernel(const ApplyParams p, float2 *scratch) {
     extern __shared__ __align__(16) unsigned char smem3[];
     float2 *S = reinterpret_cast<float2 *>(smem3);
+    __shared__ int64_t s_claim;   // rank 0: the cluster's next item
     __shared__ int64_t s_item;
+    const int rank = NR > 1 ? int(cluster_ctarank()) : 0;
     const Lines3 L(static_cast<const float2 *>(p.tw));
-    float2 *G = scratch + int64_t(blockIdx.x) * kP3 * kP3 * kP3;
+    float2 *G = scratch + int64_t(blockIdx.x / NR) * kP3 * kP3 * kP3;
+    auto sync = [] {
+        if constexpr (NR > 1) cluster_sync();
+        else __syncthreads();
+    };
     int chint = 0;
     for (;;) {
         // a launch whose waits have given up (status word set) takes no more items
-        if (threadIdx.x == 0)
-            s_item = ld_volatile_s32(p.ctrl + 2) != 0
-                         ? p.total_items
-                         : int64_t(atomicAdd(reinterpret_cast<unsigned long long *>(p.ctrl), 1ull));
+        if (rank == 0 && threadIdx.x == 0)
+            s_claim = ld_volatile_s32(p.ctrl + 2) != 0
+                          ? p.total_items
+                          : int64_t(atomicAdd(reinterpret_cast<unsigned long long *>(p.ctrl), 1ull));
+        // every CTA is done with the previous item's scratch volume, and the
+        // claim is visible
+        sync();
+        if (threadIdx.x == 0) s_item = NR > 1 ? ld_cluster_s64(&s_claim, 0) : s_claim;
         __syncthreads();
         const int64_t item = s_item;
         if (item >= p.total_items) break;
         const Item3 it = decode_item3(p, item, chint);
-        phase1_3d<ADJ>(p, it, G, S, L);
-        phase2_3d<ADJ>(p, it, G, S, L);
-        if (!wait_deps_3d(p, it, 1)) break;
-        // planes kept: the L0 of the output box, or the n0 of the input box (adjoint)
-        const int m0 = ADJ ? it.tile.in_ext[0] : it.tile.in_ext[0] + it.tile.kext[0] - 1;
-        phase3_3d<ADJ>(p, it, G, S, L, 0, m0, p.done + int64_t(it.ti) * p.done_ld + it.pair);
+        phase1_3d<ADJ>(p, it, G, S, L, rank, NR);
+        sync();
+        phase2_3d<ADJ>(p, it, G, S, L, rank, NR);
+        sync();
+        // this CTA's planes; a failed wait abandons them (the status word is
+        // then set, so the next claim ends the launch) and the CTA still
+        // takes part in the cluster barriers
+        int zb, ze;
+        group_span<ADJ>(it.tile, rank, NR, zb, ze);
+        const int base = ADJ ? it.tile.in_lo[0] : it.tile.out_lo[0];
+        if (wait_deps_3d<ADJ>(p, it, NR, zb, ze))
+            phase3_3d<ADJ>(p, it, G, S, L, zb - base, ze - base, 1,
+                           p.done + int64_t(it.ti) * p.done_ld + int64_t(it.pair) * NR + rank);
     }
+    // no CTA leaves while another may still read its shared memory
+    if constexpr (NR > 1) cluster_sync();
 }
 
 // Split form used with the tensor-core first-axis transform: items
@@ -335,7 +385,7 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase1_kernel(const Apply
     int chint = 0;
     for (int64_t item = c0 + blockIdx.x; item < c1; item += gridDim.x) {
         const Item3 it = decode_item3(p, item, chint);
-        phase1_3d<false>(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L);
+        phase1_3d<false>(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L, 0, 1);
     }
 }
 
@@ -364,38 +414,85 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase3_kernel(const Apply
         const int64_t item = piece / NG;
         const int g = int(piece % NG);
         const Item3 it = decode_item3(p, item, chint);
-        if (!wait_deps_3d(p, it, NG)) break;
         const int L0 = it.tile.in_ext[0] + it.tile.kext[0] - 1;
+        int zb, ze;
+        group_span<false>(it.tile, g, NG, zb, ze);
+        if (!wait_deps_3d<false>(p, it, NG, zb, ze)) break;
         phase3_3d<false>(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L, (L0 * g) / NG, (L0 * (g + 1)) / NG,
-                  p.done + int64_t(it.ti) * p.done_ld + int64_t(it.pair) * NG + g);
+                         1, p.done + int64_t(it.ti) * p.done_ld + int64_t(it.pair) * NG + g);
     }
 }
 
+// Clusters of the fused kernel (forward, adjoint) that fit on the device at
+// once, per device (set by fft3d_configure).
+static int g_fft3d_clusters[64][2];
+
+static cudaLaunchConfig_t fft3d_config(cudaLaunchAttribute *attr, int cluster, int64_t clusters, cudaStream_t s) {
+    attr->id = cudaLaunchAttributeClusterDimension;
+    attr->val.clusterDim.x = unsigned(cluster);
+    attr->val.clusterDim.y = 1;
+    attr->val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(unsigned(clusters * cluster));
+    cfg.blockDim = dim3(kThreads3d);
+    cfg.dynamicSmemBytes = kSmem3;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
 cudaError_t fft3d_configure(int *ctas_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(fft3d_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
+    cudaError_t e = cudaFuncSetAttribute(fft3d_kernel<false, kCluster3dFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fft3d_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
+        e = cudaFuncSetAttribute(fft3d_kernel<true, kCluster3dAdj>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fft3d_phase3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
+    static_assert(kCluster3dMax <= 8, "portable cluster sizes only");
     int n = 0, na = 0;
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fft3d_kernel<false>, kThreads3d, kSmem3);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fft3d_kernel<false, kCluster3dFwd>, kThreads3d, kSmem3);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&na, fft3d_kernel<true>, kThreads3d, kSmem3);
-    // one CTA count serves both directions (the per-CTA scratch volumes are sized by it)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&na, fft3d_kernel<true, kCluster3dAdj>, kThreads3d, kSmem3);
+    // one CTA count serves both directions (the scratch volumes are sized by it)
     if (ctas_per_sm) *ctas_per_sm = std::min(n, na);
+    int dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) {
+        const int per_sm = std::max(1, std::min(n, na));
+        cudaLaunchAttribute af{}, aa{};
+        cudaLaunchConfig_t cf = fft3d_config(&af, kCluster3dFwd, int64_t(sms) * per_sm, nullptr);
+        cudaLaunchConfig_t ca = fft3d_config(&aa, kCluster3dAdj, int64_t(sms) * per_sm, nullptr);
+        int c0 = 0, c1 = 0;
+        e = cudaOccupancyMaxActiveClusters(&c0, fft3d_kernel<false, kCluster3dFwd>, &cf);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&c1, fft3d_kernel<true, kCluster3dAdj>, &ca);
+        g_fft3d_clusters[dev][0] = c0;
+        g_fft3d_clusters[dev][1] = c1;
+        if (e == cudaSuccess && (c0 < 1 || c1 < 1) && ctas_per_sm) *ctas_per_sm = 0;
+    }
     return e;
 }
 
+// `ctas`: the operator's CTA budget; the launch runs min(ctas / cluster,
+// items, resident clusters) clusters, each on its own scratch volume.
 cudaError_t launch_fft3d(const ApplyParams &p, int ctas, void *scratch, cudaStream_t s, bool adjoint) {
-    if (adjoint)
-        fft3d_kernel<true><<<ctas, kThreads3d, kSmem3, s>>>(p, static_cast<float2 *>(scratch));
-    else
-        fft3d_kernel<false><<<ctas, kThreads3d, kSmem3, s>>>(p, static_cast<float2 *>(scratch));
-    return cudaGetLastError();
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const int cluster = adjoint ? kCluster3dAdj : kCluster3dFwd;
+    int64_t clusters = std::min<int64_t>(ctas / cluster, p.total_items);
+    if (dev >= 0 && dev < 64 && g_fft3d_clusters[dev][adjoint ? 1 : 0] > 0)
+        clusters = std::min<int64_t>(clusters, g_fft3d_clusters[dev][adjoint ? 1 : 0]);
+    if (clusters < 1) return cudaErrorInvalidConfiguration;
+    cudaLaunchAttribute attr{};
+    const cudaLaunchConfig_t cfg = fft3d_config(&attr, cluster, clusters, s);
+    float2 *g = static_cast<float2 *>(scratch);
+    return adjoint ? cudaLaunchKernelEx(&cfg, fft3d_kernel<true, kCluster3dAdj>, p, g) : cudaLaunchKernelEx(&cfg, fft3d_kernel<false, kCluster3dFwd>, p, g);
 }
 
-size_t fft3d_scratch_bytes(int ctas) { return size_t(ctas) * kP3 * kP3 * kP3 * sizeof(float2); }
+size_t fft3d_volume_bytes() { return size_t(kP3) * kP3 * kP3 * sizeof(float2); }
+size_t fft3d_scratch_bytes(int ctas) { return size_t(std::max(1, ctas / kCluster3dMin)) * fft3d_volume_bytes(); }
 
 cudaError_t launch_fft3d_phase1(const ApplyParams &p, int ctas, void *scratch, int64_t c0, int64_t c1,
                                 cudaStream_t s) {

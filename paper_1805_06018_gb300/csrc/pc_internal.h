@@ -388,16 +388,31 @@ constexpr int kBigFft = 256;
 // d_psi: [nspec][W][W] FP64 windows placed at [0, W)^2; spectra [nspec][P/2+1][P]
 cudaError_t build_spectra_2d(const double *d_psi, int nspec, int W, int P, pc_precision prec, void *d_spec,
                              const double2 *d_tw64, cudaStream_t s);
-// 3D patch path (pc_fft3d.cu), FP32, P = 64
+// 3D patch path (pc_fft3d.cu), FP32, P = 64.  The fused kernel runs clusters
+// of CTAs, one scratch volume each: launch_fft3d takes the operator's whole
+// CTA budget (not clamped to the item count) and a scratch of
+// fft3d_scratch_bytes(that budget).
 cudaError_t fft3d_configure(int *ctas_per_sm);
 cudaError_t launch_fft3d(const ApplyParams &p, int ctas, void *scratch, cudaStream_t s, bool adjoint = false);
 size_t fft3d_scratch_bytes(int ctas);
+size_t fft3d_volume_bytes();   // one 64^3 complex FP32 volume
 cudaError_t build_spectra_3d(const double *d_psi, int nspec, int W, int P, void *d_spec, const double2 *d_tw64,
                              cudaStream_t s);
 // split 3D path: phase 1 and phase 3 over items [c0, c1), scratch volume of
-// item i at scratch + (i - c0) * fft3d_scratch_bytes(1).  Phase 3 keeps
+// item i at scratch + (i - c0) * fft3d_volume_bytes().  Phase 3 keeps
 // kPhase3Groups ordering flags per (tile, pair): done_ld >= npairs * groups.
 constexpr int kPhase3Groups = 4;
+// The fused 3D kernel runs clusters of CTAs (kCluster3dFwd for Ã, kCluster3dAdj
+// for Ã*), each CTA adding one contiguous group of an item's output planes
+// under its own ordering flag.
+constexpr int kCluster3dFwd = 2;
+constexpr int kCluster3dAdj = 1;
+constexpr int kCluster3dMax = kCluster3dFwd > kCluster3dAdj ? kCluster3dFwd : kCluster3dAdj;
+constexpr int kCluster3dMin = kCluster3dFwd < kCluster3dAdj ? kCluster3dFwd : kCluster3dAdj;
+// ordering flags per (tile, pair) of an apply (either direction)
+inline int flag_groups(int d, pc_precision prec) {
+    return d == 3 ? (prec == PC_BF16X3 ? kPhase3Groups : kCluster3dMax) : 1;
+}
 cudaError_t launch_fft3d_phase1(const ApplyParams &p, int ctas, void *scratch, int64_t c0, int64_t c1,
                                 cudaStream_t s);
 cudaError_t launch_fft3d_phase3(const ApplyParams &p, int ctas, const void *scratch, int64_t c0, int64_t c1,
