@@ -48,13 +48,17 @@ WORKLOADS = {
                 "(the correctness configuration: latency-bound)", "fft2d_kernel<double,64>",
                 ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_overlap.cuh"]),
     "fp32_128c": ("128^3 regular 8x8x8 grid (r=512), axis-aligned Gaussian R=12, 64^3 patch FFTs, 32 RHS",
-                  "fft3d_kernel<false>", ["pc_fft3d.cu", "pc_fftcore.cuh", "pc_ptx.cuh"]),
+                  "fft3d_kernel<false,2>", ["pc_fft3d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_cluster.cuh"]),
     "bf16x3_128c": ("128^3 regular 8x8x8 grid (r=512), axis-aligned Gaussian R=12, 64^3 patches: plane FFTs in "
                     "FP32, first-axis DFTs as split-BF16 tensor-core GEMMs, 32 RHS",
                     "tc3d_axis0_kernel", ["pc_tc3d.cu", "pc_tc.cuh", "pc_ptx.cuh"]),
+    "bf16x3_128c_adjoint": ("adjoint apply (Eq. adjoint_random_z) of the 128^3 regular 8x8x8 grid (r=512) operator, "
+                            "axis-aligned Gaussian R=12, 64^3 patches: plane FFTs in FP32, first-axis correlation as "
+                            "split-BF16 tensor-core GEMMs, 32 RHS", "tc3d_axis0_adj_kernel",
+                            ["pc_tc3d.cu", "pc_tc.cuh", "pc_ptx.cuh"]),
     "fp32_128c_adjoint": ("adjoint apply (Eq. adjoint_random_z) of the 128^3 regular 8x8x8 grid (r=512) operator, "
-                          "axis-aligned Gaussian R=12, 64^3 patch FFTs, 32 RHS", "fft3d_kernel<true>",
-                          ["pc_fft3d.cu", "pc_fftcore.cuh", "pc_ptx.cuh"]),
+                          "axis-aligned Gaussian R=12, 64^3 patch FFTs, 32 RHS", "fft3d_kernel<true,1>",
+                          ["pc_fft3d.cu", "pc_fftcore.cuh", "pc_ptx.cuh", "pc_cluster.cuh"]),
     "fp32_512_adjoint": ("adjoint apply (Eq. adjoint_random_z) of the 512x512 regular 16x16 grid (r=256) "
                          "operator, anisotropic Gaussian R=24, 128^2 patch FFTs, 64 RHS",
                          "fft2d_kernel<float,128,true>", ["pc_fft2d.cu", "pc_fftcore.cuh", "pc_ptx.cuh",
@@ -83,7 +87,7 @@ WORKLOAD_OPERATOR = {"fp64_64": ("fp64_64", "fp64"), "fp32_512": ("fp32_512", "f
                      "fp32_512_estimator": ("fp32_512", "fp32"), "fp32_512_block": ("fp32_512", "fp32"),
                      "fp32_512_blocks": ("fp32_512", "fp32"),
                      "fp32_128c": ("fp32_128c", "fp32"), "bf16x3_128c": ("fp32_128c", "bf16x3"),
-                     "fp32_128c_adjoint": ("fp32_128c", "fp32"),
+                     "fp32_128c_adjoint": ("fp32_128c", "fp32"), "bf16x3_128c_adjoint": ("fp32_128c", "bf16x3"),
                      "adaptive_1024": ("adaptive_1024", "fp32")}
 
 
@@ -823,7 +827,9 @@ def roofline_of(pcg, wl, info, precision, kms, workload):
         # phase 1 = forward axes 1, 2; tensor stage = axis 0 forward + inverse
         # + product; phase 3 = inverse axes 1, 2.  Executed tensor-core flops
         # count the MMAs the tensor stage issues (3 split products per step).
-        stage_names = ["fft3d_phase1_kernel", "tc3d_axis0_kernel", "fft3d_phase3_kernel"]
+        adj = workload.endswith("_adjoint")
+        stage_names = ["fft3d_phase1_kernel", "tc3d_axis0_adj_kernel" if adj else "tc3d_axis0_kernel",
+                       "fft3d_phase3_kernel"]
         st_ms = np.mean(np.array(kms), axis=0)
         npairs = (wl.nrhs + 1) // 2
         f_stage = [0.0, 0.0, 0.0]
@@ -836,7 +842,9 @@ def roofline_of(pcg, wl, info, precision, kms, workload):
             f_stage[0] += 2.5 * L * (math.log2(Ls[1]) + math.log2(Ls[2]))
             f_stage[1] += 5.0 * L * math.log2(Ls[0]) + 3.0 * L
             f_stage[2] += 2.5 * L * (math.log2(Ls[1]) + math.log2(Ls[2]))
-            mma_flops += npairs * 32 * 3 * ((2 * n[0] + 15) // 16 + 8) * 2.0 * 128 * 128 * 16
+            # GEMM 1 over the n0 input planes (adjoint: the L0 output-box planes), GEMM 2 over 2 P
+            rows_in = Ls[0] if adj else n[0]
+            mma_flops += npairs * 32 * 3 * ((2 * rows_in + 15) // 16 + 8) * 2.0 * 128 * 128 * 16
         f_stage = [f * wl.nrhs for f in f_stage]
         bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
         tc_ach = mma_flops / (st_ms[1] / 1e3) / 1e12

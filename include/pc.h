@@ -270,7 +270,9 @@ pc_status pc_apply_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t
  * probes (Section 2.6).  Same arguments, layouts, stream semantics and
  * determinism as pc_apply_batched (y overwritten; each y element sums its
  * contributions in a fixed order).  PC_FP32 and PC_FP64 operators, 2D and
- * 3D; PC_BF16X3 operators return PC_ERR_UNSUPPORTED. */
+ * 3D, and PC_BF16X3 operators (the first-axis correlation as split-BF16
+ * tensor-core GEMMs over all 2 P columns of the DFT, the conjugate spectrum
+ * between them). */
 pc_status pc_apply_adjoint_batched(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx,
                                    void *y, int64_t ldy, pc_stream stream);
 
@@ -308,8 +310,8 @@ pc_status pc_apply_adjoint_batched(pc_operator *op, int32_t nrhs, const void *x,
  * `stream`, and work queued on `stream` after the call starts once y is
  * complete.  x and y must stay valid until then and should be page-locked
  * (cudaHostAlloc or cudaHostRegister) for the copies to run asynchronously.
- * Calls on one operator must be serialised (one stream).  The adjoint
- * covers PC_FP32 and PC_FP64 operators. */
+ * Calls on one operator must be serialised (one stream).  adjoint: 0 (A~)
+ * or 1 (A~*), for every operator. */
 pc_status pc_apply_host(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
                         int32_t adjoint, int32_t chunk, pc_stream stream);
 
@@ -487,9 +489,9 @@ pc_status pc_block_plan_destroy(pc_block_plan *plan);
  *          (the call synchronises `stream`).
  * The library applies A~* to z (as pc_apply_adjoint_batched, into scratch
  * that it allocates and keeps) and reduces each cell in FP64 in a fixed
- * order, so eta is bitwise reproducible.  PC_FP32 and PC_FP64 operators,
- * 2D and 3D (cells as closed boxes); PC_BF16X3 operators return
- * PC_ERR_UNSUPPORTED. */
+ * order, so eta is bitwise reproducible.  Every operator, 2D and 3D (cells
+ * as closed boxes); for PC_BF16X3 operators A~* z runs on the tensor-core
+ * path. */
 pc_status pc_estimate_cell_errors(pc_operator *op, int32_t q, const void *z, int64_t ldz, const void *y,
                                   int64_t ldy, double *eta, pc_stream stream);
 
@@ -585,8 +587,7 @@ pc_status pc_serve_create(pc_context *ctx, const pc_serve_config *cfg, pc_server
  * before the launch, which may synchronise the device).  Errors:
  * PC_ERR_UNSUPPORTED for operators the server cannot launch, PC_ERR_BUDGET
  * if the operator and request alone exceed the budget, PC_ERR_ARG for bad
- * arguments.  flags: 0, or PC_SERVE_ADJOINT for Y = A~* X (not for
- * PC_BF16X3 operators: PC_ERR_UNSUPPORTED). */
+ * arguments.  flags: 0, or PC_SERVE_ADJOINT for Y = A~* X. */
 pc_status pc_serve_submit(pc_server *srv, pc_operator *op, int32_t nrhs, const void *x, void *y, uint32_t flags,
                           uint64_t *ticket);
 

@@ -99,6 +99,7 @@ const char *free_operator(pc_operator *op) {
     chk(cudaFree(op->d_scratch), "scratch volumes");
     chk(cudaFree(op->d_big_scratch), "256^2 scratch fields");
     chk(cudaFree(op->d_tc_ops), "tensor-core operands");
+    chk(cudaFree(op->d_tc_ops_adj), "tensor-core operands (adjoint)");
     for (auto &kv : op->tc_orders) chk(cudaFree(kv.second), "unit orders");
     chk(cudaFree(op->d_cells), "cells");
     chk(cudaFree(op->d_cell_sums), "cell sums");
@@ -632,6 +633,9 @@ static pc_status build_operator(pc_context *ctx, const pc_box *box, const pc_gri
         e = pc::tc3d_configure();
         if (e == cudaSuccess) e = pc::tc3d_build_operands(op->tc_k1cap, &op->d_tc_ops);
         if (e == cudaSuccess) acct += size_t(op->tc_k1cap) * 512 + 65536;
+        // the adjoint's GEMM 1 runs over every first-axis plane (K = 2 P)
+        if (e == cudaSuccess) e = pc::tc3d_build_operands(2 * P, &op->d_tc_ops_adj);
+        if (e == cudaSuccess) acct += size_t(2 * P) * 512 + 65536;
     }
     // every upload and spectrum kernel above has landed before the operator
     // is handed out (its applies run on the caller's streams)
@@ -721,7 +725,7 @@ static pc_status ensure_split3d_scratch(pc_operator *op, int64_t total) {
     return PC_OK;
 }
 
-static pc_status apply_split3d(pc_operator *op, const pc::ApplyParams &p, cudaStream_t s) {
+static pc_status apply_split3d(pc_operator *op, const pc::ApplyParams &p, cudaStream_t s, bool adjoint) {
     pc_context *ctx = op->ctx;
     const int64_t total = p.total_items;
     const int64_t chunk = std::min<int64_t>(total, pc::kTc3dChunkItems);
@@ -778,15 +782,17 @@ static pc_status apply_split3d(pc_operator *op, const pc::ApplyParams &p, cudaSt
         const int ctas = int(std::min<int64_t>(op->ctas, c1 - c0));
         cudaEvent_t *ev = &op->stage_ev[size_t(c) * 6];
         cudaEventRecord(ev[0], s);
-        e = pc::launch_fft3d_phase1(p, ctas, op->d_scratch, c0, c1, s);
+        e = pc::launch_fft3d_phase1(p, ctas, op->d_scratch, c0, c1, s, adjoint);
         cudaEventRecord(ev[1], s);
         if (e != cudaSuccess) break;
         cudaEventRecord(ev[2], s);
-        e = pc::launch_tc3d_axis0(p, ctx->num_sms, op->d_scratch, order, c0, c1, op->d_tc_ops, op->tc_k1cap, s);
+        e = adjoint ? pc::launch_tc3d_axis0_adjoint(p, ctx->num_sms, op->d_scratch, order, c0, c1, op->d_tc_ops_adj, s)
+                    : pc::launch_tc3d_axis0(p, ctx->num_sms, op->d_scratch, order, c0, c1, op->d_tc_ops,
+                                            op->tc_k1cap, s);
         cudaEventRecord(ev[3], s);
         if (e != cudaSuccess) break;
         cudaEventRecord(ev[4], s);
-        e = pc::launch_fft3d_phase3(p, ctas, op->d_scratch, c0, c1, s);
+        e = pc::launch_fft3d_phase3(p, ctas, op->d_scratch, c0, c1, s, adjoint);
         cudaEventRecord(ev[5], s);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the 3D split path");
@@ -839,8 +845,6 @@ static pc_status apply_batched(pc_operator *op, int32_t nrhs, const void *x, int
                                pc_stream stream, bool adjoint) {
     if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
     pc_context *ctx = op->ctx;
-    if (adjoint && op->prec == PC_BF16X3)
-        return fail(ctx, PC_ERR_UNSUPPORTED, "the adjoint apply covers FP32 and FP64 operators");
     if (nrhs < 0) return fail(ctx, PC_ERR_ARG, "nrhs < 0");
     if (nrhs == 0) return PC_OK;
     if (!x || !y) return fail(ctx, PC_ERR_ARG, "null x or y");
@@ -893,7 +897,7 @@ static pc_status apply_batched(pc_operator *op, int32_t nrhs, const void *x, int
         if (e == cudaSuccess) e = cudaEventCreate(&op->ev_end);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "creating events");
     }
-    if (split3d) return apply_split3d(op, p, s);
+    if (split3d) return apply_split3d(op, p, s, adjoint);
     cudaError_t e = pc::launch_zero(p, op->N, op->prec, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launching the zero kernel");
     if (!op->parts.empty()) return apply_parts(op, p, s, adjoint);
@@ -1205,8 +1209,6 @@ pc_status pc_apply_host(pc_operator *op, int32_t nrhs, const void *x, int64_t ld
     if (!op) return fail(nullptr, PC_ERR_ARG, "operator is null");
     pc_context *ctx = op->ctx;
     if (adjoint != 0 && adjoint != 1) return fail(ctx, PC_ERR_ARG, "adjoint must be 0 or 1");
-    if (adjoint && op->prec == PC_BF16X3)
-        return fail(ctx, PC_ERR_UNSUPPORTED, "the adjoint apply covers FP32 and FP64 operators");
     if (nrhs < 0 || chunk < 0) return fail(ctx, PC_ERR_ARG, "nrhs and chunk must be >= 0");
     if (nrhs == 0) return PC_OK;
     if (!x || !y) return fail(ctx, PC_ERR_ARG, "null x or y");
@@ -1246,8 +1248,6 @@ pc_status pc_estimate_cell_errors(pc_operator *op, int32_t q, const void *z, int
     pc_context *ctx = op->ctx;
     if (q < 1) return fail(ctx, PC_ERR_ARG, "q must be >= 1");
     if (!z || !y || !eta) return fail(ctx, PC_ERR_ARG, "null z, y or eta");
-    if (op->prec == PC_BF16X3)
-        return fail(ctx, PC_ERR_UNSUPPORTED, "the error estimator covers FP32 and FP64 operators");
     if (ldy < op->N) return fail(ctx, PC_ERR_ARG, "ldy must be >= N");
     if (reinterpret_cast<uintptr_t>(y) % op->elem) return fail(ctx, PC_ERR_ARG, "y must be aligned to the element size");
     DeviceGuard dg(ctx->device);

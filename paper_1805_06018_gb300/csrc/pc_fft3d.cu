@@ -31,6 +31,7 @@
 
 #include "pc_fftcore.cuh"
 #include "pc_internal.h"
+#include "pc_cluster.cuh"
 #include "pc_ptx.cuh"
 
 namespace pc {
@@ -378,6 +379,7 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_kernel(const ApplyParams 
 // Split form used with the tensor-core first-axis transform: items
 // [c0, c1) of one chunk, each with its own scratch volume G[item - c0].
 // Phase 1 needs no ordering.
+template <bool ADJ>
 __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase1_kernel(const ApplyParams p, float2 *scratch,
                                                                      int64_t c0, int64_t c1) {
     __shared__ __align__(16) float2 S[kP3 * kP3];
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase1_kernel(const Apply
     int chint = 0;
     for (int64_t item = c0 + blockIdx.x; item < c1; item += gridDim.x) {
         const Item3 it = decode_item3(p, item, chint);
-        phase1_3d<false>(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L, 0, 1);
+        phase1_3d<ADJ>(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L, 0, 1);
     }
 }
 
@@ -395,6 +397,7 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase1_kernel(const Apply
 // lower-colour tile, so each voxel still sums its contributions in colour
 // order (the groups of one tile write disjoint planes); the pieces shorten
 // the chain of waits through the colours by the group count.
+template <bool ADJ>
 __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase3_kernel(const ApplyParams p, const float2 *scratch,
                                                                      int64_t c0, int64_t c1) {
     extern __shared__ __align__(16) unsigned char smem3[];
@@ -414,12 +417,12 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase3_kernel(const Apply
         const int64_t item = piece / NG;
         const int g = int(piece % NG);
         const Item3 it = decode_item3(p, item, chint);
-        const int L0 = it.tile.in_ext[0] + it.tile.kext[0] - 1;
         int zb, ze;
-        group_span<false>(it.tile, g, NG, zb, ze);
-        if (!wait_deps_3d<false>(p, it, NG, zb, ze)) break;
-        phase3_3d<false>(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L, (L0 * g) / NG, (L0 * (g + 1)) / NG,
-                         1, p.done + int64_t(it.ti) * p.done_ld + int64_t(it.pair) * NG + g);
+        group_span<ADJ>(it.tile, g, NG, zb, ze);
+        if (!wait_deps_3d<ADJ>(p, it, NG, zb, ze)) break;
+        const int base = ADJ ? it.tile.in_lo[0] : it.tile.out_lo[0];
+        phase3_3d<ADJ>(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L, zb - base, ze - base, 1,
+                       p.done + int64_t(it.ti) * p.done_ld + int64_t(it.pair) * NG + g);
     }
 }
 
@@ -447,7 +450,9 @@ cudaError_t fft3d_configure(int *ctas_per_sm) {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fft3d_kernel<true, kCluster3dAdj>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fft3d_phase3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
+        e = cudaFuncSetAttribute(fft3d_phase3_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fft3d_phase3_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem3);
     static_assert(kCluster3dMax <= 8, "portable cluster sizes only");
     int n = 0, na = 0;
     if (e == cudaSuccess)
@@ -495,17 +500,23 @@ size_t fft3d_volume_bytes() { return size_t(kP3) * kP3 * kP3 * sizeof(float2); }
 size_t fft3d_scratch_bytes(int ctas) { return size_t(std::max(1, ctas / kCluster3dMin)) * fft3d_volume_bytes(); }
 
 cudaError_t launch_fft3d_phase1(const ApplyParams &p, int ctas, void *scratch, int64_t c0, int64_t c1,
-                                cudaStream_t s) {
-    fft3d_phase1_kernel<<<ctas, kThreads3d, 0, s>>>(p, static_cast<float2 *>(scratch), c0, c1);
+                                cudaStream_t s, bool adjoint) {
+    if (adjoint)
+        fft3d_phase1_kernel<true><<<ctas, kThreads3d, 0, s>>>(p, static_cast<float2 *>(scratch), c0, c1);
+    else
+        fft3d_phase1_kernel<false><<<ctas, kThreads3d, 0, s>>>(p, static_cast<float2 *>(scratch), c0, c1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fft3d_phase3(const ApplyParams &p, int ctas, const void *scratch, int64_t c0, int64_t c1,
-                                cudaStream_t s) {
+                                cudaStream_t s, bool adjoint) {
     // claim counter of this chunk
     cudaError_t e = cudaMemsetAsync(p.ctrl, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    fft3d_phase3_kernel<<<ctas, kThreads3d, kSmem3, s>>>(p, static_cast<const float2 *>(scratch), c0, c1);
+    if (adjoint)
+        fft3d_phase3_kernel<true><<<ctas, kThreads3d, kSmem3, s>>>(p, static_cast<const float2 *>(scratch), c0, c1);
+    else
+        fft3d_phase3_kernel<false><<<ctas, kThreads3d, kSmem3, s>>>(p, static_cast<const float2 *>(scratch), c0, c1);
     return cudaGetLastError();
 }
 

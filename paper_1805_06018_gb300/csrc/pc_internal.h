@@ -244,6 +244,7 @@ struct pc_operator {
     void *d_scratch = nullptr;   // 3D: per-CTA spectrum volumes (FP32) or per-item volumes of a chunk (BF16x3)
     int64_t scratch_items = 0;   // BF16x3 3D: items d_scratch holds
     void *d_tc_ops = nullptr;    // BF16x3 3D: DFT operand tiles for the tensor cores
+    void *d_tc_ops_adj = nullptr;   // BF16x3 3D: the adjoint's (GEMM 1 over all 2 P columns)
     int tc_k1cap = 0;            // BF16x3 3D: K columns of the GEMM-1 operands
     // BF16x3 3D: per batch shape (pairs), the per-chunk item order of the tensor stage
     std::unordered_map<int32_t, int32_t *> tc_orders;
@@ -414,9 +415,9 @@ inline int flag_groups(int d, pc_precision prec) {
     return d == 3 ? (prec == PC_BF16X3 ? kPhase3Groups : kCluster3dMax) : 1;
 }
 cudaError_t launch_fft3d_phase1(const ApplyParams &p, int ctas, void *scratch, int64_t c0, int64_t c1,
-                                cudaStream_t s);
+                                cudaStream_t s, bool adjoint = false);
 cudaError_t launch_fft3d_phase3(const ApplyParams &p, int ctas, const void *scratch, int64_t c0, int64_t c1,
-                                cudaStream_t s);
+                                cudaStream_t s, bool adjoint = false);
 // tensor-core first-axis transform (pc_tc3d.cu), one CTA per SM.  Tiles of
 // a BF16x3 operator are at most kTc3dMaxTile wide along the first axis, so
 // GEMM 1 needs K <= kTc3dMaxK1 = 2 kTc3dMaxTile.
@@ -430,6 +431,10 @@ cudaError_t tc3d_configure();
 // item indices, entries c0 ... c1 - 1)
 cudaError_t launch_tc3d_axis0(const ApplyParams &p, int ctas, void *scratch, const int32_t *order, int64_t c0,
                               int64_t c1, const void *ops, int k1cap, cudaStream_t s);
+// the adjoint's tensor stage: ops_full = tc3d_build_operands(2 P) (GEMM 1
+// over all first-axis planes)
+cudaError_t launch_tc3d_axis0_adjoint(const ApplyParams &p, int ctas, void *scratch, const int32_t *order, int64_t c0,
+                                      int64_t c1, const void *ops_full, cudaStream_t s);
 pc_status plain_apply(pc_operator *op, int32_t nrhs, const void *x, int64_t ldx, void *y, int64_t ldy,
                       cudaStream_t s, std::string &err);
 void plain_free(pc_operator *op);

@@ -465,8 +465,6 @@ pc_status pc_serve_submit(pc_server *s, pc_operator *op, int32_t nrhs, const voi
     if (!op || nrhs < 1 || !x || !y || (flags & ~PC_SERVE_ADJOINT) != 0)
         return srv_fail(s, PC_ERR_ARG, "bad request arguments");
     const bool adjoint = (flags & PC_SERVE_ADJOINT) != 0;
-    if (adjoint && op->prec == PC_BF16X3)
-        return srv_fail(s, PC_ERR_UNSUPPORTED, "adjoint requests need an FP32 operator");
     if (op->ctx->device != s->ctx->device) return srv_fail(s, PC_ERR_ARG, "operator lives on another device");
     // the multi-request kernel covers 2D FP32 operators with fft_size 128;
     // every other operator runs its requests alone through its own apply

@@ -89,15 +89,19 @@ __device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const uint8_t *a_til
     }
 }
 
-// One unit: 128 consecutive (k2, k1) lines of one work item.
+// One unit: 128 consecutive (k2, k1) lines of one work item.  GEMM 1 reads
+// rows_in planes (the n0 input planes; adjoint: the L0 output-box planes,
+// those outside Omega read as zero), GEMM 2 keeps rows_out (L0; adjoint n0).
 struct Unit {
     int line0, n0, L0, steps1, spec;
+    int rows_in, rows_out, g0;   // g0: first-axis origin of the rows_in planes
     float2 *G;   // the item's scratch volume [plane][k2][k1]
 };
 
 // Units of a chunk: u -> block index blk = u / nitems, then the chunk's items
 // in the host-built order order[c0 + r] (sorted by tile, then pair), so that
 // consecutive units share the tile and block and with them the spectrum block.
+template <bool ADJ = false>
 __device__ __forceinline__ Unit unit_of(const ApplyParams &p, float2 *scratch, const int32_t *order, int64_t c0,
                                         int64_t nitems, int64_t u) {
     const int blk = int(u / nitems);
@@ -110,7 +114,10 @@ __device__ __forceinline__ Unit unit_of(const ApplyParams &p, float2 *scratch, c
     Unit x;
     x.n0 = tile.in_ext[0];
     x.L0 = x.n0 + tile.kext[0] - 1;
-    x.steps1 = (2 * x.n0 + 15) / 16;
+    x.rows_in = ADJ ? x.L0 : x.n0;
+    x.rows_out = ADJ ? x.n0 : x.L0;
+    x.g0 = tile.out_lo[0];
+    x.steps1 = (2 * x.rows_in + 15) / 16;
     x.spec = tile.spec;
     x.G = scratch + (item - c0) * int64_t(kP) * kPlane;
     x.line0 = blk * kBlock;
@@ -118,26 +125,31 @@ __device__ __forceinline__ Unit unit_of(const ApplyParams &p, float2 *scratch, c
 }
 
 // GEMM-1 input of a unit: thread (m = tid % 128, h = tid / 128) holds groups
-// g = h + 4 e (e < 3, g < k1cap / 8) of 4 planes (8 K values) of line
-// line0 + m.  All loads are issued before any is used.
-constexpr int kGroups = kTc3dMaxK1 / 8 / kQuads;   // groups per thread
+// g = h + 4 e (e < GROUPS, g < k1cap / 8) of 4 planes (8 K values) of line
+// line0 + m.  All loads are issued before any is used.  CLIP: planes outside
+// Omega along the first axis read as zero (the adjoint's phase 1 skips them).
+constexpr int kGroups = kTc3dMaxK1 / 8 / kQuads;   // groups per thread (forward)
+constexpr int kGroupsAdj = 2 * kP / 8 / kQuads;    // adjoint: K up to 2 P
 static_assert(kGroups * kQuads * 8 == kTc3dMaxK1, "staging groups");
-__device__ __forceinline__ void stage_load(const Unit &x, int tid, float2 (&z)[4 * kGroups]) {
+template <int GROUPS, bool CLIP>
+__device__ __forceinline__ void stage_load(const ApplyParams &p, const Unit &x, int tid, float2 (&z)[4 * GROUPS]) {
     const int m = tid & (kBlock - 1), h = tid >> 7;
 #pragma unroll
-    for (int e = 0; e < kGroups; ++e)
+    for (int e = 0; e < GROUPS; ++e)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int i0 = 4 * (h + kQuads * e) + q;
-            z[4 * e + q] = i0 < x.n0 ? __ldcg(x.G + int64_t(i0) * kPlane + x.line0 + m) : make_float2(0.f, 0.f);
+            const bool in = i0 < x.rows_in && (!CLIP || (x.g0 + i0 >= 0 && x.g0 + i0 < p.nx[0]));
+            z[4 * e + q] = in ? __ldcg(x.G + int64_t(i0) * kPlane + x.line0 + m) : make_float2(0.f, 0.f);
         }
 }
 
-__device__ __forceinline__ void stage_store(const Unit &x, int tid, const float2 (&z)[4 * kGroups], uint8_t *sA1,
+template <int GROUPS>
+__device__ __forceinline__ void stage_store(const Unit &x, int tid, const float2 (&z)[4 * GROUPS], uint8_t *sA1,
                                             int k1cap) {
     const int m = tid & (kBlock - 1), h = tid >> 7;
 #pragma unroll
-    for (int e = 0; e < kGroups; ++e) {
+    for (int e = 0; e < GROUPS; ++e) {
         const int g = h + kQuads * e;
         if (g < 2 * x.steps1) {
             float v[8];
@@ -152,7 +164,8 @@ __device__ __forceinline__ void stage_store(const Unit &x, int tid, const float2
 }
 
 // spectrum of the thread's line, k0 = 16 part ... 16 part + 15 (Hermitian
-// mirror for k2 > P/2)
+// mirror for k2 > P/2); conjugated for the adjoint
+template <bool ADJ = false>
 __device__ __forceinline__ void spectrum_load(const ApplyParams &p, const Unit &x, int erow, int part,
                                               float2 (&f)[16]) {
     const int line = x.line0 + erow, k2 = line / kP, k1 = line % kP;
@@ -163,7 +176,7 @@ __device__ __forceinline__ void spectrum_load(const ApplyParams &p, const Unit &
     for (int j = 0; j < 16; ++j) {
         const int k0 = 16 * part + j;
         f[j] = __ldg(sp + (mirror ? ((kP - k0) & (kP - 1)) : k0));
-        if (mirror) f[j].y = -f[j].y;
+        if (mirror != ADJ) f[j].y = -f[j].y;
     }
 }
 
@@ -217,13 +230,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc3d_axis0_kernel(const ApplyPara
     Unit cur{}, nxt{};
     if (u < nunits) {
         cur = unit_of(p, scratch, order, c0, nitems, u);
-        stage_load(cur, tid, z);
+        stage_load<kGroups, false>(p, cur, tid, z);
     }
     bool ok = __syncthreads_and(mbar_wait_bounded(bar_ld, 0, kSpin));
     bool pend1 = false, pend2 = false;
     uint32_t ph1 = 0, ph2 = 0;
     if (ok && u < nunits) {
-        stage_store(cur, tid, z, sA1, k1cap);
+        stage_store<kGroups>(cur, tid, z, sA1, k1cap);
         fence_proxy_async_smem();
         tc::fence_before_sync();
         __syncthreads();
@@ -235,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc3d_axis0_kernel(const ApplyPara
         pend1 = true;
         if (u + stride < nunits) {
             nxt = unit_of(p, scratch, order, c0, nitems, u + stride);
-            stage_load(nxt, tid, z);
+            stage_load<kGroups, false>(p, nxt, tid, z);
         }
         spectrum_load(p, cur, erow, part, f);
     }
@@ -275,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc3d_axis0_kernel(const ApplyPara
         // the loads of the unit after it and of the next unit's spectrum
         const bool has_next = u + stride < nunits;
         if (has_next) {
-            stage_store(nxt, tid, z, sA1, k1cap);
+            stage_store<kGroups>(nxt, tid, z, sA1, k1cap);
             fence_proxy_async_smem();
             tc::fence_before_sync();
             __syncthreads();
@@ -289,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc3d_axis0_kernel(const ApplyPara
         Unit nn = nxt;
         if (u + 2 * stride < nunits) {
             nn = unit_of(p, scratch, order, c0, nitems, u + 2 * stride);
-            stage_load(nn, tid, z);
+            stage_load<kGroups, false>(p, nn, tid, z);
         }
         // the spectrum registers stay valid while the tile and block repeat
         if (has_next && (nxt.spec != cur.spec || nxt.line0 != cur.line0)) spectrum_load(p, nxt, erow, part, f);
@@ -308,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc3d_axis0_kernel(const ApplyPara
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int o0 = 16 * part + j;
-                if (o0 < cur.L0) __stcg(g + int64_t(o0) * kPlane, make_float2(v[2 * j], v[2 * j + 1]));
+                if (o0 < cur.rows_out) __stcg(g + int64_t(o0) * kPlane, make_float2(v[2 * j], v[2 * j + 1]));
             }
         }
         tc::fence_before_sync();
@@ -320,6 +333,151 @@ __global__ void __launch_bounds__(kThreads, 1) tc3d_axis0_kernel(const ApplyPara
         if (tid == 0) atomicExch(p.ctrl + 2, 1);
         // give MMAs still in flight a bounded chance to finish before the
         // tensor memory is released
+        if (pend1) (void)__syncthreads_and(mbar_wait_bounded(bar_g1, ph1, kSpin));
+        if (pend2) (void)__syncthreads_and(mbar_wait_bounded(bar_g2, ph2, kSpin));
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// The adjoint (Eq. adjoint_random_z): GEMM 1 takes the L0 output-box planes
+// (K = 2 L0 <= 2 P, so F1 is the whole DFT matrix), the product takes the
+// conjugate spectrum, and GEMM 2 keeps the n0 input-box planes.  With F1 of
+// K = 128 the two data tiles no longer fit beside F1 and F2, so GEMM 1 and
+// GEMM 2 share one data tile and a unit runs its steps one after another:
+// stage, GEMM 1, epilogue 1 (into the same tile, which GEMM 1 has finished
+// reading), GEMM 2, epilogue 2.  The next unit's loads are in flight meanwhile.
+__host__ __device__ constexpr int smem_bytes_adj() { return 2 * tile_bytes(2 * kP) + 2 * kTile + 2 * kTile + 64; }
+static_assert(smem_bytes_adj() <= 227 * 1024, "shared memory");
+
+__global__ void __launch_bounds__(kThreads, 1) tc3d_axis0_adj_kernel(const ApplyParams p, float2 *scratch,
+                                                                     const int32_t *order, int64_t c0, int64_t c1,
+                                                                     const uint8_t *ops) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    constexpr int K1 = 2 * kP;
+    constexpr int t1 = tile_bytes(K1);
+    uint8_t *sF1 = sm, *sF2 = sm + 2 * t1, *sA = sF2 + 2 * kTile;
+    uint64_t *bar_ld = reinterpret_cast<uint64_t *>(sA + 2 * kTile);
+    uint64_t *bar_g1 = bar_ld + 1, *bar_g2 = bar_ld + 2;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(bar_ld + 3);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t nitems = c1 - c0;
+    const int64_t u_begin = nitems * kUnitsPerItem * blockIdx.x / gridDim.x;
+    const int64_t nunits = nitems * kUnitsPerItem * (blockIdx.x + 1) / gridDim.x;
+    const uint32_t sbo1 = uint32_t(K1) * 16u;
+    const int steps2 = kK / 16;
+
+    if (tid == 0) {
+        mbar_init(bar_ld, 1);
+        mbar_init(bar_g1, 1);
+        mbar_init(bar_g2, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(slot, 256);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *slot;
+    const uint32_t d1 = tmem, d2 = tmem + 128u;
+    if (tid == 0) {
+        mbar_arrive_expect_tx(bar_ld, uint32_t(2 * t1 + 2 * kTile));
+        bulk_g2s(sF1, ops, uint32_t(2 * t1), bar_ld);
+        bulk_g2s(sF2, ops + 2 * t1, uint32_t(2 * kTile), bar_ld);
+    }
+    const int quarter = warp & 3, part = warp >> 2;
+    const int erow = 32 * quarter + lane;
+    const uint32_t lane_base = uint32_t(32 * quarter) << 16;
+
+    float2 z[4 * kGroupsAdj];   // GEMM-1 input of the next unit to be staged
+    float2 f[16];               // spectrum of the current unit
+    Unit cur{};
+    int spec_of_f = -1, line_of_f = -1;
+    if (u_begin < nunits) {
+        cur = unit_of<true>(p, scratch, order, c0, nitems, u_begin);
+        stage_load<kGroupsAdj, true>(p, cur, tid, z);
+    }
+    bool ok = __syncthreads_and(mbar_wait_bounded(bar_ld, 0, kSpin));
+    bool pend1 = false, pend2 = false;
+    uint32_t ph1 = 0, ph2 = 0;
+    for (int64_t u = u_begin; ok && u < nunits; ++u) {
+        // ---- stage (the data tile is free: the previous GEMM 2 has completed)
+        stage_store<kGroupsAdj>(cur, tid, z, sA, K1);
+        fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            issue_gemm(d1, sA, sF1, t1, sbo1, cur.steps1);
+            tc::mma_commit(bar_g1);
+        }
+        pend1 = true;
+        // the next unit's loads and this unit's spectrum while GEMM 1 runs
+        Unit nxt = cur;
+        if (u + 1 < nunits) {
+            nxt = unit_of<true>(p, scratch, order, c0, nitems, u + 1);
+            stage_load<kGroupsAdj, true>(p, nxt, tid, z);
+        }
+        if (cur.spec != spec_of_f || cur.line0 != line_of_f) {
+            spectrum_load<true>(p, cur, erow, part, f);
+            spec_of_f = cur.spec;
+            line_of_f = cur.line0;
+        }
+        // ---- epilogue 1: V^ = D1 * conj(phi^), split into the data tile
+        ok = __syncthreads_and(mbar_wait_bounded(bar_g1, ph1, kSpin));
+        if (!ok) break;
+        pend1 = false;
+        ph1 ^= 1u;
+        tc::fence_after_sync();
+        {
+            float v[32];
+            tc::tmem_ld32(d1 + lane_base + uint32_t(32 * part), v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float2 w = f[j];
+                const float re = v[2 * j] * w.x - v[2 * j + 1] * w.y;
+                const float im = v[2 * j] * w.y + v[2 * j + 1] * w.x;
+                v[2 * j] = re;
+                v[2 * j + 1] = im;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                split8_store(sA, kTile, tc::kmajor_offset(erow, 32 * part + 8 * r, kK, 2), v + 8 * r);
+        }
+        fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            issue_gemm(d2, sA, sF2, kTile, kSBO2, steps2);
+            tc::mma_commit(bar_g2);
+        }
+        pend2 = true;
+        // ---- epilogue 2: the n0 input-box planes back into G (in place)
+        ok = __syncthreads_and(mbar_wait_bounded(bar_g2, ph2, kSpin));
+        if (!ok) break;
+        pend2 = false;
+        ph2 ^= 1u;
+        tc::fence_after_sync();
+        {
+            float2 *g = cur.G + cur.line0 + erow;
+            float v[32];
+            tc::tmem_ld32(d2 + lane_base + uint32_t(32 * part), v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int o0 = 16 * part + j;
+                if (o0 < cur.rows_out) __stcg(g + int64_t(o0) * kPlane, make_float2(v[2 * j], v[2 * j + 1]));
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        cur = nxt;
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(p.ctrl + 2, 1);
         if (pend1) (void)__syncthreads_and(mbar_wait_bounded(bar_g1, ph1, kSpin));
         if (pend2) (void)__syncthreads_and(mbar_wait_bounded(bar_g2, ph2, kSpin));
     }
@@ -347,7 +505,7 @@ int tc3d_k1cap(int tile) { return 16 * ((2 * tile + 15) / 16); }
 
 // F1 hi, F1 lo (K = k1cap), F2 hi, F2 lo in the shared-memory operand layout
 cudaError_t tc3d_build_operands(int k1cap, void **d_ops) {
-    if (k1cap < 16 || k1cap > kTc3dMaxK1 || k1cap % 16) return cudaErrorInvalidValue;
+    if (k1cap < 16 || k1cap > 2 * kP || k1cap % 16) return cudaErrorInvalidValue;
     const int t1 = tile_bytes(k1cap);
     std::vector<uint8_t> h(size_t(2 * t1 + 2 * kTile), 0);
     const long double two_pi = 6.283185307179586476925286766559005768L;
@@ -382,8 +540,11 @@ cudaError_t tc3d_build_operands(int k1cap, void **d_ops) {
 }
 
 cudaError_t tc3d_configure() {
-    return cudaFuncSetAttribute(tc3d_axis0_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem_bytes(kTc3dMaxK1));
+    cudaError_t e =
+        cudaFuncSetAttribute(tc3d_axis0_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(kTc3dMaxK1));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc3d_axis0_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes_adj());
+    return e;
 }
 
 cudaError_t launch_tc3d_axis0(const ApplyParams &p, int ctas, void *scratch, const int32_t *order, int64_t c0,
@@ -393,6 +554,15 @@ cudaError_t launch_tc3d_axis0(const ApplyParams &p, int ctas, void *scratch, con
     const int grid = int(std::min<int64_t>(ctas, units));
     tc3d_axis0_kernel<<<grid, kThreads, smem_bytes(k1cap), s>>>(p, static_cast<float2 *>(scratch), order, c0, c1,
                                                                 static_cast<const uint8_t *>(ops), k1cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc3d_axis0_adjoint(const ApplyParams &p, int ctas, void *scratch, const int32_t *order, int64_t c0,
+                                      int64_t c1, const void *ops_full, cudaStream_t s) {
+    const int64_t units = (c1 - c0) * kUnitsPerItem;
+    const int grid = int(std::min<int64_t>(ctas, units));
+    tc3d_axis0_adj_kernel<<<grid, kThreads, smem_bytes_adj(), s>>>(p, static_cast<float2 *>(scratch), order, c0, c1,
+                                                                   static_cast<const uint8_t *>(ops_full));
     return cudaGetLastError();
 }
 

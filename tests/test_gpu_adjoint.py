@@ -154,14 +154,33 @@ def test_adjoint_3d_workload_128_sampled():
     assert np.all(err <= TOL["fp32"]), err
 
 
-def test_adjoint_bf16x3_unsupported():
-    import paper_1805_06018_gb300 as pcg
-    from paper_1805_06018_gb300.binding import PC_ERR_UNSUPPORTED
-    shape = (24, 20, 18)
-    cells = workloads.regular_grid(shape, (2, 2, 2))
-    kern = workloads.GaussianAxis3D(lambda x: 1.5 + 0 * x[..., 0], lambda x: 1.2 + 0 * x[..., 0],
-                                    lambda x: 1.0 + 0 * x[..., 0], 4)
-    op, _ = make_pair(shape, cells, kern, "bf16x3")
-    with pytest.raises(pcg.PCError) as ei:
-        run_adjoint(op, workloads.rhs(76, 1, shape))
-    assert ei.value.status == PC_ERR_UNSUPPORTED
+def test_adjoint_bf16x3():
+    """BF16x3 operators: the first-axis correlation as split-BF16 tensor-core
+    GEMMs (GEMM 1 over all first-axis planes of the output box, those outside
+    Omega read as zero, the conjugate spectrum, GEMM 2 keeping the input-box
+    planes).  Against the oracle's adjoint within the BF16x3 bound (1e-4 per
+    right-hand side, the forward's; see test_gpu_tensor.py), against the FP32
+    operator's adjoint, and the duality <A~ x, y> = <x, A~* y> to the same
+    bound; odd batch, ragged tiles, output boxes cut by the boundary."""
+    shape = (45, 29, 38)
+    cells = workloads.regular_grid(shape, (4, 2, 3))
+    kern = workloads.GaussianAxis3D(lambda x: 2.0 + 0.5 * np.cos(x[..., 1] / 6.0), lambda x: 1.5 + 0 * x[..., 0],
+                                    lambda x: 1.2 + 0.2 * np.sin(x[..., 2] / 4.0), 9)
+    op16, orc = make_pair(shape, cells, kern, "bf16x3")
+    op32, _ = make_pair(shape, cells, kern, "fp32")
+    x = workloads.rhs(76, 5, shape)
+    z16 = run_adjoint(op16, x)
+    ref = orc.apply_adjoint(x)
+    err = rel_l2(z16, ref)
+    assert np.all(err <= 1e-4), err
+    assert np.all(rel_l2(z16, run_adjoint(op32, x)) <= 1e-4)
+    # duality against the BF16x3 forward apply
+    y = workloads.rhs(77, 5, shape)
+    ax = run_forward(op16, x).reshape(5, -1).astype(np.float64)
+    aty = run_adjoint(op16, y).reshape(5, -1).astype(np.float64)
+    lhs = np.sum(ax * y.reshape(5, -1), axis=1)
+    rhs_ = np.sum(x.reshape(5, -1) * aty, axis=1)
+    scale = np.linalg.norm(ax, axis=1) * np.linalg.norm(y.reshape(5, -1), axis=1)
+    assert np.all(np.abs(lhs - rhs_) <= 2e-4 * scale), (lhs, rhs_)
+    # bitwise reproducible
+    assert np.array_equal(run_adjoint(op16, x), z16)

@@ -112,16 +112,23 @@ def test_estimator_3d_fp32():
     assert np.all(ref > 0)
 
 
-def test_estimator_bf16x3_unsupported():
-    import paper_1805_06018_gb300 as pcg
-    from paper_1805_06018_gb300.binding import PC_ERR_UNSUPPORTED
+def test_estimator_bf16x3():
+    """BF16x3 operators estimate through the tensor-core adjoint: the per-cell
+    estimates equal the FP32 operator's to the BF16x3 bound."""
     shape = (24, 20, 18)
     cells = workloads.regular_grid(shape, (2, 2, 2))
     kern = workloads.GaussianAxis3D(lambda x: 1.5 + 0 * x[..., 0], lambda x: 1.2 + 0 * x[..., 0],
                                     lambda x: 1.0 + 0 * x[..., 0], 4)
-    op, _ = make_pair(shape, cells, kern, "bf16x3")
-    z = _dev(workloads.rhs(84, 1, shape), "fp32")
-    with pytest.raises(pcg.PCError) as ei:
-        op.estimate_cell_errors(z, z, len(cells))
-    assert ei.value.status == PC_ERR_UNSUPPORTED
-    assert Grid(shape, cells).r > 0
+    op16, _ = make_pair(shape, cells, kern, "bf16x3")
+    op32, _ = make_pair(shape, cells, kern, "fp32")
+    A = workloads.dense_operator(shape, kern)
+    Z = workloads.rhs(84, 6, shape).reshape(6, -1).astype(np.float64)
+    Y = (Z @ A).astype(np.float32).astype(np.float64)
+    eta16 = op16.estimate_cell_errors(_dev(Z, "fp32"), _dev(Y, "fp32"), len(cells))
+    op16.check()
+    eta32 = op32.estimate_cell_errors(_dev(Z, "fp32"), _dev(Y, "fp32"), len(cells))
+    op32.check()
+    # |eta16[C] - eta32[C]| <= ||(Y~16 - Y~32)[C, .]|| / sqrt(q) (reverse
+    # triangle inequality), and each Y~ is within 1e-4 of A~* Z per column
+    yt = np.linalg.norm(Z @ A)
+    assert np.all(np.abs(np.asarray(eta16) - np.asarray(eta32)) <= 2e-4 * yt / np.sqrt(6)), (eta16, eta32)

@@ -153,8 +153,8 @@ def test_3d_requests_in_the_mix(ops):
 def test_adjoint_requests_in_the_mix(ops):
     """Adjoint requests (PC_SERVE_ADJOINT, the estimator's probes A~* Z)
     among forward ones, 2D and 3D: runs of one direction share launches, and
-    every result equals the request applied alone, bit for bit; BF16x3
-    operators refuse adjoint requests."""
+    every result equals the request applied alone, bit for bit, BF16x3
+    adjoint requests included."""
     import paper_1805_06018_gb300 as pcg
     shape = (30, 28, 26)
     cells = workloads.regular_grid(shape, (3, 3, 3))
@@ -180,10 +180,14 @@ def test_adjoint_requests_in_the_mix(ops):
     st = srv.stats()
     assert st["launches"] < len(jobs)
     op16 = make_pair(shape, cells, kern, "bf16x3")[0]
-    x = torch.zeros(1, *shape, device="cuda")
-    with pytest.raises(pcg.PCError) as e:
-        srv.submit(op16, x, torch.empty_like(x), adjoint=True)
-    assert e.value.status == pcg.binding.PC_ERR_UNSUPPORTED
+    x = torch.from_numpy(workloads.rhs(760, 3, shape)).cuda()
+    y = torch.full_like(x, float("nan"))
+    t = srv.submit(op16, x, y, adjoint=True)
+    done = _wait(srv, [t], timeout=120.0)
+    assert done[t]["status"] == 0
+    alone = op16.apply_adjoint(x)
+    torch.cuda.synchronize()
+    assert torch.equal(y, alone)
     srv.close()
 
 
