@@ -648,11 +648,12 @@ def run_blocks(args, rank, world):
         dist.destroy_process_group()
 
 
-def serve_operators(pcg, ctx, with_3d=True):
+def serve_operators(pcg, ctx, with_3d=True, autotune=False):
     """The served operator mix: 2D 256^2 (9x9 grid), 512^2 (the benchmark
     operator), 1024^2 (adaptive quadtree, heavy-tailed, R = 64) and 2048^2
     (65x65 grid), FP32 with 128^2 patch FFTs; and 3D 64^3 ... 160^3 in FP32
-    and BF16x3."""
+    and BF16x3.  autotune: every operator's launch shape from the library's
+    autotuner (a NULL pc_tuning) instead."""
     import workloads
     from workloads import configs
     wls = []
@@ -671,7 +672,7 @@ def serve_operators(pcg, ctx, with_3d=True):
         pts = pcg.pc_sample_points(shape, cells)
         # regular grids: 128^2 patch FFTs, batched with the other requests; the
         # adaptive operator: per-patch FFT sizes (its requests then run alone)
-        tune = WORKLOAD_TUNING.get(name, {"fft_size": 128})
+        tune = {"autotune": True} if autotune else WORKLOAD_TUNING.get(name, {"fft_size": 128})
         ops.append((name, pcg.Operator(ctx, shape, cells, R, workloads.impulse_windows(shape, pts, kern),
                                        precision="fp32", **tune)))
     if with_3d:
@@ -686,7 +687,8 @@ def serve_operators(pcg, ctx, with_3d=True):
             pts = pcg.pc_sample_points(shape, cells)
             phi = workloads.impulse_windows(shape, pts, kern)
             for prec in ("fp32", "bf16x3"):
-                ops.append(("gaussian3d_%d_%s" % (L, prec), pcg.Operator(ctx, shape, cells, 12, phi, precision=prec)))
+                ops.append(("gaussian3d_%d_%s" % (L, prec), pcg.Operator(ctx, shape, cells, 12, phi, precision=prec,
+                                                                         autotune=autotune)))
     return ops
 
 
@@ -782,15 +784,21 @@ def run_serve(args):
     from paper_1805_06018_gb300 import build as libbuild
     libbuild.build()
     ctx = pcg.Context(0)
-    ops = serve_operators(pcg, ctx, with_3d=not args.serve_2d)
+    t0 = time.time()
+    ops = serve_operators(pcg, ctx, with_3d=not args.serve_2d, autotune=not args.serve_fixed_shapes)
+    build_s = time.time() - t0
     m = serve_measure(pcg, ctx, ops, args.serve_requests, np.random.default_rng(17))
     line = {"metric": "served product-convolution RHS/s; p50/p99 latency", "mode": "serve",
             "value": m["saturated"]["rhs_per_s"], "unit": "RHS/s", "n_gpus": 1, "higher_is_better": True,
             "dtype": "f32", "data": "synthetic", "saturated": m["saturated"], "loads": m["loads"],
             "plain_gpu_rhs_per_s": m.get("plain_gpu_rhs_per_s"),
             "config": {"operators": [n for n, _ in ops], "rhs_per_request": "U[1,64]", "budget_bytes": 120 << 30,
-                       "shapes": {n: {k: op.info()[k] for k in ("fft_size", "window_split", "num_parts")}
+                       "shapes": {n: {k: op.info()[k] for k in ("fft_size", "window_split", "tile", "ctas_per_sm",
+                                                                "num_parts", "autotuned", "tuned_candidates")}
                                   for n, op in ops},
+                       "shapes_from": "the library's autotuner (NULL pc_tuning)" if not args.serve_fixed_shapes else
+                                      "fixed: 128^2 patch FFTs, per-patch shapes for the adaptive operator",
+                       "operator_build_s": round(build_s, 1),
                        "arrivals": "Poisson at 50/80/95% of the saturated rate",
                        "modes": "2D FP32" if args.serve_2d else "2D FP32; 3D FP32 and BF16x3 (tensor-core first axis)",
                        "requests_after_warmup": m["requests_after_warmup"],
@@ -988,11 +996,17 @@ def suite(pcg, ctx, args):
     del flush
     if args.suite_serve_requests > 0:
         try:
-            ops = serve_operators(pcg, ctx, with_3d=False)
+            t0 = time.time()
+            ops = serve_operators(pcg, ctx, with_3d=False, autotune=not args.serve_fixed_shapes)
+            build_s = time.time() - t0
             m = serve_measure(pcg, ctx, ops, args.suite_serve_requests, np.random.default_rng(17))
             m["config"] = {"operators": [n for n, _ in ops], "rhs_per_request": "U[1,64]", "budget_bytes": 120 << 30,
-                           "shapes": {n: {k: op.info()[k] for k in ("fft_size", "window_split", "num_parts")}
+                           "shapes": {n: {k: op.info()[k] for k in ("fft_size", "window_split", "tile", "ctas_per_sm",
+                                                                    "num_parts", "autotuned", "tuned_candidates")}
                                       for n, op in ops},
+                           "shapes_from": "the library's autotuner (NULL pc_tuning)" if not args.serve_fixed_shapes
+                                          else "fixed: 128^2 patch FFTs, per-patch shapes for the adaptive operator",
+                           "operator_build_s": round(build_s, 1),
                            "arrivals": "Poisson at 50/80/95% of the saturated rate",
                            "plain_gpu": "the saturated request set, one request after another, "
                                         "without the per-patch operator's requests (no plain path)"}
@@ -1015,6 +1029,9 @@ def main():
     ap.add_argument("--serve", action="store_true", help="serving benchmark instead of the batched apply")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-2d", action="store_true", help="serve the 2D operators of the mix only")
+    ap.add_argument("--serve-fixed-shapes", action="store_true",
+                    help="serve operators with fixed launch shapes (128^2 patch FFTs, per-patch shapes for the "
+                         "adaptive operator) instead of the shapes the library's autotuner chooses")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--nrhs", type=int, default=0,
                     help="override the workload's batch (smaller cases for profiler captures)")
