@@ -154,6 +154,20 @@ def test_adjoint_3d_workload_128_sampled():
     assert np.all(err <= TOL["fp32"]), err
 
 
+def test_adjoint_bf16x3_workload_128_sampled():
+    """The 128^3 operator in BF16x3 at its batch of 32, through the tensor-core
+    adjoint (two chunks of the split path): 256 seeded voxels of every
+    right-hand side against the oracle, within the BF16x3 bound."""
+    wl = configs.fp32_128c()
+    op, orc = make_pair(wl.shape, wl.cells, wl.kernel, "bf16x3")
+    x = workloads.rhs(wl.rhs_seed, 32, wl.shape)
+    y = run_adjoint(op, x).reshape(32, -1)
+    pts = np.random.default_rng(80).choice(wl.n, 256, replace=False)
+    ref = orc.apply_adjoint(x, points=pts)
+    err = np.linalg.norm(y[:, pts] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert np.all(err <= 1e-4), err
+
+
 def test_adjoint_bf16x3():
     """BF16x3 operators: the first-axis correlation as split-BF16 tensor-core
     GEMMs (GEMM 1 over all first-axis planes of the output box, those outside
