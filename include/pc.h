@@ -563,10 +563,15 @@ pc_status pc_noalloc_check(pc_context *ctx, pc_stream stream);
  * streams, so a new launch starts while earlier ones finish.  Each request
  * is computed exactly as pc_apply_batched would compute it alone.
  * 2D PC_FP32 operators with fft_size 128 are batched together as above.
- * Any other operator (2D with fft_size 64 or PC_FP64, 3D PC_FP32 /
- * PC_BF16X3) runs each request alone on a launch slot through the operator's
- * own apply, one request per such operator at a time; requests of different
- * operators, and the batched launches, overlap on the other slots.
+ * Any other operator (2D with fft_size 64, PC_FP64 or per-patch shapes, 3D
+ * PC_FP32 / PC_BF16X3) runs its requests on a launch slot through the
+ * operator's own apply, one launch per such operator at a time: the request
+ * at the head of the queue together with the requests on the same operator
+ * and direction queued right behind it (at most 64 right-hand sides), whose
+ * x blocks the server copies side by side into a staging buffer of the slot
+ * (counted in the budget while the launch runs) and whose y blocks it copies
+ * back.  Requests of different operators, and the batched launches, overlap
+ * on the other slots.
  * --------------------------------------------------------------------- */
 
 /* Create a server on ctx's device: a scheduler thread, `streams` launch

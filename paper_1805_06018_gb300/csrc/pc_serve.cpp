@@ -14,13 +14,22 @@
 // slot and memory free up.
 //
 // Operators the multi-request kernel does not cover (3D FP32 or BF16x3, 2D
-// with fft_size 64 or FP64) run each request alone: a request at the head of
-// the queue takes a free slot on its own and runs the operator's own apply
-// on that slot's stream.  Such an operator has at most one request in flight
-// (its ordering flags and scratch volumes are per operator); different
-// operators run concurrently on different slots.  The buffers such an apply grows on demand
-// are grown by the scheduler thread just before the launch (the only thread
-// that touches a served operator), which may synchronise the device once.
+// with fft_size 64 or FP64, per-patch shapes) run their requests through the
+// operator's own apply: a request at the head of the queue takes a free slot
+// and, with the requests on the same operator and direction queued right
+// behind it (up to kSoloMaxRhs right-hand sides), one apply on that slot's
+// stream.  Several requests share the apply through a staging buffer of the
+// slot: their x blocks are copied side by side, each starting at an even
+// column so that its right-hand sides form the same pairs as alone (an odd
+// block's last pair gets a zero column), and their y blocks are copied back,
+// so each result is bitwise the request applied alone.  The apply's time is
+// bounded below by the chain of ordering waits through the colours, so a
+// batch of several small requests costs little more than one.  Such an
+// operator has at most one launch in flight (its ordering flags and scratch
+// volumes are per operator); different operators run concurrently on
+// different slots.  The buffers such an apply grows on demand are grown by
+// the scheduler thread just before the launch (the only thread that touches
+// a served operator), which may synchronise the device once.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -39,6 +48,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr int64_t kFlagArenaWords = int64_t(1) << 22;   // ordering flags per launch slot
 constexpr int kMaxInflightCap = 1024;
+constexpr int32_t kSoloMaxRhs = 64;   // right-hand sides (staging columns) of one shared solo apply
 
 struct Request {
     uint64_t ticket = 0;
@@ -74,7 +84,9 @@ struct LaunchSlot {
     int32_t *d_status = nullptr;
     cudaEvent_t done = nullptr;
     bool busy = false;
-    bool solo = false;                  // running one request through its operator's own apply
+    bool solo = false;                  // running requests through their operator's own apply
+    void *d_stage = nullptr;            // solo applies shared by several requests: x, then y columns
+    int64_t stage_bytes = 0;
     std::vector<Request *> reqs;
 };
 
@@ -194,46 +206,111 @@ void reap(pc_server *s) {
     }
 }
 
-// A solo request at the head of the queue, alone on slot sl.  Returns false if
-// it has to wait (FIFO: nothing behind it overtakes).
+// The solo request at the head of the queue, with the requests on the same
+// operator and direction right behind it, on slot sl.  Returns false if it
+// has to wait (FIFO: nothing behind it overtakes).
 bool launch_solo(pc_server *s, LaunchSlot &sl) {
     Request *r = s->queue.front();
-    if (s->op_inflight.count(r->op)) return false;              // one request per solo operator
+    pc_operator *op = r->op;
+    if (s->op_inflight.count(op)) return false;                 // one launch per solo operator
     if (s->inflight >= s->cfg.max_inflight) return false;
-    // Grow the operator's ordering flags and scratch for this request here,
+    std::vector<Request *> take{r};
+    auto cols_of = [](const Request *q) { return q->nrhs + (q->nrhs & 1); };
+    int32_t cols = cols_of(r);
+    for (size_t i = 1; i < s->queue.size(); ++i) {
+        Request *q = s->queue[i];
+        if (q->op != op || q->adjoint != r->adjoint) break;
+        if (int(take.size()) >= s->cfg.max_requests_per_launch) break;
+        if (s->inflight + int(take.size()) >= s->cfg.max_inflight) break;
+        if (cols + cols_of(q) > kSoloMaxRhs) break;
+        take.push_back(q);
+        cols += cols_of(q);
+    }
+    const int64_t N = op->N, el = op->elem;
+    int64_t stage = take.size() > 1 ? 2 * int64_t(cols) * N * el : 0;
+    if (stage && s->budget_used + admission_bytes(s, r) + stage > s->cfg.hbm_budget_bytes) {
+        take.resize(1);   // the head request alone fits better than a shared apply
+        stage = 0;
+    }
+    if (stage > sl.stage_bytes) {
+        // the slot is idle: nothing of its own uses the old staging buffer
+        cudaFree(sl.d_stage);
+        sl.d_stage = nullptr;
+        sl.stage_bytes = 0;
+        if (cudaMalloc(&sl.d_stage, size_t(stage)) == cudaSuccess) {
+            sl.stage_bytes = stage;
+        } else {
+            cudaGetLastError();
+            take.resize(1);
+            stage = 0;
+        }
+    }
+    if (take.size() == 1) cols = r->nrhs;
+    // Grow the operator's ordering flags and scratch for this launch here,
     // on the scheduler thread, the only thread that touches a served
     // operator.  Growing synchronises the device first, so no launch still
     // uses the buffers it frees.
-    const pc_status pst = pc::prepare_batch(r->op, r->nrhs);
+    const pc_status pst = pc::prepare_batch(op, cols);
     if (pst != PC_OK) {
         s->queue.pop_front();
         r->state = 3;
         r->status = int(pst);
-        r->error = r->op->ctx->last_error;
+        r->error = op->ctx->last_error;
         return true;
     }
-    if (s->budget_used + admission_bytes(s, r) > s->cfg.hbm_budget_bytes) return false;
-    s->budget_used += admission_bytes(s, r);
-    s->op_bytes[r->op] = int64_t(r->op->device_bytes);
-    s->op_inflight[r->op]++;
-    ++s->inflight;
+    if (s->budget_used + admission_bytes(s, r) + stage > s->cfg.hbm_budget_bytes) return false;
+    s->budget_used += admission_bytes(s, r) + stage;
+    s->op_bytes[op] = int64_t(op->device_bytes);
+    r->scratch_bytes = stage;   // released with the head request
+    const double t = s->now();
+    for (Request *q : take) {
+        s->op_inflight[op]++;
+        ++s->inflight;
+        s->queue.pop_front();
+        q->state = 1;
+        q->launch_s = t;
+        q->launch_requests = int(take.size());
+    }
     s->budget_peak = std::max(s->budget_peak, s->budget_used);
-    s->queue.pop_front();
-    r->state = 1;
-    r->launch_s = s->now();
-    r->launch_requests = 1;
-    pc_status st = r->adjoint ? pc_apply_adjoint_batched(r->op, r->nrhs, r->x, r->op->N, r->y, r->op->N, sl.stream)
-                              : pc_apply_batched(r->op, r->nrhs, r->x, r->op->N, r->y, r->op->N, sl.stream);
-    cudaError_t e = st == PC_OK ? cudaEventRecord(sl.done, sl.stream) : cudaSuccess;
+    auto apply = [&](const void *x, void *y, int32_t nrhs) {
+        return r->adjoint ? pc_apply_adjoint_batched(op, nrhs, x, N, y, N, sl.stream)
+                          : pc_apply_batched(op, nrhs, x, N, y, N, sl.stream);
+    };
+    pc_status st = PC_OK;
+    cudaError_t e = cudaSuccess;
+    if (take.size() == 1) {
+        st = apply(r->x, r->y, r->nrhs);
+    } else {
+        char *xs = static_cast<char *>(sl.d_stage), *ys = xs + int64_t(cols) * N * el;
+        int64_t off = 0;
+        for (Request *q : take) {
+            const int64_t bytes = int64_t(q->nrhs) * N * el;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(xs + off, q->x, size_t(bytes), cudaMemcpyDeviceToDevice, sl.stream);
+            if (e == cudaSuccess && (q->nrhs & 1))
+                e = cudaMemsetAsync(xs + off + bytes, 0, size_t(N * el), sl.stream);   // the odd block's partner
+            off += int64_t(cols_of(q)) * N * el;
+        }
+        if (e == cudaSuccess) st = apply(xs, ys, cols);
+        off = 0;
+        for (Request *q : take) {
+            if (e == cudaSuccess && st == PC_OK)
+                e = cudaMemcpyAsync(q->y, ys + off, size_t(int64_t(q->nrhs) * N * el), cudaMemcpyDeviceToDevice,
+                                    sl.stream);
+            off += int64_t(cols_of(q)) * N * el;
+        }
+    }
+    if (st == PC_OK && e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
     if (st != PC_OK || e != cudaSuccess) {
-        r->state = 3;
-        r->status = st != PC_OK ? int(st) : int(PC_ERR_CUDA);
-        r->error = st != PC_OK ? r->op->ctx->last_error : std::string(cudaGetErrorString(e));
-        release_budget(s, r);
+        for (Request *q : take) {
+            q->state = 3;
+            q->status = st != PC_OK ? int(st) : int(PC_ERR_CUDA);
+            q->error = st != PC_OK ? op->ctx->last_error : std::string(cudaGetErrorString(e));
+            release_budget(s, q);
+        }
         return true;
     }
-    sl.reqs.assign(1, r);
-    r->attached = true;
+    sl.reqs = take;
+    for (Request *q : take) q->attached = true;
     sl.busy = true;
     sl.solo = true;
     ++s->launches;
@@ -380,6 +457,7 @@ void free_server(pc_server *s) {
         cudaFree(sl.d_seg_done);
         cudaFree(sl.d_counter);
         cudaFree(sl.d_status);
+        cudaFree(sl.d_stage);
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }

@@ -235,3 +235,48 @@ def test_early_completions_polled_while_their_launch_runs():
         alone = op.apply(x)
         torch.cuda.synchronize()
         assert torch.equal(y, alone)
+
+
+def test_solo_requests_share_an_apply():
+    """Requests on operators the multi-request kernel does not cover (3D FP32,
+    BF16x3, per-patch shapes) queued back to back on the same operator and
+    direction share one apply through the slot's staging buffer, up to 64
+    right-hand sides: odd and even counts (each block starts at an even
+    column, an odd block pairs its last column with a zero one), forward and
+    adjoint runs, more right-hand sides than one apply takes.  Every result is
+    bitwise the request applied alone, and there are fewer launches than
+    requests."""
+    import paper_1805_06018_gb300 as pcg
+    shape = (40, 36, 30)
+    cells = workloads.regular_grid(shape, (3, 3, 3))
+    kern = workloads.GaussianAxis3D(lambda x: 1.2 + 0.3 * np.sin(x[..., 0] / 7.0), lambda x: 1.6 + 0 * x[..., 0],
+                                    lambda x: 1.0 + 0.2 * np.cos(x[..., 2] / 5.0), 5)
+    op32 = make_pair(shape, cells, kern, "fp32")[0]
+    op16 = make_pair(shape, cells, kern, "bf16x3")[0]
+    shp2 = (160, 150)
+    pp = make_pair(shp2, workloads.quadtree_grid(shp2, 1, 4, lambda lo, hi: lo[0] < 50 and lo[1] < 50),
+                   workloads.HeavyTailed(lambda x: 2.0 + 2.0 * (x[..., 0] / 160.0), 30), "fp32", per_patch=True)[0]
+    assert pp.info()["num_parts"] >= 2
+    rng = np.random.default_rng(5)
+    plan = []
+    for op, n in ((op32, 9), (pp, 8), (op16, 6)):
+        for k in range(n):
+            adj = op is op32 and k >= 6   # a run of adjoint requests after the forward ones
+            plan.append((op, adj, int(rng.integers(1, 14))))
+    srv = pcg.Server(context(), budget_bytes=16 << 30, streams=2, max_requests_per_launch=8)
+    prepared = []
+    for q, (op, adj, nrhs) in enumerate(plan):
+        x = torch.from_numpy(workloads.rhs(1100 + q, nrhs, op.shape)).cuda()
+        prepared.append((op, adj, x, torch.full_like(x, float("nan"))))
+    torch.cuda.synchronize()
+    jobs = [(op, adj, x, y, srv.submit(op, x, y, adjoint=adj)) for op, adj, x, y in prepared]
+    done = _wait(srv, [j[4] for j in jobs], timeout=120.0)
+    st = srv.stats()
+    srv.close()
+    for op, adj, x, y, t in jobs:
+        assert done[t]["status"] == 0
+        alone = op.apply_adjoint(x) if adj else op.apply(x)
+        torch.cuda.synchronize()
+        assert torch.equal(y, alone)
+    assert st["completed"] == len(jobs)
+    assert st["launches"] < len(jobs)
