@@ -671,7 +671,7 @@ def serve_operators(pcg, ctx, with_3d=True, autotune=False):
     for name, shape, cells, kern, R in wls:
         pts = pcg.pc_sample_points(shape, cells)
         # regular grids: 128^2 patch FFTs, batched with the other requests; the
-        # adaptive operator: per-patch FFT sizes (its requests then run alone)
+        # adaptive operator: per-patch FFT sizes (its requests then run through its own apply)
         tune = {"autotune": True} if autotune else WORKLOAD_TUNING.get(name, {"fft_size": 128})
         ops.append((name, pcg.Operator(ctx, shape, cells, R, workloads.impulse_windows(shape, pts, kern),
                                        precision="fp32", **tune)))

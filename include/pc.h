@@ -112,7 +112,7 @@ typedef struct {
                                 its own bbox(U_k); the patches of each shape form a part,
                                 applied by its own launch (fft_size, tile and window_split
                                 are then ignored).  Such operators support the applies, the
-                                host-buffer apply, serving (alone on a slot), the estimator
+                                host-buffer apply, serving (own apply on a slot), the estimator
                                 and the entries; block plans, the incremental estimator
                                 and the plain path refuse them (PC_ERR_UNSUPPORTED) */
     int32_t reserved[2];

@@ -63,7 +63,7 @@ struct Request {
     int status = PC_OK;
     int hslot = -1;     // host completion flag index
     int launch_requests = 0;
-    bool solo = false;  // runs alone through the operator's own apply (not a batched 2D operator)
+    bool solo = false;  // runs through the operator's own apply (not a batched 2D operator)
     bool adjoint = false;   // Y = A~* X (Eq. adjoint_random_z)
     // a launch slot still lists the request (until its launch ends); a
     // request polled before that is deleted by the slot, not by the poll

@@ -117,7 +117,7 @@ def test_autotune_picks_a_valid_shape():
 
 def test_3d_requests_in_the_mix(ops):
     """3D operators (FP32 fused and BF16x3 tensor-core) served beside 2D ones:
-    each 3D request runs alone on a slot, one per operator at a time, and
+    3D requests run through their operator's apply on a slot, one launch per operator at a time, and
     every result equals the request applied alone, bit for bit."""
     import paper_1805_06018_gb300 as pcg
     shape = (40, 36, 30)
