@@ -743,7 +743,8 @@ static pc_status apply_split3d(pc_operator *op, const pc::ApplyParams &p, cudaSt
         // table per batch shape, kept until the operator is destroyed, so
         // applies in flight never see their table replaced.
         const int32_t np = p.npairs;
-        std::vector<int32_t> ord(static_cast<size_t>(total));
+        // [total] item indices, then [total] their tiles
+        std::vector<int32_t> ord(static_cast<size_t>(2 * total));
         std::vector<std::pair<int64_t, int32_t>> key;
         for (int c = 0; c < nchunks; ++c) {
             const int64_t c0 = int64_t(c) * chunk, c1 = std::min<int64_t>(total, c0 + chunk);
@@ -757,7 +758,10 @@ static pc_status apply_split3d(pc_operator *op, const pc::ApplyParams &p, cudaSt
                 key.emplace_back(ti * np + pair, int32_t(item));
             }
             std::sort(key.begin(), key.end());
-            for (size_t i = 0; i < key.size(); ++i) ord[size_t(c0) + i] = key[i].second;
+            for (size_t i = 0; i < key.size(); ++i) {
+                ord[size_t(c0) + i] = key[i].second;
+                ord[size_t(total + c0) + i] = int32_t(key[i].first / np);
+            }
         }
         if ((e = cudaMalloc(&order, ord.size() * sizeof(int32_t))) != cudaSuccess)
             return cuda_fail(ctx, e, "allocating the unit order");

@@ -428,7 +428,8 @@ int tc3d_k1cap(int tile);   // GEMM-1 K columns for tiles of extent <= tile
 cudaError_t tc3d_build_operands(int k1cap, void **d_ops);
 cudaError_t tc3d_configure();
 // order: the items of every chunk [c0, c1) in tile-then-pair order (absolute
-// item indices, entries c0 ... c1 - 1)
+// item indices, entries c0 ... c1 - 1), then, at total_items + i, the tile
+// of item order[i]
 cudaError_t launch_tc3d_axis0(const ApplyParams &p, int ctas, void *scratch, const int32_t *order, int64_t c0,
                               int64_t c1, const void *ops, int k1cap, cudaStream_t s);
 // the adjoint's tensor stage: ops_full = tc3d_build_operands(2 P) (GEMM 1

@@ -101,16 +101,15 @@ struct Unit {
 // Units of a chunk: u -> block index blk = u / nitems, then the chunk's items
 // in the host-built order order[c0 + r] (sorted by tile, then pair), so that
 // consecutive units share the tile and block and with them the spectrum block.
+// order[total_items + i] is the tile of item order[i], so that no unit walks
+// the colour table.
 template <bool ADJ = false>
 __device__ __forceinline__ Unit unit_of(const ApplyParams &p, float2 *scratch, const int32_t *order, int64_t c0,
                                         int64_t nitems, int64_t u) {
     const int blk = int(u / nitems);
-    const int64_t item = order[c0 + (u - int64_t(blk) * nitems)];
-    int c = 0;
-    while (int64_t(p.color_start[c + 1]) * p.npairs <= item) ++c;
-    const int64_t cbase = int64_t(p.color_start[c]) * p.npairs;
-    const int ntc = p.color_start[c + 1] - p.color_start[c];
-    const Tile &tile = p.tiles[p.color_start[c] + int((item - cbase) % ntc)];
+    const int64_t r = c0 + (u - int64_t(blk) * nitems);
+    const int64_t item = order[r];
+    const Tile &tile = p.tiles[order[p.total_items + r]];
     Unit x;
     x.n0 = tile.in_ext[0];
     x.L0 = x.n0 + tile.kext[0] - 1;
