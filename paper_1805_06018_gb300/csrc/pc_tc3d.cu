@@ -252,6 +252,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc3d_axis0_kernel(const ApplyPara
         spectrum_load(p, cur, erow, part, f);
     }
     for (; ok && u < nunits; u += stride) {
+        // the unit after the next one: its table entries load while this
+        // unit's MMAs and epilogues run
+        Unit nn = nxt;
+        const bool has_nn = u + 2 * stride < nunits;
+        if (has_nn) nn = unit_of(p, scratch, order, c0, nitems, u + 2 * stride);
         // ---- epilogue 1 of `cur`: V^ = D1 * phi^, split into A2 (K = (k0, re|im))
         ok = __syncthreads_and(mbar_wait_bounded(bar_g1, ph1, kSpin));
         if (!ok) break;
@@ -298,11 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc3d_axis0_kernel(const ApplyPara
             }
             pend1 = true;
         }
-        Unit nn = nxt;
-        if (u + 2 * stride < nunits) {
-            nn = unit_of(p, scratch, order, c0, nitems, u + 2 * stride);
-            stage_load<kGroups, false>(p, nn, tid, z);
-        }
+        if (has_nn) stage_load<kGroups, false>(p, nn, tid, z);
         // the spectrum registers stay valid while the tile and block repeat
         if (has_next && (nxt.spec != cur.spec || nxt.line0 != cur.line0)) spectrum_load(p, nxt, erow, part, f);
 
