@@ -385,9 +385,22 @@ __global__ void __launch_bounds__(kThreads3d, 3) fft3d_phase1_kernel(const Apply
     __shared__ __align__(16) float2 S[kP3 * kP3];
     const Lines3 L(static_cast<const float2 *>(p.tw));
     int chint = 0;
-    for (int64_t item = c0 + blockIdx.x; item < c1; item += gridDim.x) {
-        const Item3 it = decode_item3(p, item, chint);
-        phase1_3d<ADJ>(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L, 0, 1);
+    if constexpr (ADJ) {
+        // the adjoint gathers the L0 output-box planes (up to P): tasks of one
+        // item's planes g, g + 16, ... balance better than whole items
+        constexpr int kTasks = 16;
+        for (int64_t task = c0 * kTasks + blockIdx.x; task < c1 * kTasks; task += gridDim.x) {
+            const int64_t item = task / kTasks;
+            const int g = int(task % kTasks);
+            const Item3 it = decode_item3(p, item, chint);
+            if (g >= it.tile.in_ext[0] + it.tile.kext[0] - 1) continue;   // uniform across the CTA
+            phase1_3d<ADJ>(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L, g, kTasks);
+        }
+    } else {
+        for (int64_t item = c0 + blockIdx.x; item < c1; item += gridDim.x) {
+            const Item3 it = decode_item3(p, item, chint);
+            phase1_3d<ADJ>(p, it, scratch + (item - c0) * kP3 * kP3 * kP3, S, L, 0, 1);
+        }
     }
 }
 
