@@ -402,7 +402,7 @@ cudaError_t build_spectra_3d(const double *d_psi, int nspec, int W, int P, void 
 // split 3D path: phase 1 and phase 3 over items [c0, c1), scratch volume of
 // item i at scratch + (i - c0) * fft3d_volume_bytes().  Phase 3 keeps
 // kPhase3Groups ordering flags per (tile, pair): done_ld >= npairs * groups.
-constexpr int kPhase3Groups = 4;
+constexpr int kPhase3Groups = 8;
 // The fused 3D kernel runs clusters of CTAs (kCluster3dFwd for Ã, kCluster3dAdj
 // for Ã*), each CTA adding one contiguous group of an item's output planes
 // under its own ordering flag.
