@@ -20,10 +20,11 @@
 //
 // F1 (K limited to k1cap = 16 ceil(2 T / 16) columns, T <= 48 the tile
 // extent) and F2 are copied into shared memory once per CTA by the bulk-copy
-// (TMA) engine; the data tiles are split and written by the threads; D1 and D2
-// live in two 128-column blocks of tensor memory.  Two units are in flight:
-// GEMM 2 of unit u and GEMM 1 of unit u+1 run back to back on the tensor
-// pipe while the threads finish unit u and stage unit u+2.
+// (TMA) engine; the data tiles are split and written by the threads; two D1
+// accumulators and D2 live in 128-column blocks of tensor memory.  Two units
+// are in flight: GEMM 1 of unit u+1 is issued as soon as GEMM 1 of unit u is
+// done, so it runs while the threads do unit u's epilogue 1 (into the other
+// D1); then GEMM 2 of unit u runs while they load unit u+2.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -204,14 +205,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc3d_axis0_kernel(const ApplyPara
         fence_mbar_init();
     }
     if (warp == 0) {
-        tc::tmem_alloc(slot, 256);
+        tc::tmem_alloc(slot, 512);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *slot;
-    const uint32_t d1 = tmem, d2 = tmem + 128u;
+    // two D1 accumulators (GEMM 1 of the next unit runs while this unit's
+    // epilogue 1 reads its own), one D2
+    const uint32_t d2 = tmem + 256u;
     if (tid == 0) {
         mbar_arrive_expect_tx(bar_ld, uint32_t(2 * t1 + 2 * kTile));
         bulk_g2s(sF1, ops, uint32_t(2 * t1), bar_ld);
@@ -234,6 +237,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc3d_axis0_kernel(const ApplyPara
     bool ok = __syncthreads_and(mbar_wait_bounded(bar_ld, 0, kSpin));
     bool pend1 = false, pend2 = false;
     uint32_t ph1 = 0, ph2 = 0;
+    int kb = 0;   // D1 buffer of `cur`
     if (ok && u < nunits) {
         stage_store<kGroups>(cur, tid, z, sA1, k1cap);
         fence_proxy_async_smem();
@@ -241,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc3d_axis0_kernel(const ApplyPara
         __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
-            issue_gemm(d1, sA1, sF1, t1, sbo1, cur.steps1);
+            issue_gemm(tmem, sA1, sF1, t1, sbo1, cur.steps1);
             tc::mma_commit(bar_g1);
         }
         pend1 = true;
@@ -252,17 +256,32 @@ __global__ void __launch_bounds__(kThreads, 1) tc3d_axis0_kernel(const ApplyPara
         spectrum_load(p, cur, erow, part, f);
     }
     for (; ok && u < nunits; u += stride) {
-        // the unit after the next one: its table entries load while this
-        // unit's MMAs and epilogues run
+        // the unit after the next one: its table entries load meanwhile
         Unit nn = nxt;
-        const bool has_nn = u + 2 * stride < nunits;
+        const bool has_next = u + stride < nunits, has_nn = u + 2 * stride < nunits;
         if (has_nn) nn = unit_of(p, scratch, order, c0, nitems, u + 2 * stride);
-        // ---- epilogue 1 of `cur`: V^ = D1 * phi^, split into A2 (K = (k0, re|im))
+        const uint32_t d1 = tmem + 128u * uint32_t(kb);
         ok = __syncthreads_and(mbar_wait_bounded(bar_g1, ph1, kSpin));
         if (!ok) break;
         pend1 = false;
         ph1 ^= 1u;
         tc::fence_after_sync();
+        // ---- GEMM 1 of the next unit first (A1 is free: GEMM 1 of `cur` is
+        // done; it writes the other D1), so it runs during epilogue 1
+        if (has_next) {
+            stage_store<kGroups>(nxt, tid, z, sA1, k1cap);
+            fence_proxy_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                issue_gemm(tmem + 128u * uint32_t(kb ^ 1), sA1, sF1, t1, sbo1, nxt.steps1);
+                tc::mma_commit(bar_g1);
+            }
+            pend1 = true;
+        }
+        // ---- epilogue 1 of `cur`: V^ = D1 * phi^, split into A2 (free: GEMM 2
+        // of the previous unit is done)
         {
             float v[32];
             tc::tmem_ld32(d1 + lane_base + uint32_t(32 * part), v);
@@ -287,22 +306,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc3d_axis0_kernel(const ApplyPara
             tc::mma_commit(bar_g2);
         }
         pend2 = true;
-
-        // ---- GEMM 1 of the next unit (its input tile and D1 are free), then
-        // the loads of the unit after it and of the next unit's spectrum
-        const bool has_next = u + stride < nunits;
-        if (has_next) {
-            stage_store<kGroups>(nxt, tid, z, sA1, k1cap);
-            fence_proxy_async_smem();
-            tc::fence_before_sync();
-            __syncthreads();
-            if (tid == 0) {
-                tc::fence_after_sync();
-                issue_gemm(d1, sA1, sF1, t1, sbo1, nxt.steps1);
-                tc::mma_commit(bar_g1);
-            }
-            pend1 = true;
-        }
         if (has_nn) stage_load<kGroups, false>(p, nn, tid, z);
         // the spectrum registers stay valid while the tile and block repeat
         if (has_next && (nxt.spec != cur.spec || nxt.line0 != cur.line0)) spectrum_load(p, nxt, erow, part, f);
@@ -328,6 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc3d_axis0_kernel(const ApplyPara
         __syncthreads();
         cur = nxt;
         nxt = nn;
+        kb ^= 1;
     }
     if (!ok) {
         if (tid == 0) atomicExch(p.ctrl + 2, 1);
@@ -338,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc3d_axis0_kernel(const ApplyPara
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
 // The adjoint (Eq. adjoint_random_z): GEMM 1 takes the L0 output-box planes
